@@ -1,0 +1,163 @@
+"""Graph-form ADMM, FP64 (Algorithm 1 + over-relaxation + Algorithm 3), on the
+pre-conditioned problem of Eq. 12, returning the unscaled half-step tuple.
+
+Readings of places where the paper is silent or ambiguous (each one is also listed in
+the design notes):
+  * rho^0 = params.rho0 (default 1); x^0 = y^0 = x~^0 = y~^0 = 0 (Algorithm 1).
+  * Over-relaxation (Section 3.2) replaces x^{k+1/2} by alpha x^{k+1/2} + (1-alpha) x^k in
+    the projection input and the dual update only; mu^{k+1/2}, nu^{k+1/2} and the
+    residuals use the unrelaxed half step (Section 3.3, Eq. 11).
+  * Residuals, their tolerances and the gap are measured on the pre-conditioned
+    (iterated) problem: eps_pri = eps_abs + eps_rel ||y^{k+1/2}||,
+    eps_dual = eps_abs + eps_rel ||mu^{k+1/2}|| (Section 3.4), literal norms.
+  * Gap test: the half-step tuple is Fenchel feasible (Section 3.3), so its gap is
+    eta = y^T nu + x^T mu (Eq. 7); with gap_stop it must also satisfy
+    |eta| <= eps_abs + eps_rel |f(y) + g(x)| (Section 3.4's eps_gap).  gap_stop = False is
+    Algorithm 3 verbatim.
+  * Algorithm 3: the convergence test is taken first; when it fails, rho is updated
+    (dual test before primal test, both strict), with l = u = 0 and the iteration
+    counter k = 0, 1, ...; on a change x~, y~ are rescaled by rho^k / rho^{k+1}
+    (Section 3.2, 'Varying penalty').
+  * Returned tuple (Section 5): x = E x^, y = D^{-1} y^, mu = E^{-1} mu^, nu = D nu^
+    (the dual scalings follow from nu^T y = nu^^T y^ and mu^T x = mu^^T x^).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from .equil import Equilibration, equilibrate, fold_f, fold_g, default_gamma
+from .project import Projector
+from .prox import prox_f, f_value
+
+
+@dataclasses.dataclass
+class Params:
+    abs_tol: float = 1e-4
+    rel_tol: float = 1e-3
+    max_iter: int = 10000          # Section 6.1
+    rho0: float = 1.0
+    alpha: float = 1.7             # Section 5
+    delta: float = 1.05            # Section 5
+    tau: float = 0.8               # Section 5
+    sk_sweeps: int = 10
+    gamma: float | None = None     # None -> (m+n) sqrt(2^-23)
+    adaptive_rho: bool = True
+    gap_stop: bool = True
+    equil: bool = True
+
+
+@dataclasses.dataclass
+class Result:
+    status: int          # 0 converged, 1 max_iter reached
+    iters: int
+    rho: float
+    x: np.ndarray        # unscaled half-step tuple
+    y: np.ndarray
+    mu: np.ndarray
+    nu: np.ndarray
+    xh: np.ndarray       # pre-conditioned half-step tuple
+    yh: np.ndarray
+    muh: np.ndarray
+    nuh: np.ndarray
+    r_pri: float
+    r_dual: float
+    eps_pri: float
+    eps_dual: float
+    gap: float
+    obj: float
+    D: np.ndarray
+    E: np.ndarray
+    history: list
+
+
+def _identity_equil(A):
+    m, n = A.shape
+    return Equilibration(np.ones(m), np.ones(n), A.copy())
+
+
+def solve(A, f, g, params: Params | None = None, eq: Equilibration | None = None,
+          record: bool = False) -> Result:
+    p = params or Params()
+    A = np.asarray(A, np.float64)
+    m, n = A.shape
+    if eq is None:
+        if p.equil:
+            eq = equilibrate(A, p.sk_sweeps, p.gamma if p.gamma is not None else default_gamma(m, n))
+        else:
+            eq = _identity_equil(A)
+    Ah, D, E = eq.Ahat, eq.D, eq.E
+    fh, gh = fold_f(f, D), fold_g(g, E)
+    proj = Projector(Ah)
+
+    x, xt = np.zeros(n), np.zeros(n)
+    y, yt = np.zeros(m), np.zeros(m)
+    rho = float(p.rho0)
+    l = u = 0
+    hist = []
+    status, iters = 1, p.max_iter
+    xh = yh = mu = nu = None
+    r_pri = r_dual = eps_pri = eps_dual = gap = obj = np.nan
+    for k in range(p.max_iter):
+        # Algorithm 1, prox step
+        vx, vy = x - xt, y - yt
+        xh = prox_f(gh, vx, rho)
+        yh = prox_f(fh, vy, rho)
+        # Section 3.3: feasible half-step duals
+        mu = -rho * (xh - x + xt)
+        nu = -rho * (yh - y + yt)
+        # Section 3.2: over-relaxation
+        xr = p.alpha * xh + (1.0 - p.alpha) * x
+        yr = p.alpha * yh + (1.0 - p.alpha) * y
+        # Algorithm 1, projection and dual update
+        xn, yn = proj(xr + xt, yr + yt)
+        xt = xt + xr - xn
+        yt = yt + yr - yn
+        x, y = xn, yn
+        # Eq. 11 residuals and Section 3.4 tolerances
+        r_pri = float(np.linalg.norm(Ah @ xh - yh))
+        r_dual = float(np.linalg.norm(Ah.T @ nu + mu))
+        eps_pri = p.abs_tol + p.rel_tol * float(np.linalg.norm(yh))
+        eps_dual = p.abs_tol + p.rel_tol * float(np.linalg.norm(mu))
+        gap = float(yh @ nu + xh @ mu)
+        obj = float(np.sum(f_value(fh, yh, 1e-9)) + np.sum(f_value(gh, xh, 1e-9)))
+        eps_gap = p.abs_tol + p.rel_tol * abs(obj)
+        if record:
+            hist.append(dict(k=k, rho=rho, r_pri=r_pri, r_dual=r_dual, eps_pri=eps_pri,
+                             eps_dual=eps_dual, gap=gap, obj=obj,
+                             dual_inv=float(np.linalg.norm(xt + Ah.T @ yt))))
+        converged = r_pri < eps_pri and r_dual < eps_dual and (not p.gap_stop or abs(gap) < eps_gap)
+        if converged:
+            status, iters = 0, k + 1
+            break
+        # Algorithm 3
+        if p.adaptive_rho:
+            rho_new = rho
+            if r_dual < eps_dual and p.tau * k > l:
+                rho_new = p.delta * rho
+                u = k
+            elif r_pri < eps_pri and p.tau * k > u:
+                rho_new = rho / p.delta
+                l = k
+            if rho_new != rho:
+                xt = xt * (rho / rho_new)
+                yt = yt * (rho / rho_new)
+                rho = rho_new
+
+    return Result(status=status, iters=iters, rho=rho,
+                  x=E * xh, y=yh / D, mu=mu / E, nu=D * nu,
+                  xh=xh, yh=yh, muh=mu, nuh=nu,
+                  r_pri=r_pri, r_dual=r_dual, eps_pri=eps_pri, eps_dual=eps_dual,
+                  gap=gap, obj=obj, D=D, E=E, history=hist)
+
+
+def objective(A, f, g, x, y, tol=1e-7) -> float:
+    """f(y) + g(x) of the original problem (Eq. 1)."""
+    return float(np.sum(f_value(f, y, tol)) + np.sum(f_value(g, x, tol)))
+
+
+def unscaled_residuals(A, x, y, mu, nu):
+    """||A x - y|| and ||A^T nu + mu|| of the original problem (Eqs. 4, 5)."""
+    A = np.asarray(A, np.float64)
+    return float(np.linalg.norm(A @ x - y)), float(np.linalg.norm(A.T @ nu + mu))

@@ -1,0 +1,268 @@
+"""Seeded synthetic problem generators shared by the CUDA path's tests/bench and the oracle.
+
+This module holds no arithmetic of the solver itself: it only draws problem data
+(a matrix A and the per-element parameters of the separable functions f and g) the
+way the paper's appendix describes its random problem classes (Appendix A), with the
+matrix distributions and sizes of the workloads used here.
+
+Every function is encoded in the parametric form of Section 5,
+
+    f_i(y_i) = c_i * h_i(a_i * y_i - b_i) + d_i * y_i + (e_i / 2) * y_i**2,
+
+and likewise g_j(x_j).  ``H`` below lists the integer codes of the base functions h;
+they are the values of the ``pogs_h`` enum of the C interface.
+
+Seeds: ``numpy.random.Generator(PCG64(seed))``.  Data is drawn and stored in FP32
+(``A`` row-major m x n, parameters as FP32 arrays) -- the oracle upcasts exactly these
+FP32 values to FP64, so data rounding is never counted as solver error.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# Base-function codes h (values of the C enum ``pogs_h``).
+H = dict(
+    ZERO=0,        # h(z) = 0
+    ABS=1,         # |z|
+    SQUARE=2,      # z^2 / 2
+    HUBER=3,       # z^2/2 if |z| <= 1 else |z| - 1/2
+    LOGISTIC=4,    # log(1 + e^z)
+    HINGE=5,       # max(0, 1 - z)
+    MAXPOS=6,      # max(0, z)
+    IND_GE0=7,     # indicator of z >= 0
+    IND_LE0=8,     # indicator of z <= 0
+    IND_EQ0=9,     # indicator of z == 0
+    IND_BOX01=10,  # indicator of 0 <= z <= 1
+)
+H_NAMES = {v: k for k, v in H.items()}
+
+
+@dataclasses.dataclass
+class FnParams:
+    """Parameters (h, a, b, c, d, e) of a separable function, one entry per element."""
+    h: np.ndarray  # uint8
+    a: np.ndarray  # float32
+    b: np.ndarray
+    c: np.ndarray
+    d: np.ndarray
+    e: np.ndarray
+
+    @staticmethod
+    def make(k: int, h: int, a=1.0, b=0.0, c=1.0, d=0.0, e=0.0) -> "FnParams":
+        def arr(v):
+            out = np.empty(k, np.float32)
+            out[...] = v
+            return out
+        return FnParams(np.full(k, h, np.uint8), arr(a), arr(b), arr(c), arr(d), arr(e))
+
+    def __len__(self):
+        return len(self.h)
+
+
+@dataclasses.dataclass
+class Problem:
+    """minimize f(y) + g(x) subject to y = A x (Eq. 1)."""
+    name: str
+    A: np.ndarray          # float32, (m, n), C-contiguous
+    f: FnParams            # length m
+    g: FnParams            # length n
+    meta: dict
+
+    @property
+    def m(self) -> int:
+        return self.A.shape[0]
+
+    @property
+    def n(self) -> int:
+        return self.A.shape[1]
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _normal32(rng, shape, mean=0.0, std=1.0) -> np.ndarray:
+    A = rng.standard_normal(shape, dtype=np.float32)
+    if std != 1.0:
+        A *= np.float32(std)
+    if mean != 0.0:
+        A += np.float32(mean)
+    return A
+
+
+def _sparse_vector(rng, n, frac, std=1.0) -> np.ndarray:
+    """frac*n nonzeros (at least 1) drawn N(0, std^2) at uniformly chosen positions."""
+    k = max(1, int(round(frac * n)))
+    v = np.zeros(n)
+    idx = rng.choice(n, size=k, replace=False)
+    v[idx] = rng.standard_normal(k) * std
+    return v
+
+
+def lasso(m: int, n: int, seed: int, nnz_frac=0.1, noise_std=0.01, lam_frac=0.1) -> Problem:
+    """Lasso (Appendix A.4): f(y) = 1/2 ||y - b||^2, g(x) = lambda ||x||_1.
+
+    A ~ N(0, 1/n); x_true has nnz_frac nonzeros ~ N(0, 1); b = A x_true + N(0, noise_std^2);
+    lambda = lam_frac * ||A^T b||_inf.
+    """
+    rng = _rng(seed)
+    A = _normal32(rng, (m, n), std=1.0 / math.sqrt(n))
+    x_true = _sparse_vector(rng, n, nnz_frac)
+    b = (A.astype(np.float64) @ x_true + rng.standard_normal(m) * noise_std).astype(np.float32)
+    lam = float(lam_frac * np.max(np.abs(A.T.astype(np.float64) @ b.astype(np.float64))))
+    f = FnParams.make(m, H["SQUARE"], b=b)
+    g = FnParams.make(n, H["ABS"], c=lam)
+    return Problem("lasso", A, f, g, dict(lam=lam, seed=seed))
+
+
+def logistic(m: int, n: int, seed: int, nnz_frac=0.05, lam_frac=0.05) -> Problem:
+    """l1-regularised logistic regression (Appendix A.5).
+
+    f_i(y) = log(1 + e^y) - b_i y  (LOGISTIC with d = -b_i), g(x) = lambda ||x||_1,
+    labels b_i in {0,1} with P(b_i = 1) = sigma(a_i^T x_true),
+    lambda = lam_frac * ||A^T (1/2 - b)||_inf.
+    """
+    rng = _rng(seed)
+    A = _normal32(rng, (m, n), std=1.0 / math.sqrt(n))
+    x_true = _sparse_vector(rng, n, nnz_frac)
+    z = A.astype(np.float64) @ x_true
+    p1 = 1.0 / (1.0 + np.exp(-z))
+    b = (rng.random(m) < p1).astype(np.float32)
+    lam = float(lam_frac * np.max(np.abs(A.T.astype(np.float64) @ (0.5 - b.astype(np.float64)))))
+    f = FnParams.make(m, H["LOGISTIC"], d=-b)
+    g = FnParams.make(n, H["ABS"], c=lam)
+    return Problem("logistic", A, f, g, dict(lam=lam, seed=seed))
+
+
+def huber(m: int, n: int, seed: int) -> Problem:
+    """Huber fitting (Appendix A.3): f_i(y) = huber(y_i - b_i) (M = 1), g = 0.
+
+    b = A v + eps, v ~ N(0, 1/n), eps ~ N(0, 1/4) w.p. 0.95 else U[0, 10].
+    """
+    rng = _rng(seed)
+    A = _normal32(rng, (m, n), std=1.0 / math.sqrt(n))
+    v = rng.standard_normal(n) / math.sqrt(n)
+    outlier = rng.random(m) >= 0.95
+    eps = np.where(outlier, rng.uniform(0.0, 10.0, m), rng.standard_normal(m) * 0.5)
+    b = (A.astype(np.float64) @ v + eps).astype(np.float32)
+    f = FnParams.make(m, H["HUBER"], b=b)
+    g = FnParams.make(n, H["ZERO"])
+    return Problem("huber", A, f, g, dict(seed=seed))
+
+
+def svm(m: int, n: int, seed: int, lam=1.0) -> Problem:
+    """Support vector machine (Appendix A.9): f_i(y) = lambda max(0, y_i + 1), g(x) = x^T x,
+    with y = diag(b) A x; the stored matrix is diag(b) A.
+
+    Rows i < m/2 have label +1 and entries N(+1/n, 1/n); the rest label -1, N(-1/n, 1/n).
+    """
+    rng = _rng(seed)
+    half = m // 2
+    A = np.empty((m, n), np.float32)
+    A[:half] = _normal32(rng, (half, n), mean=1.0 / n, std=1.0 / math.sqrt(n))
+    A[half:] = _normal32(rng, (m - half, n), mean=-1.0 / n, std=1.0 / math.sqrt(n))
+    A[half:] *= -1.0   # diag(b) A with b = -1 on the second class
+    f = FnParams.make(m, H["MAXPOS"], a=1.0, b=-1.0, c=lam)
+    g = FnParams.make(n, H["SQUARE"], c=2.0)
+    return Problem("svm", A, f, g, dict(lam=lam, seed=seed))
+
+
+def nnls(m: int, n: int, seed: int) -> Problem:
+    """Non-negative least squares (Appendix A.7): f = 1/2 ||y - b||^2, g = indicator(x >= 0).
+
+    A ~ N(0, 1/n); v ~ N(1/n, 1/n); b = A v + N(0, 1/4).
+    """
+    rng = _rng(seed)
+    A = _normal32(rng, (m, n), std=1.0 / math.sqrt(n))
+    v = 1.0 / n + rng.standard_normal(n) / math.sqrt(n)
+    b = (A.astype(np.float64) @ v + rng.standard_normal(m) * 0.5).astype(np.float32)
+    f = FnParams.make(m, H["SQUARE"], b=b)
+    g = FnParams.make(n, H["IND_GE0"])
+    return Problem("nnls", A, f, g, dict(seed=seed))
+
+
+def lp(m: int, n: int, seed: int, density=0.1) -> Problem:
+    """Inequality-form LP (Appendix A.6 with x >= 0): minimize c^T x s.t. A x <= b, x >= 0.
+
+    A has `density` nonzeros ~ N(0,1) (stored dense); v = |N(0, 1/n)|; b = A v + U[0, 0.1];
+    c = -A^T u with u ~ U[0,1]^m, which makes the problem feasible (x = v) and bounded.
+    f_i = indicator(y_i - b_i <= 0), g_j(x_j) = c_j x_j + indicator(x_j >= 0).
+    """
+    rng = _rng(seed)
+    A = _normal32(rng, (m, n))
+    A *= (rng.random((m, n), dtype=np.float32) < density)
+    v = np.abs(rng.standard_normal(n) / math.sqrt(n))
+    A64 = A.astype(np.float64)
+    b = (A64 @ v + rng.uniform(0.0, 0.1, m)).astype(np.float32)
+    u = rng.uniform(0.0, 1.0, m)
+    c = (-(A64.T @ u)).astype(np.float32)
+    f = FnParams.make(m, H["IND_LE0"], b=b)
+    g = FnParams.make(n, H["IND_GE0"], d=c)
+    return Problem("lp", A, f, g, dict(seed=seed))
+
+
+CLASSES = dict(lasso=lasso, logistic=logistic, huber=huber, svm=svm, nnls=nnls, lp=lp)
+
+
+def _log_uniform_int(rng, lo, hi) -> int:
+    return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+
+def lasso_small(seed: int = 0) -> Problem:
+    """Plain single Lasso solve: 200 x 100, A ~ N(0, 1/100), 10% nonzeros, noise N(0, 0.01^2)."""
+    return lasso(200, 100, seed, nnz_frac=0.1, noise_std=0.01, lam_frac=0.1)
+
+
+def lasso_tall_large(seed: int = 10_000) -> Problem:
+    """Large dense tall Lasso: 40000 x 10000 (1.6 GB FP32)."""
+    return lasso(40000, 10000, seed, nnz_frac=0.1, noise_std=0.01, lam_frac=0.1)
+
+
+def logistic_fat_large(seed: int = 10_001) -> Problem:
+    """Large dense fat l1-logistic regression: 2000 x 40000."""
+    return logistic(2000, 40000, seed, nnz_frac=0.05, lam_frac=0.05)
+
+
+def batch_mix(count: int = 2048, base_seed: int = 20_000, m_range=(64, 2048), n_range=(32, 512),
+              classes=("lasso", "huber", "svm", "nnls")) -> list:
+    """Many small independent instances: class uniform over `classes`, m and n log-uniform."""
+    out = []
+    for i in range(count):
+        rng = _rng(base_seed + i)
+        cls = classes[int(rng.integers(len(classes)))]
+        m = _log_uniform_int(rng, *m_range)
+        n = _log_uniform_int(rng, *n_range)
+        out.append(CLASSES[cls](m, n, base_seed + 100_000 + i))
+    return out
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival_s: float
+    cls: str
+    m: int
+    n: int
+    seed: int
+
+    def problem(self) -> Problem:
+        return CLASSES[self.cls](self.m, self.n, self.seed)
+
+
+def serve_trace(count: int = 20000, rate_hz: float = 2000.0, base_seed: int = 40_000,
+                m_range=(100, 8000), n_range=(50, 4000),
+                classes=("lasso", "logistic", "huber", "svm", "nnls")) -> list:
+    """Poisson arrival stream of mixed-size requests (exponential inter-arrival gaps)."""
+    rng = _rng(base_seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate_hz))
+        cls = classes[int(rng.integers(len(classes)))]
+        m = _log_uniform_int(rng, *m_range)
+        n = _log_uniform_int(rng, *n_range)
+        out.append(Request(i, t, cls, m, n, base_seed + 100_000 + i))
+    return out
