@@ -1,0 +1,172 @@
+/*
+ * pogs.h -- C interface of a B300-native (sm_103a) graph-form ADMM solver.
+ *
+ * Problem (Eq. 1):   minimize f(y) + g(x)   subject to   y = A x,
+ * with A dense m x n (FP32) and f, g separable in the parametric form of Section 5:
+ *
+ *     f_i(y_i) = c_i h_i(a_i y_i - b_i) + d_i y_i + (e_i / 2) y_i^2,   a_i != 0, c_i >= 0, e_i >= 0,
+ *
+ * (g_j likewise).  The solver runs Algorithm 1 (graph projection splitting) with
+ * over-relaxation (Section 3.2), the Section 3.4 residual stopping test plus a duality-gap
+ * test on the half-step tuple, and Algorithm 3 (adaptive rho), on the problem
+ * pre-conditioned by regularized Sinkhorn-Knopp (Algorithm 2) and the Frobenius rescale
+ * (Section 4.1.2).  The projection uses the dense reduced updates of Section 3.5 with a
+ * factor cached at setup (factorization caching).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: 0 (POGS_OK) or 1 (POGS_MAX_ITER, a valid but unconverged result) on
+ *    success, a negative POGS_ERR_* code on failure.  No entry point aborts the process
+ *    or traps on the device; device-side failures come back as status codes.
+ *  - Pointers documented "host or device" may point to host memory (pageable or pinned)
+ *    or to device memory of the current CUDA device; the library detects which.
+ *  - All device work is issued on the CUDA stream given to pogs_setup (NULL = legacy
+ *    default stream); calls that return results synchronise that stream.
+ *  - Vectors are FP32, contiguous, with the lengths stated.  A is row-major
+ *    ('R': element (i,j) at A[i*lda + j], lda >= n) or column-major ('C': A[j*lda + i],
+ *    lda >= m).
+ */
+#ifndef POGS_B300_H
+#define POGS_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Base functions h of the Section 5 library. */
+typedef enum {
+  POGS_ZERO = 0,      /* 0                                   */
+  POGS_ABS = 1,       /* |z|                                 */
+  POGS_SQUARE = 2,    /* z^2 / 2                             */
+  POGS_HUBER = 3,     /* z^2/2 if |z| <= 1, else |z| - 1/2   */
+  POGS_LOGISTIC = 4,  /* log(1 + e^z)                        */
+  POGS_HINGE = 5,     /* max(0, 1 - z)                       */
+  POGS_MAXPOS = 6,    /* max(0, z)                           */
+  POGS_IND_GE0 = 7,   /* indicator of z >= 0                 */
+  POGS_IND_LE0 = 8,   /* indicator of z <= 0                 */
+  POGS_IND_EQ0 = 9,   /* indicator of z == 0                 */
+  POGS_IND_BOX01 = 10 /* indicator of 0 <= z <= 1            */
+} pogs_h;
+
+/* Status / error codes. */
+enum {
+  POGS_OK = 0,
+  POGS_MAX_ITER = 1,
+  POGS_ERR_ARG = -1,       /* invalid argument (sizes, NULL, a == 0, c < 0, e < 0, bad enum) */
+  POGS_ERR_OOM = -2,       /* device allocation failed                                       */
+  POGS_ERR_NONFINITE = -3, /* NaN/Inf in the input or in an iterate norm                     */
+  POGS_ERR_NUMERIC = -4,   /* non-positive Cholesky pivot (cannot happen for I + G in exact
+                              arithmetic; reports corrupted input)                           */
+  POGS_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up                             */
+  POGS_ERR_CUDA = -6,      /* a CUDA runtime call failed                                     */
+  POGS_ERR_CAPACITY = -7   /* request exceeds a fixed capacity (batch/server/no-alloc sizes) */
+};
+
+/* Precision of the one-time Gram formation G = A^T A (m >= n) or A A^T (m < n). */
+enum {
+  POGS_GRAM_BF16 = 0,   /* BF16 tensor-core MMA, FP32 accumulation                          */
+  POGS_GRAM_TF32 = 1,   /* TF32 tensor-core MMA, FP32 accumulation                          */
+  POGS_GRAM_BF16X3 = 2, /* split A = hi + lo (both BF16): hi*hi + hi*lo + lo*hi, FP32 accum. */
+  POGS_GRAM_FP32 = 3    /* FP32 SIMT                                                        */
+};
+
+/* One separable function: per-element parameters, each array of length k (k = m for f,
+ * k = n for g), host or device.  NULL a or c means all ones; NULL b, d or e means zeros;
+ * h must not be NULL.  Read during pogs_solve only (not retained). */
+typedef struct {
+  const uint8_t* h;
+  const float *a, *b, *c, *d, *e;
+} pogs_fn;
+
+/* Solver parameters; pogs_default_params() gives the paper's choices (Section 5). */
+typedef struct {
+  double abs_tol;    /* eps_abs  (default 1e-4), Section 3.4                          */
+  double rel_tol;    /* eps_rel  (default 1e-3)                                        */
+  int max_iter;      /* default 10000 (Section 6.1)                                    */
+  double rho0;       /* initial rho (default 1)                                        */
+  double alpha;      /* over-relaxation (default 1.7, Section 5)                       */
+  double delta;      /* Algorithm 3 step (default 1.05)                                */
+  double tau;        /* Algorithm 3 hysteresis (default 0.8)                           */
+  int sk_sweeps;     /* Algorithm 2 sweeps, fixed count (default 10); 0 = no SK        */
+  double gamma;      /* Algorithm 2 regularizer; <= 0 selects (m+n) sqrt(2^-23)        */
+  int gram_prec;     /* POGS_GRAM_* (default POGS_GRAM_BF16X3)                         */
+  int refine_steps;  /* iterative-refinement steps per projection, 0 or 1 (default 0) */
+  int gap_stop;      /* 1: also require |y^T nu + x^T mu| <= eps_abs + eps_rel |f+g|   */
+  int adaptive_rho;  /* 1: Algorithm 3 (default); 0: fixed rho                         */
+  int equil;         /* 1: Sinkhorn-Knopp + rescale (default); 0: rescale only         */
+  int verbose;       /* 0 silent                                                       */
+  int loop_mode;     /* 0: device-side loop in one CUDA graph (conditional WHILE node);
+                        1: host loop over captured iterations, status read every
+                        check_every iterations                                         */
+  int check_every;   /* loop_mode 1 only (default 10)                                  */
+} pogs_params;
+
+/* Per-solve report.  Residuals/tolerances/gap are those of the pre-conditioned problem
+ * the iteration runs on (Section 3.4); *_unscaled are ||A x - y|| and ||A^T nu + mu|| of
+ * the original problem at the returned tuple. */
+typedef struct {
+  int status, iters;
+  double rho, r_pri, r_dual, eps_pri, eps_dual, gap, obj;
+  double r_pri_unscaled, r_dual_unscaled;
+  double setup_ms, solve_ms;
+} pogs_info;
+
+typedef struct pogs_handle pogs_handle;
+
+/* Fill *p with the defaults listed above. */
+void pogs_default_params(pogs_params* p);
+
+/* One-time setup for matrix A (Section 3.5 'factorization caching', Section 4.2, 5):
+ * copies A to the device (host or device source), runs Algorithm 2 for p->sk_sweeps
+ * sweeps, applies the Frobenius rescale, forms G = A^T A (m >= n) or A A^T (m < n) in
+ * p->gram_prec, factors I + G = L L^T in FP64 and caches the factor (as FP32 L^{-1} in
+ * 128 x 128 packed tiles).  The caller keeps ownership of A.  `stream` is a cudaStream_t
+ * (NULL = default).  On success *out owns all device memory until pogs_free.
+ * Errors: ARG (m or n < 1, lda too small, order not 'R'/'C', NULL), OOM, NONFINITE,
+ * NUMERIC, CUDA. */
+int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order,
+               const pogs_params* p, void* stream, pogs_handle** out);
+
+/* Solve with the cached factor: Algorithm 1 + over-relaxation + Algorithm 3 until the
+ * Section 3.4 test holds (status 0) or p->max_iter iterations (status 1).  f has m
+ * elements, g has n.  Outputs are the unscaled half-step tuple returned by POGS
+ * (Section 5): x, mu of length n and y, nu of length m, caller-owned, host or device;
+ * any output may be NULL.  info may be NULL.  p may differ from the setup parameters in
+ * everything except sk_sweeps, gamma, equil and gram_prec (fixed at setup).
+ * Errors: ARG (bad h code, a == 0, c < 0, e < 0), NONFINITE, TIMEOUT, CUDA. */
+int pogs_solve(pogs_handle* hdl, const pogs_fn* f, const pogs_fn* g, const pogs_params* p,
+               float* x, float* y, float* mu, float* nu, pogs_info* info);
+
+/* Release everything the handle owns.  pogs_free(NULL) is a no-op. */
+void pogs_free(pogs_handle* hdl);
+
+/* ---- step-level entry points (the same device code the solver runs) ---------------- */
+
+/* Elementwise parametric prox of Section 5 on device arrays of length k:
+ * out_i = argmin_y c_i h_i(a_i y - b_i) + d_i y + (e_i/2) y^2 + (rho_i/2)(y - v_i)^2,
+ * rho_i = rho_vec[i] if rho_vec != NULL else rho.  fn arrays, v, rho_vec and out must be
+ * device pointers.  Errors: ARG. */
+int pogs_prox_eval(const pogs_fn* fn, int64_t k, const float* v, const float* rho_vec,
+                   float rho, float* out, void* stream);
+
+/* Copy the equilibration diagonals D (length m) and E (length n) after the rescale
+ * (Algorithm 2 + Section 4.1.2); host or device destinations. */
+int pogs_get_equil(const pogs_handle* hdl, float* D, float* E);
+
+/* Copy the pre-conditioned matrix A^ = D A E, row-major m x n (ld = n), host or device. */
+int pogs_get_ahat(const pogs_handle* hdl, float* Ahat);
+
+/* Apply the cached graph projection (Eq. 9 via the Section 3.5 reduced update) in the
+ * pre-conditioned variables: (x, y) = Pi(c, d), c and x of length n, d and y of length m,
+ * host or device.  Uses the same kernels as one ADMM iteration (including
+ * p->refine_steps refinement steps; p may be NULL for the setup parameters). */
+int pogs_project(pogs_handle* hdl, const float* c, const float* d, float* x, float* y,
+                 const pogs_params* p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POGS_B300_H */

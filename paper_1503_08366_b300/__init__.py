@@ -1,0 +1,11 @@
+"""B300-native (sm_103a) graph-form ADMM: the per-iteration hot path of POGS
+(separable proxes + graph projection with a cached Cholesky factor) behind a C ABI.
+
+The Python layer only marshals arguments to libpogs_b300.so (include/pogs.h); there is
+no CPU fallback -- importing fails if the CUDA library has not been built.
+"""
+from ._lib import (  # noqa: F401
+    ERR, GRAM, H, LIB_PATH, MAX_ITER, OK, PogsError, lib, pogs_default_params, pogs_fn, pogs_free,
+    pogs_get_ahat, pogs_get_equil, pogs_info, pogs_params, pogs_project, pogs_prox_eval, pogs_setup,
+    pogs_solve)
+from .solver import Solver  # noqa: F401

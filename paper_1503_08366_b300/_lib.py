@@ -1,0 +1,217 @@
+"""ctypes binding of include/pogs.h -- argument marshalling only; every step of the
+solver runs inside libpogs_b300.so.  Fails loudly when the library has not been built."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpogs_b300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(python -m paper_1503_08366_b300.build)")
+
+lib = C.CDLL(LIB_PATH)
+
+# ---- enums -----------------------------------------------------------------------------
+H = dict(ZERO=0, ABS=1, SQUARE=2, HUBER=3, LOGISTIC=4, HINGE=5, MAXPOS=6, IND_GE0=7, IND_LE0=8,
+         IND_EQ0=9, IND_BOX01=10)
+OK, MAX_ITER = 0, 1
+ERR = {-1: "ARG", -2: "OOM", -3: "NONFINITE", -4: "NUMERIC", -5: "TIMEOUT", -6: "CUDA", -7: "CAPACITY"}
+GRAM = dict(BF16=0, TF32=1, BF16X3=2, FP32=3)
+
+
+class pogs_fn(C.Structure):
+    _fields_ = [("h", C.c_void_p), ("a", C.c_void_p), ("b", C.c_void_p), ("c", C.c_void_p),
+                ("d", C.c_void_p), ("e", C.c_void_p)]
+
+
+class pogs_params(C.Structure):
+    _fields_ = [("abs_tol", C.c_double), ("rel_tol", C.c_double), ("max_iter", C.c_int),
+                ("rho0", C.c_double), ("alpha", C.c_double), ("delta", C.c_double), ("tau", C.c_double),
+                ("sk_sweeps", C.c_int), ("gamma", C.c_double), ("gram_prec", C.c_int),
+                ("refine_steps", C.c_int), ("gap_stop", C.c_int), ("adaptive_rho", C.c_int),
+                ("equil", C.c_int), ("verbose", C.c_int), ("loop_mode", C.c_int), ("check_every", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pogs_info(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("rho", C.c_double), ("r_pri", C.c_double),
+                ("r_dual", C.c_double), ("eps_pri", C.c_double), ("eps_dual", C.c_double),
+                ("gap", C.c_double), ("obj", C.c_double), ("r_pri_unscaled", C.c_double),
+                ("r_dual_unscaled", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = C.c_void_p
+lib.pogs_default_params.argtypes = [C.POINTER(pogs_params)]
+lib.pogs_default_params.restype = None
+lib.pogs_setup.argtypes = [_P, C.c_int64, C.c_int64, C.c_int64, C.c_char, C.POINTER(pogs_params), _P, C.POINTER(_P)]
+lib.pogs_setup.restype = C.c_int
+lib.pogs_solve.argtypes = [_P, C.POINTER(pogs_fn), C.POINTER(pogs_fn), C.POINTER(pogs_params), _P, _P, _P, _P,
+                           C.POINTER(pogs_info)]
+lib.pogs_solve.restype = C.c_int
+lib.pogs_free.argtypes = [_P]
+lib.pogs_free.restype = None
+lib.pogs_prox_eval.argtypes = [C.POINTER(pogs_fn), C.c_int64, _P, _P, C.c_float, _P, _P]
+lib.pogs_prox_eval.restype = C.c_int
+lib.pogs_get_equil.argtypes = [_P, _P, _P]
+lib.pogs_get_equil.restype = C.c_int
+lib.pogs_get_ahat.argtypes = [_P, _P]
+lib.pogs_get_ahat.restype = C.c_int
+lib.pogs_project.argtypes = [_P, _P, _P, _P, _P, C.POINTER(pogs_params)]
+lib.pogs_project.restype = C.c_int
+
+
+class PogsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where} failed with status {code} ({ERR.get(code, '?')})")
+        self.code = code
+
+
+def _check(code: int, where: str) -> int:
+    if code < 0:
+        raise PogsError(code, where)
+    return code
+
+
+# ---- marshalling helpers ------------------------------------------------------------------
+def _ptr(a, dtype, keep: list):
+    """Raw pointer of a contiguous numpy array or torch tensor (host or device); None -> NULL."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):   # torch tensor
+        import torch
+        want = {np.float32: torch.float32, np.uint8: torch.uint8}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            a = a.to(want).contiguous()
+        keep.append(a)
+        return a.data_ptr()
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    keep.append(arr)
+    return arr.ctypes.data
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def make_fn(p, keep: list) -> pogs_fn:
+    """pogs_fn from an object with attributes h, a, b, c, d, e (arrays or tensors; a..e may be None)."""
+    return pogs_fn(_ptr(p.h, np.uint8, keep), _ptr(getattr(p, "a", None), np.float32, keep),
+                   _ptr(getattr(p, "b", None), np.float32, keep), _ptr(getattr(p, "c", None), np.float32, keep),
+                   _ptr(getattr(p, "d", None), np.float32, keep), _ptr(getattr(p, "e", None), np.float32, keep))
+
+
+# ---- C entry points, same names ---------------------------------------------------------------
+def pogs_default_params(**overrides) -> pogs_params:
+    p = pogs_params()
+    lib.pogs_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if isinstance(v, str) and k == "gram_prec":
+            v = GRAM[v.upper()]
+        setattr(p, k, v)
+    return p
+
+
+def pogs_setup(A, params: pogs_params | None = None, stream=None, order: str = "R"):
+    """A: 2-D float32 numpy array (host) or torch tensor (host or CUDA), logical shape (m, n).
+    order 'R' passes A's row-major storage, 'C' its column-major storage. Returns a handle."""
+    keep: list = []
+    m, n = A.shape
+    o = order.upper()
+    if hasattr(A, "data_ptr"):
+        import torch
+        src = A.to(torch.float32)
+        src = src.contiguous() if o == "R" else src.t().contiguous()
+        ptr = src.data_ptr()
+        keep.append(src)
+    else:
+        src = np.ascontiguousarray(A, np.float32) if o == "R" else np.asfortranarray(A, np.float32)
+        ptr = src.ctypes.data
+        keep.append(src)
+    lda = n if o == "R" else m
+    h = _P()
+    rc = lib.pogs_setup(ptr, m, n, lda, o.encode(), C.byref(params) if params is not None else None,
+                        _stream_ptr(stream), C.byref(h))
+    _check(rc, "pogs_setup")
+    return h.value
+
+
+def pogs_solve(handle, f, g, params: pogs_params | None = None, x=None, y=None, mu=None, nu=None) -> pogs_info:
+    """Outputs x, y, mu, nu: preallocated float32 arrays/tensors (host or device) or None."""
+    keep: list = []
+    fs, gs = make_fn(f, keep), make_fn(g, keep)
+    info = pogs_info()
+    rc = lib.pogs_solve(handle, C.byref(fs), C.byref(gs), C.byref(params) if params is not None else None,
+                        _outptr(x), _outptr(y), _outptr(mu), _outptr(nu), C.byref(info))
+    _check(rc, "pogs_solve")
+    return info
+
+
+def _outptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous() and str(a.dtype) == "torch.float32"
+        return a.data_ptr()
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def pogs_free(handle) -> None:
+    lib.pogs_free(handle)
+
+
+def pogs_prox_eval(fn, v, rho: float = 1.0, rho_vec=None, out=None, stream=None):
+    """All arrays must be CUDA tensors of length k (the parametric prox of Section 5)."""
+    keep: list = []
+    fs = make_fn(fn, keep)
+    import torch
+    k = v.numel()
+    if out is None:
+        out = torch.empty_like(v)
+    rc = lib.pogs_prox_eval(C.byref(fs), k, _ptr(v, np.float32, keep), _ptr(rho_vec, np.float32, keep),
+                            C.c_float(rho), out.data_ptr(), _stream_ptr(stream))
+    _check(rc, "pogs_prox_eval")
+    return out
+
+
+def pogs_get_equil(handle, m: int, n: int):
+    D = np.empty(m, np.float32)
+    E = np.empty(n, np.float32)
+    _check(lib.pogs_get_equil(handle, D.ctypes.data, E.ctypes.data), "pogs_get_equil")
+    return D, E
+
+
+def pogs_get_ahat(handle, m: int, n: int):
+    Ah = np.empty((m, n), np.float32)
+    _check(lib.pogs_get_ahat(handle, Ah.ctypes.data), "pogs_get_ahat")
+    return Ah
+
+
+def pogs_project(handle, c, d, params: pogs_params | None = None):
+    keep: list = []
+    n, m = len(c), len(d)
+    x = np.empty(n, np.float32)
+    y = np.empty(m, np.float32)
+    rc = lib.pogs_project(handle, _ptr(c, np.float32, keep), _ptr(d, np.float32, keep), x.ctypes.data,
+                          y.ctypes.data, C.byref(params) if params is not None else None)
+    _check(rc, "pogs_project")
+    return x, y

@@ -1,0 +1,105 @@
+// Shared device helpers, device-side solver state and launch constants.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pogs.h"
+
+#define POGS_DEV __device__ __forceinline__
+
+namespace pogs {
+
+constexpr int kWarp = 32;
+constexpr int kTile = 128;          // packed-triangle tile edge (L^{-1} storage)
+constexpr int kLdaAlign = 32;       // row pitch of A^ in floats (128 bytes)
+
+// Scalars of the ADMM loop that live on the device (Algorithm 1 + Algorithm 3).
+struct DevState {
+  double rho;         // rho^k
+  double pend;        // pending rescale factor rho^{k-1}/rho^k for x~, y~ (applied on read)
+  double r_pri, r_dual, eps_pri, eps_dual, gap, obj;
+  double r_pri_u, r_dual_u;
+  int k;              // iteration counter
+  int l, u;           // Algorithm 3 bookkeeping
+  int done;           // 1 once converged / max_iter / error
+  int status;         // POGS_OK, POGS_MAX_ITER, or negative error
+  int err;            // device-side error flag (e.g. NUMERIC pivot, TIMEOUT)
+  int pad_;
+};
+
+// Parameters read by the check kernel (copied by value into the launch).
+struct LoopParams {
+  double abs_tol, rel_tol, alpha, delta, tau;
+  int max_iter, gap_stop, adaptive;
+};
+
+// Per-element function parameters (pre-conditioned), structure of arrays.
+struct FnDev {
+  const uint8_t* h;
+  const float *a, *b, *c, *d, *e;
+};
+
+// ---- reductions -------------------------------------------------------------------------
+POGS_DEV float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+POGS_DEV double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide FP64 sum of NV values per thread; result valid in thread 0. `sh` holds
+// NV * (blockDim/32) doubles. Deterministic (fixed shuffle tree + fixed warp order).
+template <int NV>
+POGS_DEV void block_sum(double (&v)[NV], double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int t = 0; t < NV; ++t) v[t] = warp_sum(v[t]);
+  if (lane == 0) {
+#pragma unroll
+    for (int t = 0; t < NV; ++t) sh[t * nw + wid] = v[t];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sh[t * nw + w];
+      v[t] = s;
+    }
+  }
+  __syncthreads();
+}
+
+POGS_DEV float4 ldg_stream(const float4* p) {
+  float4 r;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "l"(p));
+  return r;
+}
+
+// "Last block done" protocol: every block of a group publishes its partial results,
+// fences, and bumps the group's counter; the block that brings the counter to `total`
+// reduces the partials in a fixed order and resets the counter for the next launch.
+POGS_DEV bool arrive_last(unsigned* counter, unsigned total) {
+  __shared__ unsigned s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(counter, 1u);
+    s_last = (prev == total - 1) ? 1u : 0u;
+    if (s_last) *counter = 0u;   // reset for the next use (no other block touches it now)
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace pogs

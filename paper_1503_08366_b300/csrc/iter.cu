@@ -1,0 +1,665 @@
+// Per-iteration kernels of graph-form ADMM (Algorithm 1 + Section 3.2 over-relaxation +
+// Section 3.4 stopping + Algorithm 3), all on the pre-conditioned problem (Eq. 12).
+//
+// One iteration, tall case (m >= n), reading A^ twice and the cached factor twice:
+//   prox_step   : x^{1/2}, y^{1/2}, mu^{1/2}, nu^{1/2}, c = x_r + x~, d = y_r + y~   (m+n elts)
+//   gemv_t      : [t, s] = A^T [d, nu^{1/2}]  ->  r = c + t, ||s + mu||               (A pass 1)
+//   trmv (N)    : z = L^{-1} r                                                          (L pass 1)
+//   trmv (T)    : x^{k+1} = L^{-T} z, x~ = c - x^{k+1}                                  (L pass 2)
+//   gemv_n      : [y^{k+1}, w] = A [x^{k+1}, x^{1/2}] -> y~ = d - y^{k+1}, ||w - y^{1/2}|| (A pass 2)
+//   check       : Section 3.4 test, gap, Algorithm 3, graph conditional
+// The fat case (m < n) swaps the roles of the two GEMVs (Section 3.5 reduced update).
+#include <cstdio>
+
+#include "kernels.h"
+#include "prox.cuh"
+
+namespace pogs {
+
+// ------------------------------------------------------------------------------------------
+// Prox step (Algorithm 1 step 3, Section 3.2, Section 3.3).
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) prox_step_kernel(
+    int n, int m, const float* __restrict__ x, const float* __restrict__ xt, float* __restrict__ xh,
+    float* __restrict__ cx, float* __restrict__ mu, const float* __restrict__ y,
+    const float* __restrict__ yt, float* __restrict__ yh, float* __restrict__ dy,
+    float* __restrict__ nu, FnDev g, FnDev f, const DevState* __restrict__ st,
+    const DevCfg* __restrict__ cfg, double* __restrict__ part) {
+  __shared__ double sh[6 * 8];
+  if (st->done) return;
+  const float rho = (float)st->rho;
+  const float pend = (float)st->pend;
+  const float alpha = (float)cfg->alpha;
+  double acc[6] = {0, 0, 0, 0, 0, 0};   // ||mu||^2, x.mu, g(x), ||y||^2, y.nu, f(y)
+  const int total = n + m;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    if (i < n) {
+      const int j = i;
+      const float xtj = pend * xt[j], xj = x[j], v = xj - xtj;
+      const int h = g.h[j];
+      const float a = g.a[j], b = g.b[j], c = g.c[j], d = g.d[j], e = g.e[j];
+      const float xhj = prox_param(h, a, b, c, d, e, rho, v);
+      const float muj = -rho * (xhj - v);
+      const float xr = alpha * xhj + (1.0f - alpha) * xj;
+      xh[j] = xhj;
+      cx[j] = xr + xtj;
+      mu[j] = muj;
+      acc[0] += (double)muj * muj;
+      acc[1] += (double)xhj * muj;
+      acc[2] += (double)f_param(h, a, b, c, d, e, xhj);
+    } else {
+      const int k = i - n;
+      const float ytk = pend * yt[k], yk = y[k], v = yk - ytk;
+      const int h = f.h[k];
+      const float a = f.a[k], b = f.b[k], c = f.c[k], d = f.d[k], e = f.e[k];
+      const float yhk = prox_param(h, a, b, c, d, e, rho, v);
+      const float nuk = -rho * (yhk - v);
+      const float yr = alpha * yhk + (1.0f - alpha) * yk;
+      yh[k] = yhk;
+      dy[k] = yr + ytk;
+      nu[k] = nuk;
+      acc[3] += (double)yhk * yhk;
+      acc[4] += (double)yhk * nuk;
+      acc[5] += (double)f_param(h, a, b, c, d, e, yhk);
+    }
+  }
+  block_sum<6>(acc, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int t = 0; t < 6; ++t) part[blockIdx.x * 6 + t] = acc[t];
+  }
+}
+
+void launch_prox_step(int n, int m, const float* x, const float* xt, float* xh, float* cx, float* mu,
+                      const float* y, const float* yt, float* yh, float* dy, float* nu, FnDev g, FnDev f,
+                      const DevState* st, const DevCfg* cfg, double* part, int nblocks, cudaStream_t s) {
+  prox_step_kernel<<<nblocks, 256, 0, s>>>(n, m, x, xt, xh, cx, mu, y, yt, yh, dy, nu, g, f, st, cfg, part);
+}
+
+// ------------------------------------------------------------------------------------------
+// Column sums t = A^T [v1, v2] (A row-major m x lda, zero-padded columns).  Block (bx, by)
+// streams rows [by*R, by*R+R) of the 1024-column slab bx (256 threads x float4); partial
+// sums go to part[by][rhs][col]; the last block of each slab reduces the splits in a fixed
+// order and applies the epilogue.
+// ------------------------------------------------------------------------------------------
+template <int EPI>
+__device__ __forceinline__ void epi_t(const EpiArgs& ep, int j, float t1, float t2, double* res) {
+  if constexpr (EPI == EPT_RAW) {
+    ep.out1[j] = t1;
+    if (ep.out2) ep.out2[j] = t2;
+  } else if constexpr (EPI == EPT_TALL_R) {
+    ep.r[j] = ep.cx[j] + t1;
+    const float dr = t2 + ep.mu[j];
+    res[0] += (double)dr * dr;
+    const float du = dr / ep.E[j];
+    res[1] += (double)du * du;
+  } else if constexpr (EPI == EPT_FAT_X) {
+    const float c = ep.cx[j];
+    const float xp = c + t1;
+    ep.x[j] = xp;
+    ep.xt[j] = c - xp;
+    const float dr = t2 + ep.mu[j];
+    res[0] += (double)dr * dr;
+    const float du = dr / ep.E[j];
+    res[1] += (double)du * du;
+  } else if constexpr (EPI == EPT_SK_COL) {
+    // sk_num < 0: keep e (Frobenius norm only, no Sinkhorn-Knopp update)
+    float ej;
+    if (ep.sk_num > 0.0f) {
+      ej = ep.sk_num / (t1 + ep.sk_reg);
+      ep.sk_vec[j] = ej;
+    } else {
+      ej = ep.sk_vec[j];
+    }
+    res[0] += (double)ej * (double)t1;   // sum_ij d_i A_ij^2 e_j = ||D A E||_F^2 (p = 2)
+  } else if constexpr (EPI == EPT_REFINE) {
+    ep.out1[j] = ep.in1[j] - ep.in2[j] - t1;
+  }
+}
+
+template <int NRHS, bool SQ, int EPI>
+__global__ void __launch_bounds__(256) gemv_t_kernel(const float* __restrict__ A, int64_t lda, int m, int n,
+                                                     const float* __restrict__ v1,
+                                                     const float* __restrict__ v2, int rows,
+                                                     float* __restrict__ part, unsigned* __restrict__ cnt,
+                                                     EpiArgs ep, const DevState* __restrict__ guard) {
+  __shared__ double sh[2 * 8];
+  if (guard && guard->done) return;
+  const int tid = threadIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.x * 1024 + 4 * tid;
+  const bool active = c0 < lda;
+  const int r0 = blockIdx.y * rows;
+  const int r1 = min(m, r0 + rows);
+  float acc[NRHS][4];
+#pragma unroll
+  for (int r = 0; r < NRHS; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.0f;
+  if (active) {
+    const float* Ap = A + c0;
+    int i = r0;
+    for (; i + 8 <= r1; i += 8) {
+      float4 a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = ldg_stream(reinterpret_cast<const float4*>(Ap + (int64_t)(i + u) * lda));
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        float4 av = a[u];
+        if (SQ) { av.x *= av.x; av.y *= av.y; av.z *= av.z; av.w *= av.w; }
+        const float w1 = __ldg(v1 + i + u);
+        acc[0][0] = fmaf(av.x, w1, acc[0][0]); acc[0][1] = fmaf(av.y, w1, acc[0][1]);
+        acc[0][2] = fmaf(av.z, w1, acc[0][2]); acc[0][3] = fmaf(av.w, w1, acc[0][3]);
+        if constexpr (NRHS == 2) {
+          const float w2 = __ldg(v2 + i + u);
+          acc[1][0] = fmaf(av.x, w2, acc[1][0]); acc[1][1] = fmaf(av.y, w2, acc[1][1]);
+          acc[1][2] = fmaf(av.z, w2, acc[1][2]); acc[1][3] = fmaf(av.w, w2, acc[1][3]);
+        }
+      }
+    }
+    for (; i < r1; ++i) {
+      float4 av = ldg_stream(reinterpret_cast<const float4*>(Ap + (int64_t)i * lda));
+      if (SQ) { av.x *= av.x; av.y *= av.y; av.z *= av.z; av.w *= av.w; }
+      const float w1 = __ldg(v1 + i);
+      acc[0][0] = fmaf(av.x, w1, acc[0][0]); acc[0][1] = fmaf(av.y, w1, acc[0][1]);
+      acc[0][2] = fmaf(av.z, w1, acc[0][2]); acc[0][3] = fmaf(av.w, w1, acc[0][3]);
+      if constexpr (NRHS == 2) {
+        const float w2 = __ldg(v2 + i);
+        acc[1][0] = fmaf(av.x, w2, acc[1][0]); acc[1][1] = fmaf(av.y, w2, acc[1][1]);
+        acc[1][2] = fmaf(av.z, w2, acc[1][2]); acc[1][3] = fmaf(av.w, w2, acc[1][3]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r)
+      *reinterpret_cast<float4*>(part + ((int64_t)blockIdx.y * NRHS + r) * lda + c0) =
+          make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+  }
+  if (!arrive_last(cnt + blockIdx.x, gridDim.y)) return;
+  double res[2] = {0.0, 0.0};
+  if (active) {
+    float s[NRHS][4];
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) s[r][0] = s[r][1] = s[r][2] = s[r][3] = 0.0f;
+    for (int sp = 0; sp < (int)gridDim.y; ++sp) {
+#pragma unroll
+      for (int r = 0; r < NRHS; ++r) {
+        const float4 p = __ldcg(reinterpret_cast<const float4*>(part + ((int64_t)sp * NRHS + r) * lda + c0));
+        s[r][0] += p.x; s[r][1] += p.y; s[r][2] += p.z; s[r][3] += p.w;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t j = c0 + u;
+      if (j < n) epi_t<EPI>(ep, (int)j, s[0][u], NRHS == 2 ? s[NRHS - 1][u] : 0.0f, res);
+    }
+  }
+  block_sum<2>(res, sh);
+  if (threadIdx.x == 0 && ep.res_part) {
+    ep.res_part[2 * blockIdx.x] = res[0];
+    ep.res_part[2 * blockIdx.x + 1] = res[1];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Row dots u = A [x1, x2].  Block (bx, by) covers rows [bx*RB, bx*RB+RB) and the column
+// chunk by (CB floats, staged from x1/x2 in shared memory); one warp per row, float4 lanes,
+// shuffle reduction; partials part[by][rhs][row]; the last chunk-block of a row block
+// reduces in a fixed order and applies the epilogue.
+// ------------------------------------------------------------------------------------------
+template <int EPI>
+__device__ __forceinline__ void epi_n(const EpiArgs& ep, int i, float u1, float u2, double* res) {
+  if constexpr (EPI == EPN_RAW) {
+    ep.out1[i] = u1;
+    if (ep.out2) ep.out2[i] = u2;
+  } else if constexpr (EPI == EPN_TALL_Y) {
+    ep.y[i] = u1;
+    ep.yt[i] = ep.dy[i] - u1;
+    const float pr = u2 - ep.yh[i];
+    res[0] += (double)pr * pr;
+    const float pu = pr / ep.D[i];
+    res[1] += (double)pu * pu;
+  } else if constexpr (EPI == EPN_FAT_R) {
+    ep.r[i] = u1 - ep.dy[i];
+    const float pr = u2 - ep.yh[i];
+    res[0] += (double)pr * pr;
+    const float pu = pr / ep.D[i];
+    res[1] += (double)pu * pu;
+  } else if constexpr (EPI == EPN_SK_ROW) {
+    ep.sk_vec[i] = ep.sk_num / (u1 + ep.sk_reg);
+  } else if constexpr (EPI == EPN_REFINE) {
+    ep.out1[i] = ep.in1[i] - ep.in2[i] - u1;
+  }
+}
+
+template <int NRHS, bool SQ, int EPI>
+__global__ void __launch_bounds__(256) gemv_n_kernel(const float* __restrict__ A, int64_t lda, int m, int n,
+                                                     const float* __restrict__ x1,
+                                                     const float* __restrict__ x2, int rows, int cols,
+                                                     float* __restrict__ part, unsigned* __restrict__ cnt,
+                                                     EpiArgs ep, const DevState* __restrict__ guard) {
+  extern __shared__ float4 sx[];
+  __shared__ double sh[2 * 8];
+  if (guard && guard->done) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t cbeg = (int64_t)blockIdx.y * cols;
+  const int64_t cend = min((int64_t)lda, cbeg + cols);
+  const int nq = (int)((cend - cbeg) >> 2);      // valid float4 in this chunk (lda % 4 == 0)
+  const int nqs = cols >> 2;                     // shared-memory stride per rhs
+  for (int qq = tid; qq < nq; qq += blockDim.x) {
+    sx[qq] = __ldg(reinterpret_cast<const float4*>(x1 + cbeg) + qq);
+    if constexpr (NRHS == 2) sx[nqs + qq] = __ldg(reinterpret_cast<const float4*>(x2 + cbeg) + qq);
+  }
+  __syncthreads();
+  const int r0 = blockIdx.x * rows;
+  const int r1 = min(m, r0 + rows);
+  for (int row = r0 + warp; row < r1; row += 8) {
+    const float4* Ar = reinterpret_cast<const float4*>(A + (int64_t)row * lda + cbeg);
+    float s1 = 0.0f, s2 = 0.0f;
+    int qq = lane;
+    for (; qq + 96 < nq; qq += 128) {
+      float4 a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = ldg_stream(Ar + qq + 32 * u);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float4 av = a[u];
+        if (SQ) { av.x *= av.x; av.y *= av.y; av.z *= av.z; av.w *= av.w; }
+        const float4 xv = sx[qq + 32 * u];
+        s1 = fmaf(av.x, xv.x, fmaf(av.y, xv.y, fmaf(av.z, xv.z, fmaf(av.w, xv.w, s1))));
+        if constexpr (NRHS == 2) {
+          const float4 xw = sx[nqs + qq + 32 * u];
+          s2 = fmaf(av.x, xw.x, fmaf(av.y, xw.y, fmaf(av.z, xw.z, fmaf(av.w, xw.w, s2))));
+        }
+      }
+    }
+    for (; qq < nq; qq += 32) {
+      float4 av = ldg_stream(Ar + qq);
+      if (SQ) { av.x *= av.x; av.y *= av.y; av.z *= av.z; av.w *= av.w; }
+      const float4 xv = sx[qq];
+      s1 = fmaf(av.x, xv.x, fmaf(av.y, xv.y, fmaf(av.z, xv.z, fmaf(av.w, xv.w, s1))));
+      if constexpr (NRHS == 2) {
+        const float4 xw = sx[nqs + qq];
+        s2 = fmaf(av.x, xw.x, fmaf(av.y, xw.y, fmaf(av.z, xw.z, fmaf(av.w, xw.w, s2))));
+      }
+    }
+    s1 = warp_sum(s1);
+    if constexpr (NRHS == 2) s2 = warp_sum(s2);
+    if (lane == 0) {
+      part[((int64_t)blockIdx.y * NRHS) * m + row] = s1;
+      if constexpr (NRHS == 2) part[((int64_t)blockIdx.y * NRHS + 1) * m + row] = s2;
+    }
+  }
+  if (!arrive_last(cnt + blockIdx.x, gridDim.y)) return;
+  double res[2] = {0.0, 0.0};
+  for (int row = r0 + tid; row < r1; row += blockDim.x) {
+    float u1 = 0.0f, u2 = 0.0f;
+    for (int sp = 0; sp < (int)gridDim.y; ++sp) {
+      u1 += __ldcg(part + ((int64_t)sp * NRHS) * m + row);
+      if constexpr (NRHS == 2) u2 += __ldcg(part + ((int64_t)sp * NRHS + 1) * m + row);
+    }
+    epi_n<EPI>(ep, row, u1, u2, res);
+  }
+  block_sum<2>(res, sh);
+  if (threadIdx.x == 0 && ep.res_part) {
+    ep.res_part[2 * blockIdx.x] = res[0];
+    ep.res_part[2 * blockIdx.x + 1] = res[1];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Triangular products with the cached inverse factor M = L^{-1}, stored as 128 x 128 tiles
+// of the lower triangle (tile (I,J), J <= I, at linear index I(I+1)/2 + J, row-major inside;
+// padding rows/cols are zero).  One block per tile; partial tile products are reduced by
+// the last block of each tile row (z = M v) or tile column (x = M^T v).
+// ------------------------------------------------------------------------------------------
+template <int EPI>
+__device__ __forceinline__ void epi_r(const EpiArgs& ep, int idx, int q, float v) {
+  if constexpr (EPI == EPR_RAW) {
+    ep.out1[idx] = v;
+  } else if constexpr (EPI == EPR_ADD) {
+    if (idx < q) ep.out1[idx] = ep.in1[idx] + v;
+  } else if constexpr (EPI == EPR_TALL_X) {
+    if (idx < q) {
+      const float c = ep.cx[idx];
+      const float xv = ep.in1 ? ep.in1[idx] + v : v;   // in1: refinement base x0
+      ep.x[idx] = xv;
+      ep.xt[idx] = c - xv;
+    }
+  } else if constexpr (EPI == EPR_FAT_Y) {
+    if (idx < q) {
+      const float d = ep.dy[idx];
+      const float yp = d + (ep.in1 ? ep.in1[idx] + v : v);
+      ep.y[idx] = yp;
+      ep.yt[idx] = d - yp;
+      ep.w[idx] = d - yp;
+    }
+  }
+}
+
+__device__ __forceinline__ void tile_coords(int b, int& I, int& J) {
+  int i = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= b) ++i;
+  while (i * (i + 1) / 2 > b) --i;
+  I = i;
+  J = b - i * (i + 1) / 2;
+}
+
+template <bool TRANS, int EPI>
+__global__ void __launch_bounds__(256) trmv_kernel(const float* __restrict__ Mt, int T, int q,
+                                                   const float* __restrict__ vin, float* __restrict__ part,
+                                                   unsigned* __restrict__ cnt, EpiArgs ep,
+                                                   const DevState* __restrict__ guard) {
+  __shared__ float4 shc[8][32];
+  if (guard && guard->done) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = blockIdx.x;
+  int I, J;
+  tile_coords(b, I, J);
+  const float4* tile = reinterpret_cast<const float4*>(Mt + (int64_t)b * kTile * kTile);
+  if (!TRANS) {
+    const float4 rv = __ldg(reinterpret_cast<const float4*>(vin + (int64_t)J * kTile) + lane);
+    float4 a[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) a[u] = ldg_stream(tile + (warp * 16 + u) * 32 + lane);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      float s = a[u].x * rv.x + a[u].y * rv.y + a[u].z * rv.z + a[u].w * rv.w;
+      s = warp_sum(s);
+      if (lane == 0) part[(int64_t)b * kTile + warp * 16 + u] = s;
+    }
+    if (!arrive_last(cnt + I, I + 1)) return;
+    if (tid < kTile) {
+      const int64_t base = (int64_t)I * (I + 1) / 2;
+      float s = 0.0f;
+      for (int jj = 0; jj <= I; ++jj) s += __ldcg(part + (base + jj) * kTile + tid);
+      epi_r<EPI>(ep, I * kTile + tid, q, s);
+    }
+  } else {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 a[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) a[u] = ldg_stream(tile + (warp * 16 + u) * 32 + lane);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const float zr = __ldg(vin + (int64_t)I * kTile + warp * 16 + u);
+      acc.x = fmaf(a[u].x, zr, acc.x); acc.y = fmaf(a[u].y, zr, acc.y);
+      acc.z = fmaf(a[u].z, zr, acc.z); acc.w = fmaf(a[u].w, zr, acc.w);
+    }
+    shc[warp][lane] = acc;
+    __syncthreads();
+    const int64_t slot = (int64_t)J * T - (int64_t)J * (J - 1) / 2 + (I - J);
+    if (tid < kTile) {
+      const float* shf = reinterpret_cast<const float*>(&shc[0][0]);
+      float s = 0.0f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) s += shf[w * kTile + tid];
+      part[slot * kTile + tid] = s;
+    }
+    if (!arrive_last(cnt + J, T - J)) return;
+    if (tid < kTile) {
+      const int64_t base = (int64_t)J * T - (int64_t)J * (J - 1) / 2;
+      float s = 0.0f;
+      for (int ii = 0; ii < T - J; ++ii) s += __ldcg(part + (base + ii) * kTile + tid);
+      epi_r<EPI>(ep, J * kTile + tid, q, s);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Stopping test (Section 3.4 + half-tuple gap) and Algorithm 3, single block.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) check_kernel(DevState* st, const DevCfg* __restrict__ cfg,
+                                                    const double* __restrict__ prox_part, int nprox,
+                                                    const double* __restrict__ pri_part, int npri,
+                                                    const double* __restrict__ dual_part, int ndual,
+                                                    cudaGraphConditionalHandle h, int use_cond) {
+  __shared__ double sh[10 * 8];
+  if (st->done) {
+    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
+  double v[10];
+#pragma unroll
+  for (int t = 0; t < 10; ++t) v[t] = 0.0;
+  for (int i = threadIdx.x; i < nprox; i += blockDim.x) {
+#pragma unroll
+    for (int t = 0; t < 6; ++t) v[t] += prox_part[6 * i + t];
+  }
+  for (int i = threadIdx.x; i < npri; i += blockDim.x) {
+    v[6] += pri_part[2 * i];
+    v[7] += pri_part[2 * i + 1];
+  }
+  for (int i = threadIdx.x; i < ndual; i += blockDim.x) {
+    v[8] += dual_part[2 * i];
+    v[9] += dual_part[2 * i + 1];
+  }
+  block_sum<10>(v, sh);
+  if (threadIdx.x != 0) return;
+  const double mu2 = v[0], xmu = v[1], gobj = v[2], yh2 = v[3], ynu = v[4], fobj = v[5];
+  const double r_pri = sqrt(v[6]), r_pri_u = sqrt(v[7]), r_dual = sqrt(v[8]), r_dual_u = sqrt(v[9]);
+  const double eps_pri = cfg->abs_tol + cfg->rel_tol * sqrt(yh2);
+  const double eps_dual = cfg->abs_tol + cfg->rel_tol * sqrt(mu2);
+  const double gap = ynu + xmu;
+  const double obj = fobj + gobj;
+  const double eps_gap = cfg->abs_tol + cfg->rel_tol * fabs(obj);
+  st->r_pri = r_pri; st->r_dual = r_dual; st->eps_pri = eps_pri; st->eps_dual = eps_dual;
+  st->gap = gap; st->obj = obj; st->r_pri_u = r_pri_u; st->r_dual_u = r_dual_u;
+  const int k = st->k;
+  st->k = k + 1;
+  int done = 0;
+  if (st->err != 0) {
+    st->status = st->err;
+    done = 1;
+  } else if (!isfinite(r_pri) || !isfinite(r_dual) || !isfinite(gap) || !isfinite(obj)) {
+    st->status = POGS_ERR_NONFINITE;
+    done = 1;
+  } else if (r_pri < eps_pri && r_dual < eps_dual && (!cfg->gap_stop || fabs(gap) < eps_gap)) {
+    st->status = POGS_OK;
+    done = 1;
+  } else if (k + 1 >= cfg->max_iter) {
+    st->status = POGS_MAX_ITER;
+    done = 1;
+  }
+  double pend = 1.0;
+  if (!done && cfg->adaptive) {
+    const double rho = st->rho;
+    double rho_new = rho;
+    if (r_dual < eps_dual && cfg->tau * k > st->l) {
+      rho_new = cfg->delta * rho;
+      st->u = k;
+    } else if (r_pri < eps_pri && cfg->tau * k > st->u) {
+      rho_new = rho / cfg->delta;
+      st->l = k;
+    }
+    pend = rho / rho_new;
+    st->rho = rho_new;
+  }
+  st->pend = pend;
+  st->done = done;
+  if (use_cond) cudaGraphSetConditional(h, done ? 0u : 1u);
+}
+
+// ------------------------------------------------------------------------------------------
+// Small elementwise kernels.
+// ------------------------------------------------------------------------------------------
+__global__ void prox_eval_kernel(FnDev fn, int64_t k, const float* v, const float* rv, float rho, float* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+    const float r = rv ? rv[i] : rho;
+    out[i] = prox_param(fn.h[i], fn.a[i], fn.b[i], fn.c[i], fn.d[i], fn.e[i], r, v[i]);
+  }
+}
+
+// Pre-conditioned parameters (Eq. 12): f^(y^) = f(y^/D): a/D, d/D, e/D^2 (is_f);
+// g^(x^) = g(E x^): a E, d E, e E^2.  Validates a != 0, c >= 0, e >= 0, h in range.
+__global__ void fold_kernel(FnDev raw, int64_t k, const float* scale, int is_f, uint8_t* h, float* a,
+                            float* b, float* c, float* d, float* e, int* err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+    const int hv = raw.h[i];
+    const float av = raw.a ? raw.a[i] : 1.0f, bv = raw.b ? raw.b[i] : 0.0f;
+    const float cv = raw.c ? raw.c[i] : 1.0f, dv = raw.d ? raw.d[i] : 0.0f, ev = raw.e ? raw.e[i] : 0.0f;
+    if (hv < 0 || hv > POGS_IND_BOX01 || !(av != 0.0f) || !(cv >= 0.0f) || !(ev >= 0.0f) ||
+        !isfinite(av) || !isfinite(bv) || !isfinite(cv) || !isfinite(dv) || !isfinite(ev))
+      atomicCAS(err, 0, POGS_ERR_ARG);   // first error wins
+    const float s = scale[i];
+    const float m1 = is_f ? 1.0f / s : s;
+    h[i] = (uint8_t)hv;
+    a[i] = av * m1;
+    b[i] = bv;
+    c[i] = cv;
+    d[i] = dv * m1;
+    e[i] = ev * m1 * m1;
+  }
+}
+
+__global__ void fill_kernel(float* p, int64_t k, float v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// Returned tuple (Section 5) in the original variables: x = E x^, mu = mu^/E, y = y^/D, nu = D nu^.
+__global__ void unscale_kernel(int n, int m, const float* xh, const float* mu, const float* yh,
+                               const float* nu, const float* D, const float* E, float* x, float* muo,
+                               float* y, float* nuo) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
+    if (i < n) {
+      if (x) x[i] = E[i] * xh[i];
+      if (muo) muo[i] = mu[i] / E[i];
+    } else {
+      const int k = i - n;
+      if (y) y[k] = yh[k] / D[k];
+      if (nuo) nuo[k] = D[k] * nu[k];
+    }
+  }
+}
+
+__global__ void axpby_kernel(int64_t k, float a, const float* x, float b, const float* y, float* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a * x[i] + b * y[i];
+}
+
+static int grid_for(int64_t k, int per = 256) {
+  int64_t g = (k + per - 1) / per;
+  if (g < 1) g = 1;
+  if (g > 148 * 8) g = 148 * 8;
+  return (int)g;
+}
+
+void launch_prox_eval(FnDev fn, int64_t k, const float* v, const float* rv, float rho, float* out, cudaStream_t s) {
+  prox_eval_kernel<<<grid_for(k), 256, 0, s>>>(fn, k, v, rv, rho, out);
+}
+void launch_fold(FnDev raw, int64_t k, const float* scale, int is_f, uint8_t* h, float* a, float* b, float* c,
+                 float* d, float* e, int* err, cudaStream_t s) {
+  fold_kernel<<<grid_for(k), 256, 0, s>>>(raw, k, scale, is_f, h, a, b, c, d, e, err);
+}
+void launch_fill(float* p, int64_t k, float v, cudaStream_t s) { fill_kernel<<<grid_for(k), 256, 0, s>>>(p, k, v); }
+void launch_unscale(int n, int m, const float* xh, const float* mu, const float* yh, const float* nu,
+                    const float* D, const float* E, float* x, float* muo, float* y, float* nuo, cudaStream_t s) {
+  unscale_kernel<<<grid_for(n + m), 256, 0, s>>>(n, m, xh, mu, yh, nu, D, E, x, muo, y, nuo);
+}
+void launch_axpby(int64_t k, float a, const float* x, float b, const float* y, float* out, cudaStream_t s) {
+  axpby_kernel<<<grid_for(k), 256, 0, s>>>(k, a, x, b, y, out);
+}
+
+// ------------------------------------------------------------------------------------------
+// Dispatch.
+// ------------------------------------------------------------------------------------------
+GemvGeom choose_geometry(int64_t m, int64_t n, int64_t lda, int num_sms) {
+  GemvGeom g{};
+  // column sums: 1024-column slabs, rows split so that the grid covers ~4 blocks per SM
+  g.t_cols_per_blk = 1024;
+  g.t_ncolblk = (int)cdiv(lda, 1024);
+  int64_t target = (int64_t)num_sms * 4;
+  int64_t nsplit = cdiv(target, g.t_ncolblk);
+  int64_t rows = cdiv(m, nsplit);
+  rows = rows < 8 ? 8 : rows;
+  g.t_rows = (int)rows;
+  g.t_nsplit = (int)cdiv(m, rows);
+  // row dots: column chunks of <= 4096 floats; rows per block chosen for ~8 blocks per SM
+  int64_t nchunk = cdiv(lda, 4096);
+  int64_t cols = round_up(cdiv(lda, nchunk), 128);
+  g.n_cols = (int)cols;
+  g.n_ncolsplit = (int)cdiv(lda, cols);
+  int64_t tgt = (int64_t)num_sms * 8;
+  int64_t nrb = cdiv(tgt, g.n_ncolsplit);
+  int64_t rb = cdiv(m, nrb);
+  rb = rb < 8 ? 8 : (rb > 256 ? 256 : rb);
+  g.n_rows = (int)rb;
+  g.n_nrowblk = (int)cdiv(m, rb);
+  return g;
+}
+
+template <int NRHS, bool SQ>
+static void gemv_t_dispatch(int epi, const float* A, int64_t lda, int m, int n, const float* v1, const float* v2,
+                            const GemvGeom& g, float* part, unsigned* cnt, const EpiArgs& ep,
+                            const DevState* guard, cudaStream_t s) {
+  dim3 grid(g.t_ncolblk, g.t_nsplit);
+#define POGS_T(E) gemv_t_kernel<NRHS, SQ, E><<<grid, 256, 0, s>>>(A, lda, m, n, v1, v2, g.t_rows, part, cnt, ep, guard)
+  switch (epi) {
+    case EPT_RAW: POGS_T(EPT_RAW); break;
+    case EPT_TALL_R: POGS_T(EPT_TALL_R); break;
+    case EPT_FAT_X: POGS_T(EPT_FAT_X); break;
+    case EPT_SK_COL: POGS_T(EPT_SK_COL); break;
+    case EPT_REFINE: POGS_T(EPT_REFINE); break;
+  }
+#undef POGS_T
+}
+
+void launch_gemv_t(int nrhs, bool sq, int epi, const float* A, int64_t lda, int m, int n, const float* v1,
+                   const float* v2, const GemvGeom& g, float* part, unsigned* cnt, const EpiArgs& ep,
+                   const DevState* guard, cudaStream_t s) {
+  if (nrhs == 2) gemv_t_dispatch<2, false>(epi, A, lda, m, n, v1, v2, g, part, cnt, ep, guard, s);
+  else if (sq) gemv_t_dispatch<1, true>(epi, A, lda, m, n, v1, v2, g, part, cnt, ep, guard, s);
+  else gemv_t_dispatch<1, false>(epi, A, lda, m, n, v1, v2, g, part, cnt, ep, guard, s);
+}
+
+template <int NRHS, bool SQ>
+static void gemv_n_dispatch(int epi, const float* A, int64_t lda, int m, int n, const float* x1, const float* x2,
+                            const GemvGeom& g, float* part, unsigned* cnt, const EpiArgs& ep,
+                            const DevState* guard, cudaStream_t s) {
+  dim3 grid(g.n_nrowblk, g.n_ncolsplit);
+  const size_t smem = (size_t)NRHS * g.n_cols * sizeof(float);
+  // smem <= 2 x 4096 floats = 32 KB: no opt-in needed (and nothing to set during capture)
+#define POGS_N(E) \
+  gemv_n_kernel<NRHS, SQ, E><<<grid, 256, smem, s>>>(A, lda, m, n, x1, x2, g.n_rows, g.n_cols, part, cnt, ep, guard)
+  switch (epi) {
+    case EPN_RAW: POGS_N(EPN_RAW); break;
+    case EPN_TALL_Y: POGS_N(EPN_TALL_Y); break;
+    case EPN_FAT_R: POGS_N(EPN_FAT_R); break;
+    case EPN_SK_ROW: POGS_N(EPN_SK_ROW); break;
+    case EPN_REFINE: POGS_N(EPN_REFINE); break;
+  }
+#undef POGS_N
+}
+
+void launch_gemv_n(int nrhs, bool sq, int epi, const float* A, int64_t lda, int m, int n, const float* x1,
+                   const float* x2, const GemvGeom& g, float* part, unsigned* cnt, const EpiArgs& ep,
+                   const DevState* guard, cudaStream_t s) {
+  if (nrhs == 2) gemv_n_dispatch<2, false>(epi, A, lda, m, n, x1, x2, g, part, cnt, ep, guard, s);
+  else if (sq) gemv_n_dispatch<1, true>(epi, A, lda, m, n, x1, x2, g, part, cnt, ep, guard, s);
+  else gemv_n_dispatch<1, false>(epi, A, lda, m, n, x1, x2, g, part, cnt, ep, guard, s);
+}
+
+void launch_trmv(bool trans, int epi, const float* Mt, int T, int q, const float* vin, float* part, unsigned* cnt,
+                 const EpiArgs& ep, const DevState* guard, cudaStream_t s) {
+  const int nt = T * (T + 1) / 2;
+#define POGS_R(TR, E) trmv_kernel<TR, E><<<nt, 256, 0, s>>>(Mt, T, q, vin, part, cnt, ep, guard)
+  if (!trans) {
+    switch (epi) {
+      case EPR_RAW: POGS_R(false, EPR_RAW); break;
+      case EPR_ADD: POGS_R(false, EPR_ADD); break;
+    }
+  } else {
+    switch (epi) {
+      case EPR_RAW: POGS_R(true, EPR_RAW); break;
+      case EPR_TALL_X: POGS_R(true, EPR_TALL_X); break;
+      case EPR_FAT_Y: POGS_R(true, EPR_FAT_Y); break;
+      case EPR_ADD: POGS_R(true, EPR_ADD); break;
+    }
+  }
+#undef POGS_R
+}
+
+void launch_check(DevState* st, const DevCfg* cfg, const double* prox_part, int nprox, const double* pri_part,
+                  int npri, const double* dual_part, int ndual, unsigned long long cond_handle, int use_cond,
+                  cudaStream_t s) {
+  check_kernel<<<1, 256, 0, s>>>(st, cfg, prox_part, nprox, pri_part, npri, dual_part, ndual,
+                                 (cudaGraphConditionalHandle)cond_handle, use_cond);
+}
+
+}  // namespace pogs

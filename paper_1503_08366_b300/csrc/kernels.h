@@ -1,0 +1,110 @@
+// Launch wrappers for the device kernels (definitions in iter.cu and setup.cu).
+#pragma once
+#include "common.cuh"
+
+namespace pogs {
+
+// Epilogues of the column-sum GEMV  t = A^T [v1, v2]  (one column per output element).
+enum EpiT : int {
+  EPT_RAW = 0,      // out1 = t1, out2 = t2
+  EPT_TALL_R = 1,   // tall projection input r = c + A^T d; dual residual from t2 = A^T nu
+  EPT_FAT_X = 2,    // fat x^{k+1} = c + A^T (d - y^{k+1}); x~ = c - x^{k+1}; dual residual
+  EPT_SK_COL = 3,   // Algorithm 2 e-update; Frobenius partial sum e_j * colsum_j
+  EPT_REFINE = 4,   // refinement residual out1 = r - x0 - t1 (tall)
+};
+// Epilogues of the row-dot GEMV  u = A [x1, x2]  (one row per output element).
+enum EpiN : int {
+  EPN_RAW = 0,      // out1 = u1, out2 = u2
+  EPN_TALL_Y = 1,   // tall y^{k+1} = A x^{k+1}; y~ = d - y^{k+1}; primal residual from u2 = A x^{1/2}
+  EPN_FAT_R = 2,    // fat projection input r = A c - d; primal residual
+  EPN_SK_ROW = 3,   // Algorithm 2 d-update
+  EPN_REFINE = 4,   // refinement residual out1 = r - y0 - u1 (fat)
+};
+// Epilogues of the packed-triangle products z = M v (M = L^{-1}) and M^T v.
+enum EpiR : int {
+  EPR_RAW = 0,      // out1 = result (all padded entries)
+  EPR_TALL_X = 1,   // x^{k+1} = result; x~ = c - x^{k+1}
+  EPR_FAT_Y = 2,    // y^{k+1} = d + result; y~ = d - y^{k+1}; w = d - y^{k+1}
+  EPR_ADD = 3,      // out1 = in1 + result (refinement correction)
+};
+
+// Everything an epilogue may read or write.  Unused fields are null.
+struct EpiArgs {
+  float *out1, *out2;
+  const float *in1, *in2;             // extra inputs (refinement)
+  const float *cx, *dy, *yh, *mu;     // c, d, y^{1/2}, mu^{1/2}
+  float *x, *xt, *y, *yt, *r, *w;
+  const float *D, *E;                 // diagonal scalings (unscaled residuals)
+  float* sk_vec;                      // SK output vector (d or e)
+  float sk_num, sk_reg;               // n and gamma/m (rows) or m and gamma/n (cols)
+  double* res_part;                   // 2 doubles per block: residual^2, unscaled residual^2
+};
+
+// Loop parameters in device memory (so a captured graph survives parameter changes).
+struct DevCfg {
+  double abs_tol, rel_tol, alpha, delta, tau;
+  int max_iter, gap_stop, adaptive, pad_;
+};
+
+// Geometry of the two GEMV shapes, chosen at setup.
+struct GemvGeom {
+  int t_cols_per_blk;   // 1024 (fixed: 256 threads x float4)
+  int t_ncolblk, t_nsplit, t_rows;
+  int n_rows, n_cols, n_nrowblk, n_ncolsplit;
+};
+GemvGeom choose_geometry(int64_t m, int64_t n, int64_t lda, int num_sms);
+
+// ---- iteration kernels (iter.cu) --------------------------------------------------------
+void launch_prox_step(int n, int m, const float* x, const float* xt, float* xh, float* cx, float* mu,
+                      const float* y, const float* yt, float* yh, float* dy, float* nu,
+                      FnDev g, FnDev f, const DevState* st, const DevCfg* cfg, double* part,
+                      int nblocks, cudaStream_t s);
+void launch_gemv_t(int nrhs, bool sq, int epi, const float* A, int64_t lda, int m, int n,
+                   const float* v1, const float* v2, const GemvGeom& g, float* part, unsigned* cnt,
+                   const EpiArgs& ep, const DevState* guard, cudaStream_t s);
+void launch_gemv_n(int nrhs, bool sq, int epi, const float* A, int64_t lda, int m, int n,
+                   const float* x1, const float* x2, const GemvGeom& g, float* part, unsigned* cnt,
+                   const EpiArgs& ep, const DevState* guard, cudaStream_t s);
+void launch_trmv(bool trans, int epi, const float* Mt, int T, int q, const float* vin, float* part,
+                 unsigned* cnt, const EpiArgs& ep, const DevState* guard, cudaStream_t s);
+void launch_check(DevState* st, const DevCfg* cfg, const double* prox_part, int nprox,
+                  const double* pri_part, int npri, const double* dual_part, int ndual,
+                  unsigned long long cond_handle, int use_cond, cudaStream_t s);
+void launch_prox_eval(FnDev fn, int64_t k, const float* v, const float* rho_vec, float rho, float* out,
+                      cudaStream_t s);
+void launch_fold(FnDev raw, int64_t k, const float* scale, int is_f, uint8_t* h, float* a, float* b,
+                 float* c, float* d, float* e, int* err, cudaStream_t s);
+void launch_fill(float* p, int64_t k, float v, cudaStream_t s);
+void launch_unscale(int n, int m, const float* xh, const float* mu, const float* yh, const float* nu,
+                    const float* D, const float* E, float* x, float* muo, float* y, float* nuo,
+                    cudaStream_t s);
+void launch_axpby(int64_t k, float a, const float* x, float b, const float* y, float* out, cudaStream_t s);
+
+// ---- setup kernels (setup.cu) -------------------------------------------------------------
+void launch_copy_in(const float* src, int64_t m, int64_t n, int64_t lds, bool colmajor, float* A,
+                    int64_t lda, int* err, cudaStream_t s);
+void launch_scale(float* A, int64_t lda, int64_t m, int64_t n, const float* D, const float* E,
+                  cudaStream_t s);
+void launch_sk_finish(const float* dvec, const float* evec, int64_t m, int64_t n, const double* frob_part,
+                      int nfrob, int64_t q, float* D, float* E, cudaStream_t s);
+// C[M x N] = alpha op(A) op(B) + beta C (row-major, SIMT); lower_only skips tiles above
+// the diagonal of C.
+void gemm_f32(bool ta, bool tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+              const float* B, int64_t ldb, float beta, float* C, int64_t ldc, bool lower_only,
+              cudaStream_t s);
+void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+              const double* B, int64_t ldb, double beta, double* C, int64_t ldc, bool lower_only,
+              cudaStream_t s);
+void launch_gram_to_f64(const float* G, int64_t ldg, int64_t q, double* H, int64_t ldh, cudaStream_t s);
+int chol_f64(double* H, int64_t ldh, int64_t q, double* work, int* err, cudaStream_t s);
+void launch_leaf_inverse(const double* L, int64_t ldl, int64_t q, float* Minv, int64_t ldm, cudaStream_t s);
+void launch_l_to_f32(const double* L, int64_t ldl, int64_t q, float* Lf, int64_t ldf, cudaStream_t s);
+void tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ldm, float* work,
+                     cudaStream_t s);
+void launch_pack_tiles(const float* M, int64_t ldm, int64_t q, int T, float* Mt, cudaStream_t s);
+// Tensor-core Gram (gram.cu): G = X X^T over the K-major packed operand(s).
+int gram_tensor(int prec, const float* A, int64_t lda, int64_t m, int64_t n, bool tall, float* G,
+                int64_t ldg, void* scratch, size_t scratch_bytes, size_t* need_bytes, int* err,
+                cudaStream_t s);
+
+}  // namespace pogs

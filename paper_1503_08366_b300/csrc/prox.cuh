@@ -1,0 +1,77 @@
+// Separable proximal operators (Section 5): base functions h and the parametric formula
+//   prox_f(v) = (1/a) ( prox_{h, (e+rho)/(c a^2)} ( a (v rho - d)/(e + rho) - b ) + b ).
+#pragma once
+#include "common.cuh"
+
+namespace pogs {
+
+POGS_DEV float sigmoidf(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+// argmin_z log(1+e^z) + (r/2)(z - v)^2: the root of sigma(z) + r (z - v) = 0, which lies in
+// [v - 1/r, v].  Newton steps kept inside a shrinking bracket (bisection when a step
+// leaves it); the map is strictly increasing so the root is unique.
+POGS_DEV float prox_logistic(float v, float r) {
+  float lo = v - 1.0f / r, hi = v;
+  float z = v - sigmoidf(v) / (1.0f + r);   // one implicit-Euler guess, inside the bracket
+  z = fminf(fmaxf(z, lo), hi);
+#pragma unroll 1
+  for (int it = 0; it < 40; ++it) {
+    const float s = sigmoidf(z);
+    const float phi = s + r * (z - v);
+    if (phi > 0.0f) hi = z; else lo = z;
+    float zn = z - phi / (s * (1.0f - s) + r);
+    if (!(zn > lo && zn < hi)) zn = 0.5f * (lo + hi);
+    const bool stop = fabsf(zn - z) <= 1e-7f * (1.0f + fabsf(zn)) || hi - lo <= 1e-7f * (1.0f + fabsf(zn));
+    z = zn;
+    if (stop) break;
+  }
+  return z;
+}
+
+// argmin_z h(z) + (r/2)(z - v)^2 for the base functions of the library.
+POGS_DEV float prox_h(int h, float v, float r) {
+  const float ir = 1.0f / r;
+  switch (h) {
+    case POGS_ZERO: return v;
+    case POGS_ABS: return copysignf(fmaxf(fabsf(v) - ir, 0.0f), v);
+    case POGS_SQUARE: return r * v / (1.0f + r);
+    case POGS_HUBER: return fabsf(v) <= 1.0f + ir ? r * v / (1.0f + r) : v - copysignf(ir, v);
+    case POGS_LOGISTIC: return prox_logistic(v, r);
+    case POGS_HINGE: return v < 1.0f - ir ? v + ir : (v > 1.0f ? v : 1.0f);
+    case POGS_MAXPOS: return v > ir ? v - ir : (v < 0.0f ? v : 0.0f);
+    case POGS_IND_GE0: return fmaxf(v, 0.0f);
+    case POGS_IND_LE0: return fminf(v, 0.0f);
+    case POGS_IND_EQ0: return 0.0f;
+    case POGS_IND_BOX01: return fminf(fmaxf(v, 0.0f), 1.0f);
+    default: return v;
+  }
+}
+
+// h(z) for the objective.  Indicators are evaluated as 0: the solver only evaluates f and g
+// at prox outputs, which lie in the function's domain by construction.
+POGS_DEV float h_value(int h, float z) {
+  switch (h) {
+    case POGS_ABS: return fabsf(z);
+    case POGS_SQUARE: return 0.5f * z * z;
+    case POGS_HUBER: return fabsf(z) <= 1.0f ? 0.5f * z * z : fabsf(z) - 0.5f;
+    case POGS_LOGISTIC: return fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z)));
+    case POGS_HINGE: return fmaxf(0.0f, 1.0f - z);
+    case POGS_MAXPOS: return fmaxf(0.0f, z);
+    default: return 0.0f;
+  }
+}
+
+// Parametric prox of Section 5 at parameter rho.  c == 0 drops the h term (identity inner
+// prox, the c -> 0 limit of the formula).
+POGS_DEV float prox_param(int h, float a, float b, float c, float d, float e, float rho, float v) {
+  const float w = a * (v * rho - d) / (e + rho) - b;
+  const float z = c > 0.0f ? prox_h(h, w, (e + rho) / (c * a * a)) : w;
+  return (z + b) / a;
+}
+
+POGS_DEV float f_param(int h, float a, float b, float c, float d, float e, float y) {
+  const float hv = c > 0.0f ? c * h_value(h, a * y - b) : 0.0f;
+  return hv + d * y + 0.5f * e * y * y;
+}
+
+}  // namespace pogs

@@ -1,0 +1,364 @@
+// One-time setup kernels: ingest of A, Sinkhorn-Knopp finish + Frobenius rescale
+// (Algorithm 2, Section 4.1.2), the dense SIMT GEMM used for the FP32 Gram mode, the FP64
+// blocked Cholesky of I + G (Section 3.5, factorization caching) and the FP32 triangular
+// inverse M = L^{-1} that the iteration applies, packed into 128 x 128 tiles.
+#include <algorithm>
+#include <cstdio>
+
+#include "kernels.h"
+
+namespace pogs {
+
+// ---- ingest --------------------------------------------------------------------------------
+// Row-major (or column-major) source -> padded row-major A (pitch lda, zero padding),
+// flagging non-finite entries.
+__global__ void copy_rowmajor_kernel(const float* __restrict__ src, int64_t m, int64_t n, int64_t lds,
+                                     float* __restrict__ A, int64_t lda, int* err) {
+  const int64_t total = m * lda;
+  int bad = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / lda, j = e - i * lda;
+    float v = 0.0f;
+    if (j < n) {
+      v = src[i * lds + j];
+      if (!isfinite(v)) bad = 1;
+    }
+    A[e] = v;
+  }
+  if (bad) atomicCAS(err, 0, POGS_ERR_NONFINITE);   // first error wins
+}
+
+__global__ void copy_colmajor_kernel(const float* __restrict__ src, int64_t m, int64_t n, int64_t lds,
+                                     float* __restrict__ A, int64_t lda, int* err) {
+  __shared__ float t[32][33];
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  int bad = 0;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t j = j0 + r, i = i0 + threadIdx.x;   // read along i (contiguous in column-major)
+    float v = 0.0f;
+    if (i < m && j < n) {
+      v = src[j * lds + i];
+      if (!isfinite(v)) bad = 1;
+    }
+    t[r][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t i = i0 + r, j = j0 + threadIdx.x;
+    if (i < m && j < lda) A[i * lda + j] = (j < n) ? t[threadIdx.x][r] : 0.0f;
+  }
+  if (bad) atomicCAS(err, 0, POGS_ERR_NONFINITE);   // first error wins
+}
+
+void launch_copy_in(const float* src, int64_t m, int64_t n, int64_t lds, bool colmajor, float* A, int64_t lda,
+                    int* err, cudaStream_t s) {
+  if (!colmajor) {
+    int64_t g = std::min<int64_t>((m * lda + 255) / 256, 148 * 16);
+    copy_rowmajor_kernel<<<(int)g, 256, 0, s>>>(src, m, n, lds, A, lda, err);
+  } else {
+    dim3 grid((unsigned)cdiv(lda, 32), (unsigned)cdiv(m, 32));
+    copy_colmajor_kernel<<<grid, dim3(32, 8), 0, s>>>(src, m, n, lds, A, lda, err);
+  }
+}
+
+// A^ = D A E in place (Section 4.1).
+__global__ void scale_kernel(float* A, int64_t lda, int64_t m, int64_t n, const float* D, const float* E) {
+  const int64_t total = m * lda;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / lda, j = e - i * lda;
+    if (j < n) A[e] *= D[i] * E[j];
+  }
+}
+
+void launch_scale(float* A, int64_t lda, int64_t m, int64_t n, const float* D, const float* E, cudaStream_t s) {
+  int64_t g = std::min<int64_t>((m * lda + 255) / 256, 148 * 16);
+  scale_kernel<<<(int)g, 256, 0, s>>>(A, lda, m, n, D, E);
+}
+
+// D = sqrt(d / s), E = sqrt(e / s) with s = ||diag(d)^{1/2} A diag(e)^{1/2}||_F / sqrt(q):
+// Algorithm 2's D = diag(d)^{1/p}, E = diag(e)^{1/p} (p = 2) rescaled evenly (Section 4.1.2).
+__global__ void sk_finish_kernel(const float* dvec, const float* evec, int64_t m, int64_t n, const double* frob_part,
+                                 int nfrob, int64_t q, float* D, float* E) {
+  __shared__ double sh[32];
+  __shared__ double s_inv;
+  double v[1] = {0.0};
+  for (int i = threadIdx.x; i < nfrob; i += blockDim.x) v[0] += frob_part[2 * i];
+  block_sum<1>(v, sh);
+  if (threadIdx.x == 0) s_inv = 1.0 / sqrt(v[0] / (double)q);
+  __syncthreads();
+  const double si = s_inv;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) D[i] = (float)sqrt((double)dvec[i] * si);
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) E[j] = (float)sqrt((double)evec[j] * si);
+}
+
+void launch_sk_finish(const float* dvec, const float* evec, int64_t m, int64_t n, const double* frob_part, int nfrob,
+                      int64_t q, float* D, float* E, cudaStream_t s) {
+  sk_finish_kernel<<<1, 1024, 0, s>>>(dvec, evec, m, n, frob_part, nfrob, q, D, E);
+}
+
+// ---- dense SIMT GEMM -----------------------------------------------------------------------
+// C = alpha op(A) op(B) + beta C, row-major.  op(A)[i][k] = TA ? A[k*lda+i] : A[i*lda+k],
+// op(B)[k][j] = TB ? B[j*ldb+k] : B[k*ldb+j].  256 threads, (BM/TM) x (BN/TN) = 16 x 16
+// thread grid, interleaved register tiles (conflict-free shared reads).
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool TA, bool TB>
+__global__ void __launch_bounds__(256) gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha,
+                                                   const T* A, int64_t lda, const T* B, int64_t ldb, T beta, T* C,
+                                                   int64_t ldc, int lower_only) {
+  // A and C may alias (in-place panel update): each block reads its own rows of A fully
+  // before it writes C, and no other block touches those rows.
+  constexpr int GX = BN / TN, GY = BM / TM;
+  static_assert(GX * GY == 256, "thread grid");
+  const int64_t bm = blockIdx.y, bn = blockIdx.x;
+  const int64_t row0 = (int64_t)bm * BM, col0 = (int64_t)bn * BN;
+  if (lower_only && col0 > row0 + BM - 1) return;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int tx = threadIdx.x % GX, ty = threadIdx.x / GX;
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+    for (int e = threadIdx.x; e < BM * BK; e += 256) {
+      int i, k;
+      if (TA) { k = e / BM; i = e % BM; } else { i = e / BK; k = e % BK; }
+      const int64_t gi = row0 + i, gk = k0 + k;
+      T v = T(0);
+      if (gi < M && gk < K) v = TA ? A[gk * lda + gi] : A[gi * lda + gk];
+      As[k][i] = v;
+    }
+    for (int e = threadIdx.x; e < BN * BK; e += 256) {
+      int j, k;
+      if (TB) { j = e / BK; k = e % BK; } else { k = e / BN; j = e % BN; }
+      const int64_t gj = col0 + j, gk = k0 + k;
+      T v = T(0);
+      if (gj < N && gk < K) v = TB ? B[gj * ldb + gk] : B[gk * ldb + gj];
+      Bs[k][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      T a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[k][ty + i * GY];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[k][tx + j * GX];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int64_t gi = row0 + ty + i * GY;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int64_t gj = col0 + tx + j * GX;
+      if (gj >= N) continue;
+      T c = alpha * acc[i][j];
+      if (beta != T(0)) c = fma(beta, C[gi * ldc + gj], c);
+      C[gi * ldc + gj] = c;
+    }
+  }
+}
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+static void gemm_launch(bool ta, bool tb, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda,
+                        const T* B, int64_t ldb, T beta, T* C, int64_t ldc, bool lower_only, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((unsigned)cdiv(N, BN), (unsigned)cdiv(M, BM));
+  const int lo = lower_only ? 1 : 0;
+  if (!ta && !tb) gemm_kernel<T, BM, BN, BK, TM, TN, false, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lo);
+  else if (!ta && tb) gemm_kernel<T, BM, BN, BK, TM, TN, false, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lo);
+  else if (ta && !tb) gemm_kernel<T, BM, BN, BK, TM, TN, true, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lo);
+  else gemm_kernel<T, BM, BN, BK, TM, TN, true, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lo);
+}
+
+void gemm_f32(bool ta, bool tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+              const float* B, int64_t ldb, float beta, float* C, int64_t ldc, bool lower_only, cudaStream_t s) {
+  gemm_launch<float, 128, 128, 8, 8, 8>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, s);
+}
+void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+              const double* B, int64_t ldb, double beta, double* C, int64_t ldc, bool lower_only, cudaStream_t s) {
+  gemm_launch<double, 64, 64, 8, 4, 4>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, s);
+}
+
+// H = I + G (lower triangle, FP64), zero above the diagonal.
+__global__ void gram_to_f64_kernel(const float* G, int64_t ldg, int64_t q, double* H, int64_t ldh) {
+  const int64_t total = q * q;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / q, j = e - i * q;
+    double v = 0.0;
+    if (j <= i) v = (double)G[i * ldg + j] + (i == j ? 1.0 : 0.0);
+    H[i * ldh + j] = v;
+  }
+}
+void launch_gram_to_f64(const float* G, int64_t ldg, int64_t q, double* H, int64_t ldh, cudaStream_t s) {
+  int64_t g = std::min<int64_t>((q * q + 255) / 256, 148 * 16);
+  gram_to_f64_kernel<<<(int)g, 256, 0, s>>>(G, ldg, q, H, ldh);
+}
+
+// ---- FP64 blocked Cholesky (right-looking) ------------------------------------------------
+constexpr int kNB = 64;
+
+// Factor the nb x nb diagonal block in place and write its inverse factor to Linv (ld kNB).
+// The inverse is built column by column (forward substitution on e_c, one column per
+// thread) and kept transposed in the strict upper triangle of the same shared tile.
+__global__ void __launch_bounds__(256) potrf_diag_kernel(double* Hk, int64_t ldh, int nb, double* Linv, int* err) {
+  __shared__ double s[kNB][kNB + 1];
+  __shared__ double dl[kNB], dx[kNB];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    s[i][j] = (j <= i) ? Hk[(int64_t)i * ldh + j] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (tid == 0) {
+      double djj = s[j][j];
+      if (!(djj > 0.0) || !isfinite(djj)) {
+        atomicCAS(err, 0, POGS_ERR_NUMERIC);
+        djj = 1.0;
+      }
+      s[j][j] = sqrt(djj);
+    }
+    __syncthreads();
+    const double ljj = s[j][j];
+    for (int i = j + 1 + tid; i < nb; i += blockDim.x) s[i][j] /= ljj;
+    __syncthreads();
+    const int rem = nb - j - 1;
+    for (int e = tid; e < rem * rem; e += blockDim.x) {
+      const int i = j + 1 + e / rem, k = j + 1 + e % rem;
+      if (k <= i) s[i][k] -= s[i][j] * s[k][j];
+    }
+    __syncthreads();
+  }
+  if (tid < nb) dl[tid] = s[tid][tid];
+  __syncthreads();
+  if (tid < nb) {
+    const int c = tid;
+    const double xcc = 1.0 / dl[c];
+    dx[c] = xcc;
+    for (int i = c + 1; i < nb; ++i) {
+      double acc = -s[i][c] * xcc;
+      for (int k = c + 1; k < i; ++k) acc -= s[i][k] * s[c][k];   // X[k][c] lives at s[c][k]
+      s[c][i] = acc / dl[i];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    Hk[(int64_t)i * ldh + j] = (j < i) ? s[i][j] : (j == i ? dl[i] : 0.0);
+    Linv[i * kNB + j] = (j < i) ? s[j][i] : (j == i ? dx[i] : 0.0);
+  }
+}
+
+int chol_f64(double* H, int64_t ldh, int64_t q, double* work, int* err, cudaStream_t s) {
+  for (int64_t k0 = 0; k0 < q; k0 += kNB) {
+    const int nb = (int)std::min<int64_t>(kNB, q - k0);
+    potrf_diag_kernel<<<1, 256, 0, s>>>(H + k0 * ldh + k0, ldh, nb, work, err);
+    const int64_t rest = q - k0 - nb;
+    if (rest > 0) {
+      double* P = H + (k0 + nb) * ldh + k0;
+      // panel: P <- P L_kk^{-T} (in place: one block column covers all nb <= 64 columns)
+      gemm_f64(false, true, rest, nb, nb, 1.0, P, ldh, work, kNB, 0.0, P, ldh, false, s);
+      // trailing update: H22 <- H22 - P P^T (lower tiles)
+      gemm_f64(false, true, rest, rest, nb, -1.0, P, ldh, P, ldh, 1.0, H + (k0 + nb) * ldh + (k0 + nb), ldh, true, s);
+    }
+  }
+  return 0;
+}
+
+// ---- FP32 inverse factor M = L^{-1} ---------------------------------------------------------
+// Diagonal 128 x 128 blocks of M inverted in FP64 from the FP64 factor (one block per CTA,
+// one column per thread, forward substitution on e_c), written as FP32.  Column c of the
+// inverse is kept transposed in the strict upper triangle of the shared tile.
+__global__ void __launch_bounds__(128) leaf_inverse_kernel(const double* L, int64_t ldl, int64_t q, float* M,
+                                                           int64_t ldm) {
+  extern __shared__ double sm[];
+  double* s = sm;                        // [128][129]
+  double* dl = sm + 128 * 129;           // [128] diagonal of L
+  const int64_t r0 = (int64_t)blockIdx.x * kTile;
+  const int nb = (int)(q - r0 < kTile ? q - r0 : kTile);
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    if (j < i) s[i * 129 + j] = L[(r0 + i) * ldl + r0 + j];
+    else if (j == i) dl[i] = L[(r0 + i) * ldl + r0 + j];
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c < nb) {
+    const double xcc = 1.0 / dl[c];
+    M[(r0 + c) * ldm + r0 + c] = (float)xcc;
+    for (int i = c + 1; i < nb; ++i) {
+      double acc = -s[i * 129 + c] * xcc;
+      for (int k = c + 1; k < i; ++k) acc -= s[i * 129 + k] * s[c * 129 + k];
+      const double v = acc / dl[i];
+      s[c * 129 + i] = v;
+      M[(r0 + i) * ldm + r0 + c] = (float)v;
+    }
+  }
+}
+
+void launch_leaf_inverse(const double* L, int64_t ldl, int64_t q, float* Minv, int64_t ldm, cudaStream_t s) {
+  const int T = (int)cdiv(q, kTile);
+  const size_t smem = (size_t)(128 * 129 + 128) * sizeof(double);
+  cudaFuncSetAttribute(leaf_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  leaf_inverse_kernel<<<T, 128, smem, s>>>(L, ldl, q, Minv, ldm);
+}
+
+__global__ void l_to_f32_kernel(const double* L, int64_t ldl, int64_t q, float* Lf, int64_t ldf) {
+  const int64_t total = q * q;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / q, j = e - i * q;
+    Lf[i * ldf + j] = (j <= i) ? (float)L[i * ldl + j] : 0.0f;
+  }
+}
+void launch_l_to_f32(const double* L, int64_t ldl, int64_t q, float* Lf, int64_t ldf, cudaStream_t s) {
+  int64_t g = std::min<int64_t>((q * q + 255) / 256, 148 * 16);
+  l_to_f32_kernel<<<(int)g, 256, 0, s>>>(L, ldl, q, Lf, ldf);
+}
+
+// Recursive 2 x 2 block inverse of a lower-triangular matrix:
+//   inv([[L11, 0], [L21, L22]]) = [[M11, 0], [-M22 L21 M11, M22]],
+// splitting at multiples of 128 so the leaves are the FP64-inverted diagonal blocks.
+static void inv_rec(const float* L, int64_t ldl, float* M, int64_t ldm, int64_t r0, int64_t nsz, float* work,
+                    cudaStream_t s) {
+  if (nsz <= kTile) return;
+  const int64_t nblk = cdiv(nsz, kTile);
+  const int64_t n1 = (nblk / 2) * kTile, n2 = nsz - n1;
+  inv_rec(L, ldl, M, ldm, r0, n1, work, s);
+  inv_rec(L, ldl, M, ldm, r0 + n1, n2, work, s);
+  gemm_f32(false, false, n2, n1, n1, 1.0f, L + (r0 + n1) * ldl + r0, ldl, M + r0 * ldm + r0, ldm, 0.0f, work, n1,
+           false, s);
+  gemm_f32(false, false, n2, n1, n2, -1.0f, M + (r0 + n1) * ldm + r0 + n1, ldm, work, n1, 0.0f,
+           M + (r0 + n1) * ldm + r0, ldm, false, s);
+}
+
+void tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ldm, float* work, cudaStream_t s) {
+  inv_rec(L, ldl, M, ldm, 0, q, work, s);
+}
+
+// Pack the lower triangle of M (dense, ld ldm) into 128 x 128 tiles, zero outside.
+__global__ void __launch_bounds__(256) pack_tiles_kernel(const float* M, int64_t ldm, int64_t q, float* Mt) {
+  const int b = blockIdx.x;
+  int I = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
+  while ((I + 1) * (I + 2) / 2 <= b) ++I;
+  while (I * (I + 1) / 2 > b) --I;
+  const int J = b - I * (I + 1) / 2;
+  float* out = Mt + (int64_t)b * kTile * kTile;
+  for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+    const int rr = e / kTile, cc = e % kTile;
+    const int64_t gi = (int64_t)I * kTile + rr, gj = (int64_t)J * kTile + cc;
+    out[e] = (gi < q && gj < q && gj <= gi) ? M[gi * ldm + gj] : 0.0f;
+  }
+}
+void launch_pack_tiles(const float* M, int64_t ldm, int64_t q, int T, float* Mt, cudaStream_t s) {
+  pack_tiles_kernel<<<T * (T + 1) / 2, 256, 0, s>>>(M, ldm, q, Mt);
+}
+
+}  // namespace pogs

@@ -1,0 +1,690 @@
+// Host orchestration and the C interface (include/pogs.h).
+//
+// Setup (Section 3.5 'factorization caching', Algorithm 2, Section 4.1.2, Section 5):
+//   ingest A -> Sinkhorn-Knopp sweeps (row pass + column pass per sweep) -> Frobenius rescale
+//   -> A^ = D A E in place -> Gram G -> FP64 Cholesky of I + G -> FP32 M = L^{-1} in tiles.
+// Solve: fold D, E into the function parameters (Eq. 12), then run the iteration body
+//   (iter.cu) inside a CUDA graph whose conditional WHILE node is cleared by the on-device
+//   stopping test, so a whole solve is one graph launch with no host round trip.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace pogs;
+
+struct pogs_handle {
+  int64_t m = 0, n = 0, lda = 0, q = 0;
+  bool tall = true;
+  int T = 0;
+  int64_t nv = 0, mv = 0;
+  int num_sms = 148;
+  cudaStream_t stream = nullptr;   // caller's stream
+  cudaStream_t cap = nullptr;      // private stream used for graph capture
+  pogs_params sp{};
+  GemvGeom geom{};
+  int nprox = 0;
+  int gram_used = -1;
+  float* A = nullptr;
+  float *D = nullptr, *E = nullptr;
+  float* Mt = nullptr;
+  float *x = nullptr, *y = nullptr, *xt = nullptr, *yt = nullptr, *xh = nullptr, *yh = nullptr;
+  float *cx = nullptr, *dy = nullptr, *mu = nullptr, *nu = nullptr, *r = nullptr, *z = nullptr, *w = nullptr;
+  float *x0 = nullptr, *v0 = nullptr, *r2 = nullptr, *tn = nullptr;
+  float *ox = nullptr, *oy = nullptr, *omu = nullptr, *onu = nullptr;
+  uint8_t *fh = nullptr, *gh = nullptr, *rh = nullptr;
+  float *fa, *fb, *fc, *fd, *fe, *ga, *gb, *gc, *gd, *ge, *ra, *rb, *rc, *rd, *re;
+  float *part_t = nullptr, *part_n = nullptr, *part_tr = nullptr;
+  unsigned *cnt_t = nullptr, *cnt_n = nullptr, *cnt_tr = nullptr;
+  double *prox_part = nullptr, *pri_part = nullptr, *dual_part = nullptr;
+  DevState* st = nullptr;
+  DevCfg* cfg = nullptr;
+  DevState* st_host = nullptr;     // pinned mirror
+  DevCfg* cfg_host = nullptr;      // pinned staging
+  cudaGraphExec_t gexec = nullptr;
+  int graph_refine = -1, graph_mode = -1;
+  double setup_ms = 0.0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      if (getenv("POGS_DEBUG")) fprintf(stderr, "pogs: %s failed: %s (%s:%d)\n", #call, \
+                                        cudaGetErrorString(e_), __FILE__, __LINE__);  \
+      return e_ == cudaErrorMemoryAllocation ? POGS_ERR_OOM : POGS_ERR_CUDA;          \
+    }                                                                                 \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+int dalloc(pogs_handle* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return POGS_ERR_OOM;
+  }
+  h->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  if (cudaMemsetAsync(q, 0, count * sizeof(T), h->stream) != cudaSuccess) return POGS_ERR_CUDA;
+  return 0;
+}
+
+// Scratch that lives only during setup.
+struct Scratch {
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  int get(T** p, size_t count, cudaStream_t s) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, (count ? count : 1) * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return POGS_ERR_OOM;
+    }
+    ptrs.push_back(q);
+    *p = static_cast<T*>(q);
+    if (cudaMemsetAsync(q, 0, (count ? count : 1) * sizeof(T), s) != cudaSuccess) return POGS_ERR_CUDA;
+    return 0;
+  }
+};
+
+#define TRY(x)          \
+  do {                  \
+    int rc_ = (x);      \
+    if (rc_ < 0) return rc_; \
+  } while (0)
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+FnDev fn_f(const pogs_handle* h) { return FnDev{h->fh, h->fa, h->fb, h->fc, h->fd, h->fe}; }
+FnDev fn_g(const pogs_handle* h) { return FnDev{h->gh, h->ga, h->gb, h->gc, h->gd, h->ge}; }
+
+EpiArgs epi0() {
+  EpiArgs e;
+  memset(&e, 0, sizeof(e));
+  return e;
+}
+
+// The projection of one iteration (tall or fat), optionally with refinement.
+void enqueue_projection(pogs_handle* h, int refine, cudaStream_t s) {
+  const int m = (int)h->m, n = (int)h->n, q = (int)h->q;
+  const GemvGeom& g = h->geom;
+  if (h->tall) {
+    // r = c + A^T d ; dual residual ||A^T nu + mu||
+    EpiArgs e1 = epi0();
+    e1.r = h->r; e1.cx = h->cx; e1.mu = h->mu; e1.E = h->E; e1.res_part = h->dual_part;
+    launch_gemv_t(2, false, EPT_TALL_R, h->A, h->lda, m, n, h->dy, h->nu, g, h->part_t, h->cnt_t, e1, h->st, s);
+    EpiArgs e2 = epi0();
+    e2.out1 = h->z;
+    launch_trmv(false, EPR_RAW, h->Mt, h->T, q, h->r, h->part_tr, h->cnt_tr, e2, h->st, s);
+    EpiArgs e3 = epi0();
+    e3.x = h->x; e3.xt = h->xt; e3.cx = h->cx;
+    launch_trmv(true, EPR_TALL_X, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, e3, h->st, s);
+    if (refine) {
+      // r2 = r - x0 - A^T (A x0);  x = x0 + L^{-T} L^{-1} r2
+      EpiArgs e4 = epi0();
+      e4.out1 = h->v0;
+      launch_gemv_n(1, false, EPN_RAW, h->A, h->lda, m, n, h->x, nullptr, g, h->part_n, h->cnt_n, e4, h->st, s);
+      EpiArgs e5 = epi0();
+      e5.out1 = h->r2; e5.in1 = h->r; e5.in2 = h->x;
+      launch_gemv_t(1, false, EPT_REFINE, h->A, h->lda, m, n, h->v0, nullptr, g, h->part_t, h->cnt_t, e5, h->st, s);
+      EpiArgs e6 = epi0();
+      e6.out1 = h->z;
+      launch_trmv(false, EPR_RAW, h->Mt, h->T, q, h->r2, h->part_tr, h->cnt_tr, e6, h->st, s);
+      EpiArgs e7 = epi0();
+      e7.x = h->x; e7.xt = h->xt; e7.cx = h->cx; e7.in1 = h->x;
+      launch_trmv(true, EPR_TALL_X, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, e7, h->st, s);
+    }
+    // [y, w] = A [x, x^{1/2}] ; y~ = d - y ; primal residual ||A x^{1/2} - y^{1/2}||
+    EpiArgs e8 = epi0();
+    e8.y = h->y; e8.yt = h->yt; e8.dy = h->dy; e8.yh = h->yh; e8.D = h->D; e8.res_part = h->pri_part;
+    launch_gemv_n(2, false, EPN_TALL_Y, h->A, h->lda, m, n, h->x, h->xh, g, h->part_n, h->cnt_n, e8, h->st, s);
+  } else {
+    // r = A c - d ; primal residual
+    EpiArgs e1 = epi0();
+    e1.r = h->r; e1.dy = h->dy; e1.yh = h->yh; e1.D = h->D; e1.res_part = h->pri_part;
+    launch_gemv_n(2, false, EPN_FAT_R, h->A, h->lda, m, n, h->cx, h->xh, g, h->part_n, h->cnt_n, e1, h->st, s);
+    EpiArgs e2 = epi0();
+    e2.out1 = h->z;
+    launch_trmv(false, EPR_RAW, h->Mt, h->T, q, h->r, h->part_tr, h->cnt_tr, e2, h->st, s);
+    if (!refine) {
+      EpiArgs e3 = epi0();
+      e3.y = h->y; e3.yt = h->yt; e3.dy = h->dy; e3.w = h->w;
+      launch_trmv(true, EPR_FAT_Y, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, e3, h->st, s);
+    } else {
+      EpiArgs e3 = epi0();
+      e3.out1 = h->v0;
+      launch_trmv(true, EPR_RAW, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, e3, h->st, s);
+      // r2 = r - v0 - A (A^T v0)
+      EpiArgs e4 = epi0();
+      e4.out1 = h->tn;
+      launch_gemv_t(1, false, EPT_RAW, h->A, h->lda, m, n, h->v0, nullptr, g, h->part_t, h->cnt_t, e4, h->st, s);
+      EpiArgs e5 = epi0();
+      e5.out1 = h->r2; e5.in1 = h->r; e5.in2 = h->v0;
+      launch_gemv_n(1, false, EPN_REFINE, h->A, h->lda, m, n, h->tn, nullptr, g, h->part_n, h->cnt_n, e5, h->st, s);
+      EpiArgs e6 = epi0();
+      e6.out1 = h->z;
+      launch_trmv(false, EPR_RAW, h->Mt, h->T, q, h->r2, h->part_tr, h->cnt_tr, e6, h->st, s);
+      EpiArgs e7 = epi0();
+      e7.y = h->y; e7.yt = h->yt; e7.dy = h->dy; e7.w = h->w; e7.in1 = h->v0;
+      launch_trmv(true, EPR_FAT_Y, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, e7, h->st, s);
+    }
+    // x = c + A^T (d - y) ; x~ = c - x ; dual residual
+    EpiArgs e8 = epi0();
+    e8.x = h->x; e8.xt = h->xt; e8.cx = h->cx; e8.mu = h->mu; e8.E = h->E; e8.res_part = h->dual_part;
+    launch_gemv_t(2, false, EPT_FAT_X, h->A, h->lda, m, n, h->w, h->nu, g, h->part_t, h->cnt_t, e8, h->st, s);
+  }
+}
+
+void enqueue_iteration(pogs_handle* h, int refine, cudaStream_t s, unsigned long long cond, int use_cond) {
+  launch_prox_step((int)h->n, (int)h->m, h->x, h->xt, h->xh, h->cx, h->mu, h->y, h->yt, h->yh, h->dy, h->nu,
+                   fn_g(h), fn_f(h), h->st, h->cfg, h->prox_part, h->nprox, s);
+  enqueue_projection(h, refine, s);
+  launch_check(h->st, h->cfg, h->prox_part, h->nprox, h->pri_part, h->geom.n_nrowblk, h->dual_part,
+               h->geom.t_ncolblk, cond, use_cond, s);
+}
+
+int build_graph(pogs_handle* h, int refine, int mode) {
+  if (h->gexec && h->graph_refine == refine && h->graph_mode == mode) return 0;
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  if (mode == 0) {
+    cudaGraphConditionalHandle ch;
+    CK(cudaGraphConditionalHandleCreate(&ch, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = ch;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    enqueue_iteration(h, refine, h->cap, (unsigned long long)ch, 1);
+    cudaGraph_t captured = nullptr;
+    CK(cudaStreamEndCapture(h->cap, &captured));
+  } else {
+    CK(cudaStreamBeginCaptureToGraph(h->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    enqueue_iteration(h, refine, h->cap, 0ull, 0);
+    cudaGraph_t captured = nullptr;
+    CK(cudaStreamEndCapture(h->cap, &captured));
+  }
+  CK(cudaGraphInstantiate(&h->gexec, g, 0));
+  cudaGraphDestroy(g);
+  h->graph_refine = refine;
+  h->graph_mode = mode;
+  return 0;
+}
+
+int validate_params(const pogs_params* p) {
+  if (!p) return POGS_ERR_ARG;
+  if (!(p->abs_tol >= 0) || !(p->rel_tol >= 0) || p->max_iter < 1 || !(p->rho0 > 0) || !(p->alpha > 0) ||
+      !(p->alpha < 2) || !(p->delta >= 1) || !(p->tau > 0) || p->sk_sweeps < 0 || p->refine_steps < 0 ||
+      p->refine_steps > 1 || p->gram_prec < POGS_GRAM_BF16 || p->gram_prec > POGS_GRAM_FP32 ||
+      p->loop_mode < 0 || p->loop_mode > 1)
+    return POGS_ERR_ARG;
+  return 0;
+}
+
+int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order) {
+  const int64_t m = h->m, n = h->n, q = h->q;
+  cudaStream_t s = h->stream;
+  Scratch scr;
+  double tmark = now_ms();
+  auto phase = [&](const char* name) {
+    if (h->sp.verbose <= 0) return;
+    cudaStreamSynchronize(s);
+    const double t = now_ms();
+    fprintf(stderr, "pogs setup %-10s %9.3f ms\n", name, t - tmark);
+    tmark = t;
+  };
+  // ---- ingest -------------------------------------------------------------------------
+  TRY(dalloc(h, &h->A, (size_t)(m * h->lda)));
+  int* err = &h->st->err;
+  const bool colmajor = (order == 'C' || order == 'c');
+  if (is_device_ptr(A)) {
+    launch_copy_in(A, m, n, lds, colmajor, h->A, h->lda, err, s);
+  } else {
+    const int64_t rows = colmajor ? n : m, cols = colmajor ? m : n;
+    if (!colmajor && lds == n) {
+      // contiguous host rows straight into the padded layout
+      CK(cudaMemcpy2DAsync(h->A, h->lda * sizeof(float), A, lds * sizeof(float), n * sizeof(float), m,
+                           cudaMemcpyHostToDevice, s));
+      launch_copy_in(h->A, m, n, h->lda, false, h->A, h->lda, err, s);
+    } else {
+      float* stage = nullptr;
+      TRY(scr.get(&stage, (size_t)(rows * lds), s));
+      (void)cols;
+      CK(cudaMemcpyAsync(stage, A, (size_t)(rows * lds) * sizeof(float), cudaMemcpyHostToDevice, s));
+      launch_copy_in(stage, m, n, lds, colmajor, h->A, h->lda, err, s);
+    }
+  }
+  CK(cudaGetLastError());
+  phase("ingest");
+  {
+    // a non-finite matrix ends setup here (one stream sync; nothing after depends on it)
+    int err_host = 0;
+    CK(cudaMemcpyAsync(&err_host, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (err_host != 0) return err_host;
+  }
+  // ---- Algorithm 2 + rescale ----------------------------------------------------------
+  float *dvec = nullptr, *evec = nullptr;
+  TRY(scr.get(&dvec, (size_t)h->mv, s));
+  TRY(scr.get(&evec, (size_t)h->nv, s));
+  launch_fill(evec, n, 1.0f, s);
+  launch_fill(dvec, m, 1.0f, s);
+  const double gamma = h->sp.gamma > 0 ? h->sp.gamma : (double)(m + n) * sqrt(1.1920928955078125e-07);
+  const int sweeps = h->sp.equil ? h->sp.sk_sweeps : 0;
+  for (int it = 0; it < sweeps; ++it) {
+    EpiArgs er = epi0();
+    er.sk_vec = dvec; er.sk_num = (float)n; er.sk_reg = (float)(gamma / (double)m);
+    launch_gemv_n(1, true, EPN_SK_ROW, h->A, h->lda, (int)m, (int)n, evec, nullptr, h->geom, h->part_n, h->cnt_n,
+                  er, nullptr, s);
+    EpiArgs ec = epi0();
+    ec.sk_vec = evec; ec.sk_num = (float)m; ec.sk_reg = (float)(gamma / (double)n); ec.res_part = h->dual_part;
+    launch_gemv_t(1, true, EPT_SK_COL, h->A, h->lda, (int)m, (int)n, dvec, nullptr, h->geom, h->part_t, h->cnt_t,
+                  ec, nullptr, s);
+  }
+  if (sweeps == 0) {
+    // D = E = I: only the Frobenius norm is needed (sk_num < 0 keeps e = 1)
+    EpiArgs ec = epi0();
+    ec.sk_vec = evec; ec.sk_num = -1.0f; ec.res_part = h->dual_part;
+    launch_gemv_t(1, true, EPT_SK_COL, h->A, h->lda, (int)m, (int)n, dvec, nullptr, h->geom, h->part_t, h->cnt_t,
+                  ec, nullptr, s);
+  }
+  launch_sk_finish(dvec, evec, m, n, h->dual_part, h->geom.t_ncolblk, q, h->D, h->E, s);
+  launch_scale(h->A, h->lda, m, n, h->D, h->E, s);
+  CK(cudaGetLastError());
+  phase("equil");
+  // ---- Gram -----------------------------------------------------------------------------
+  float* G = nullptr;
+  TRY(scr.get(&G, (size_t)(q * q), s));
+  int used = -1;
+  if (h->sp.gram_prec != POGS_GRAM_FP32) {
+    size_t need = 0;
+    int rc = gram_tensor(h->sp.gram_prec, h->A, h->lda, m, n, h->tall, G, q, nullptr, 0, &need, err, s);
+    if (rc == 0 && need > 0) {
+      void* ws = nullptr;
+      char* wsc = nullptr;
+      TRY(scr.get(&wsc, need, s));
+      ws = wsc;
+      rc = gram_tensor(h->sp.gram_prec, h->A, h->lda, m, n, h->tall, G, q, ws, need, &need, err, s);
+      if (rc == 0) used = h->sp.gram_prec;
+    }
+  }
+  if (used < 0) {
+    if (h->tall) gemm_f32(true, false, q, q, m, 1.0f, h->A, h->lda, h->A, h->lda, 0.0f, G, q, true, s);
+    else gemm_f32(false, true, q, q, n, 1.0f, h->A, h->lda, h->A, h->lda, 0.0f, G, q, true, s);
+    used = POGS_GRAM_FP32;
+  }
+  h->gram_used = used;
+  CK(cudaGetLastError());
+  phase("gram");
+  // ---- FP64 Cholesky of I + G -------------------------------------------------------------
+  double* H = nullptr;
+  TRY(scr.get(&H, (size_t)(q * q), s));
+  launch_gram_to_f64(G, q, q, H, q, s);
+  double* work = nullptr;
+  TRY(scr.get(&work, 64 * 64, s));
+  chol_f64(H, q, q, work, err, s);
+  CK(cudaGetLastError());
+  phase("cholesky");
+  // ---- M = L^{-1} (FP32), packed tiles --------------------------------------------------
+  float *Lf = nullptr, *Md = nullptr, *wk = nullptr;
+  TRY(scr.get(&Md, (size_t)(q * q), s));
+  launch_leaf_inverse(H, q, q, Md, q, s);
+  Lf = G;   // G is no longer needed: reuse its storage for the FP32 factor
+  launch_l_to_f32(H, q, q, Lf, q, s);
+  TRY(scr.get(&wk, (size_t)(q * (q / 2 + kTile)), s));
+  tri_inverse_f32(Lf, q, q, Md, q, wk, s);
+  TRY(dalloc(h, &h->Mt, (size_t)h->T * (h->T + 1) / 2 * kTile * kTile));
+  launch_pack_tiles(Md, q, q, h->T, h->Mt, s);
+  CK(cudaGetLastError());
+  phase("inverse");
+  CK(cudaStreamSynchronize(s));
+  return 0;
+}
+
+int alloc_state(pogs_handle* h) {
+  const size_t nv = (size_t)h->nv, mv = (size_t)h->mv;
+  float** nvecs[] = {&h->x, &h->xt, &h->xh, &h->cx, &h->mu, &h->ox, &h->omu, &h->tn, &h->ga, &h->gb, &h->gc, &h->gd, &h->ge};
+  for (auto p : nvecs) TRY(dalloc(h, p, nv));
+  float** mvecs[] = {&h->y, &h->yt, &h->yh, &h->dy, &h->nu, &h->w, &h->oy, &h->onu, &h->fa, &h->fb, &h->fc, &h->fd, &h->fe};
+  for (auto p : mvecs) TRY(dalloc(h, p, mv));
+  // projection work vectors hold q-, m- or n-length data (tall refinement writes A x0 into v0):
+  // max(nv, mv) covers m, lda and T*128 in both orientations
+  const size_t qv = nv > mv ? nv : mv;
+  float** qvecs[] = {&h->r, &h->z, &h->x0, &h->v0, &h->r2};
+  for (auto p : qvecs) TRY(dalloc(h, p, qv));
+  const size_t kmax = nv > mv ? nv : mv;
+  float** rvecs[] = {&h->ra, &h->rb, &h->rc, &h->rd, &h->re};
+  for (auto p : rvecs) TRY(dalloc(h, p, kmax));
+  TRY(dalloc(h, &h->rh, kmax));
+  TRY(dalloc(h, &h->fh, mv));
+  TRY(dalloc(h, &h->gh, nv));
+  TRY(dalloc(h, &h->D, mv));
+  TRY(dalloc(h, &h->E, nv));
+  const GemvGeom& g = h->geom;
+  TRY(dalloc(h, &h->part_t, (size_t)g.t_nsplit * 2 * h->lda));
+  TRY(dalloc(h, &h->cnt_t, (size_t)g.t_ncolblk));
+  TRY(dalloc(h, &h->part_n, (size_t)g.n_ncolsplit * 2 * h->m));
+  TRY(dalloc(h, &h->cnt_n, (size_t)g.n_nrowblk));
+  TRY(dalloc(h, &h->part_tr, (size_t)h->T * (h->T + 1) / 2 * kTile));
+  TRY(dalloc(h, &h->cnt_tr, (size_t)h->T));
+  TRY(dalloc(h, &h->prox_part, (size_t)h->nprox * 6));
+  TRY(dalloc(h, &h->pri_part, (size_t)g.n_nrowblk * 2));
+  TRY(dalloc(h, &h->dual_part, (size_t)g.t_ncolblk * 2));
+  TRY(dalloc(h, &h->st, 1));
+  TRY(dalloc(h, &h->cfg, 1));
+  void* pin = nullptr;
+  CK(cudaMallocHost(&pin, sizeof(DevState) + sizeof(DevCfg)));
+  h->st_host = static_cast<DevState*>(pin);
+  h->cfg_host = reinterpret_cast<DevCfg*>(static_cast<char*>(pin) + sizeof(DevState));
+  return 0;
+}
+
+void release(pogs_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  delete h;
+}
+
+// Copy a host or device source array into a device array (or return the device pointer).
+template <class T>
+int stage_in(const T* src, T* staging, int64_t k, cudaStream_t s, const T** out) {
+  if (!src) {
+    *out = nullptr;
+    return 0;
+  }
+  if (is_device_ptr(src)) {
+    *out = src;
+    return 0;
+  }
+  CK(cudaMemcpyAsync(staging, src, (size_t)k * sizeof(T), cudaMemcpyHostToDevice, s));
+  *out = staging;
+  return 0;
+}
+
+int upload_fn(pogs_handle* h, const pogs_fn* fn, int64_t k, int is_f) {
+  cudaStream_t s = h->stream;
+  if (!fn || !fn->h) return POGS_ERR_ARG;
+  FnDev raw{};
+  TRY(stage_in(fn->h, h->rh, k, s, &raw.h));
+  TRY(stage_in(fn->a, h->ra, k, s, &raw.a));
+  TRY(stage_in(fn->b, h->rb, k, s, &raw.b));
+  TRY(stage_in(fn->c, h->rc, k, s, &raw.c));
+  TRY(stage_in(fn->d, h->rd, k, s, &raw.d));
+  TRY(stage_in(fn->e, h->re, k, s, &raw.e));
+  if (is_f) launch_fold(raw, k, h->D, 1, h->fh, h->fa, h->fb, h->fc, h->fd, h->fe, &h->st->err, s);
+  else launch_fold(raw, k, h->E, 0, h->gh, h->ga, h->gb, h->gc, h->gd, h->ge, &h->st->err, s);
+  CK(cudaGetLastError());
+  return 0;
+}
+
+int reset_state(pogs_handle* h, const pogs_params* p) {
+  cudaStream_t s = h->stream;
+  // serialise against the previous use of the pinned staging
+  CK(cudaStreamSynchronize(s));
+  DevState init;
+  memset(&init, 0, sizeof(init));
+  init.rho = p->rho0;
+  init.pend = 1.0;
+  init.status = POGS_MAX_ITER;
+  *h->st_host = init;
+  DevCfg c;
+  memset(&c, 0, sizeof(c));
+  c.abs_tol = p->abs_tol; c.rel_tol = p->rel_tol; c.alpha = p->alpha; c.delta = p->delta; c.tau = p->tau;
+  c.max_iter = p->max_iter; c.gap_stop = p->gap_stop; c.adaptive = p->adaptive_rho;
+  *h->cfg_host = c;
+  CK(cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->cfg, h->cfg_host, sizeof(DevCfg), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(h->x, 0, h->nv * sizeof(float), s));
+  CK(cudaMemsetAsync(h->xt, 0, h->nv * sizeof(float), s));
+  CK(cudaMemsetAsync(h->y, 0, h->mv * sizeof(float), s));
+  CK(cudaMemsetAsync(h->yt, 0, h->mv * sizeof(float), s));
+  return 0;
+}
+
+int copy_out(const float* dsrc, float* dst, int64_t k, cudaStream_t s) {
+  if (!dst) return 0;
+  CK(cudaMemcpyAsync(dst, dsrc, (size_t)k * sizeof(float), is_device_ptr(dst) ? cudaMemcpyDeviceToDevice
+                                                                                  : cudaMemcpyDeviceToHost, s));
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pogs_default_params(pogs_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->abs_tol = 1e-4;
+  p->rel_tol = 1e-3;
+  p->max_iter = 10000;
+  p->rho0 = 1.0;
+  p->alpha = 1.7;
+  p->delta = 1.05;
+  p->tau = 0.8;
+  p->sk_sweeps = 10;
+  p->gamma = 0.0;
+  p->gram_prec = POGS_GRAM_BF16X3;
+  p->refine_steps = 0;
+  p->gap_stop = 1;
+  p->adaptive_rho = 1;
+  p->equil = 1;
+  p->verbose = 0;
+  p->loop_mode = 0;
+  p->check_every = 10;
+}
+
+int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order, const pogs_params* p, void* stream,
+               pogs_handle** out) {
+  if (!out) return POGS_ERR_ARG;
+  *out = nullptr;
+  if (!A || m < 1 || n < 1 || m > (1ll << 31) - 1 || n > (1ll << 31) - 1) return POGS_ERR_ARG;
+  const bool colmajor = (order == 'C' || order == 'c');
+  if (!(colmajor || order == 'R' || order == 'r')) return POGS_ERR_ARG;
+  if ((!colmajor && lda < n) || (colmajor && lda < m)) return POGS_ERR_ARG;
+  pogs_params def;
+  pogs_default_params(&def);
+  if (!p) p = &def;
+  if (validate_params(p) != 0) return POGS_ERR_ARG;
+  const double t0 = now_ms();
+  pogs_handle* h = new (std::nothrow) pogs_handle();
+  if (!h) return POGS_ERR_OOM;
+  h->m = m;
+  h->n = n;
+  h->tall = m >= n;
+  h->q = h->tall ? n : m;
+  h->lda = round_up(n, kLdaAlign);
+  h->T = (int)cdiv(h->q, kTile);
+  h->nv = round_up(std::max<int64_t>(h->lda, h->tall ? (int64_t)h->T * kTile : 0), kTile);
+  h->mv = round_up(std::max<int64_t>(m, h->tall ? 0 : (int64_t)h->T * kTile), kTile);
+  h->sp = *p;
+  h->stream = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return POGS_ERR_CUDA;
+  }
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return POGS_ERR_CUDA;
+  }
+  h->geom = choose_geometry(m, n, h->lda, h->num_sms);
+  h->nprox = (int)std::min<int64_t>(cdiv(m + n, 256), (int64_t)h->num_sms * 4);
+  int rc = alloc_state(h);
+  if (rc == 0) rc = setup_impl(h, A, lda, order);
+  if (rc == 0) {
+    if (cudaMemcpy(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess) rc = POGS_ERR_CUDA;
+    else if (h->st_host->err != 0) rc = h->st_host->err;
+  }
+  if (rc != 0) {
+    release(h);
+    return rc;
+  }
+  h->setup_ms = now_ms() - t0;
+  *out = h;
+  return 0;
+}
+
+int pogs_solve(pogs_handle* h, const pogs_fn* f, const pogs_fn* g, const pogs_params* p, float* x, float* y,
+               float* mu, float* nu, pogs_info* info) {
+  if (!h || !f || !g) return POGS_ERR_ARG;
+  if (!p) p = &h->sp;
+  if (validate_params(p) != 0) return POGS_ERR_ARG;
+  const double t0 = now_ms();
+  cudaStream_t s = h->stream;
+  TRY(reset_state(h, p));
+  TRY(upload_fn(h, f, h->m, 1));
+  TRY(upload_fn(h, g, h->n, 0));
+  const int refine = p->refine_steps;
+  TRY(build_graph(h, refine, p->loop_mode));
+  if (p->loop_mode == 0) {
+    CK(cudaGraphLaunch(h->gexec, s));
+  } else {
+    const int every = p->check_every > 0 ? p->check_every : 10;
+    int launched = 0;
+    while (launched < p->max_iter) {
+      for (int i = 0; i < every && launched < p->max_iter; ++i, ++launched) CK(cudaGraphLaunch(h->gexec, s));
+      CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (h->st_host->done) break;
+    }
+  }
+  launch_unscale((int)h->n, (int)h->m, h->xh, h->mu, h->yh, h->nu, h->D, h->E, x ? h->ox : nullptr,
+                 mu ? h->omu : nullptr, y ? h->oy : nullptr, nu ? h->onu : nullptr, s);
+  CK(cudaGetLastError());
+  TRY(copy_out(h->ox, x, h->n, s));
+  TRY(copy_out(h->omu, mu, h->n, s));
+  TRY(copy_out(h->oy, y, h->m, s));
+  TRY(copy_out(h->onu, nu, h->m, s));
+  CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const DevState& st = *h->st_host;
+  int status = st.status;
+  if (st.err != 0) status = st.err;
+  if (info) {
+    info->status = status;
+    info->iters = st.k;
+    info->rho = st.rho;
+    info->r_pri = st.r_pri;
+    info->r_dual = st.r_dual;
+    info->eps_pri = st.eps_pri;
+    info->eps_dual = st.eps_dual;
+    info->gap = st.gap;
+    info->obj = st.obj;
+    info->r_pri_unscaled = st.r_pri_u;
+    info->r_dual_unscaled = st.r_dual_u;
+    info->setup_ms = h->setup_ms;
+    info->solve_ms = now_ms() - t0;
+  }
+  return status;
+}
+
+void pogs_free(pogs_handle* h) { release(h); }
+
+int pogs_prox_eval(const pogs_fn* fn, int64_t k, const float* v, const float* rho_vec, float rho, float* out,
+                   void* stream) {
+  if (!fn || !fn->h || !v || !out || k < 0) return POGS_ERR_ARG;
+  if (k == 0) return 0;
+  FnDev d{fn->h, fn->a, fn->b, fn->c, fn->d, fn->e};
+  // NULL parameter arrays take their defaults through a temporary filled array
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* tmp = nullptr;
+  const bool need = !fn->a || !fn->b || !fn->c || !fn->d || !fn->e;
+  if (need) {
+    if (cudaMalloc(&tmp, (size_t)k * 2 * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return POGS_ERR_OOM;
+    }
+    launch_fill(tmp, k, 1.0f, s);
+    launch_fill(tmp + k, k, 0.0f, s);
+    if (!d.a) d.a = tmp;
+    if (!d.c) d.c = tmp;
+    if (!d.b) d.b = tmp + k;
+    if (!d.d) d.d = tmp + k;
+    if (!d.e) d.e = tmp + k;
+  }
+  launch_prox_eval(d, k, v, rho_vec, rho, out, s);
+  cudaError_t e = cudaGetLastError();
+  if (tmp) {
+    cudaStreamSynchronize(s);
+    cudaFree(tmp);
+  }
+  return e == cudaSuccess ? 0 : POGS_ERR_CUDA;
+}
+
+int pogs_get_equil(const pogs_handle* h, float* D, float* E) {
+  if (!h) return POGS_ERR_ARG;
+  TRY(copy_out(h->D, D, h->m, h->stream));
+  TRY(copy_out(h->E, E, h->n, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return 0;
+}
+
+int pogs_get_ahat(const pogs_handle* h, float* Ahat) {
+  if (!h || !Ahat) return POGS_ERR_ARG;
+  CK(cudaMemcpy2DAsync(Ahat, h->n * sizeof(float), h->A, h->lda * sizeof(float), h->n * sizeof(float), h->m,
+                       is_device_ptr(Ahat) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return 0;
+}
+
+int pogs_project(pogs_handle* h, const float* c, const float* d, float* x, float* y, const pogs_params* p) {
+  if (!h || !c || !d) return POGS_ERR_ARG;
+  if (!p) p = &h->sp;
+  if (validate_params(p) != 0) return POGS_ERR_ARG;
+  cudaStream_t s = h->stream;
+  TRY(reset_state(h, p));
+  CK(cudaMemcpyAsync(h->cx, c, h->n * sizeof(float), is_device_ptr(c) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->dy, d, h->m * sizeof(float), is_device_ptr(d) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(h->xh, 0, h->nv * sizeof(float), s));
+  CK(cudaMemsetAsync(h->mu, 0, h->nv * sizeof(float), s));
+  CK(cudaMemsetAsync(h->yh, 0, h->mv * sizeof(float), s));
+  CK(cudaMemsetAsync(h->nu, 0, h->mv * sizeof(float), s));
+  enqueue_projection(h, p->refine_steps, s);
+  CK(cudaGetLastError());
+  TRY(copy_out(h->x, x, h->n, s));
+  TRY(copy_out(h->y, y, h->m, s));
+  CK(cudaStreamSynchronize(s));
+  return 0;
+}
+
+}  // extern "C"

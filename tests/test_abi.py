@@ -1,0 +1,70 @@
+"""The C-ABI library loads and exports every entry point include/pogs.h declares (no GPU
+needed: nothing is called except pogs_default_params, which touches no device)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def _declared():
+    names = set()
+    for hp in HEADERS:
+        src = open(hp).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:int|void|const char\s*\*|size_t|int64_t)\s+\**\s*(pogs_\w+)\s*\(", src, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("pogs_setup", "pogs_solve", "pogs_free", "pogs_default_params", "pogs_project",
+                 "pogs_prox_eval"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_1503_08366_b300 as P
+    lib = ctypes.CDLL(P.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_params_match_paper():
+    """Section 5: alpha = 1.7, (delta, tau) = (1.05, 0.8); Section 6.1: max_iter 1e4."""
+    import paper_1503_08366_b300 as P
+    p = P.pogs_default_params()
+    assert (p.alpha, p.delta, p.tau, p.max_iter) == (1.7, 1.05, 0.8, 10000)
+    assert (p.abs_tol, p.rel_tol, p.rho0) == (1e-4, 1e-3, 1.0)
+
+
+def test_enum_values_match_workloads_and_header():
+    import paper_1503_08366_b300 as P
+    import workloads as W
+    assert P.H == W.H
+    hdr = open(os.path.join(ROOT, "include", "pogs.h")).read()
+    for name, code in W.H.items():
+        assert re.search(rf"POGS_{name}\s*=\s*{code}\b", hdr), name
+
+
+def test_free_null_is_noop():
+    import paper_1503_08366_b300 as P
+    P.lib.pogs_free(None)
+
+
+def test_setup_rejects_bad_arguments_without_device_work():
+    """Argument checks happen before any CUDA call (ARG = -1)."""
+    import paper_1503_08366_b300 as P
+    h = ctypes.c_void_p()
+    assert P.lib.pogs_setup(None, 10, 5, 5, b"R", None, None, ctypes.byref(h)) == -1
+    buf = (ctypes.c_float * 50)()
+    assert P.lib.pogs_setup(buf, 10, 5, 4, b"R", None, None, ctypes.byref(h)) == -1   # lda < n
+    assert P.lib.pogs_setup(buf, 10, 5, 5, b"X", None, None, ctypes.byref(h)) == -1   # bad order
+    assert P.lib.pogs_setup(buf, 0, 5, 5, b"R", None, None, ctypes.byref(h)) == -1    # empty
+    p = P.pogs_default_params(alpha=2.5)
+    assert P.lib.pogs_setup(buf, 10, 5, 5, b"R", ctypes.byref(p), None, ctypes.byref(h)) == -1

@@ -1,0 +1,217 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle, on the same
+seeded inputs.  Sizes span several 128-tiles, several GEMV slabs/chunks and ragged tails.
+
+Tolerances (FP32 path vs FP64 oracle):
+  * prox: |got - ref| <= 2e-5 (1 + |ref| + |b/a| + |v| + |d/rho|): the FP32 formula rounds the
+    intermediate a(v rho - d)/(e + rho) - b and (z + b)/a, each of magnitude up to the bracket;
+    a few ulps (2^-23 ~ 1.2e-7) of it, times the condition of the inner prox (<= 1), plus the
+    logistic Newton stop (1e-7 relative).
+  * equilibration: 1e-5 relative (10 sweeps of FP32 row/column sums of <= 4096 terms).
+  * projection: 1e-5 relative in x and y (the stated spec bound for the FP32 path).
+  * solve: |obj - p*| <= 1e-3 max(1, |p*|), p* from the oracle at eps_rel = 1e-7; both residuals
+    below their tolerances (eps_abs = 1e-4, eps_rel = 1e-3).
+  * trajectory (adaptive rho off, 50 iterations, no stopping): 1e-4 relative.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import admm as OA
+from oracle import equil as OE
+from oracle import project as OPJ
+from oracle import prox as OP
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1503_08366_b300 as P
+    return P
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("code", OP.ALL_H, ids=[W.H_NAMES[c] for c in OP.ALL_H])
+def test_prox_eval_matches_oracle(P, code):
+    import torch
+    rng = np.random.default_rng(300 + code)
+    k = 5000
+    a = (rng.uniform(0.3, 2.5, k) * rng.choice([-1.0, 1.0], k)).astype(np.float32)
+    b = rng.normal(0, 1.5, k).astype(np.float32)
+    c = rng.uniform(0.2, 3.0, k).astype(np.float32)
+    c[::7] = 0
+    d = rng.normal(0, 1.0, k).astype(np.float32)
+    e = rng.uniform(0, 2.0, k).astype(np.float32)
+    e[::3] = 0
+    v = rng.normal(0, 3.0, k).astype(np.float32)
+    rho = np.exp(rng.uniform(np.log(0.02), np.log(50), k)).astype(np.float32)
+    fn = W.FnParams(np.full(k, code, np.uint8), a, b, c, d, e)
+    dev = lambda x: torch.from_numpy(x).cuda()
+    fd = W.FnParams(dev(fn.h), dev(a), dev(b), dev(c), dev(d), dev(e))
+    got = P.pogs_prox_eval(fd, dev(v), rho_vec=dev(rho)).cpu().numpy().astype(np.float64)
+    ref = OP.prox_f(fn, v.astype(np.float64), rho.astype(np.float64))
+    scale = 1 + np.abs(ref) + np.abs(b / a) + np.abs(v) + np.abs(d / rho)
+    err = np.abs(got - ref) / scale
+    assert err.max() <= 2e-5, (err.max(), int(err.argmax()))
+
+
+# ---------------------------------------------------------------------------------------------
+SHAPES = [(700, 300), (300, 700), (1100, 1030), (2500, 130), (130, 2500), (257, 257)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_equilibration_matches_oracle(P, shape):
+    m, n = shape
+    prob = W.lasso(m, n, seed=7)
+    prm = P.pogs_default_params(gram_prec="FP32")
+    s = P.Solver(prob.A, prm)
+    D, E = s.equil()
+    eq = OE.equilibrate(prob.A.astype(np.float64), prm.sk_sweeps, OE.default_gamma(m, n))
+    assert _rel(D, eq.D) < 1e-5 and _rel(E, eq.E) < 1e-5
+    Ah = s.ahat()
+    assert _rel(Ah, eq.Ahat) < 2e-5
+    s.close()
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("refine", [0, 1])
+def test_projection_matches_oracle(P, shape, refine):
+    m, n = shape
+    prob = W.nnls(m, n, seed=11)
+    prm = P.pogs_default_params(gram_prec="FP32", refine_steps=refine)
+    s = P.Solver(prob.A, prm)
+    Ah = s.ahat().astype(np.float64)          # the GPU's own FP32 A^, upcast
+    proj = OPJ.Projector(Ah)
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        c = rng.normal(size=n).astype(np.float32)
+        d = rng.normal(size=m).astype(np.float32)
+        x, y = s.project(c, d, prm)
+        xr, yr = proj(c.astype(np.float64), d.astype(np.float64))
+        assert _rel(x, xr) < 1e-5 and _rel(y, yr) < 1e-5, (_rel(x, xr), _rel(y, yr))
+    s.close()
+
+
+# ---------------------------------------------------------------------------------------------
+def _tight(prob):
+    return OA.solve(prob.A, prob.f, prob.g, OA.Params(abs_tol=1e-9, rel_tol=1e-7, max_iter=100000))
+
+
+CASES = [("lasso", (200, 100)), ("huber", (600, 200)), ("svm", (500, 150)), ("nnls", (600, 250)),
+         ("logistic", (500, 120)), ("lasso", (150, 600)), ("logistic", (200, 700)), ("nnls", (1300, 1300))]
+
+
+@pytest.mark.parametrize("cls,shape", CASES)
+def test_solve_matches_oracle_objective(P, cls, shape):
+    prob = W.lasso_small(0) if (cls, shape) == ("lasso", (200, 100)) else W.CLASSES[cls](*shape, seed=21)
+    prm = P.pogs_default_params(gram_prec="FP32", max_iter=5000)
+    with P.Solver(prob.A, prm) as s:
+        info, x, y, mu, nu = s.solve(prob.f, prob.g)
+    assert info.status == 0, info.as_dict()
+    assert info.r_pri < info.eps_pri and info.r_dual < info.eps_dual
+    ref = _tight(prob)
+    assert abs(info.obj - ref.obj) <= 1e-3 * max(1.0, abs(ref.obj)), (info.obj, ref.obj)
+    # the objective recomputed in FP64 from the returned (unscaled) tuple agrees too
+    obj64 = OA.objective(prob.A, prob.f, prob.g, x.astype(float), y.astype(float), tol=1e-4)
+    assert abs(obj64 - ref.obj) <= 2e-3 * max(1.0, abs(ref.obj))
+
+
+def test_lp_solution_matches_linprog(P):
+    from scipy.optimize import linprog
+    prob = W.lp(120, 60, seed=3)
+    prm = P.pogs_default_params(gram_prec="FP32", max_iter=10000)
+    with P.Solver(prob.A, prm) as s:
+        info, x, y, mu, nu = s.solve(prob.f, prob.g)
+    assert info.status == 0
+    res = linprog(prob.g.d.astype(float), A_ub=prob.A.astype(float), b_ub=prob.f.b.astype(float),
+                  bounds=[(0, None)] * prob.n, method="highs")
+    assert abs(info.obj - res.fun) <= 1e-2 * max(1.0, abs(res.fun)), (info.obj, res.fun)
+
+
+@pytest.mark.parametrize("shape", [(400, 150), (150, 400)])
+def test_trajectory_matches_oracle_fixed_rho(P, shape):
+    """Adaptive rho off, stopping off, 50 iterations: the iterates follow the oracle's."""
+    m, n = shape
+    prob = W.lasso(m, n, seed=4)
+    prm = P.pogs_default_params(gram_prec="FP32", adaptive_rho=0, abs_tol=0.0, rel_tol=0.0, gap_stop=0,
+                                max_iter=50)
+    with P.Solver(prob.A, prm) as s:
+        info, x, y, mu, nu = s.solve(prob.f, prob.g)
+        Ah = s.ahat().astype(np.float64)
+        D, E = s.equil()
+    assert info.status == 1 and info.iters == 50
+    eq = OE.Equilibration(D.astype(np.float64), E.astype(np.float64), Ah)
+    ref = OA.solve(prob.A, prob.f, prob.g, OA.Params(adaptive_rho=False, abs_tol=0, rel_tol=0, gap_stop=False,
+                                                     max_iter=50), eq=eq)
+    for got, want in ((x, ref.x), (y, ref.y), (mu, ref.mu), (nu, ref.nu)):
+        assert _rel(got, want) < 1e-4, _rel(got, want)
+
+
+def test_loop_modes_agree_bitwise(P):
+    prob = W.huber(900, 300, seed=9)
+    outs = []
+    for mode in (0, 1):
+        prm = P.pogs_default_params(gram_prec="FP32", loop_mode=mode, check_every=7)
+        with P.Solver(prob.A, prm) as s:
+            outs.append(s.solve(prob.f, prob.g))
+    (i0, *v0), (i1, *v1) = outs
+    assert i0.iters == i1.iters and i0.obj == i1.obj
+    for a, b in zip(v0, v1):
+        assert np.array_equal(a, b)
+
+
+def test_device_and_host_inputs_agree(P):
+    import torch
+    prob = W.nnls(800, 200, seed=12)
+    prm = P.pogs_default_params(gram_prec="FP32")
+    with P.Solver(prob.A, prm) as s:
+        i_h, x_h, *_ = s.solve(prob.f, prob.g)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    fd = W.FnParams(*(dev(getattr(prob.f, k)) for k in "habcde"))
+    gd = W.FnParams(*(dev(getattr(prob.g, k)) for k in "habcde"))
+    with P.Solver(dev(prob.A), prm) as s:
+        i_d, x_d, *_ = s.solve(fd, gd, device_out=True)
+    assert i_h.iters == i_d.iters
+    assert np.array_equal(x_h, x_d.cpu().numpy())
+
+
+def test_column_major_input(P):
+    prob = W.lasso(500, 220, seed=13)
+    prm = P.pogs_default_params(gram_prec="FP32")
+    with P.Solver(prob.A, prm) as s1, P.Solver(np.asfortranarray(prob.A), prm, order="C") as s2:
+        assert np.array_equal(s1.ahat(), s2.ahat())
+
+
+def test_invalid_function_parameters_are_rejected(P):
+    prob = W.lasso(100, 40, seed=1)
+    prob.f.a[3] = 0.0
+    with P.Solver(prob.A, P.pogs_default_params(gram_prec="FP32")) as s:
+        with pytest.raises(P.PogsError) as ei:
+            s.solve(prob.f, prob.g)
+    assert ei.value.code == -1
+
+
+def test_nonfinite_matrix_is_rejected(P):
+    prob = W.lasso(100, 40, seed=1)
+    prob.A[5, 7] = np.nan
+    with pytest.raises(P.PogsError) as ei:
+        P.Solver(prob.A, P.pogs_default_params(gram_prec="FP32"))
+    assert ei.value.code == -3
+
+
+def test_degenerate_sizes(P):
+    """1 x n, m x 1 and a single-tile problem all solve."""
+    for shape in ((1, 5), (6, 1), (1, 1), (128, 128)):
+        prob = W.nnls(*shape, seed=2)
+        with P.Solver(prob.A, P.pogs_default_params(gram_prec="FP32", max_iter=3000)) as s:
+            info, x, *_ = s.solve(prob.f, prob.g)
+        assert info.status in (0, 1) and np.all(np.isfinite(x))
