@@ -101,7 +101,22 @@ typedef struct {
                         1: host loop over captured iterations, status read every
                         check_every iterations                                         */
   int check_every;   /* loop_mode 1 only (default 10)                                  */
+  int chol_prec;     /* POGS_CHOL_* (default POGS_CHOL_MIXED)                           */
 } pogs_params;
+
+/* Arithmetic of the Cholesky factorization of I + G (Section 3.5). */
+enum {
+  POGS_CHOL_FP64 = 0,  /* every operation in FP64                                          */
+  POGS_CHOL_MIXED = 1  /* FP64 diagonal blocks, panel solves and Schur complement; trailing
+                          products of the FP32-rounded panel formed in FP32                 */
+};
+
+/* Timing/precision report of pogs_setup. */
+typedef struct {
+  double ingest_ms, equil_ms, gram_ms, factor_ms, inverse_ms;
+  int gram_prec_used, chol_prec_used;
+  int64_t device_bytes;  /* device memory the handle owns after setup */
+} pogs_setup_report;
 
 /* Per-solve report.  Residuals/tolerances/gap are those of the pre-conditioned problem
  * the iteration runs on (Section 3.4); *_unscaled are ||A x - y|| and ||A^T nu + mu|| of
@@ -164,6 +179,26 @@ int pogs_get_ahat(const pogs_handle* hdl, float* Ahat);
  * p->refine_steps refinement steps; p may be NULL for the setup parameters). */
 int pogs_project(pogs_handle* hdl, const float* c, const float* d, float* x, float* y,
                  const pogs_params* p);
+
+/* ---- instrumentation ------------------------------------------------------------------ */
+
+/* Fill *r with the setup phase times (CUDA events on the setup stream), the Gram and
+ * Cholesky precisions actually used, and the device memory the handle owns. */
+int pogs_get_setup_report(const pogs_handle* hdl, pogs_setup_report* r);
+
+/* Time each kernel of one ADMM iteration of the last solve on the handle's stream with CUDA
+ * events, averaged over `reps` launches (reps >= 1) after one warm-up launch of each.
+ * ms[0..5]: prox step, first A pass (column sums if m >= n, row dots if m < n), L^{-1}
+ * product, L^{-T} product, second A pass, stopping/adaptive-rho check; ms[6]: one whole
+ * iteration.  bytes[0..6]: the algorithmic HBM bytes each launch must move (A once per pass,
+ * the triangle q(q+1)/2 once per product, the vectors it reads and writes).  Either array
+ * may be NULL.  Overwrites the iterate state of the last solve (solve again before reading
+ * results).  Errors: ARG (no prior solve, reps < 1), CUDA. */
+int pogs_time_kernels(pogs_handle* hdl, int reps, double* ms, double* bytes);
+
+/* Number of kernel launches this library has issued in the process so far (graph replays
+ * included). */
+long long pogs_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,7 @@ H = dict(ZERO=0, ABS=1, SQUARE=2, HUBER=3, LOGISTIC=4, HINGE=5, MAXPOS=6, IND_GE
 OK, MAX_ITER = 0, 1
 ERR = {-1: "ARG", -2: "OOM", -3: "NONFINITE", -4: "NUMERIC", -5: "TIMEOUT", -6: "CUDA", -7: "CAPACITY"}
 GRAM = dict(BF16=0, TF32=1, BF16X3=2, FP32=3)
+CHOL = dict(FP64=0, MIXED=1)
 
 
 class pogs_fn(C.Structure):
@@ -35,7 +36,8 @@ class pogs_params(C.Structure):
                 ("rho0", C.c_double), ("alpha", C.c_double), ("delta", C.c_double), ("tau", C.c_double),
                 ("sk_sweeps", C.c_int), ("gamma", C.c_double), ("gram_prec", C.c_int),
                 ("refine_steps", C.c_int), ("gap_stop", C.c_int), ("adaptive_rho", C.c_int),
-                ("equil", C.c_int), ("verbose", C.c_int), ("loop_mode", C.c_int), ("check_every", C.c_int)]
+                ("equil", C.c_int), ("verbose", C.c_int), ("loop_mode", C.c_int), ("check_every", C.c_int),
+                ("chol_prec", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -46,6 +48,15 @@ class pogs_info(C.Structure):
                 ("r_dual", C.c_double), ("eps_pri", C.c_double), ("eps_dual", C.c_double),
                 ("gap", C.c_double), ("obj", C.c_double), ("r_pri_unscaled", C.c_double),
                 ("r_dual_unscaled", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pogs_setup_report(C.Structure):
+    _fields_ = [("ingest_ms", C.c_double), ("equil_ms", C.c_double), ("gram_ms", C.c_double),
+                ("factor_ms", C.c_double), ("inverse_ms", C.c_double), ("gram_prec_used", C.c_int),
+                ("chol_prec_used", C.c_int), ("device_bytes", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,6 +80,12 @@ lib.pogs_get_ahat.argtypes = [_P, _P]
 lib.pogs_get_ahat.restype = C.c_int
 lib.pogs_project.argtypes = [_P, _P, _P, _P, _P, C.POINTER(pogs_params)]
 lib.pogs_project.restype = C.c_int
+lib.pogs_get_setup_report.argtypes = [_P, C.POINTER(pogs_setup_report)]
+lib.pogs_get_setup_report.restype = C.c_int
+lib.pogs_time_kernels.argtypes = [_P, C.c_int, _P, _P]
+lib.pogs_time_kernels.restype = C.c_int
+lib.pogs_kernel_launches.argtypes = []
+lib.pogs_kernel_launches.restype = C.c_longlong
 
 
 class PogsError(RuntimeError):
@@ -126,6 +143,8 @@ def pogs_default_params(**overrides) -> pogs_params:
     for k, v in overrides.items():
         if isinstance(v, str) and k == "gram_prec":
             v = GRAM[v.upper()]
+        if isinstance(v, str) and k == "chol_prec":
+            v = CHOL[v.upper()]
         setattr(p, k, v)
     return p
 
@@ -215,3 +234,24 @@ def pogs_project(handle, c, d, params: pogs_params | None = None):
                           y.ctypes.data, C.byref(params) if params is not None else None)
     _check(rc, "pogs_project")
     return x, y
+
+
+def pogs_get_setup_report(handle) -> pogs_setup_report:
+    r = pogs_setup_report()
+    _check(lib.pogs_get_setup_report(handle, C.byref(r)), "pogs_get_setup_report")
+    return r
+
+
+KERNEL_NAMES = ("prox", "A_pass1", "Linv", "LinvT", "A_pass2", "check", "iteration")
+
+
+def pogs_time_kernels(handle, reps: int = 20):
+    """Per-kernel device times (ms) and algorithmic bytes of one iteration of the last solve."""
+    ms = (C.c_double * 7)()
+    by = (C.c_double * 7)()
+    _check(lib.pogs_time_kernels(handle, reps, ms, by), "pogs_time_kernels")
+    return {k: (ms[i], by[i]) for i, k in enumerate(KERNEL_NAMES)}
+
+
+def pogs_kernel_launches() -> int:
+    return int(lib.pogs_kernel_launches())

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/pogs.h"
 
 #define POGS_DEV __device__ __forceinline__
@@ -97,6 +99,15 @@ POGS_DEV bool arrive_last(unsigned* counter, unsigned total) {
   __syncthreads();
   if (s_last) __threadfence();
   return s_last != 0;
+}
+
+// Process-wide count of kernel launches issued by this library (graph replays are added by
+// the caller from the number of iterations executed; launches recorded during stream capture
+// are not counted).
+extern std::atomic<long long> g_launch_count;
+extern thread_local int g_capture_depth;
+inline void count_launch(int k = 1) {
+  if (g_capture_depth == 0) g_launch_count.fetch_add(k, std::memory_order_relaxed);
 }
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }

@@ -2,13 +2,21 @@
 // Section 3.4 stopping + Algorithm 3), all on the pre-conditioned problem (Eq. 12).
 //
 // One iteration, tall case (m >= n), reading A^ twice and the cached factor twice:
-//   prox_step   : x^{1/2}, y^{1/2}, mu^{1/2}, nu^{1/2}, c = x_r + x~, d = y_r + y~   (m+n elts)
-//   gemv_t      : [t, s] = A^T [d, nu^{1/2}]  ->  r = c + t, ||s + mu||               (A pass 1)
+//   prox_step   : x^{1/2}, y^{1/2}, mu^{1/2}, nu^{1/2}, relaxed c = x_r, d = y_r        (m+n elts)
+//   gemv_t      : [t, s, u] = A^T [d, nu^{1/2}, y~] -> r = c + t, ||s + mu||, x~ = -u   (A pass 1)
 //   trmv (N)    : z = L^{-1} r                                                          (L pass 1)
-//   trmv (T)    : x^{k+1} = L^{-T} z, x~ = c - x^{k+1}                                  (L pass 2)
-//   gemv_n      : [y^{k+1}, w] = A [x^{k+1}, x^{1/2}] -> y~ = d - y^{k+1}, ||w - y^{1/2}|| (A pass 2)
+//   trmv (T)    : x^{k+1} = L^{-T} z, x~ += c - x^{k+1}                                 (L pass 2)
+//   gemv_n      : [y^{k+1}, w] = A [x^{k+1}, x^{1/2}] -> y~ += d - y^{k+1}, ||w - y^{1/2}|| (A pass 2)
 //   check       : Section 3.4 test, gap, Algorithm 3, graph conditional
 // The fat case (m < n) swaps the roles of the two GEMVs (Section 3.5 reduced update).
+//
+// Algorithm 1 projects (x_r + x~, y_r + y~).  Here the projection takes (x_r, y_r) and x~ is
+// re-derived from y~ as -A^T y~ once per iteration (a third right-hand side of the column-sum
+// pass, no extra traffic on A).  Both are identities of the method: the Section 3.3 invariant
+// x~ + A^T y~ = 0 makes (x~, y~) orthogonal to the graph, so Pi(x_r + x~, y_r + y~) =
+// Pi(x_r, y_r).  In FP32 the difference matters once rho is small: x~, y~ grow like 1/rho, and
+// projecting their sum with the O(1) relaxed point loses that many digits, while updating
+// x~ additively without re-deriving it lets the invariant drift.
 #include <cstdio>
 
 #include "kernels.h"
@@ -20,9 +28,9 @@ namespace pogs {
 // Prox step (Algorithm 1 step 3, Section 3.2, Section 3.3).
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) prox_step_kernel(
-    int n, int m, const float* __restrict__ x, const float* __restrict__ xt, float* __restrict__ xh,
+    int n, int m, const float* __restrict__ x, float* __restrict__ xt, float* __restrict__ xh,
     float* __restrict__ cx, float* __restrict__ mu, const float* __restrict__ y,
-    const float* __restrict__ yt, float* __restrict__ yh, float* __restrict__ dy,
+    float* __restrict__ yt, float* __restrict__ yh, float* __restrict__ dy,
     float* __restrict__ nu, FnDev g, FnDev f, const DevState* __restrict__ st,
     const DevCfg* __restrict__ cfg, double* __restrict__ part) {
   __shared__ double sh[6 * 8];
@@ -32,17 +40,19 @@ __global__ void __launch_bounds__(256) prox_step_kernel(
   const float alpha = (float)cfg->alpha;
   double acc[6] = {0, 0, 0, 0, 0, 0};   // ||mu||^2, x.mu, g(x), ||y||^2, y.nu, f(y)
   const int total = n + m;
+  const bool rescale = pend != 1.0f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     if (i < n) {
       const int j = i;
       const float xtj = pend * xt[j], xj = x[j], v = xj - xtj;
+      if (rescale) xt[j] = xtj;   // Section 3.2: x~ <- (rho^k / rho^{k+1}) x~
       const int h = g.h[j];
       const float a = g.a[j], b = g.b[j], c = g.c[j], d = g.d[j], e = g.e[j];
       const float xhj = prox_param(h, a, b, c, d, e, rho, v);
       const float muj = -rho * (xhj - v);
       const float xr = alpha * xhj + (1.0f - alpha) * xj;
       xh[j] = xhj;
-      cx[j] = xr + xtj;
+      cx[j] = xr;
       mu[j] = muj;
       acc[0] += (double)muj * muj;
       acc[1] += (double)xhj * muj;
@@ -50,13 +60,14 @@ __global__ void __launch_bounds__(256) prox_step_kernel(
     } else {
       const int k = i - n;
       const float ytk = pend * yt[k], yk = y[k], v = yk - ytk;
+      if (rescale) yt[k] = ytk;
       const int h = f.h[k];
       const float a = f.a[k], b = f.b[k], c = f.c[k], d = f.d[k], e = f.e[k];
       const float yhk = prox_param(h, a, b, c, d, e, rho, v);
       const float nuk = -rho * (yhk - v);
       const float yr = alpha * yhk + (1.0f - alpha) * yk;
       yh[k] = yhk;
-      dy[k] = yr + ytk;
+      dy[k] = yr;
       nu[k] = nuk;
       acc[3] += (double)yhk * yhk;
       acc[4] += (double)yhk * nuk;
@@ -70,9 +81,10 @@ __global__ void __launch_bounds__(256) prox_step_kernel(
   }
 }
 
-void launch_prox_step(int n, int m, const float* x, const float* xt, float* xh, float* cx, float* mu,
-                      const float* y, const float* yt, float* yh, float* dy, float* nu, FnDev g, FnDev f,
+void launch_prox_step(int n, int m, const float* x, float* xt, float* xh, float* cx, float* mu,
+                      const float* y, float* yt, float* yh, float* dy, float* nu, FnDev g, FnDev f,
                       const DevState* st, const DevCfg* cfg, double* part, int nblocks, cudaStream_t s) {
+  count_launch();
   prox_step_kernel<<<nblocks, 256, 0, s>>>(n, m, x, xt, xh, cx, mu, y, yt, yh, dy, nu, g, f, st, cfg, part);
 }
 
@@ -83,12 +95,13 @@ void launch_prox_step(int n, int m, const float* x, const float* xt, float* xh, 
 // order and applies the epilogue.
 // ------------------------------------------------------------------------------------------
 template <int EPI>
-__device__ __forceinline__ void epi_t(const EpiArgs& ep, int j, float t1, float t2, double* res) {
+__device__ __forceinline__ void epi_t(const EpiArgs& ep, int j, float t1, float t2, float t3, double* res) {
   if constexpr (EPI == EPT_RAW) {
     ep.out1[j] = t1;
     if (ep.out2) ep.out2[j] = t2;
   } else if constexpr (EPI == EPT_TALL_R) {
     ep.r[j] = ep.cx[j] + t1;
+    ep.xt[j] = -t3;                     // x~ re-derived as -A^T y~ (Section 3.3 invariant)
     const float dr = t2 + ep.mu[j];
     res[0] += (double)dr * dr;
     const float du = dr / ep.E[j];
@@ -97,7 +110,7 @@ __device__ __forceinline__ void epi_t(const EpiArgs& ep, int j, float t1, float 
     const float c = ep.cx[j];
     const float xp = c + t1;
     ep.x[j] = xp;
-    ep.xt[j] = c - xp;
+    ep.xt[j] = -t3;                     // x~^{k+1} = -A^T y~^{k+1} (Section 3.3 invariant)
     const float dr = t2 + ep.mu[j];
     res[0] += (double)dr * dr;
     const float du = dr / ep.E[j];
@@ -120,7 +133,8 @@ __device__ __forceinline__ void epi_t(const EpiArgs& ep, int j, float t1, float 
 template <int NRHS, bool SQ, int EPI>
 __global__ void __launch_bounds__(256) gemv_t_kernel(const float* __restrict__ A, int64_t lda, int m, int n,
                                                      const float* __restrict__ v1,
-                                                     const float* __restrict__ v2, int rows,
+                                                     const float* __restrict__ v2,
+                                                     const float* __restrict__ v3, int rows,
                                                      float* __restrict__ part, unsigned* __restrict__ cnt,
                                                      EpiArgs ep, const DevState* __restrict__ guard) {
   __shared__ double sh[2 * 8];
@@ -147,10 +161,15 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(const float* __restrict__ A
         const float w1 = __ldg(v1 + i + u);
         acc[0][0] = fmaf(av.x, w1, acc[0][0]); acc[0][1] = fmaf(av.y, w1, acc[0][1]);
         acc[0][2] = fmaf(av.z, w1, acc[0][2]); acc[0][3] = fmaf(av.w, w1, acc[0][3]);
-        if constexpr (NRHS == 2) {
+        if constexpr (NRHS >= 2) {
           const float w2 = __ldg(v2 + i + u);
           acc[1][0] = fmaf(av.x, w2, acc[1][0]); acc[1][1] = fmaf(av.y, w2, acc[1][1]);
           acc[1][2] = fmaf(av.z, w2, acc[1][2]); acc[1][3] = fmaf(av.w, w2, acc[1][3]);
+        }
+        if constexpr (NRHS == 3) {
+          const float w3 = __ldg(v3 + i + u);
+          acc[2][0] = fmaf(av.x, w3, acc[2][0]); acc[2][1] = fmaf(av.y, w3, acc[2][1]);
+          acc[2][2] = fmaf(av.z, w3, acc[2][2]); acc[2][3] = fmaf(av.w, w3, acc[2][3]);
         }
       }
     }
@@ -160,10 +179,15 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(const float* __restrict__ A
       const float w1 = __ldg(v1 + i);
       acc[0][0] = fmaf(av.x, w1, acc[0][0]); acc[0][1] = fmaf(av.y, w1, acc[0][1]);
       acc[0][2] = fmaf(av.z, w1, acc[0][2]); acc[0][3] = fmaf(av.w, w1, acc[0][3]);
-      if constexpr (NRHS == 2) {
+      if constexpr (NRHS >= 2) {
         const float w2 = __ldg(v2 + i);
         acc[1][0] = fmaf(av.x, w2, acc[1][0]); acc[1][1] = fmaf(av.y, w2, acc[1][1]);
         acc[1][2] = fmaf(av.z, w2, acc[1][2]); acc[1][3] = fmaf(av.w, w2, acc[1][3]);
+      }
+      if constexpr (NRHS == 3) {
+        const float w3 = __ldg(v3 + i);
+        acc[2][0] = fmaf(av.x, w3, acc[2][0]); acc[2][1] = fmaf(av.y, w3, acc[2][1]);
+        acc[2][2] = fmaf(av.z, w3, acc[2][2]); acc[2][3] = fmaf(av.w, w3, acc[2][3]);
       }
     }
 #pragma unroll
@@ -187,7 +211,7 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(const float* __restrict__ A
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int64_t j = c0 + u;
-      if (j < n) epi_t<EPI>(ep, (int)j, s[0][u], NRHS == 2 ? s[NRHS - 1][u] : 0.0f, res);
+      if (j < n) epi_t<EPI>(ep, (int)j, s[0][u], NRHS >= 2 ? s[1][u] : 0.0f, NRHS == 3 ? s[NRHS - 1][u] : 0.0f, res);
     }
   }
   block_sum<2>(res, sh);
@@ -210,7 +234,7 @@ __device__ __forceinline__ void epi_n(const EpiArgs& ep, int i, float u1, float 
     if (ep.out2) ep.out2[i] = u2;
   } else if constexpr (EPI == EPN_TALL_Y) {
     ep.y[i] = u1;
-    ep.yt[i] = ep.dy[i] - u1;
+    ep.yt[i] += ep.dy[i] - u1;          // y~ <- y~ + y_r - y^{k+1}
     const float pr = u2 - ep.yh[i];
     res[0] += (double)pr * pr;
     const float pu = pr / ep.D[i];
@@ -320,14 +344,14 @@ __device__ __forceinline__ void epi_r(const EpiArgs& ep, int idx, int q, float v
       const float c = ep.cx[idx];
       const float xv = ep.in1 ? ep.in1[idx] + v : v;   // in1: refinement base x0
       ep.x[idx] = xv;
-      ep.xt[idx] = c - xv;
+      ep.xt[idx] += c - xv;             // x~ <- x~ + x_r - x^{k+1}
     }
   } else if constexpr (EPI == EPR_FAT_Y) {
     if (idx < q) {
       const float d = ep.dy[idx];
       const float yp = d + (ep.in1 ? ep.in1[idx] + v : v);
       ep.y[idx] = yp;
-      ep.yt[idx] = d - yp;
+      ep.yt[idx] += d - yp;             // y~ <- y~ + y_r - y^{k+1}
       ep.w[idx] = d - yp;
     }
   }
@@ -541,18 +565,25 @@ static int grid_for(int64_t k, int per = 256) {
 }
 
 void launch_prox_eval(FnDev fn, int64_t k, const float* v, const float* rv, float rho, float* out, cudaStream_t s) {
+  count_launch();
   prox_eval_kernel<<<grid_for(k), 256, 0, s>>>(fn, k, v, rv, rho, out);
 }
 void launch_fold(FnDev raw, int64_t k, const float* scale, int is_f, uint8_t* h, float* a, float* b, float* c,
                  float* d, float* e, int* err, cudaStream_t s) {
+  count_launch();
   fold_kernel<<<grid_for(k), 256, 0, s>>>(raw, k, scale, is_f, h, a, b, c, d, e, err);
 }
-void launch_fill(float* p, int64_t k, float v, cudaStream_t s) { fill_kernel<<<grid_for(k), 256, 0, s>>>(p, k, v); }
+void launch_fill(float* p, int64_t k, float v, cudaStream_t s) {
+  count_launch();
+  fill_kernel<<<grid_for(k), 256, 0, s>>>(p, k, v);
+}
 void launch_unscale(int n, int m, const float* xh, const float* mu, const float* yh, const float* nu,
                     const float* D, const float* E, float* x, float* muo, float* y, float* nuo, cudaStream_t s) {
+  count_launch();
   unscale_kernel<<<grid_for(n + m), 256, 0, s>>>(n, m, xh, mu, yh, nu, D, E, x, muo, y, nuo);
 }
 void launch_axpby(int64_t k, float a, const float* x, float b, const float* y, float* out, cudaStream_t s) {
+  count_launch();
   axpby_kernel<<<grid_for(k), 256, 0, s>>>(k, a, x, b, y, out);
 }
 
@@ -586,10 +617,11 @@ GemvGeom choose_geometry(int64_t m, int64_t n, int64_t lda, int num_sms) {
 
 template <int NRHS, bool SQ>
 static void gemv_t_dispatch(int epi, const float* A, int64_t lda, int m, int n, const float* v1, const float* v2,
-                            const GemvGeom& g, float* part, unsigned* cnt, const EpiArgs& ep,
+                            const float* v3, const GemvGeom& g, float* part, unsigned* cnt, const EpiArgs& ep,
                             const DevState* guard, cudaStream_t s) {
   dim3 grid(g.t_ncolblk, g.t_nsplit);
-#define POGS_T(E) gemv_t_kernel<NRHS, SQ, E><<<grid, 256, 0, s>>>(A, lda, m, n, v1, v2, g.t_rows, part, cnt, ep, guard)
+  count_launch();
+#define POGS_T(E) gemv_t_kernel<NRHS, SQ, E><<<grid, 256, 0, s>>>(A, lda, m, n, v1, v2, v3, g.t_rows, part, cnt, ep, guard)
   switch (epi) {
     case EPT_RAW: POGS_T(EPT_RAW); break;
     case EPT_TALL_R: POGS_T(EPT_TALL_R); break;
@@ -601,11 +633,12 @@ static void gemv_t_dispatch(int epi, const float* A, int64_t lda, int m, int n, 
 }
 
 void launch_gemv_t(int nrhs, bool sq, int epi, const float* A, int64_t lda, int m, int n, const float* v1,
-                   const float* v2, const GemvGeom& g, float* part, unsigned* cnt, const EpiArgs& ep,
-                   const DevState* guard, cudaStream_t s) {
-  if (nrhs == 2) gemv_t_dispatch<2, false>(epi, A, lda, m, n, v1, v2, g, part, cnt, ep, guard, s);
-  else if (sq) gemv_t_dispatch<1, true>(epi, A, lda, m, n, v1, v2, g, part, cnt, ep, guard, s);
-  else gemv_t_dispatch<1, false>(epi, A, lda, m, n, v1, v2, g, part, cnt, ep, guard, s);
+                   const float* v2, const float* v3, const GemvGeom& g, float* part, unsigned* cnt,
+                   const EpiArgs& ep, const DevState* guard, cudaStream_t s) {
+  if (nrhs == 3) gemv_t_dispatch<3, false>(epi, A, lda, m, n, v1, v2, v3, g, part, cnt, ep, guard, s);
+  else if (nrhs == 2) gemv_t_dispatch<2, false>(epi, A, lda, m, n, v1, v2, v3, g, part, cnt, ep, guard, s);
+  else if (sq) gemv_t_dispatch<1, true>(epi, A, lda, m, n, v1, v2, v3, g, part, cnt, ep, guard, s);
+  else gemv_t_dispatch<1, false>(epi, A, lda, m, n, v1, v2, v3, g, part, cnt, ep, guard, s);
 }
 
 template <int NRHS, bool SQ>
@@ -613,6 +646,7 @@ static void gemv_n_dispatch(int epi, const float* A, int64_t lda, int m, int n, 
                             const GemvGeom& g, float* part, unsigned* cnt, const EpiArgs& ep,
                             const DevState* guard, cudaStream_t s) {
   dim3 grid(g.n_nrowblk, g.n_ncolsplit);
+  count_launch();
   const size_t smem = (size_t)NRHS * g.n_cols * sizeof(float);
   // smem <= 2 x 4096 floats = 32 KB: no opt-in needed (and nothing to set during capture)
 #define POGS_N(E) \
@@ -638,6 +672,7 @@ void launch_gemv_n(int nrhs, bool sq, int epi, const float* A, int64_t lda, int 
 void launch_trmv(bool trans, int epi, const float* Mt, int T, int q, const float* vin, float* part, unsigned* cnt,
                  const EpiArgs& ep, const DevState* guard, cudaStream_t s) {
   const int nt = T * (T + 1) / 2;
+  count_launch();
 #define POGS_R(TR, E) trmv_kernel<TR, E><<<nt, 256, 0, s>>>(Mt, T, q, vin, part, cnt, ep, guard)
   if (!trans) {
     switch (epi) {
@@ -658,6 +693,7 @@ void launch_trmv(bool trans, int epi, const float* Mt, int T, int q, const float
 void launch_check(DevState* st, const DevCfg* cfg, const double* prox_part, int nprox, const double* pri_part,
                   int npri, const double* dual_part, int ndual, unsigned long long cond_handle, int use_cond,
                   cudaStream_t s) {
+  count_launch();
   check_kernel<<<1, 256, 0, s>>>(st, cfg, prox_part, nprox, pri_part, npri, dual_part, ndual,
                                  (cudaGraphConditionalHandle)cond_handle, use_cond);
 }

@@ -7,15 +7,15 @@ namespace pogs {
 // Epilogues of the column-sum GEMV  t = A^T [v1, v2]  (one column per output element).
 enum EpiT : int {
   EPT_RAW = 0,      // out1 = t1, out2 = t2
-  EPT_TALL_R = 1,   // tall projection input r = c + A^T d; dual residual from t2 = A^T nu
-  EPT_FAT_X = 2,    // fat x^{k+1} = c + A^T (d - y^{k+1}); x~ = c - x^{k+1}; dual residual
+  EPT_TALL_R = 1,   // tall projection input r = c + A^T d; dual residual from t2 = A^T nu; x~ = -A^T y~
+  EPT_FAT_X = 2,    // fat x^{k+1} = c + A^T (d - y^{k+1}); x~ = -A^T y~; dual residual
   EPT_SK_COL = 3,   // Algorithm 2 e-update; Frobenius partial sum e_j * colsum_j
   EPT_REFINE = 4,   // refinement residual out1 = r - x0 - t1 (tall)
 };
 // Epilogues of the row-dot GEMV  u = A [x1, x2]  (one row per output element).
 enum EpiN : int {
   EPN_RAW = 0,      // out1 = u1, out2 = u2
-  EPN_TALL_Y = 1,   // tall y^{k+1} = A x^{k+1}; y~ = d - y^{k+1}; primal residual from u2 = A x^{1/2}
+  EPN_TALL_Y = 1,   // tall y^{k+1} = A x^{k+1}; y~ += d - y^{k+1}; primal residual from u2 = A x^{1/2}
   EPN_FAT_R = 2,    // fat projection input r = A c - d; primal residual
   EPN_SK_ROW = 3,   // Algorithm 2 d-update
   EPN_REFINE = 4,   // refinement residual out1 = r - y0 - u1 (fat)
@@ -23,8 +23,8 @@ enum EpiN : int {
 // Epilogues of the packed-triangle products z = M v (M = L^{-1}) and M^T v.
 enum EpiR : int {
   EPR_RAW = 0,      // out1 = result (all padded entries)
-  EPR_TALL_X = 1,   // x^{k+1} = result; x~ = c - x^{k+1}
-  EPR_FAT_Y = 2,    // y^{k+1} = d + result; y~ = d - y^{k+1}; w = d - y^{k+1}
+  EPR_TALL_X = 1,   // x^{k+1} = result (+ in1); x~ += c - x^{k+1}
+  EPR_FAT_Y = 2,    // y^{k+1} = d + result (+ in1); y~ += d - y^{k+1}; w = d - y^{k+1}
   EPR_ADD = 3,      // out1 = in1 + result (refinement correction)
 };
 
@@ -55,12 +55,13 @@ struct GemvGeom {
 GemvGeom choose_geometry(int64_t m, int64_t n, int64_t lda, int num_sms);
 
 // ---- iteration kernels (iter.cu) --------------------------------------------------------
-void launch_prox_step(int n, int m, const float* x, const float* xt, float* xh, float* cx, float* mu,
-                      const float* y, const float* yt, float* yh, float* dy, float* nu,
+void launch_prox_step(int n, int m, const float* x, float* xt, float* xh, float* cx, float* mu,
+                      const float* y, float* yt, float* yh, float* dy, float* nu,
                       FnDev g, FnDev f, const DevState* st, const DevCfg* cfg, double* part,
                       int nblocks, cudaStream_t s);
 void launch_gemv_t(int nrhs, bool sq, int epi, const float* A, int64_t lda, int m, int n,
-                   const float* v1, const float* v2, const GemvGeom& g, float* part, unsigned* cnt,
+                   const float* v1, const float* v2, const float* v3, const GemvGeom& g, float* part,
+                   unsigned* cnt,
                    const EpiArgs& ep, const DevState* guard, cudaStream_t s);
 void launch_gemv_n(int nrhs, bool sq, int epi, const float* A, int64_t lda, int m, int n,
                    const float* x1, const float* x2, const GemvGeom& g, float* part, unsigned* cnt,
@@ -91,12 +92,19 @@ void launch_sk_finish(const float* dvec, const float* evec, int64_t m, int64_t n
 // the diagonal of C.
 void gemm_f32(bool ta, bool tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
               const float* B, int64_t ldb, float beta, float* C, int64_t ldc, bool lower_only,
-              cudaStream_t s);
+              cudaStream_t s, int tri = 0);
 void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
               const double* B, int64_t ldb, double beta, double* C, int64_t ldc, bool lower_only,
               cudaStream_t s);
 void launch_gram_to_f64(const float* G, int64_t ldg, int64_t q, double* H, int64_t ldh, cudaStream_t s);
-int chol_f64(double* H, int64_t ldh, int64_t q, double* work, int* err, cudaStream_t s);
+// FP64 products of FP32-rounded inputs: C (FP64) = alpha op(A) op(B) + beta C with the
+// products and their sum over K formed in FP32.
+void gemm_f64_f32prod(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                      int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                      bool lower_only, cudaStream_t s);
+// Right-looking blocked Cholesky of H (lower, in place).  mixed: trailing products in FP32
+// (FP64 diagonal blocks, panel solves and Schur complement).
+int chol_f64(double* H, int64_t ldh, int64_t q, double* work, int* err, bool mixed, cudaStream_t s);
 void launch_leaf_inverse(const double* L, int64_t ldl, int64_t q, float* Minv, int64_t ldm, cudaStream_t s);
 void launch_l_to_f32(const double* L, int64_t ldl, int64_t q, float* Lf, int64_t ldf, cudaStream_t s);
 void tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ldm, float* work,

@@ -54,9 +54,11 @@ void launch_copy_in(const float* src, int64_t m, int64_t n, int64_t lds, bool co
                     int* err, cudaStream_t s) {
   if (!colmajor) {
     int64_t g = std::min<int64_t>((m * lda + 255) / 256, 148 * 16);
+    count_launch();
     copy_rowmajor_kernel<<<(int)g, 256, 0, s>>>(src, m, n, lds, A, lda, err);
   } else {
     dim3 grid((unsigned)cdiv(lda, 32), (unsigned)cdiv(m, 32));
+    count_launch();
     copy_colmajor_kernel<<<grid, dim3(32, 8), 0, s>>>(src, m, n, lds, A, lda, err);
   }
 }
@@ -72,6 +74,7 @@ __global__ void scale_kernel(float* A, int64_t lda, int64_t m, int64_t n, const 
 
 void launch_scale(float* A, int64_t lda, int64_t m, int64_t n, const float* D, const float* E, cudaStream_t s) {
   int64_t g = std::min<int64_t>((m * lda + 255) / 256, 148 * 16);
+  count_launch();
   scale_kernel<<<(int)g, 256, 0, s>>>(A, lda, m, n, D, E);
 }
 
@@ -93,17 +96,21 @@ __global__ void sk_finish_kernel(const float* dvec, const float* evec, int64_t m
 
 void launch_sk_finish(const float* dvec, const float* evec, int64_t m, int64_t n, const double* frob_part, int nfrob,
                       int64_t q, float* D, float* E, cudaStream_t s) {
+  count_launch();
   sk_finish_kernel<<<1, 1024, 0, s>>>(dvec, evec, m, n, frob_part, nfrob, q, D, E);
 }
 
 // ---- dense SIMT GEMM -----------------------------------------------------------------------
-// C = alpha op(A) op(B) + beta C, row-major.  op(A)[i][k] = TA ? A[k*lda+i] : A[i*lda+k],
-// op(B)[k][j] = TB ? B[j*ldb+k] : B[k*ldb+j].  256 threads, (BM/TM) x (BN/TN) = 16 x 16
-// thread grid, interleaved register tiles (conflict-free shared reads).
-template <typename T, int BM, int BN, int BK, int TM, int TN, bool TA, bool TB>
-__global__ void __launch_bounds__(256) gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha,
-                                                   const T* A, int64_t lda, const T* B, int64_t ldb, T beta, T* C,
-                                                   int64_t ldc, int lower_only) {
+// C = alpha op(A) op(B) + beta C, row-major, storage type TI, products and accumulation in
+// TC (TI = double with TC = float gives FP32 products of FP32-rounded inputs added to an FP64
+// C).  op(A)[i][k] = TA ? A[k*lda+i] : A[i*lda+k], op(B)[k][j] = TB ? B[j*ldb+k] : B[k*ldb+j].
+// 256 threads, (BM/TM) x (BN/TN) = 16 x 16 thread grid, interleaved register tiles
+// (conflict-free shared reads).  `tri` skips structurally zero K ranges: bit 0 -- op(B) lower
+// triangular (op(B)[k][j] = 0 for k < j); bit 1 -- op(A) lower triangular (0 for k > i).
+template <typename TI, typename TC, int BM, int BN, int BK, int TM, int TN, bool TA, bool TB>
+__global__ void __launch_bounds__(256) gemm_kernel(int64_t M, int64_t N, int64_t K, TI alpha, const TI* A,
+                                                   int64_t lda, const TI* B, int64_t ldb, TI beta, TI* C,
+                                                   int64_t ldc, int lower_only, int tri) {
   // A and C may alias (in-place panel update): each block reads its own rows of A fully
   // before it writes C, and no other block touches those rows.
   constexpr int GX = BN / TN, GY = BM / TM;
@@ -111,35 +118,37 @@ __global__ void __launch_bounds__(256) gemm_kernel(int64_t M, int64_t N, int64_t
   const int64_t bm = blockIdx.y, bn = blockIdx.x;
   const int64_t row0 = (int64_t)bm * BM, col0 = (int64_t)bn * BN;
   if (lower_only && col0 > row0 + BM - 1) return;
-  __shared__ T As[BK][BM + 1];
-  __shared__ T Bs[BK][BN + 1];
+  __shared__ TC As[BK][BM + 1];
+  __shared__ TC Bs[BK][BN + 1];
   const int tx = threadIdx.x % GX, ty = threadIdx.x / GX;
-  T acc[TM][TN];
+  TC acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
-  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+    for (int j = 0; j < TN; ++j) acc[i][j] = TC(0);
+  const int64_t kbeg = (tri & 1) ? (col0 / BK) * BK : 0;
+  const int64_t kend = (tri & 2) ? (row0 + BM < K ? row0 + BM : K) : K;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
     for (int e = threadIdx.x; e < BM * BK; e += 256) {
       int i, k;
       if (TA) { k = e / BM; i = e % BM; } else { i = e / BK; k = e % BK; }
       const int64_t gi = row0 + i, gk = k0 + k;
-      T v = T(0);
-      if (gi < M && gk < K) v = TA ? A[gk * lda + gi] : A[gi * lda + gk];
+      TC v = TC(0);
+      if (gi < M && gk < K) v = (TC)(TA ? A[gk * lda + gi] : A[gi * lda + gk]);
       As[k][i] = v;
     }
     for (int e = threadIdx.x; e < BN * BK; e += 256) {
       int j, k;
       if (TB) { j = e / BK; k = e % BK; } else { k = e / BN; j = e % BN; }
       const int64_t gj = col0 + j, gk = k0 + k;
-      T v = T(0);
-      if (gj < N && gk < K) v = TB ? B[gj * ldb + gk] : B[gk * ldb + gj];
+      TC v = TC(0);
+      if (gj < N && gk < K) v = (TC)(TB ? B[gj * ldb + gk] : B[gk * ldb + gj]);
       Bs[k][j] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
-      T a[TM], b[TN];
+      TC a[TM], b[TN];
 #pragma unroll
       for (int i = 0; i < TM; ++i) a[i] = As[k][ty + i * GY];
 #pragma unroll
@@ -159,32 +168,45 @@ __global__ void __launch_bounds__(256) gemm_kernel(int64_t M, int64_t N, int64_t
     for (int j = 0; j < TN; ++j) {
       const int64_t gj = col0 + tx + j * GX;
       if (gj >= N) continue;
-      T c = alpha * acc[i][j];
-      if (beta != T(0)) c = fma(beta, C[gi * ldc + gj], c);
+      TI c = alpha * (TI)acc[i][j];
+      if (beta != TI(0)) c = fma(beta, C[gi * ldc + gj], c);
       C[gi * ldc + gj] = c;
     }
   }
 }
 
-template <typename T, int BM, int BN, int BK, int TM, int TN>
-static void gemm_launch(bool ta, bool tb, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda,
-                        const T* B, int64_t ldb, T beta, T* C, int64_t ldc, bool lower_only, cudaStream_t s) {
+template <typename TI, typename TC, int BM, int BN, int BK, int TM, int TN>
+static void gemm_launch(bool ta, bool tb, int64_t M, int64_t N, int64_t K, TI alpha, const TI* A, int64_t lda,
+                        const TI* B, int64_t ldb, TI beta, TI* C, int64_t ldc, bool lower_only, int tri,
+                        cudaStream_t s) {
   if (M <= 0 || N <= 0) return;
+  count_launch();
   dim3 grid((unsigned)cdiv(N, BN), (unsigned)cdiv(M, BM));
   const int lo = lower_only ? 1 : 0;
-  if (!ta && !tb) gemm_kernel<T, BM, BN, BK, TM, TN, false, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lo);
-  else if (!ta && tb) gemm_kernel<T, BM, BN, BK, TM, TN, false, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lo);
-  else if (ta && !tb) gemm_kernel<T, BM, BN, BK, TM, TN, true, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lo);
-  else gemm_kernel<T, BM, BN, BK, TM, TN, true, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lo);
+#define POGS_G(a, b) gemm_kernel<TI, TC, BM, BN, BK, TM, TN, a, b><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lo, tri)
+  if (!ta && !tb) POGS_G(false, false);
+  else if (!ta && tb) POGS_G(false, true);
+  else if (ta && !tb) POGS_G(true, false);
+  else POGS_G(true, true);
+#undef POGS_G
 }
 
 void gemm_f32(bool ta, bool tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
-              const float* B, int64_t ldb, float beta, float* C, int64_t ldc, bool lower_only, cudaStream_t s) {
-  gemm_launch<float, 128, 128, 8, 8, 8>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, s);
+              const float* B, int64_t ldb, float beta, float* C, int64_t ldc, bool lower_only, cudaStream_t s,
+              int tri) {
+  gemm_launch<float, float, 128, 128, 8, 8, 8>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only,
+                                               tri, s);
 }
 void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
               const double* B, int64_t ldb, double beta, double* C, int64_t ldc, bool lower_only, cudaStream_t s) {
-  gemm_launch<double, 64, 64, 8, 4, 4>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, s);
+  gemm_launch<double, double, 64, 64, 8, 4, 4>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, 0,
+                                               s);
+}
+void gemm_f64_f32prod(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                      int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                      bool lower_only, cudaStream_t s) {
+  gemm_launch<double, float, 128, 128, 8, 8, 8>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only,
+                                                0, s);
 }
 
 // H = I + G (lower triangle, FP64), zero above the diagonal.
@@ -199,6 +221,7 @@ __global__ void gram_to_f64_kernel(const float* G, int64_t ldg, int64_t q, doubl
 }
 void launch_gram_to_f64(const float* G, int64_t ldg, int64_t q, double* H, int64_t ldh, cudaStream_t s) {
   int64_t g = std::min<int64_t>((q * q + 255) / 256, 148 * 16);
+  count_launch();
   gram_to_f64_kernel<<<(int)g, 256, 0, s>>>(G, ldg, q, H, ldh);
 }
 
@@ -257,17 +280,23 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* Hk, int64_t ldh
   }
 }
 
-int chol_f64(double* H, int64_t ldh, int64_t q, double* work, int* err, cudaStream_t s) {
+int chol_f64(double* H, int64_t ldh, int64_t q, double* work, int* err, bool mixed, cudaStream_t s) {
   for (int64_t k0 = 0; k0 < q; k0 += kNB) {
     const int nb = (int)std::min<int64_t>(kNB, q - k0);
+    count_launch();
     potrf_diag_kernel<<<1, 256, 0, s>>>(H + k0 * ldh + k0, ldh, nb, work, err);
     const int64_t rest = q - k0 - nb;
     if (rest > 0) {
       double* P = H + (k0 + nb) * ldh + k0;
       // panel: P <- P L_kk^{-T} (in place: one block column covers all nb <= 64 columns)
       gemm_f64(false, true, rest, nb, nb, 1.0, P, ldh, work, kNB, 0.0, P, ldh, false, s);
-      // trailing update: H22 <- H22 - P P^T (lower tiles)
-      gemm_f64(false, true, rest, rest, nb, -1.0, P, ldh, P, ldh, 1.0, H + (k0 + nb) * ldh + (k0 + nb), ldh, true, s);
+      // trailing update: H22 <- H22 - P P^T (lower tiles), FP64 Schur complement; the mixed
+      // variant forms the products from the FP32-rounded panel in FP32
+      if (mixed)
+        gemm_f64_f32prod(false, true, rest, rest, nb, -1.0, P, ldh, P, ldh, 1.0, H + (k0 + nb) * ldh + (k0 + nb), ldh,
+                         true, s);
+      else
+        gemm_f64(false, true, rest, rest, nb, -1.0, P, ldh, P, ldh, 1.0, H + (k0 + nb) * ldh + (k0 + nb), ldh, true, s);
     }
   }
   return 0;
@@ -308,6 +337,7 @@ void launch_leaf_inverse(const double* L, int64_t ldl, int64_t q, float* Minv, i
   const int T = (int)cdiv(q, kTile);
   const size_t smem = (size_t)(128 * 129 + 128) * sizeof(double);
   cudaFuncSetAttribute(leaf_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  count_launch();
   leaf_inverse_kernel<<<T, 128, smem, s>>>(L, ldl, q, Minv, ldm);
 }
 
@@ -320,6 +350,7 @@ __global__ void l_to_f32_kernel(const double* L, int64_t ldl, int64_t q, float* 
 }
 void launch_l_to_f32(const double* L, int64_t ldl, int64_t q, float* Lf, int64_t ldf, cudaStream_t s) {
   int64_t g = std::min<int64_t>((q * q + 255) / 256, 148 * 16);
+  count_launch();
   l_to_f32_kernel<<<(int)g, 256, 0, s>>>(L, ldl, q, Lf, ldf);
 }
 
@@ -333,10 +364,11 @@ static void inv_rec(const float* L, int64_t ldl, float* M, int64_t ldm, int64_t 
   const int64_t n1 = (nblk / 2) * kTile, n2 = nsz - n1;
   inv_rec(L, ldl, M, ldm, r0, n1, work, s);
   inv_rec(L, ldl, M, ldm, r0 + n1, n2, work, s);
+  // T = L21 M11 (M11 lower triangular), then M21 = -M22 T (M22 lower triangular)
   gemm_f32(false, false, n2, n1, n1, 1.0f, L + (r0 + n1) * ldl + r0, ldl, M + r0 * ldm + r0, ldm, 0.0f, work, n1,
-           false, s);
+           false, s, 1);
   gemm_f32(false, false, n2, n1, n2, -1.0f, M + (r0 + n1) * ldm + r0 + n1, ldm, work, n1, 0.0f,
-           M + (r0 + n1) * ldm + r0, ldm, false, s);
+           M + (r0 + n1) * ldm + r0, ldm, false, s, 2);
 }
 
 void tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ldm, float* work, cudaStream_t s) {
@@ -358,6 +390,7 @@ __global__ void __launch_bounds__(256) pack_tiles_kernel(const float* M, int64_t
   }
 }
 void launch_pack_tiles(const float* M, int64_t ldm, int64_t q, int T, float* Mt, cudaStream_t s) {
+  count_launch();
   pack_tiles_kernel<<<T * (T + 1) / 2, 256, 0, s>>>(M, ldm, q, Mt);
 }
 

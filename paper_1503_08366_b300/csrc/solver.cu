@@ -49,8 +49,15 @@ struct pogs_handle {
   cudaGraphExec_t gexec = nullptr;
   int graph_refine = -1, graph_mode = -1;
   double setup_ms = 0.0;
+  double phase_ms[5] = {0, 0, 0, 0, 0};
+  cudaEvent_t ev[6] = {};
+  bool solved = false;
+  int64_t device_bytes = 0;
   std::vector<void*> allocs;
 };
+
+std::atomic<long long> pogs::g_launch_count{0};
+thread_local int pogs::g_capture_depth = 0;
 
 namespace {
 
@@ -85,6 +92,7 @@ int dalloc(pogs_handle* h, T** p, size_t count) {
     return POGS_ERR_OOM;
   }
   h->allocs.push_back(q);
+  h->device_bytes += (int64_t)(count * sizeof(T));
   *p = static_cast<T*>(q);
   if (cudaMemsetAsync(q, 0, count * sizeof(T), h->stream) != cudaSuccess) return POGS_ERR_CUDA;
   return 0;
@@ -136,14 +144,19 @@ void enqueue_projection(pogs_handle* h, int refine, cudaStream_t s) {
   if (h->tall) {
     // r = c + A^T d ; dual residual ||A^T nu + mu||
     EpiArgs e1 = epi0();
-    e1.r = h->r; e1.cx = h->cx; e1.mu = h->mu; e1.E = h->E; e1.res_part = h->dual_part;
-    launch_gemv_t(2, false, EPT_TALL_R, h->A, h->lda, m, n, h->dy, h->nu, g, h->part_t, h->cnt_t, e1, h->st, s);
+    e1.r = h->r; e1.cx = h->cx; e1.mu = h->mu; e1.E = h->E; e1.xt = h->xt; e1.res_part = h->dual_part;
+    launch_gemv_t(3, false, EPT_TALL_R, h->A, h->lda, m, n, h->dy, h->nu, h->yt, g, h->part_t, h->cnt_t, e1, h->st, s);
     EpiArgs e2 = epi0();
     e2.out1 = h->z;
     launch_trmv(false, EPR_RAW, h->Mt, h->T, q, h->r, h->part_tr, h->cnt_tr, e2, h->st, s);
     EpiArgs e3 = epi0();
-    e3.x = h->x; e3.xt = h->xt; e3.cx = h->cx;
-    launch_trmv(true, EPR_TALL_X, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, e3, h->st, s);
+    if (!refine) {
+      e3.x = h->x; e3.xt = h->xt; e3.cx = h->cx;
+      launch_trmv(true, EPR_TALL_X, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, e3, h->st, s);
+    } else {
+      e3.out1 = h->x;   // x0 only; the dual update waits for the refined x
+      launch_trmv(true, EPR_RAW, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, e3, h->st, s);
+    }
     if (refine) {
       // r2 = r - x0 - A^T (A x0);  x = x0 + L^{-T} L^{-1} r2
       EpiArgs e4 = epi0();
@@ -151,7 +164,8 @@ void enqueue_projection(pogs_handle* h, int refine, cudaStream_t s) {
       launch_gemv_n(1, false, EPN_RAW, h->A, h->lda, m, n, h->x, nullptr, g, h->part_n, h->cnt_n, e4, h->st, s);
       EpiArgs e5 = epi0();
       e5.out1 = h->r2; e5.in1 = h->r; e5.in2 = h->x;
-      launch_gemv_t(1, false, EPT_REFINE, h->A, h->lda, m, n, h->v0, nullptr, g, h->part_t, h->cnt_t, e5, h->st, s);
+      launch_gemv_t(1, false, EPT_REFINE, h->A, h->lda, m, n, h->v0, nullptr, nullptr, g, h->part_t, h->cnt_t, e5,
+                    h->st, s);
       EpiArgs e6 = epi0();
       e6.out1 = h->z;
       launch_trmv(false, EPR_RAW, h->Mt, h->T, q, h->r2, h->part_tr, h->cnt_tr, e6, h->st, s);
@@ -182,7 +196,8 @@ void enqueue_projection(pogs_handle* h, int refine, cudaStream_t s) {
       // r2 = r - v0 - A (A^T v0)
       EpiArgs e4 = epi0();
       e4.out1 = h->tn;
-      launch_gemv_t(1, false, EPT_RAW, h->A, h->lda, m, n, h->v0, nullptr, g, h->part_t, h->cnt_t, e4, h->st, s);
+      launch_gemv_t(1, false, EPT_RAW, h->A, h->lda, m, n, h->v0, nullptr, nullptr, g, h->part_t, h->cnt_t, e4,
+                    h->st, s);
       EpiArgs e5 = epi0();
       e5.out1 = h->r2; e5.in1 = h->r; e5.in2 = h->v0;
       launch_gemv_n(1, false, EPN_REFINE, h->A, h->lda, m, n, h->tn, nullptr, g, h->part_n, h->cnt_n, e5, h->st, s);
@@ -196,7 +211,7 @@ void enqueue_projection(pogs_handle* h, int refine, cudaStream_t s) {
     // x = c + A^T (d - y) ; x~ = c - x ; dual residual
     EpiArgs e8 = epi0();
     e8.x = h->x; e8.xt = h->xt; e8.cx = h->cx; e8.mu = h->mu; e8.E = h->E; e8.res_part = h->dual_part;
-    launch_gemv_t(2, false, EPT_FAT_X, h->A, h->lda, m, n, h->w, h->nu, g, h->part_t, h->cnt_t, e8, h->st, s);
+    launch_gemv_t(3, false, EPT_FAT_X, h->A, h->lda, m, n, h->w, h->nu, h->yt, g, h->part_t, h->cnt_t, e8, h->st, s);
   }
 }
 
@@ -206,6 +221,11 @@ void enqueue_iteration(pogs_handle* h, int refine, cudaStream_t s, unsigned long
   enqueue_projection(h, refine, s);
   launch_check(h->st, h->cfg, h->prox_part, h->nprox, h->pri_part, h->geom.n_nrowblk, h->dual_part,
                h->geom.t_ncolblk, cond, use_cond, s);
+}
+
+int kernels_per_iteration(const pogs_handle* h, int refine) {
+  (void)h;
+  return 6 + (refine ? 4 : 0);   // prox, 2 A passes, 2 triangle products, check (+ refinement)
 }
 
 int build_graph(pogs_handle* h, int refine, int mode) {
@@ -228,12 +248,16 @@ int build_graph(pogs_handle* h, int refine, int mode) {
     CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    ++g_capture_depth;
     enqueue_iteration(h, refine, h->cap, (unsigned long long)ch, 1);
+    --g_capture_depth;
     cudaGraph_t captured = nullptr;
     CK(cudaStreamEndCapture(h->cap, &captured));
   } else {
     CK(cudaStreamBeginCaptureToGraph(h->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    ++g_capture_depth;
     enqueue_iteration(h, refine, h->cap, 0ull, 0);
+    --g_capture_depth;
     cudaGraph_t captured = nullptr;
     CK(cudaStreamEndCapture(h->cap, &captured));
   }
@@ -249,7 +273,7 @@ int validate_params(const pogs_params* p) {
   if (!(p->abs_tol >= 0) || !(p->rel_tol >= 0) || p->max_iter < 1 || !(p->rho0 > 0) || !(p->alpha > 0) ||
       !(p->alpha < 2) || !(p->delta >= 1) || !(p->tau > 0) || p->sk_sweeps < 0 || p->refine_steps < 0 ||
       p->refine_steps > 1 || p->gram_prec < POGS_GRAM_BF16 || p->gram_prec > POGS_GRAM_FP32 ||
-      p->loop_mode < 0 || p->loop_mode > 1)
+      p->loop_mode < 0 || p->loop_mode > 1 || p->chol_prec < POGS_CHOL_FP64 || p->chol_prec > POGS_CHOL_MIXED)
     return POGS_ERR_ARG;
   return 0;
 }
@@ -258,13 +282,12 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order) {
   const int64_t m = h->m, n = h->n, q = h->q;
   cudaStream_t s = h->stream;
   Scratch scr;
-  double tmark = now_ms();
+  // phase boundaries are CUDA events on the setup stream (no host synchronisation)
+  int nphase = 0;
+  CK(cudaEventRecord(h->ev[nphase++], s));
   auto phase = [&](const char* name) {
-    if (h->sp.verbose <= 0) return;
-    cudaStreamSynchronize(s);
-    const double t = now_ms();
-    fprintf(stderr, "pogs setup %-10s %9.3f ms\n", name, t - tmark);
-    tmark = t;
+    (void)name;
+    if (nphase < 6) cudaEventRecord(h->ev[nphase++], s);
   };
   // ---- ingest -------------------------------------------------------------------------
   TRY(dalloc(h, &h->A, (size_t)(m * h->lda)));
@@ -311,14 +334,16 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order) {
                   er, nullptr, s);
     EpiArgs ec = epi0();
     ec.sk_vec = evec; ec.sk_num = (float)m; ec.sk_reg = (float)(gamma / (double)n); ec.res_part = h->dual_part;
-    launch_gemv_t(1, true, EPT_SK_COL, h->A, h->lda, (int)m, (int)n, dvec, nullptr, h->geom, h->part_t, h->cnt_t,
+    launch_gemv_t(1, true, EPT_SK_COL, h->A, h->lda, (int)m, (int)n, dvec, nullptr, nullptr, h->geom, h->part_t,
+                  h->cnt_t,
                   ec, nullptr, s);
   }
   if (sweeps == 0) {
     // D = E = I: only the Frobenius norm is needed (sk_num < 0 keeps e = 1)
     EpiArgs ec = epi0();
     ec.sk_vec = evec; ec.sk_num = -1.0f; ec.res_part = h->dual_part;
-    launch_gemv_t(1, true, EPT_SK_COL, h->A, h->lda, (int)m, (int)n, dvec, nullptr, h->geom, h->part_t, h->cnt_t,
+    launch_gemv_t(1, true, EPT_SK_COL, h->A, h->lda, (int)m, (int)n, dvec, nullptr, nullptr, h->geom, h->part_t,
+                  h->cnt_t,
                   ec, nullptr, s);
   }
   launch_sk_finish(dvec, evec, m, n, h->dual_part, h->geom.t_ncolblk, q, h->D, h->E, s);
@@ -355,7 +380,7 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order) {
   launch_gram_to_f64(G, q, q, H, q, s);
   double* work = nullptr;
   TRY(scr.get(&work, 64 * 64, s));
-  chol_f64(H, q, q, work, err, s);
+  chol_f64(H, q, q, work, err, h->sp.chol_prec == POGS_CHOL_MIXED, s);
   CK(cudaGetLastError());
   phase("cholesky");
   // ---- M = L^{-1} (FP32), packed tiles --------------------------------------------------
@@ -394,7 +419,7 @@ int alloc_state(pogs_handle* h) {
   TRY(dalloc(h, &h->D, mv));
   TRY(dalloc(h, &h->E, nv));
   const GemvGeom& g = h->geom;
-  TRY(dalloc(h, &h->part_t, (size_t)g.t_nsplit * 2 * h->lda));
+  TRY(dalloc(h, &h->part_t, (size_t)g.t_nsplit * 3 * h->lda));
   TRY(dalloc(h, &h->cnt_t, (size_t)g.t_ncolblk));
   TRY(dalloc(h, &h->part_n, (size_t)g.n_ncolsplit * 2 * h->m));
   TRY(dalloc(h, &h->cnt_n, (size_t)g.n_nrowblk));
@@ -419,6 +444,8 @@ void release(pogs_handle* h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->cap) cudaStreamDestroy(h->cap);
+  for (cudaEvent_t e : h->ev)
+    if (e) cudaEventDestroy(e);
   delete h;
 }
 
@@ -509,6 +536,7 @@ void pogs_default_params(pogs_params* p) {
   p->verbose = 0;
   p->loop_mode = 0;
   p->check_every = 10;
+  p->chol_prec = POGS_CHOL_MIXED;
 }
 
 int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order, const pogs_params* p, void* stream,
@@ -547,6 +575,13 @@ int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order, co
     delete h;
     return POGS_ERR_CUDA;
   }
+  for (cudaEvent_t& e : h->ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      release(h);
+      return POGS_ERR_CUDA;
+    }
+  }
   h->geom = choose_geometry(m, n, h->lda, h->num_sms);
   h->nprox = (int)std::min<int64_t>(cdiv(m + n, 256), (int64_t)h->num_sms * 4);
   int rc = alloc_state(h);
@@ -560,6 +595,14 @@ int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order, co
     return rc;
   }
   h->setup_ms = now_ms() - t0;
+  for (int k = 0; k < 5; ++k) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = -1.0f;
+    }
+    h->phase_ms[k] = ms;
+  }
   *out = h;
   return 0;
 }
@@ -598,6 +641,8 @@ int pogs_solve(pogs_handle* h, const pogs_fn* f, const pogs_fn* g, const pogs_pa
   CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const DevState& st = *h->st_host;
+  count_launch(st.k * kernels_per_iteration(h, refine));
+  h->solved = true;
   int status = st.status;
   if (st.err != 0) status = st.err;
   if (info) {
@@ -684,6 +729,140 @@ int pogs_project(pogs_handle* h, const float* c, const float* d, float* x, float
   TRY(copy_out(h->x, x, h->n, s));
   TRY(copy_out(h->y, y, h->m, s));
   CK(cudaStreamSynchronize(s));
+  return 0;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int pogs_get_setup_report(const pogs_handle* h, pogs_setup_report* r) {
+  if (!h || !r) return POGS_ERR_ARG;
+  r->ingest_ms = h->phase_ms[0];
+  r->equil_ms = h->phase_ms[1];
+  r->gram_ms = h->phase_ms[2];
+  r->factor_ms = h->phase_ms[3];
+  r->inverse_ms = h->phase_ms[4];
+  r->gram_prec_used = h->gram_used;
+  r->chol_prec_used = h->sp.chol_prec;
+  r->device_bytes = h->device_bytes;
+  return 0;
+}
+
+long long pogs_kernel_launches(void) { return g_launch_count.load(); }
+
+int pogs_time_kernels(pogs_handle* h, int reps, double* ms, double* bytes) {
+  if (!h || reps < 1 || !h->solved) return POGS_ERR_ARG;
+  cudaStream_t s = h->stream;
+  const double m = (double)h->m, n = (double)h->n, q = (double)h->q;
+  const double A = 4.0 * m * n, tri = 2.0 * q * (q + 1.0);
+  double b[7];
+  b[0] = 41.0 * (m + n);                                   // prox: x, x~, params in; x^, c, mu out
+  if (h->tall) {
+    b[1] = A + 12 * m + 20 * n;                            // A^T [d, nu, y~] ; c, mu, E in ; r, x~ out
+    b[2] = tri + 8 * q;
+    b[3] = tri + 20 * q;                                   // z, c, x~ in ; x, x~ out
+    b[4] = A + 8 * n + 24 * m;                             // A [x, x^] ; d, y^, D, y~ in ; y, y~ out
+  } else {
+    b[1] = A + 8 * n + 16 * m;                             // A [c, x^] ; d, y^, D in ; r out
+    b[2] = tri + 8 * q;
+    b[3] = tri + 24 * q;                                   // z, d, y~ in ; y, y~, w out
+    b[4] = A + 12 * m + 20 * n;                            // A^T [w, nu, y~] ; c, mu, E in ; x, x~ out
+  }
+  b[5] = 0.0;
+  b[6] = b[0] + b[1] + b[2] + b[3] + b[4];
+  // keep the stopping test from ever firing: zero tolerances, no iteration cap
+  {
+    CK(cudaStreamSynchronize(s));
+    DevCfg c = *h->cfg_host;
+    c.abs_tol = 0.0;
+    c.rel_tol = 0.0;
+    c.max_iter = 0x7fffffff;
+    *h->cfg_host = c;
+    CK(cudaMemcpyAsync(h->cfg, h->cfg_host, sizeof(DevCfg), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(&h->st->done, 0, sizeof(int), s));
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const GemvGeom& g = h->geom;
+  const int M = (int)h->m, N = (int)h->n, Q = (int)h->q;
+  auto run = [&](int k) {
+    switch (k) {
+      case 0:
+        launch_prox_step(N, M, h->x, h->xt, h->xh, h->cx, h->mu, h->y, h->yt, h->yh, h->dy, h->nu, fn_g(h), fn_f(h),
+                         h->st, h->cfg, h->prox_part, h->nprox, s);
+        break;
+      case 1: {
+        EpiArgs e = epi0();
+        if (h->tall) {
+          e.r = h->r; e.cx = h->cx; e.mu = h->mu; e.E = h->E; e.xt = h->xt; e.res_part = h->dual_part;
+          launch_gemv_t(3, false, EPT_TALL_R, h->A, h->lda, M, N, h->dy, h->nu, h->yt, g, h->part_t, h->cnt_t, e, h->st,
+                        s);
+        } else {
+          e.r = h->r; e.dy = h->dy; e.yh = h->yh; e.D = h->D; e.res_part = h->pri_part;
+          launch_gemv_n(2, false, EPN_FAT_R, h->A, h->lda, M, N, h->cx, h->xh, g, h->part_n, h->cnt_n, e, h->st, s);
+        }
+        break;
+      }
+      case 2: {
+        EpiArgs e = epi0();
+        e.out1 = h->z;
+        launch_trmv(false, EPR_RAW, h->Mt, h->T, Q, h->r, h->part_tr, h->cnt_tr, e, h->st, s);
+        break;
+      }
+      case 3: {
+        EpiArgs e = epi0();
+        if (h->tall) {
+          e.x = h->x; e.xt = h->xt; e.cx = h->cx;
+          launch_trmv(true, EPR_TALL_X, h->Mt, h->T, Q, h->z, h->part_tr, h->cnt_tr, e, h->st, s);
+        } else {
+          e.y = h->y; e.yt = h->yt; e.dy = h->dy; e.w = h->w;
+          launch_trmv(true, EPR_FAT_Y, h->Mt, h->T, Q, h->z, h->part_tr, h->cnt_tr, e, h->st, s);
+        }
+        break;
+      }
+      case 4: {
+        EpiArgs e = epi0();
+        if (h->tall) {
+          e.y = h->y; e.yt = h->yt; e.dy = h->dy; e.yh = h->yh; e.D = h->D; e.res_part = h->pri_part;
+          launch_gemv_n(2, false, EPN_TALL_Y, h->A, h->lda, M, N, h->x, h->xh, g, h->part_n, h->cnt_n, e, h->st, s);
+        } else {
+          e.x = h->x; e.xt = h->xt; e.cx = h->cx; e.mu = h->mu; e.E = h->E; e.res_part = h->dual_part;
+          launch_gemv_t(3, false, EPT_FAT_X, h->A, h->lda, M, N, h->w, h->nu, h->yt, g, h->part_t, h->cnt_t, e, h->st,
+                        s);
+        }
+        break;
+      }
+      case 5:
+        launch_check(h->st, h->cfg, h->prox_part, h->nprox, h->pri_part, g.n_nrowblk, h->dual_part, g.t_ncolblk, 0ull,
+                     0, s);
+        break;
+    }
+  };
+  double t[7];
+  for (int k = 0; k <= 6; ++k) {
+    if (k < 6) run(k);
+    else for (int j = 0; j < 6; ++j) run(j);
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) {
+      if (k < 6) run(k);
+      else for (int j = 0; j < 6; ++j) run(j);
+    }
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float el = 0.0f;
+    CK(cudaEventElapsedTime(&el, e0, e1));
+    t[k] = (double)el / reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  h->solved = false;   // iterate state is no longer a solve result
+  for (int k = 0; k < 7; ++k) {
+    if (ms) ms[k] = t[k];
+    if (bytes) bytes[k] = b[k];
+  }
   return 0;
 }
 

@@ -215,3 +215,35 @@ def test_degenerate_sizes(P):
         with P.Solver(prob.A, P.pogs_default_params(gram_prec="FP32", max_iter=3000)) as s:
             info, x, *_ = s.solve(prob.f, prob.g)
         assert info.status in (0, 1) and np.all(np.isfinite(x))
+
+
+@pytest.mark.parametrize("shape", [(1100, 1030), (300, 700)])
+@pytest.mark.parametrize("chol", ["FP64", "MIXED"])
+def test_projection_both_cholesky_precisions(P, shape, chol):
+    """Pure FP64 and mixed (FP32 trailing products, FP64 Schur complement) factorizations
+    both reproduce the FP64 projection of the same input within 1e-5."""
+    m, n = shape
+    prob = W.huber(m, n, seed=17)
+    prm = P.pogs_default_params(gram_prec="FP32", chol_prec=chol)
+    with P.Solver(prob.A, prm) as s:
+        proj = OPJ.Projector(s.ahat().astype(np.float64))
+        rng = np.random.default_rng(3)
+        c = rng.normal(size=n).astype(np.float32)
+        d = rng.normal(size=m).astype(np.float32)
+        x, y = s.project(c, d, prm)
+        assert P.pogs_get_setup_report(s.handle).chol_prec_used == P.CHOL[chol]
+    xr, yr = proj(c.astype(np.float64), d.astype(np.float64))
+    assert _rel(x, xr) < 1e-5 and _rel(y, yr) < 1e-5
+
+
+def test_instrumentation_entry_points(P):
+    prob = W.lasso(3000, 1000, seed=5)
+    before = P.pogs_kernel_launches()
+    with P.Solver(prob.A, P.pogs_default_params(gram_prec="FP32")) as s:
+        info, *_ = s.solve(prob.f, prob.g)
+        rep = P.pogs_get_setup_report(s.handle)
+        kt = P.pogs_time_kernels(s.handle, reps=3)
+    assert P.pogs_kernel_launches() - before >= 6 * info.iters
+    assert rep.factor_ms > 0 and rep.gram_ms > 0 and rep.device_bytes > 3000 * 1000 * 4
+    assert all(v[0] > 0 for v in kt.values())
+    assert kt["A_pass1"][1] >= 4 * 3000 * 1000 and kt["Linv"][1] >= 2 * 1000 * 1001
