@@ -180,6 +180,14 @@ int pogs_get_ahat(const pogs_handle* hdl, float* Ahat);
 int pogs_project(pogs_handle* hdl, const float* c, const float* d, float* x, float* y,
                  const pogs_params* p);
 
+/* Gram formation of Section 3.5 (the one dense contraction of setup) on its own:
+ * G = A^T A (q = n) if m >= n, else G = A A^T (q = m), in precision `gram_prec`
+ * (POGS_GRAM_*; BF16, TF32 and BF16x3 run on the tensor cores with FP32 accumulation).
+ * A: device, row-major m x n with leading dimension lda >= n.  G: device, q x q row-major
+ * (ld q); the lower triangle (i >= j) is written, the strict upper triangle is unspecified.
+ * Allocates and frees its own scratch.  Errors: ARG, OOM, CUDA. */
+int pogs_gram(const float* A, int64_t m, int64_t n, int64_t lda, int gram_prec, float* G, void* stream);
+
 /* ---- instrumentation ------------------------------------------------------------------ */
 
 /* Fill *r with the setup phase times (CUDA events on the setup stream), the Gram and

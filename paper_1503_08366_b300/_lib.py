@@ -84,6 +84,8 @@ lib.pogs_get_setup_report.argtypes = [_P, C.POINTER(pogs_setup_report)]
 lib.pogs_get_setup_report.restype = C.c_int
 lib.pogs_time_kernels.argtypes = [_P, C.c_int, _P, _P]
 lib.pogs_time_kernels.restype = C.c_int
+lib.pogs_gram.argtypes = [_P, C.c_int64, C.c_int64, C.c_int64, C.c_int, _P, _P]
+lib.pogs_gram.restype = C.c_int
 lib.pogs_kernel_launches.argtypes = []
 lib.pogs_kernel_launches.restype = C.c_longlong
 
@@ -255,3 +257,15 @@ def pogs_time_kernels(handle, reps: int = 20):
 
 def pogs_kernel_launches() -> int:
     return int(lib.pogs_kernel_launches())
+
+
+def pogs_gram(A, gram_prec="BF16X3", stream=None):
+    """G = A^T A (m >= n) or A A^T (m < n) for a CUDA float32 tensor A; lower triangle valid."""
+    import torch
+    m, n = A.shape
+    A = A.contiguous()
+    q = min(m, n)
+    G = torch.zeros(q, q, dtype=torch.float32, device=A.device)
+    prec = GRAM[gram_prec.upper()] if isinstance(gram_prec, str) else gram_prec
+    _check(lib.pogs_gram(A.data_ptr(), m, n, n, prec, G.data_ptr(), _stream_ptr(stream)), "pogs_gram")
+    return G

@@ -1,15 +1,385 @@
-// Tensor-core Gram formation (placeholder until the tcgen05 path lands): reports
-// "unsupported" so the caller falls back to the FP32 SIMT GEMM.
+// Tensor-core Gram formation (Section 3.5: forming A^T A or A A^T dominates the setup) and a
+// general K-major tcgen05 GEMM used by it.
+//
+//   G = X X^T,  X = A^T (q = n, m >= n) or X = A (q = m, m < n),  lower 128 x 128 tiles only.
+//
+// Operands are packed once into K-major, zero-padded buffers (rows to 128, K to one TMA box):
+//   BF16:    X_hi = bf16(X)                                  one MMA per K step
+//   BF16x3:  X_hi = bf16(X), X_lo = bf16(X - X_hi)           hi.hi + hi.lo + lo.hi per K step
+//   TF32:    X rounded to TF32 (kept in 32-bit words)        one kind::tf32 MMA per K step
+// FP32 accumulation in tensor memory, drained in K chunks.  One CTA computes one 128 x 128
+// output tile: one thread streams X tiles with TMA through a multi-stage shared-memory ring
+// (128-byte swizzle), one thread issues tcgen05.mma, four warps read the accumulator back with
+// tcgen05.ld.
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cstdio>
+#include <cstring>
+
 #include "kernels.h"
+#include "tc.cuh"
 
 namespace pogs {
 
+namespace {
+
+constexpr int kTileRows = 128;   // M = N = 128 per CTA
+constexpr int kTileBytes = kTileRows * 128;   // one operand tile: 128 rows x 128 bytes
+
+enum TcMode : int { TC_BF16 = 0, TC_BF16X3 = 1, TC_TF32 = 2 };
+
+template <int MODE>
+struct TcCfg {
+  static constexpr int kOps = MODE == TC_BF16X3 ? 4 : 2;            // operand tiles per stage
+  static constexpr int kStages = MODE == TC_BF16X3 ? 3 : 6;
+  static constexpr int kStageBytes = kOps * kTileBytes;
+  static constexpr int kElemsPerBox = MODE == TC_TF32 ? 32 : 64;     // K elements per 128-byte row
+  static constexpr int kMmaPerBox = 4;                              // 32 bytes of K per MMA
+  static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024 + 256;
+};
+
+struct TcArgs {
+  int nkb;                 // K boxes
+  int tiles;               // tiles along M (and N)
+  int lower_only;          // enumerate the lower triangle of tiles
+  int64_t M, N;            // valid output extent
+  float* C;                // FP32 output (epi 0)
+  double* C64;             // FP64 output (epi 1: C64 += alpha * acc, lower triangle)
+  int64_t ldc;
+  double alpha;
+  int epi;
+  int* err;
+};
+
+// Warp roles (192 threads): warp 0 lane 0 -- TMA producer; warp 1 lane 0 -- MMA issuer;
+// warps 2..5 -- epilogue, warp w reading TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31 (rows of the
+// tile).  The tensor-core accumulator is double-buffered in TMEM (2 x 128 columns) and
+// restarted every kChunk K boxes: the epilogue warps drain each finished chunk into FP32
+// registers with round-to-nearest adds while the next chunk accumulates.  The accumulator
+// adds inside the tensor core are not round-to-nearest, so an undrained sum over K carries
+// a bias that grows linearly with K; chunking bounds it to the chunk length.
+constexpr int kChunkBoxes = 8;   // 512 BF16 / 256 TF32 elements of K per accumulator chunk
+
+template <int MODE>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mxh, const __grid_constant__ CUtensorMap mxl,
+                   const __grid_constant__ CUtensorMap myh, const __grid_constant__ CUtensorMap myl, TcArgs a) {
+  using Cfg = TcCfg<MODE>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStageBytes);
+  uint64_t* empty = full + Cfg::kStages;
+  uint64_t* acc_full = empty + Cfg::kStages;   // [2]: chunk in buffer b complete (MMA -> epilogue)
+  uint64_t* acc_empty = acc_full + 2;          // [2]: buffer b drained (epilogue -> MMA)
+  uint64_t* drain = acc_empty + 2;             // all MMAs of this CTA complete (teardown)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  int ti, tj;
+  if (a.lower_only) {
+    const int b = blockIdx.x;
+    int i = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= b) ++i;
+    while (i * (i + 1) / 2 > b) --i;
+    ti = i;
+    tj = b - i * (i + 1) / 2;
+  } else {
+    ti = blockIdx.x / a.tiles;
+    tj = blockIdx.x % a.tiles;
+  }
+  const int nchunks = (a.nkb + kChunkBoxes - 1) / kChunkBoxes;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < Cfg::kStages; ++s) {
+      tc::mbar_init(full + s, 1);
+      tc::mbar_init(empty + s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(acc_full + b, 1);
+      tc::mbar_init(acc_empty + b, 4);   // one arrival per epilogue warp
+    }
+    tc::mbar_init(drain, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tslot, 256);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer ---------------------------------------------------------------------
+      tc::prefetch_tmap(&mxh);
+      tc::prefetch_tmap(&myh);
+      if (MODE == TC_BF16X3) {
+        tc::prefetch_tmap(&mxl);
+        tc::prefetch_tmap(&myl);
+      }
+      for (int kb = 0; kb < a.nkb; ++kb) {
+        const int s = kb % Cfg::kStages;
+        const uint32_t ph = (uint32_t)(kb / Cfg::kStages) & 1u;
+        if (kb >= Cfg::kStages && !tc::mbar_wait(empty + s, ph ^ 1u)) {
+          atomicCAS(a.err, 0, POGS_ERR_TIMEOUT);
+          break;
+        }
+        uint8_t* st = smem + s * Cfg::kStageBytes;
+        tc::mbar_arrive_expect_tx(full + s, Cfg::kStageBytes);
+        const int x = kb * Cfg::kElemsPerBox;
+        tc::tma_load_2d(st, &mxh, x, ti * kTileRows, full + s);
+        tc::tma_load_2d(st + kTileBytes, &myh, x, tj * kTileRows, full + s);
+        if (MODE == TC_BF16X3) {
+          tc::tma_load_2d(st + 2 * kTileBytes, &mxl, x, ti * kTileRows, full + s);
+          tc::tma_load_2d(st + 3 * kTileBytes, &myl, x, tj * kTileRows, full + s);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ---------------------------------------------------------------------------
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int buf = c & 1;
+        const uint32_t d = tmem + (uint32_t)(buf * 128);
+        if (c >= 2 && !tc::mbar_wait(acc_empty + buf, (uint32_t)((c >> 1) - 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const int kb1 = min(a.nkb, (c + 1) * kChunkBoxes);
+        for (int kb = c * kChunkBoxes; kb < kb1; ++kb) {
+          const int s = kb % Cfg::kStages;
+          const uint32_t ph = (uint32_t)(kb / Cfg::kStages) & 1u;
+          if (!tc::mbar_wait(full + s, ph)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          uint8_t* st = smem + s * Cfg::kStageBytes;
+          const uint64_t ah = tc::desc_sw128(st), bh = tc::desc_sw128(st + kTileBytes);
+#pragma unroll
+          for (int k = 0; k < Cfg::kMmaPerBox; ++k) {
+            const uint32_t acc = (kb > c * kChunkBoxes || k > 0) ? 1u : 0u;
+            const uint64_t adv = 2ull * k;   // +32 bytes along K
+            if (MODE == TC_TF32) {
+              tc::mma_tf32(d, ah + adv, bh + adv, tc::kIdescTF32, acc);
+            } else {
+              tc::mma_bf16(d, ah + adv, bh + adv, tc::kIdescBF16, acc);
+              if (MODE == TC_BF16X3) {
+                const uint64_t al = tc::desc_sw128(st + 2 * kTileBytes), bl = tc::desc_sw128(st + 3 * kTileBytes);
+                tc::mma_bf16(d, ah + adv, bl + adv, tc::kIdescBF16, 1u);
+                tc::mma_bf16(d, al + adv, bh + adv, tc::kIdescBF16, 1u);
+              }
+            }
+          }
+          tc::mma_commit(empty + s);   // stage s free once these MMAs have read it
+        }
+        tc::mma_commit(acc_full + buf);  // chunk complete
+      }
+      if (!ok) atomicCAS(a.err, 0, POGS_ERR_TIMEOUT);
+      // every MMA this thread issued has finished before the tensor memory is released
+      tc::mma_commit(drain);
+      if (!tc::mbar_wait(drain, 0)) atomicCAS(a.err, 0, POGS_ERR_TIMEOUT);
+    }
+  } else {
+    // ---- epilogue warps: drain chunks, accumulate in FP32 (round to nearest), store -----------
+    const int wq = warp & 3;                      // TMEM lane quarter this warp may access
+    const int64_t row = (int64_t)ti * kTileRows + wq * 32 + lane;
+    float acc[128];
+#pragma unroll
+    for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int buf = c & 1;
+      if (!tc::mbar_wait(acc_full + buf, (uint32_t)(c >> 1) & 1u)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t taddr = tmem + (static_cast<uint32_t>(wq * 32) << 16) + (uint32_t)(buf * 128);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float v[32];
+        tc::tmem_ld32(taddr + q * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[q * 32 + i] = __fadd_rn(acc[q * 32 + i], v[i]);
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(acc_empty + buf)) : "memory");
+    }
+    if (!ok) {
+      if (lane == 0) atomicCAS(a.err, 0, POGS_ERR_TIMEOUT);
+    } else if (row < a.M) {
+      const int64_t col0 = (int64_t)tj * kTileRows;
+      if (a.epi == 0) {
+        float* out = a.C + row * a.ldc + col0;
+        if (col0 + 128 <= a.N && ((reinterpret_cast<uintptr_t>(out) & 15) == 0)) {
+#pragma unroll
+          for (int i = 0; i < 128; i += 4)
+            *reinterpret_cast<float4*>(out + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 128; ++i)
+            if (col0 + i < a.N) out[i] = acc[i];
+        }
+      } else {
+        double* out = a.C64 + row * a.ldc + col0;
+#pragma unroll
+        for (int i = 0; i < 128; ++i)
+          if (col0 + i < a.N && col0 + i <= row) out[i] += a.alpha * (double)acc[i];
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, 256);
+}
+
+// ---- operand packing ----------------------------------------------------------------------
+// X (rows x K): element (r, k) = TRANS ? src[k*ld + r] : src[r*ld + k]; written K-major to a
+// zero-padded [rp x Kp] buffer (BF16 hi/lo or TF32-rounded FP32).
+template <bool TRANS, int MODE>
+__global__ void pack_kernel(const float* __restrict__ src, int64_t ld, int64_t rows, int64_t K, int64_t Kp,
+                            void* hi, void* lo) {
+  __shared__ float t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    float v = 0.0f;
+    if (TRANS) {
+      const int64_t k = k0 + i, r = r0 + threadIdx.x;     // contiguous along r in the source
+      if (r < rows && k < K) v = src[k * ld + r];
+      t[i][threadIdx.x] = v;                               // t[k][r]
+    } else {
+      const int64_t r = r0 + i, k = k0 + threadIdx.x;
+      if (r < rows && k < K) v = src[r * ld + k];
+      t[threadIdx.x][i] = v;                               // t[k][r]
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i, k = k0 + threadIdx.x;
+    const float v = t[threadIdx.x][i];
+    const int64_t o = r * Kp + k;
+    if (MODE == TC_TF32) {
+      uint32_t u;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
+      static_cast<float*>(hi)[o] = __uint_as_float(u);
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      static_cast<__nv_bfloat16*>(hi)[o] = h;
+      if (MODE == TC_BF16X3) static_cast<__nv_bfloat16*>(lo)[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Map over a K-major [rows x inner] buffer with 128-row x 128-byte boxes, 128-byte swizzle.
+int make_map(CUtensorMap* map, const void* ptr, bool tf32, uint64_t inner, uint64_t rows) {
+  auto enc = encode_fn();
+  if (!enc) return -1;
+  const uint32_t esize = tf32 ? 4 : 2;
+  cuuint64_t gdim[2] = {inner, rows};
+  cuuint64_t gstride[1] = {inner * esize};
+  cuuint32_t box[2] = {128u / esize, (cuuint32_t)kTileRows};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r = enc(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                         const_cast<void*>(ptr), gdim, gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+template <int MODE>
+int launch_tc(const CUtensorMap& xh, const CUtensorMap& xl, const CUtensorMap& yh, const CUtensorMap& yl,
+              const TcArgs& a, int ntiles, cudaStream_t s) {
+  using Cfg = TcCfg<MODE>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem) !=
+        cudaSuccess)
+      return -1;
+    attr = true;
+  }
+  count_launch();
+  tc_gemm_kernel<MODE><<<ntiles, 192, Cfg::kSmem, s>>>(xh, xl, yh, yl, a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+// G (q x q, row-major, ld ldg; lower 128-tiles written) = X X^T with X = A^T (tall) or A (fat).
 int gram_tensor(int prec, const float* A, int64_t lda, int64_t m, int64_t n, bool tall, float* G, int64_t ldg,
                 void* scratch, size_t scratch_bytes, size_t* need_bytes, int* err, cudaStream_t s) {
-  (void)prec; (void)A; (void)lda; (void)m; (void)n; (void)tall; (void)G; (void)ldg; (void)scratch;
-  (void)scratch_bytes; (void)err; (void)s;
-  if (need_bytes) *need_bytes = 0;
-  return -1;
+  int mode;
+  if (prec == POGS_GRAM_BF16) mode = TC_BF16;
+  else if (prec == POGS_GRAM_BF16X3) mode = TC_BF16X3;
+  else if (prec == POGS_GRAM_TF32) mode = TC_TF32;
+  else return -1;
+  if (!encode_fn()) return -1;
+  const int64_t q = tall ? n : m, K = tall ? m : n;
+  const int64_t rp = round_up(q, kTileRows);
+  const int64_t kbox = mode == TC_TF32 ? 32 : 64;
+  const int64_t Kp = round_up(K, kbox);
+  const size_t esize = mode == TC_TF32 ? 4 : 2;
+  const size_t one = (size_t)rp * Kp * esize;
+  const size_t need = one * (mode == TC_BF16X3 ? 2 : 1) + 256;
+  if (need_bytes) *need_bytes = need;
+  if (!scratch) return 0;
+  if (scratch_bytes < need) return -1;
+  char* base = static_cast<char*>(scratch);
+  void* hi = base;
+  void* lo = mode == TC_BF16X3 ? base + one : nullptr;
+  dim3 pg((unsigned)(Kp / 32), (unsigned)(rp / 32)), pb(32, 8);
+  count_launch();
+  if (tall) {
+    if (mode == TC_BF16) pack_kernel<true, TC_BF16><<<pg, pb, 0, s>>>(A, lda, q, K, Kp, hi, lo);
+    else if (mode == TC_BF16X3) pack_kernel<true, TC_BF16X3><<<pg, pb, 0, s>>>(A, lda, q, K, Kp, hi, lo);
+    else pack_kernel<true, TC_TF32><<<pg, pb, 0, s>>>(A, lda, q, K, Kp, hi, lo);
+  } else {
+    if (mode == TC_BF16) pack_kernel<false, TC_BF16><<<pg, pb, 0, s>>>(A, lda, q, K, Kp, hi, lo);
+    else if (mode == TC_BF16X3) pack_kernel<false, TC_BF16X3><<<pg, pb, 0, s>>>(A, lda, q, K, Kp, hi, lo);
+    else pack_kernel<false, TC_TF32><<<pg, pb, 0, s>>>(A, lda, q, K, Kp, hi, lo);
+  }
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  CUtensorMap mh, ml;
+  memset(&ml, 0, sizeof(ml));
+  if (make_map(&mh, hi, mode == TC_TF32, (uint64_t)Kp, (uint64_t)rp) != 0) return -1;
+  if (mode == TC_BF16X3 && make_map(&ml, lo, false, (uint64_t)Kp, (uint64_t)rp) != 0) return -1;
+  if (mode != TC_BF16X3) ml = mh;
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nkb = (int)(Kp / kbox);
+  a.tiles = (int)(rp / kTileRows);
+  a.lower_only = 1;
+  a.M = q;
+  a.N = q;
+  a.C = G;
+  a.ldc = ldg;
+  a.alpha = 1.0;
+  a.epi = 0;
+  a.err = err;
+  const int ntiles = a.tiles * (a.tiles + 1) / 2;
+  if (mode == TC_BF16) return launch_tc<TC_BF16>(mh, ml, mh, ml, a, ntiles, s);
+  if (mode == TC_BF16X3) return launch_tc<TC_BF16X3>(mh, ml, mh, ml, a, ntiles, s);
+  return launch_tc<TC_TF32>(mh, ml, mh, ml, a, ntiles, s);
 }
 
 }  // namespace pogs

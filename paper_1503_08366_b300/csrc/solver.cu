@@ -867,3 +867,39 @@ int pogs_time_kernels(pogs_handle* h, int reps, double* ms, double* bytes) {
 }
 
 }  // extern "C"
+
+extern "C" int pogs_gram(const float* A, int64_t m, int64_t n, int64_t lda, int gram_prec, float* G, void* stream) {
+  if (!A || !G || m < 1 || n < 1 || lda < n || gram_prec < POGS_GRAM_BF16 || gram_prec > POGS_GRAM_FP32)
+    return POGS_ERR_ARG;
+  if (!is_device_ptr(A) || !is_device_ptr(G)) return POGS_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool tall = m >= n;
+  const int64_t q = tall ? n : m;
+  int* err = nullptr;
+  CK(cudaMalloc(&err, sizeof(int)));
+  CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+  int rc = 0;
+  if (gram_prec == POGS_GRAM_FP32) {
+    if (tall) gemm_f32(true, false, q, q, m, 1.0f, A, lda, A, lda, 0.0f, G, q, true, s);
+    else gemm_f32(false, true, q, q, n, 1.0f, A, lda, A, lda, 0.0f, G, q, true, s);
+  } else {
+    size_t need = 0;
+    rc = gram_tensor(gram_prec, A, lda, m, n, tall, G, q, nullptr, 0, &need, err, s);
+    void* ws = nullptr;
+    if (rc == 0 && cudaMalloc(&ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      rc = POGS_ERR_OOM;
+    }
+    if (rc == 0 && gram_tensor(gram_prec, A, lda, m, n, tall, G, q, ws, need, &need, err, s) != 0) rc = POGS_ERR_CUDA;
+    cudaStreamSynchronize(s);
+    if (ws) cudaFree(ws);
+  }
+  int herr = 0;
+  if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    rc = POGS_ERR_CUDA;
+  cudaFree(err);
+  if (rc == 0 && herr != 0) rc = herr;
+  if (rc == 0 && cudaGetLastError() != cudaSuccess) rc = POGS_ERR_CUDA;
+  return rc;
+}
