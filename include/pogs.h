@@ -188,6 +188,24 @@ int pogs_project(pogs_handle* hdl, const float* c, const float* d, float* x, flo
  * Allocates and frees its own scratch.  Errors: ARG, OOM, CUDA. */
 int pogs_gram(const float* A, int64_t m, int64_t n, int64_t lda, int gram_prec, float* G, void* stream);
 
+/* The same Gram formation as pogs_gram for callers that cannot allocate device memory at
+ * this point: processes whose device memory is owned by another allocator or admitted
+ * against a fixed budget, and latency-critical paths that cannot afford the implicit
+ * synchronisation of cudaMalloc/cudaFree.  (The paper has no counterpart; this is an
+ * interface convenience.)  Same arguments, results and errors as pogs_gram; it calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ * Scratch: one fixed 32 MiB device array inside the library, reserved on every device that
+ * loads it and held until the process exits.  Its first 256 bytes hold a status word; the
+ * rest holds the packed operands, rp * Kp * b bytes with rp = q rounded up to 128, Kp = the
+ * contraction length (m if m >= n, else n) rounded up to 64 (32 for TF32), and b = 2 for
+ * BF16, 4 for TF32 and BF16x3; POGS_GRAM_FP32 needs none.  Larger problems are rejected
+ * with POGS_ERR_CAPACITY before any device work.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every call
+ * shares the one array and leaves its last contents there: calls that overlap on the GPU
+ * (different streams or threads) race and must be serialised by the caller. */
+int pogs_gram_noalloc(const float* A, int64_t m, int64_t n, int64_t lda, int gram_prec, float* G, void* stream);
+
 /* ---- instrumentation ------------------------------------------------------------------ */
 
 /* Fill *r with the setup phase times (CUDA events on the setup stream), the Gram and

@@ -86,6 +86,8 @@ lib.pogs_time_kernels.argtypes = [_P, C.c_int, _P, _P]
 lib.pogs_time_kernels.restype = C.c_int
 lib.pogs_gram.argtypes = [_P, C.c_int64, C.c_int64, C.c_int64, C.c_int, _P, _P]
 lib.pogs_gram.restype = C.c_int
+lib.pogs_gram_noalloc.argtypes = [_P, C.c_int64, C.c_int64, C.c_int64, C.c_int, _P, _P]
+lib.pogs_gram_noalloc.restype = C.c_int
 lib.pogs_kernel_launches.argtypes = []
 lib.pogs_kernel_launches.restype = C.c_longlong
 
@@ -269,3 +271,12 @@ def pogs_gram(A, gram_prec="BF16X3", stream=None):
     prec = GRAM[gram_prec.upper()] if isinstance(gram_prec, str) else gram_prec
     _check(lib.pogs_gram(A.data_ptr(), m, n, n, prec, G.data_ptr(), _stream_ptr(stream)), "pogs_gram")
     return G
+
+
+def pogs_gram_noalloc(A, G, gram_prec="BF16X3", stream=None):
+    """pogs_gram into a caller-provided CUDA tensor G (q x q), using the library's fixed scratch."""
+    m, n = A.shape
+    prec = GRAM[gram_prec.upper()] if isinstance(gram_prec, str) else gram_prec
+    assert A.is_contiguous() and G.is_contiguous() and G.shape == (min(m, n), min(m, n))
+    return _check(lib.pogs_gram_noalloc(A.data_ptr(), m, n, n, prec, G.data_ptr(), _stream_ptr(stream)),
+                  "pogs_gram_noalloc")
