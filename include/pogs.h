@@ -157,6 +157,36 @@ int pogs_solve(pogs_handle* hdl, const pogs_fn* f, const pogs_fn* g, const pogs_
 /* Release everything the handle owns.  pogs_free(NULL) is a no-op. */
 void pogs_free(pogs_handle* hdl);
 
+/* ---- many independent instances ------------------------------------------------------ */
+
+/* One problem of a batch: A row-major m x n (lda >= n), host or device; f has m elements,
+ * g has n (same conventions as pogs_solve). */
+typedef struct {
+  const float* A;
+  int64_t m, n, lda;
+  pogs_fn f, g;
+} pogs_problem;
+
+/* Caller-owned outputs of one problem (host or device, each may be NULL) and its report. */
+typedef struct {
+  float *x, *y, *mu, *nu;
+  pogs_info info;
+} pogs_result;
+
+/* Solve `count` independent problems with the same parameters (each one is exactly the
+ * problem pogs_setup + pogs_solve would solve).  Problems with min(m, n) <= 512 run in one
+ * persistent kernel, one CTA per problem at a time taken from a device work queue, after a
+ * batched setup (one CTA per problem); larger ones run through the single-problem path.
+ * A problem's result does not depend on which other problems share the batch, on their
+ * order, or on the launch configuration (fixed block size and reduction order).  The launch
+ * configuration (grid, schedule order, shared-memory staging budget) is chosen by timing a
+ * few candidates on the first batch of a given size class (p->verbose > 1 prints them) and
+ * cached.  Returns 0 if every problem converged, 1 if some stopped at max_iter (see each
+ * out[i].info.status); negative on an error that stopped the batch.  Per-problem setup errors
+ * (ARG, NONFINITE, NUMERIC) are reported in out[i].info.status and do not stop the others. */
+int pogs_solve_batch(int count, const pogs_problem* probs, const pogs_params* p, pogs_result* out,
+                     void* stream);
+
 /* ---- step-level entry points (the same device code the solver runs) ---------------- */
 
 /* Elementwise parametric prox of Section 5 on device arrays of length k:

@@ -62,6 +62,15 @@ class pogs_setup_report(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pogs_problem(C.Structure):
+    _fields_ = [("A", C.c_void_p), ("m", C.c_int64), ("n", C.c_int64), ("lda", C.c_int64), ("f", pogs_fn),
+                ("g", pogs_fn)]
+
+
+class pogs_result(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("mu", C.c_void_p), ("nu", C.c_void_p), ("info", pogs_info)]
+
+
 _P = C.c_void_p
 lib.pogs_default_params.argtypes = [C.POINTER(pogs_params)]
 lib.pogs_default_params.restype = None
@@ -88,6 +97,8 @@ lib.pogs_gram.argtypes = [_P, C.c_int64, C.c_int64, C.c_int64, C.c_int, _P, _P]
 lib.pogs_gram.restype = C.c_int
 lib.pogs_gram_noalloc.argtypes = [_P, C.c_int64, C.c_int64, C.c_int64, C.c_int, _P, _P]
 lib.pogs_gram_noalloc.restype = C.c_int
+lib.pogs_solve_batch.argtypes = [C.c_int, C.POINTER(pogs_problem), C.POINTER(pogs_params), C.POINTER(pogs_result), _P]
+lib.pogs_solve_batch.restype = C.c_int
 lib.pogs_kernel_launches.argtypes = []
 lib.pogs_kernel_launches.restype = C.c_longlong
 
@@ -280,3 +291,26 @@ def pogs_gram_noalloc(A, G, gram_prec="BF16X3", stream=None):
     assert A.is_contiguous() and G.is_contiguous() and G.shape == (min(m, n), min(m, n))
     return _check(lib.pogs_gram_noalloc(A.data_ptr(), m, n, n, prec, G.data_ptr(), _stream_ptr(stream)),
                   "pogs_gram_noalloc")
+
+
+def pogs_solve_batch(problems, params: pogs_params | None = None, stream=None):
+    """problems: objects with A (m x n float32, host array or CUDA tensor), f and g (h, a..e).
+    Returns a list of (info, x, y, mu, nu) with host float32 outputs."""
+    keep: list = []
+    n_p = len(problems)
+    probs = (pogs_problem * max(1, n_p))()
+    res = (pogs_result * max(1, n_p))()
+    outs = []
+    for i, pb in enumerate(problems):
+        m, n = pb.A.shape
+        probs[i].A = _ptr(pb.A, np.float32, keep)
+        probs[i].m, probs[i].n, probs[i].lda = m, n, n
+        probs[i].f = make_fn(pb.f, keep)
+        probs[i].g = make_fn(pb.g, keep)
+        o = [np.empty(n, np.float32), np.empty(m, np.float32), np.empty(n, np.float32), np.empty(m, np.float32)]
+        outs.append(o)
+        res[i].x, res[i].y, res[i].mu, res[i].nu = (a.ctypes.data for a in o)
+    rc = lib.pogs_solve_batch(n_p, probs, C.byref(params) if params is not None else None, res,
+                              _stream_ptr(stream))
+    _check(rc, "pogs_solve_batch")
+    return [(res[i].info, *outs[i]) for i in range(n_p)]

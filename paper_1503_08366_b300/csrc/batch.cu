@@ -1,0 +1,610 @@
+// Batched graph-form ADMM: many independent small instances of uneven (m, n).
+//
+// Setup runs one CTA per instance (Algorithm 2 + Frobenius rescale, folding of D and E into
+// the parameters, Gram + I in FP64, blocked Cholesky, FP32 inverse factor).  The iteration is
+// a persistent kernel: each CTA takes the next instance from a device work queue and runs the
+// whole ADMM loop for it (Algorithm 1 + over-relaxation + Section 3.4 stopping + Algorithm 3)
+// with block-level synchronisation between the phases, then takes the next one.  An
+// instance's matrix and factor stay resident in L2 (or in shared memory when small enough)
+// across its iterations.
+//
+// Every instance is computed by one CTA of kBatchThreads threads with fixed loop and
+// reduction orders, so its result does not depend on which other instances share the batch,
+// on the grid size, on the schedule or on whether its matrix is staged in shared memory.
+#include <cstdio>
+
+#include "batch.h"
+#include "prox.cuh"
+
+namespace pogs {
+
+namespace {
+
+constexpr int NT = kBatchThreads;
+constexpr int NW = NT / 32;
+
+// Block-wide FP64 sums of NV values per thread, result in every thread (fixed order).
+template <int NV>
+__device__ __forceinline__ void bsum(double (&v)[NV], double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < NV; ++t) v[t] = warp_sum(v[t]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int t = 0; t < NV; ++t) sh[t * NW + wid] = v[t];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s += sh[t * NW + w];
+    v[t] = s;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Setup 1: Sinkhorn-Knopp (Algorithm 2, p = 2), Frobenius rescale (Section 4.1.2), A^ = D A E,
+// folded parameters (Eq. 12).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) bsetup_equil_kernel(BInst* insts, BCfg cfg, BOut* out) {
+  __shared__ double sh[4 * NW];
+  __shared__ int s_err;
+  BInst I = insts[blockIdx.x];
+  const int m = I.m, n = I.n, lda = I.lda, q = I.q;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* d = I.D;   // d, then D
+  float* e = I.E;   // e, then E
+  if (tid == 0) s_err = 0;
+  for (int j = tid; j < n; j += NT) e[j] = 1.0f;
+  for (int i = tid; i < m; i += NT) d[i] = 1.0f;
+  // non-finite input check
+  int bad = 0;
+  for (int i = 0; i < m; ++i)
+    for (int j = tid; j < n; j += NT)
+      if (!isfinite(I.A[(int64_t)i * lda + j])) bad = 1;
+  if (bad) atomicExch(&s_err, POGS_ERR_NONFINITE);
+  __syncthreads();
+  const double gamma = cfg.gamma_scale > 0 ? cfg.gamma_scale : (double)(m + n) * sqrt(1.1920928955078125e-07);
+  const float rreg = (float)(gamma / m), creg = (float)(gamma / n);
+  const int sweeps = cfg.equil ? cfg.sk_sweeps : 0;
+  double fro[1] = {0.0};
+  for (int s = 0; s < sweeps; ++s) {
+    for (int i = warp; i < m; i += NW) {
+      float acc = 0.0f;
+      for (int j = lane; j < n; j += 32) {
+        const float a = I.A[(int64_t)i * lda + j];
+        acc = fmaf(a * a, e[j], acc);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) d[i] = (float)n / (acc + rreg);
+    }
+    __syncthreads();
+    fro[0] = 0.0;
+    for (int j = tid; j < n; j += NT) {
+      float acc = 0.0f;
+      for (int i = 0; i < m; ++i) {
+        const float a = I.A[(int64_t)i * lda + j];
+        acc = fmaf(a * a, d[i], acc);
+      }
+      const float ej = (float)m / (acc + creg);
+      e[j] = ej;
+      fro[0] += (double)ej * (double)acc;
+    }
+    __syncthreads();
+  }
+  if (sweeps == 0) {
+    fro[0] = 0.0;
+    for (int j = tid; j < n; j += NT) {
+      float acc = 0.0f;
+      for (int i = 0; i < m; ++i) {
+        const float a = I.A[(int64_t)i * lda + j];
+        acc = fmaf(a, a, acc);
+      }
+      fro[0] += (double)acc;
+    }
+  }
+  bsum<1>(fro, sh);
+  const double sinv = 1.0 / sqrt(fro[0] / (double)q);
+  for (int i = tid; i < m; i += NT) d[i] = (float)sqrt((double)d[i] * sinv);
+  for (int j = tid; j < n; j += NT) e[j] = (float)sqrt((double)e[j] * sinv);
+  __syncthreads();
+  for (int i = 0; i < m; ++i)
+    for (int j = tid; j < n; j += NT) I.A[(int64_t)i * lda + j] *= d[i] * e[j];
+  // parameters of f^ (length m) and g^ (length n)
+  for (int k = tid; k < m + n; k += NT) {
+    const bool isf = k < m;
+    const int i = isf ? k : k - m;
+    const uint8_t* h0 = isf ? I.fh0 : I.gh0;
+    const float *a0 = isf ? I.fa0 : I.ga0, *b0 = isf ? I.fb0 : I.gb0, *c0 = isf ? I.fc0 : I.gc0;
+    const float *d0 = isf ? I.fd0 : I.gd0, *e0 = isf ? I.fe0 : I.ge0;
+    const int hv = h0[i];
+    const float av = a0 ? a0[i] : 1.0f, bv = b0 ? b0[i] : 0.0f, cv = c0 ? c0[i] : 1.0f;
+    const float dv = d0 ? d0[i] : 0.0f, ev = e0 ? e0[i] : 0.0f;
+    if (hv < 0 || hv > POGS_IND_BOX01 || !(av != 0.0f) || !(cv >= 0.0f) || !(ev >= 0.0f) || !isfinite(av) ||
+        !isfinite(bv) || !isfinite(cv) || !isfinite(dv) || !isfinite(ev))
+      atomicCAS(&s_err, 0, POGS_ERR_ARG);
+    const float sc = isf ? 1.0f / d[i] : e[i];
+    if (isf) {
+      I.fh[i] = (uint8_t)hv; I.fa[i] = av * sc; I.fb[i] = bv; I.fc[i] = cv; I.fd[i] = dv * sc; I.fe[i] = ev * sc * sc;
+    } else {
+      I.gh[i] = (uint8_t)hv; I.ga[i] = av * sc; I.gb[i] = bv; I.gc[i] = cv; I.gd[i] = dv * sc; I.ge[i] = ev * sc * sc;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) out[blockIdx.x].status = s_err;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Setup 2: H = I + G in FP64 (lower), G = A^T A (tall) or A A^T (fat), FP32 products, 32 x 32
+// tiles with 32-deep K chunks staged in shared memory.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) bsetup_gram_kernel(BInst* insts, BOut* out) {
+  __shared__ float Xs[32][33], Ys[32][33];
+  BInst I = insts[blockIdx.x];
+  if (out[blockIdx.x].status != 0) return;
+  const int q = I.q, K = I.tall ? I.m : I.n, lda = I.lda;
+  const int T = (q + 31) / 32;
+  const int tid = threadIdx.x;
+  const int r = tid >> 3, c4 = (tid & 7) * 4;
+  for (int t = 0; t < T * (T + 1) / 2; ++t) {
+    int ti = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    while (ti * (ti + 1) / 2 > t) --ti;
+    const int tj = t - ti * (ti + 1) / 2;
+    const int r0 = ti * 32, s0 = tj * 32;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 0; k0 < K; k0 += 32) {
+      for (int e = tid; e < 32 * 32; e += NT) {
+        const int kk = e >> 5, rr = e & 31;
+        float xv = 0.f, yv = 0.f;
+        if (I.tall) {   // X = A^T: X[row][k] = A[k][row], read along rows of A
+          if (k0 + kk < K && r0 + rr < q) xv = I.A[(int64_t)(k0 + kk) * lda + r0 + rr];
+          if (k0 + kk < K && s0 + rr < q) yv = I.A[(int64_t)(k0 + kk) * lda + s0 + rr];
+          Xs[kk][rr] = xv;
+          Ys[kk][rr] = yv;
+        } else {        // X = A: X[row][k] = A[row][k]
+          const int kk2 = e & 31, rr2 = e >> 5;
+          if (k0 + kk2 < K && r0 + rr2 < q) xv = I.A[(int64_t)(r0 + rr2) * lda + k0 + kk2];
+          if (k0 + kk2 < K && s0 + rr2 < q) yv = I.A[(int64_t)(s0 + rr2) * lda + k0 + kk2];
+          Xs[kk2][rr2] = xv;
+          Ys[kk2][rr2] = yv;
+        }
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < 32; ++kk) {
+        const float a = Xs[kk][r];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fmaf(a, Ys[kk][c4 + u], acc[u]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int gi = r0 + r, gj = s0 + c4 + u;
+      if (gi < q && gj < q && gj <= gi) I.H[(int64_t)gi * q + gj] = (double)acc[u] + (gi == gj ? 1.0 : 0.0);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Setup 3: right-looking blocked Cholesky of H (32-column panels): FP64 diagonal blocks and
+// panel solves; trailing update from the FP32-rounded panel in FP32 (mixed) or in FP64.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) bsetup_chol_kernel(BInst* insts, BOut* out, int mixed) {
+  extern __shared__ float Pf[];            // [q][33] FP32 panel
+  __shared__ double Ld[32][33], Xi[32][33];
+  __shared__ int s_err;
+  BInst I = insts[blockIdx.x];
+  if (out[blockIdx.x].status != 0) return;
+  const int q = I.q;
+  double* H = I.H;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_err = 0;
+  for (int k0 = 0; k0 < q; k0 += 32) {
+    const int nb = min(32, q - k0);
+    for (int e = tid; e < 32 * 32; e += NT) {
+      const int i = e >> 5, j = e & 31;
+      Ld[i][j] = (i < nb && j <= i) ? H[(int64_t)(k0 + i) * q + k0 + j] : 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int j = 0; j < nb; ++j) {
+        if (lane == 0) {
+          double djj = Ld[j][j];
+          if (!(djj > 0.0) || !isfinite(djj)) {
+            atomicCAS(&s_err, 0, POGS_ERR_NUMERIC);
+            djj = 1.0;
+          }
+          Ld[j][j] = sqrt(djj);
+        }
+        __syncwarp();
+        const double ljj = Ld[j][j];
+        for (int i = j + 1 + lane; i < nb; i += 32) Ld[i][j] /= ljj;
+        __syncwarp();
+        for (int i = j + 1 + lane; i < nb; i += 32)
+          for (int k = j + 1; k <= i; ++k) Ld[i][k] -= Ld[i][j] * Ld[k][j];
+        __syncwarp();
+      }
+      // inverse of the diagonal factor, one column per lane
+      if (lane < nb) {
+        const int c = lane;
+        for (int i = 0; i < nb; ++i) {
+          double v = 0.0;
+          if (i >= c) {
+            double acc = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) acc -= Ld[i][k] * Xi[k][c];
+            v = acc / Ld[i][i];
+          }
+          Xi[i][c] = v;
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < nb * nb; e += NT) {
+      const int i = e / nb, j = e % nb;
+      if (j <= i) H[(int64_t)(k0 + i) * q + k0 + j] = Ld[i][j];
+    }
+    // panel: rows below the block, P = H_panel L_kk^{-T} (FP64); FP32 copy for the update
+    const int R = q - k0 - nb;
+    for (int ii = tid; ii < R; ii += NT) {
+      double h[32];
+      double* row = H + (int64_t)(k0 + nb + ii) * q + k0;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) h[k] = k < nb ? row[k] : 0.0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (j < nb) {
+          double p = 0.0;
+          for (int k = 0; k <= j; ++k) p += h[k] * Xi[j][k];
+          row[j] = p;
+          Pf[ii * 33 + j] = (float)p;
+        }
+      }
+    }
+    __syncthreads();
+    // trailing update of the lower triangle
+    for (int ii = 0; ii < R; ++ii) {
+      double* hrow = H + (int64_t)(k0 + nb + ii) * q + k0 + nb;
+      for (int jj = tid; jj <= ii; jj += NT) {
+        if (mixed) {
+          float acc = 0.0f;
+          for (int k = 0; k < nb; ++k) acc = fmaf(Pf[ii * 33 + k], Pf[jj * 33 + k], acc);
+          hrow[jj] -= (double)acc;
+        } else {
+          const double* pi = H + (int64_t)(k0 + nb + ii) * q + k0;
+          const double* pj = H + (int64_t)(k0 + nb + jj) * q + k0;
+          double acc = 0.0;
+          for (int k = 0; k < nb; ++k) acc += pi[k] * pj[k];
+          hrow[jj] -= acc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && s_err != 0) out[blockIdx.x].status = s_err;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Setup 4: M = L^{-1} (FP32, dense lower, ld q), one column per thread by forward substitution
+// with FP64 accumulation.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) bsetup_inverse_kernel(BInst* insts, BOut* out) {
+  BInst I = insts[blockIdx.x];
+  if (out[blockIdx.x].status != 0) return;
+  const int q = I.q;
+  const double* L = I.H;
+  float* M = I.M;
+  for (int c = threadIdx.x; c < q; c += NT) {
+    for (int i = 0; i < c; ++i) M[(int64_t)i * q + c] = 0.0f;
+    M[(int64_t)c * q + c] = (float)(1.0 / L[(int64_t)c * q + c]);
+    for (int i = c + 1; i < q; ++i) {
+      const double* li = L + (int64_t)i * q;
+      double acc = 0.0;
+      for (int k = c; k < i; ++k) acc -= li[k] * (double)M[(int64_t)k * q + c];
+      M[(int64_t)i * q + c] = (float)(acc / li[i]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Iteration phases (one CTA).
+// ---------------------------------------------------------------------------------------------
+struct Loop {
+  double rho, pend;
+  int k, l, u, done, status;
+};
+
+__device__ __forceinline__ void zero_state(const BInst& I) {
+  for (int j = threadIdx.x; j < I.n; j += NT) { I.x[j] = 0.0f; I.xt[j] = 0.0f; }
+  for (int i = threadIdx.x; i < I.m; i += NT) { I.y[i] = 0.0f; I.yt[i] = 0.0f; }
+}
+
+// Row dots u = A [x1, x2] for the rows of the instance (warp per row).
+__device__ __forceinline__ void rowdots(const float* A, int lda, int m, int n, const float* x1, const float* x2,
+                                        int i, float& u1, float& u2) {
+  const int lane = threadIdx.x & 31;
+  const float* a = A + (int64_t)i * lda;
+  float s1 = 0.f, s2 = 0.f;
+  for (int j = lane; j < n; j += 32) {
+    const float av = a[j];
+    s1 = fmaf(av, x1[j], s1);
+    s2 = fmaf(av, x2[j], s2);
+  }
+  u1 = warp_sum(s1);
+  u2 = warp_sum(s2);
+}
+
+// Column sums t_j = sum_i A_ij v_i for three vectors (thread per column).
+__device__ __forceinline__ void colsum3(const float* A, int lda, int m, int j, const float* v1, const float* v2,
+                                        const float* v3, float& t1, float& t2, float& t3) {
+  float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  for (int i = 0; i < m; ++i) {
+    const float av = A[(int64_t)i * lda + j];
+    s1 = fmaf(av, v1[i], s1);
+    s2 = fmaf(av, v2[i], s2);
+    s3 = fmaf(av, v3[i], s3);
+  }
+  t1 = s1;
+  t2 = s2;
+  t3 = s3;
+}
+
+__device__ void run_instance(const BInst& I, const BCfg& cfg, BOut* out, float* smemA, double* red, Loop* L) {
+  const int m = I.m, n = I.n, q = I.q, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* A = I.A;
+  int lda = I.lda;
+  if (I.stage_smem) {   // same values, same loop order: only where they are read from changes
+    for (int i = 0; i < m; ++i)
+      for (int j = tid; j < n; j += NT) smemA[i * n + j] = I.A[(int64_t)i * I.lda + j];
+    A = smemA;
+    lda = n;
+  }
+  zero_state(I);
+  if (tid == 0) {
+    L->rho = cfg.rho0;
+    L->pend = 1.0;
+    L->k = L->l = L->u = L->done = 0;
+    L->status = POGS_MAX_ITER;
+  }
+  __syncthreads();
+  const float alpha = (float)cfg.alpha;
+  while (true) {
+    const float rho = (float)L->rho, pend = (float)L->pend;
+    const bool rescale = pend != 1.0f;
+    // ---- prox step (Algorithm 1, Section 3.2, 3.3) ----
+    double pv[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = tid; k < n + m; k += NT) {
+      if (k < n) {
+        const int j = k;
+        const float xtj = pend * I.xt[j], xj = I.x[j], v = xj - xtj;
+        if (rescale) I.xt[j] = xtj;
+        const int h = I.gh[j];
+        const float a = I.ga[j], b = I.gb[j], c = I.gc[j], d = I.gd[j], e = I.ge[j];
+        const float xhj = prox_param(h, a, b, c, d, e, rho, v);
+        const float muj = -rho * (xhj - v);
+        I.xh[j] = xhj;
+        I.cx[j] = alpha * xhj + (1.0f - alpha) * xj;
+        I.mu[j] = muj;
+        pv[0] += (double)muj * muj;
+        pv[1] += (double)xhj * muj;
+        pv[2] += (double)f_param(h, a, b, c, d, e, xhj);
+      } else {
+        const int i = k - n;
+        const float yti = pend * I.yt[i], yi = I.y[i], v = yi - yti;
+        if (rescale) I.yt[i] = yti;
+        const int h = I.fh[i];
+        const float a = I.fa[i], b = I.fb[i], c = I.fc[i], d = I.fd[i], e = I.fe[i];
+        const float yhi = prox_param(h, a, b, c, d, e, rho, v);
+        const float nui = -rho * (yhi - v);
+        I.yh[i] = yhi;
+        I.dy[i] = alpha * yhi + (1.0f - alpha) * yi;
+        I.nu[i] = nui;
+        pv[3] += (double)yhi * yhi;
+        pv[4] += (double)yhi * nui;
+        pv[5] += (double)f_param(h, a, b, c, d, e, yhi);
+      }
+    }
+    bsum<6>(pv, red);   // includes the barrier that publishes the prox outputs
+    double rs[4] = {0, 0, 0, 0};   // primal^2, primal_u^2, dual^2, dual_u^2
+    if (I.tall) {
+      // r = c + A^T d ; x~ = -A^T y~ ; dual residual (A^T nu + mu)
+      for (int j = tid; j < n; j += NT) {
+        float t1, t2, t3;
+        colsum3(A, lda, m, j, I.dy, I.nu, I.yt, t1, t2, t3);
+        I.r[j] = I.cx[j] + t1;
+        I.xt[j] = -t3;
+        const float dr = t2 + I.mu[j];
+        rs[2] += (double)dr * dr;
+        const float du = dr / I.E[j];
+        rs[3] += (double)du * du;
+      }
+      __syncthreads();
+      for (int i = warp; i < q; i += NW) {   // z = M r
+        const float* mi = I.M + (int64_t)i * q;
+        float s = 0.f;
+        for (int k = lane; k <= i; k += 32) s = fmaf(mi[k], I.r[k], s);
+        s = warp_sum(s);
+        if (lane == 0) I.z[i] = s;
+      }
+      __syncthreads();
+      for (int j = tid; j < q; j += NT) {     // x = M^T z ; x~ += c - x
+        float s = 0.f;
+        for (int i = j; i < q; ++i) s = fmaf(I.M[(int64_t)i * q + j], I.z[i], s);
+        I.x[j] = s;
+        I.xt[j] += I.cx[j] - s;
+      }
+      __syncthreads();
+      for (int i = warp; i < m; i += NW) {    // y = A x, w = A x^ ; y~ += d - y ; primal residual
+        float u1, u2;
+        rowdots(A, lda, m, n, I.x, I.xh, i, u1, u2);
+        if (lane == 0) {
+          I.y[i] = u1;
+          I.yt[i] += I.dy[i] - u1;
+          const float pr = u2 - I.yh[i];
+          rs[0] += (double)pr * pr;
+          const float pu = pr / I.D[i];
+          rs[1] += (double)pu * pu;
+        }
+      }
+    } else {
+      for (int i = warp; i < m; i += NW) {    // r = A c - d ; primal residual
+        float u1, u2;
+        rowdots(A, lda, m, n, I.cx, I.xh, i, u1, u2);
+        if (lane == 0) {
+          I.r[i] = u1 - I.dy[i];
+          const float pr = u2 - I.yh[i];
+          rs[0] += (double)pr * pr;
+          const float pu = pr / I.D[i];
+          rs[1] += (double)pu * pu;
+        }
+      }
+      __syncthreads();
+      for (int i = warp; i < q; i += NW) {    // z = M r
+        const float* mi = I.M + (int64_t)i * q;
+        float s = 0.f;
+        for (int k = lane; k <= i; k += 32) s = fmaf(mi[k], I.r[k], s);
+        s = warp_sum(s);
+        if (lane == 0) I.z[i] = s;
+      }
+      __syncthreads();
+      for (int i = tid; i < q; i += NT) {     // v = M^T z ; y = d + v ; y~ += d - y ; w = d - y
+        float s = 0.f;
+        for (int k = i; k < q; ++k) s = fmaf(I.M[(int64_t)k * q + i], I.z[k], s);
+        const float d = I.dy[i], yp = d + s;
+        I.y[i] = yp;
+        I.yt[i] += d - yp;
+        I.w[i] = d - yp;
+      }
+      __syncthreads();
+      for (int j = tid; j < n; j += NT) {     // x = c + A^T w ; x~ = -A^T y~ ; dual residual
+        float t1, t2, t3;
+        colsum3(A, lda, m, j, I.w, I.nu, I.yt, t1, t2, t3);
+        const float c = I.cx[j], xp = c + t1;
+        I.x[j] = xp;
+        I.xt[j] = -t3;
+        const float dr = t2 + I.mu[j];
+        rs[2] += (double)dr * dr;
+        const float du = dr / I.E[j];
+        rs[3] += (double)du * du;
+      }
+    }
+    bsum<4>(rs, red);
+    // ---- stopping test (Section 3.4 + gap) and Algorithm 3 ----
+    if (tid == 0) {
+      const double r_pri = sqrt(rs[0]), r_dual = sqrt(rs[2]);
+      const double eps_pri = cfg.abs_tol + cfg.rel_tol * sqrt(pv[3]);
+      const double eps_dual = cfg.abs_tol + cfg.rel_tol * sqrt(pv[0]);
+      const double gap = pv[4] + pv[1], obj = pv[5] + pv[2];
+      const double eps_gap = cfg.abs_tol + cfg.rel_tol * fabs(obj);
+      const int k = L->k;
+      L->k = k + 1;
+      int done = 0;
+      if (!isfinite(r_pri) || !isfinite(r_dual) || !isfinite(gap) || !isfinite(obj)) {
+        L->status = POGS_ERR_NONFINITE;
+        done = 1;
+      } else if (r_pri < eps_pri && r_dual < eps_dual && (!cfg.gap_stop || fabs(gap) < eps_gap)) {
+        L->status = POGS_OK;
+        done = 1;
+      } else if (k + 1 >= cfg.max_iter) {
+        L->status = POGS_MAX_ITER;
+        done = 1;
+      }
+      double pend_new = 1.0;
+      if (!done && cfg.adaptive) {
+        const double rho0 = L->rho;
+        double rho1 = rho0;
+        if (r_dual < eps_dual && cfg.tau * k > L->l) {
+          rho1 = cfg.delta * rho0;
+          L->u = k;
+        } else if (r_pri < eps_pri && cfg.tau * k > L->u) {
+          rho1 = rho0 / cfg.delta;
+          L->l = k;
+        }
+        pend_new = rho0 / rho1;
+        L->rho = rho1;
+      }
+      L->pend = pend_new;
+      L->done = done;
+      if (done) {
+        BOut o;
+        o.status = L->status;
+        o.iters = L->k;
+        o.rho = L->rho;
+        o.r_pri = r_pri;
+        o.r_dual = r_dual;
+        o.eps_pri = eps_pri;
+        o.eps_dual = eps_dual;
+        o.gap = gap;
+        o.obj = obj;
+        o.r_pri_u = sqrt(rs[1]);
+        o.r_dual_u = sqrt(rs[3]);
+        *out = o;
+      }
+    }
+    __syncthreads();
+    if (L->done) break;
+  }
+  // returned tuple in the original variables (Section 5)
+  for (int j = tid; j < n; j += NT) {
+    I.ox[j] = I.E[j] * I.xh[j];
+    I.omu[j] = I.mu[j] / I.E[j];
+  }
+  for (int i = tid; i < m; i += NT) {
+    I.oy[i] = I.yh[i] / I.D[i];
+    I.onu[i] = I.D[i] * I.nu[i];
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(NT) batch_admm_kernel(BInst* insts, int count, BCfg cfg, BOut* out,
+                                                       int* queue, const int* order) {
+  extern __shared__ float smemA[];
+  __shared__ double red[6 * NW];
+  __shared__ Loop L;
+  __shared__ int s_idx;
+  while (true) {
+    if (threadIdx.x == 0) s_idx = atomicAdd(queue, 1);
+    __syncthreads();
+    const int pos = s_idx;
+    __syncthreads();
+    if (pos >= count) break;
+    const int idx = order ? order[pos] : pos;
+    if (out[idx].status != 0 && out[idx].iters == 0) continue;   // setup failed: reported as is
+    run_instance(insts[idx], cfg, out + idx, smemA, red, &L);
+  }
+}
+
+}  // namespace
+
+int batch_max_smem() { return 200 * 1024; }
+
+int batch_setup(BInst* d_inst, int count, const BCfg& cfg, BOut* d_out, cudaStream_t s) {
+  if (count <= 0) return 0;
+  count_launch(4);
+  bsetup_equil_kernel<<<count, NT, 0, s>>>(d_inst, cfg, d_out);
+  bsetup_gram_kernel<<<count, NT, 0, s>>>(d_inst, d_out);
+  const int chol_smem = 512 * 33 * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(bsetup_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, chol_smem);
+    cudaFuncSetAttribute(batch_admm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_max_smem());
+    attr = true;
+  }
+  bsetup_chol_kernel<<<count, NT, chol_smem, s>>>(d_inst, d_out, cfg.mixed_chol);
+  bsetup_inverse_kernel<<<count, NT, 0, s>>>(d_inst, d_out);
+  return cudaGetLastError() == cudaSuccess ? 0 : POGS_ERR_CUDA;
+}
+
+int batch_iterate(BInst* d_inst, int count, const BCfg& cfg, BOut* d_out, int* d_queue, const int* d_order,
+                  int grid, int smem_bytes, cudaStream_t s) {
+  if (count <= 0) return 0;
+  count_launch();
+  batch_admm_kernel<<<grid, NT, smem_bytes, s>>>(d_inst, count, cfg, d_out, d_queue, d_order);
+  return cudaGetLastError() == cudaSuccess ? 0 : POGS_ERR_CUDA;
+}
+
+}  // namespace pogs

@@ -1,0 +1,42 @@
+// Batched many-instance solver: device descriptors shared by batch.cu and the server.
+#pragma once
+#include "common.cuh"
+
+namespace pogs {
+
+// One instance, all pointers into a device arena.  Pre-conditioned data (A^ = D A E, folded
+// function parameters) and the FP32 inverse factor M = L^{-1} (dense lower triangle, ld q).
+struct BInst {
+  int m, n, lda, q, tall, stage_smem;
+  float* A;
+  float* M;
+  double* H;            // FP64 q x q factorization workspace
+  float *D, *E;
+  const uint8_t *fh0, *gh0;                     // raw parameters (as given)
+  const float *fa0, *fb0, *fc0, *fd0, *fe0, *ga0, *gb0, *gc0, *gd0, *ge0;
+  uint8_t *fh, *gh;                             // folded parameters
+  float *fa, *fb, *fc, *fd, *fe, *ga, *gb, *gc, *gd, *ge;
+  float *x, *y, *xt, *yt, *xh, *yh, *cx, *dy, *mu, *nu, *r, *z, *w;
+  float *ox, *oy, *omu, *onu;                   // unscaled outputs
+};
+
+// Per-instance report (mirrors pogs_info).
+struct BOut {
+  int status, iters;
+  double rho, r_pri, r_dual, eps_pri, eps_dual, gap, obj, r_pri_u, r_dual_u;
+};
+
+struct BCfg {
+  double abs_tol, rel_tol, rho0, alpha, delta, tau, gamma_scale;
+  int max_iter, gap_stop, adaptive, sk_sweeps, equil, mixed_chol;
+};
+
+constexpr int kBatchThreads = 256;   // fixed: per-instance arithmetic never depends on the batch
+
+// setup (one CTA per instance) and the persistent iteration kernel
+int batch_setup(BInst* d_inst, int count, const BCfg& cfg, BOut* d_out, cudaStream_t s);
+int batch_iterate(BInst* d_inst, int count, const BCfg& cfg, BOut* d_out, int* d_queue, const int* d_order,
+                  int grid, int smem_bytes, cudaStream_t s);
+int batch_max_smem();
+
+}  // namespace pogs

@@ -1,0 +1,356 @@
+// pogs_solve_batch: host side of the batched solver (arena layout, ingest, launch-configuration
+// autotuning, CUDA-graph launch of the persistent kernel, results).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <tuple>
+#include <vector>
+
+#include "batch.h"
+#include "kernels.h"
+
+using namespace pogs;
+
+namespace {
+
+constexpr int kMaxBatchQ = 512;   // batched setup keeps a q x 32 FP32 panel in shared memory
+
+bool is_dev(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Launch configurations the tuner chooses between; none changes per-instance arithmetic.
+struct LaunchCfg {
+  int grid_mult;     // resident CTAs per SM
+  int smem;          // shared-memory budget for staging an instance's matrix (0: stream from L2)
+  int largest_first; // schedule order
+};
+const LaunchCfg kCandidates[] = {{1, 200 * 1024, 1}, {2, 100 * 1024, 1}, {2, 0, 1},
+                                 {4, 0, 1},          {3, 64 * 1024, 1},  {2, 100 * 1024, 0}};
+std::map<std::tuple<int, int, int>, LaunchCfg> g_tuned;
+std::mutex g_tuned_mu;
+
+#define BCK(call)                                   \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) {                        \
+      cudaGetLastError();                           \
+      rc = (e_ == cudaErrorMemoryAllocation) ? POGS_ERR_OOM : POGS_ERR_CUDA; \
+      goto done;                                    \
+    }                                               \
+  } while (0)
+
+}  // namespace
+
+extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs_params* p, pogs_result* out,
+                                void* stream) {
+  if (count < 0 || (count > 0 && (!probs || !out))) return POGS_ERR_ARG;
+  pogs_params def;
+  pogs_default_params(&def);
+  if (!p) p = &def;
+  for (int i = 0; i < count; ++i) {
+    const pogs_problem& pr = probs[i];
+    if (!pr.A || pr.m < 1 || pr.n < 1 || pr.lda < pr.n || !pr.f.h || !pr.g.h) return POGS_ERR_ARG;
+    memset(&out[i].info, 0, sizeof(pogs_info));
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<int> small, large;
+  for (int i = 0; i < count; ++i) (std::min(probs[i].m, probs[i].n) <= kMaxBatchQ ? small : large).push_back(i);
+  int worst = 0;
+  // ---- large problems: the single-problem path -------------------------------------------
+  for (int i : large) {
+    pogs_handle* h = nullptr;
+    const pogs_problem& pr = probs[i];
+    int rc = pogs_setup(pr.A, pr.m, pr.n, pr.lda, 'R', p, stream, &h);
+    if (rc == 0) {
+      rc = pogs_solve(h, &pr.f, &pr.g, p, out[i].x, out[i].y, out[i].mu, out[i].nu, &out[i].info);
+      pogs_free(h);
+    }
+    out[i].info.status = rc;
+    if (rc == POGS_MAX_ITER) worst = std::max(worst, 1);
+    if (rc < 0 && rc != POGS_ERR_ARG && rc != POGS_ERR_NONFINITE && rc != POGS_ERR_NUMERIC) return rc;
+  }
+  if (small.empty()) return worst;
+
+  // ---- small problems: arena layout (inputs first, contiguous, so host inputs go in one copy)
+  const int ns = (int)small.size();
+  std::vector<BInst> inst(ns);
+  std::vector<size_t> offA(ns), offM(ns), offH(ns), offD(ns), offE(ns), offIn(ns * 12), offF(ns * 12), offV(ns);
+  size_t cur = 0;
+  for (int k = 0; k < ns; ++k) {
+    const pogs_problem& pr = probs[small[k]];
+    const int lda4 = (int)round_up(pr.n, 4);
+    offA[k] = cur;
+    cur = al(cur + (size_t)pr.m * lda4 * 4);
+    for (int t = 0; t < 12; ++t) {   // raw f: h,a..e (m) then g: h,a..e (n)
+      const int64_t len = t < 6 ? pr.m : pr.n;
+      offIn[k * 12 + t] = cur;
+      cur = al(cur + (size_t)len * ((t % 6) == 0 ? 1 : 4));
+    }
+  }
+  const size_t in_end = cur;
+  for (int k = 0; k < ns; ++k) {
+    const pogs_problem& pr = probs[small[k]];
+    const int64_t q = std::min(pr.m, pr.n), vlen = std::max(pr.m, pr.n);
+    offM[k] = cur;
+    cur = al(cur + (size_t)q * q * 4);
+    offH[k] = cur;
+    cur = al(cur + (size_t)q * q * 8);
+    offD[k] = cur;
+    cur = al(cur + (size_t)pr.m * 4);
+    offE[k] = cur;
+    cur = al(cur + (size_t)pr.n * 4);
+    for (int t = 0; t < 12; ++t) {
+      const int64_t len = t < 6 ? pr.m : pr.n;
+      offF[k * 12 + t] = cur;
+      cur = al(cur + (size_t)len * ((t % 6) == 0 ? 1 : 4));
+    }
+    offV[k] = cur;
+    cur = al(cur + (size_t)17 * vlen * 4);
+  }
+  const size_t total = cur;
+
+  int rc = 0;
+  char* arena = nullptr;
+  BInst* d_inst = nullptr;
+  BOut* d_out = nullptr;
+  int *d_queue = nullptr, *d_order = nullptr;
+  std::vector<char> stage;
+  std::vector<BOut> hout(ns);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap = nullptr;
+  BCfg cfg;
+  LaunchCfg lc = kCandidates[0];
+  int num_sms = 148, dev = 0;
+  std::vector<int> order_big(ns), order_in(ns);
+  bool any_host_in = false;
+  BCK(cudaMalloc(&arena, total));
+  BCK(cudaMalloc(&d_inst, sizeof(BInst) * ns));
+  BCK(cudaMalloc(&d_out, sizeof(BOut) * ns));
+  BCK(cudaMalloc(&d_queue, sizeof(int)));
+  BCK(cudaMalloc(&d_order, sizeof(int) * ns));
+  BCK(cudaMemsetAsync(d_out, 0, sizeof(BOut) * ns, s));
+  // ---- ingest -------------------------------------------------------------------------------
+  for (int k = 0; k < ns && !any_host_in; ++k) any_host_in = !is_dev(probs[small[k]].A);
+  if (any_host_in) stage.assign(in_end, 0);
+  for (int k = 0; k < ns; ++k) {
+    const pogs_problem& pr = probs[small[k]];
+    const int lda4 = (int)round_up(pr.n, 4);
+    if (is_dev(pr.A)) {
+      BCK(cudaMemcpy2DAsync(arena + offA[k], (size_t)lda4 * 4, pr.A, (size_t)pr.lda * 4, (size_t)pr.n * 4, pr.m,
+                            cudaMemcpyDeviceToDevice, s));
+    } else {
+      for (int64_t i = 0; i < pr.m; ++i)
+        memcpy(stage.data() + offA[k] + (size_t)i * lda4 * 4, pr.A + i * pr.lda, (size_t)pr.n * 4);
+    }
+    const void* src[12] = {pr.f.h, pr.f.a, pr.f.b, pr.f.c, pr.f.d, pr.f.e, pr.g.h, pr.g.a, pr.g.b, pr.g.c, pr.g.d, pr.g.e};
+    for (int t = 0; t < 12; ++t) {
+      if (!src[t]) continue;
+      const size_t bytes = (size_t)(t < 6 ? pr.m : pr.n) * ((t % 6) == 0 ? 1 : 4);
+      if (is_dev(src[t])) {
+        BCK(cudaMemcpyAsync(arena + offIn[k * 12 + t], src[t], bytes, cudaMemcpyDeviceToDevice, s));
+      } else {
+        if (stage.empty()) stage.assign(in_end, 0);
+        memcpy(stage.data() + offIn[k * 12 + t], src[t], bytes);
+      }
+    }
+  }
+  if (!stage.empty()) {
+    // inputs that came from the device were copied already; copy the host ones region by region
+    for (int k = 0; k < ns; ++k) {
+      const pogs_problem& pr = probs[small[k]];
+      const int lda4 = (int)round_up(pr.n, 4);
+      if (!is_dev(pr.A))
+        BCK(cudaMemcpyAsync(arena + offA[k], stage.data() + offA[k], (size_t)pr.m * lda4 * 4, cudaMemcpyHostToDevice,
+                            s));
+      const void* src[12] = {pr.f.h, pr.f.a, pr.f.b, pr.f.c, pr.f.d, pr.f.e, pr.g.h, pr.g.a, pr.g.b, pr.g.c, pr.g.d, pr.g.e};
+      for (int t = 0; t < 12; ++t)
+        if (src[t] && !is_dev(src[t]))
+          BCK(cudaMemcpyAsync(arena + offIn[k * 12 + t], stage.data() + offIn[k * 12 + t],
+                              (size_t)(t < 6 ? pr.m : pr.n) * ((t % 6) == 0 ? 1 : 4), cudaMemcpyHostToDevice, s));
+    }
+  }
+  for (int k = 0; k < ns; ++k) {
+    const pogs_problem& pr = probs[small[k]];
+    BInst& I = inst[k];
+    memset(&I, 0, sizeof(I));
+    I.m = (int)pr.m;
+    I.n = (int)pr.n;
+    I.lda = (int)round_up(pr.n, 4);
+    I.q = (int)std::min(pr.m, pr.n);
+    I.tall = pr.m >= pr.n;
+    I.A = reinterpret_cast<float*>(arena + offA[k]);
+    I.M = reinterpret_cast<float*>(arena + offM[k]);
+    I.H = reinterpret_cast<double*>(arena + offH[k]);
+    I.D = reinterpret_cast<float*>(arena + offD[k]);
+    I.E = reinterpret_cast<float*>(arena + offE[k]);
+    const void* src[12] = {pr.f.h, pr.f.a, pr.f.b, pr.f.c, pr.f.d, pr.f.e, pr.g.h, pr.g.a, pr.g.b, pr.g.c, pr.g.d, pr.g.e};
+    auto in = [&](int t) -> void* { return src[t] ? (void*)(arena + offIn[k * 12 + t]) : nullptr; };
+    I.fh0 = (const uint8_t*)in(0); I.fa0 = (const float*)in(1); I.fb0 = (const float*)in(2);
+    I.fc0 = (const float*)in(3); I.fd0 = (const float*)in(4); I.fe0 = (const float*)in(5);
+    I.gh0 = (const uint8_t*)in(6); I.ga0 = (const float*)in(7); I.gb0 = (const float*)in(8);
+    I.gc0 = (const float*)in(9); I.gd0 = (const float*)in(10); I.ge0 = (const float*)in(11);
+    auto fo = [&](int t) { return arena + offF[k * 12 + t]; };
+    I.fh = (uint8_t*)fo(0); I.fa = (float*)fo(1); I.fb = (float*)fo(2); I.fc = (float*)fo(3); I.fd = (float*)fo(4);
+    I.fe = (float*)fo(5);
+    I.gh = (uint8_t*)fo(6); I.ga = (float*)fo(7); I.gb = (float*)fo(8); I.gc = (float*)fo(9); I.gd = (float*)fo(10);
+    I.ge = (float*)fo(11);
+    const int64_t vlen = std::max(pr.m, pr.n);
+    float* v = reinterpret_cast<float*>(arena + offV[k]);
+    float** vecs[] = {&I.x, &I.y, &I.xt, &I.yt, &I.xh, &I.yh, &I.cx, &I.dy, &I.mu, &I.nu, &I.r, &I.z, &I.w,
+                      &I.ox, &I.oy, &I.omu, &I.onu};
+    for (int t = 0; t < 17; ++t) *vecs[t] = v + (size_t)t * vlen;
+  }
+  // ---- configuration ------------------------------------------------------------------------
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.abs_tol = p->abs_tol;
+  cfg.rel_tol = p->rel_tol;
+  cfg.rho0 = p->rho0;
+  cfg.alpha = p->alpha;
+  cfg.delta = p->delta;
+  cfg.tau = p->tau;
+  cfg.gamma_scale = p->gamma;
+  cfg.max_iter = p->max_iter;
+  cfg.gap_stop = p->gap_stop;
+  cfg.adaptive = p->adaptive_rho;
+  cfg.sk_sweeps = p->sk_sweeps;
+  cfg.equil = p->equil;
+  cfg.mixed_chol = p->chol_prec == POGS_CHOL_MIXED;
+  BCK(cudaGetDevice(&dev));
+  BCK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  std::iota(order_in.begin(), order_in.end(), 0);
+  order_big = order_in;
+  std::stable_sort(order_big.begin(), order_big.end(), [&](int a, int b) {
+    return (int64_t)inst[a].m * inst[a].n > (int64_t)inst[b].m * inst[b].n;
+  });
+  BCK(cudaMemcpyAsync(d_inst, inst.data(), sizeof(BInst) * ns, cudaMemcpyHostToDevice, s));
+  rc = batch_setup(d_inst, ns, cfg, d_out, s);
+  if (rc != 0) goto done;
+  {
+    // size class of this batch: log2 of the count, of the largest q and of the mean m n
+    double mn = 0;
+    int qmax = 0;
+    for (auto& I : inst) {
+      mn += (double)I.m * I.n;
+      qmax = std::max(qmax, I.q);
+    }
+    const auto key = std::make_tuple((int)std::log2(ns + 1.0), (int)std::log2(qmax + 1.0), (int)std::log2(mn / ns + 1.0));
+    bool have = false;
+    {
+      std::lock_guard<std::mutex> g(g_tuned_mu);
+      auto it = g_tuned.find(key);
+      if (it != g_tuned.end()) {
+        lc = it->second;
+        have = true;
+      }
+    }
+    if (!have && ns >= 32) {
+      // time each candidate on this batch: 20 iterations of every instance, stopping disabled
+      BCfg tc = cfg;
+      tc.max_iter = std::min(20, cfg.max_iter);
+      tc.abs_tol = 0.0;
+      tc.rel_tol = 0.0;
+      cudaEvent_t e0, e1;
+      BCK(cudaEventCreate(&e0));
+      BCK(cudaEventCreate(&e1));
+      float best = 1e30f;
+      for (const LaunchCfg& c : kCandidates) {
+        for (auto& I : inst) I.stage_smem = c.smem > 0 && (int64_t)I.m * I.n * 4 <= c.smem;
+        BCK(cudaMemcpyAsync(d_inst, inst.data(), sizeof(BInst) * ns, cudaMemcpyHostToDevice, s));
+        BCK(cudaMemcpyAsync(d_order, (c.largest_first ? order_big : order_in).data(), sizeof(int) * ns,
+                            cudaMemcpyHostToDevice, s));
+        BCK(cudaMemsetAsync(d_queue, 0, sizeof(int), s));
+        BCK(cudaEventRecord(e0, s));
+        rc = batch_iterate(d_inst, ns, tc, d_out, d_queue, d_order, num_sms * c.grid_mult, c.smem, s);
+        if (rc != 0) goto done;
+        BCK(cudaEventRecord(e1, s));
+        BCK(cudaEventSynchronize(e1));
+        float ms = 0;
+        BCK(cudaEventElapsedTime(&ms, e0, e1));
+        if (p->verbose > 1)
+          fprintf(stderr, "pogs batch tune: grid %dx%d smem %d order %d: %.3f ms\n", c.grid_mult, num_sms, c.smem,
+                  c.largest_first, ms);
+        if (ms < best) {
+          best = ms;
+          lc = c;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      std::lock_guard<std::mutex> g(g_tuned_mu);
+      g_tuned[key] = lc;
+    }
+  }
+  for (auto& I : inst) I.stage_smem = lc.smem > 0 && (int64_t)I.m * I.n * 4 <= lc.smem;
+  BCK(cudaMemcpyAsync(d_inst, inst.data(), sizeof(BInst) * ns, cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(d_order, (lc.largest_first ? order_big : order_in).data(), sizeof(int) * ns,
+                      cudaMemcpyHostToDevice, s));
+  // the persistent launch (with its queue reset) runs as one captured CUDA graph
+  BCK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  BCK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  ++g_capture_depth;
+  cudaMemsetAsync(d_queue, 0, sizeof(int), cap);
+  rc = batch_iterate(d_inst, ns, cfg, d_out, d_queue, d_order, num_sms * lc.grid_mult, lc.smem, cap);
+  --g_capture_depth;
+  BCK(cudaStreamEndCapture(cap, &graph));
+  if (rc != 0) goto done;
+  BCK(cudaGraphInstantiate(&gexec, graph, 0));
+  BCK(cudaGraphLaunch(gexec, s));
+  count_launch(1);
+  // ---- results ------------------------------------------------------------------------------
+  BCK(cudaMemcpyAsync(hout.data(), d_out, sizeof(BOut) * ns, cudaMemcpyDeviceToHost, s));
+  for (int k = 0; k < ns; ++k) {
+    pogs_result& r = out[small[k]];
+    const BInst& I = inst[k];
+    const float* srcs[4] = {I.ox, I.oy, I.omu, I.onu};
+    float* dsts[4] = {r.x, r.y, r.mu, r.nu};
+    const int lens[4] = {I.n, I.m, I.n, I.m};
+    for (int t = 0; t < 4; ++t)
+      if (dsts[t])
+        BCK(cudaMemcpyAsync(dsts[t], srcs[t], (size_t)lens[t] * 4,
+                            is_dev(dsts[t]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  }
+  BCK(cudaStreamSynchronize(s));
+  for (int k = 0; k < ns; ++k) {
+    pogs_info& info = out[small[k]].info;
+    const BOut& o = hout[k];
+    info.status = o.status;
+    info.iters = o.iters;
+    info.rho = o.rho;
+    info.r_pri = o.r_pri;
+    info.r_dual = o.r_dual;
+    info.eps_pri = o.eps_pri;
+    info.eps_dual = o.eps_dual;
+    info.gap = o.gap;
+    info.obj = o.obj;
+    info.r_pri_unscaled = o.r_pri_u;
+    info.r_dual_unscaled = o.r_dual_u;
+    if (o.status == POGS_MAX_ITER) worst = std::max(worst, 1);
+  }
+  rc = worst;
+done:
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (graph) cudaGraphDestroy(graph);
+  if (cap) cudaStreamDestroy(cap);
+  cudaStreamSynchronize(s);
+  cudaFree(arena);
+  cudaFree(d_inst);
+  cudaFree(d_out);
+  cudaFree(d_queue);
+  cudaFree(d_order);
+  return rc;
+}

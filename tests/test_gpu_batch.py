@@ -1,0 +1,73 @@
+"""Batched solver (one persistent kernel, one CTA per instance) vs the FP64 oracle, and its
+determinism: an instance's result is bitwise the same alone and in any mix."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import admm as OA
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1503_08366_b300 as P
+    return P
+
+
+def _tight(prob):
+    return OA.solve(prob.A, prob.f, prob.g, OA.Params(abs_tol=1e-9, rel_tol=1e-7, max_iter=50000))
+
+
+def test_batch_matches_oracle_per_instance(P):
+    """Mixed Lasso / Huber / SVM / NNLS instances, m in [64, 2048], n in [32, 512] (tall and fat)."""
+    probs = W.batch_mix(count=40, base_seed=70_000)
+    res = P.pogs_solve_batch(probs, P.pogs_default_params(max_iter=5000))
+    for k, (prob, (info, x, y, mu, nu)) in enumerate(zip(probs, res)):
+        assert info.status == 0, (k, prob.name, prob.A.shape, info.as_dict())
+        assert info.r_pri < info.eps_pri and info.r_dual < info.eps_dual
+        if k % 4 == 0:   # oracle at tight tolerance on every fourth instance (keeps the test short)
+            ref = _tight(prob)
+            assert abs(info.obj - ref.obj) <= 1e-3 * max(1.0, abs(ref.obj)), (k, prob.name, info.obj, ref.obj)
+            obj64 = OA.objective(prob.A, prob.f, prob.g, x.astype(float), y.astype(float), tol=1e-4)
+            assert abs(obj64 - ref.obj) <= 2e-3 * max(1.0, abs(ref.obj))
+
+
+def test_batch_result_is_the_same_alone_and_in_any_mix(P):
+    probs = W.batch_mix(count=48, base_seed=71_000)
+    prm = P.pogs_default_params(max_iter=5000)
+    mix = P.pogs_solve_batch(probs, prm)
+    pick = [3, 17, 29, 40]
+    alone = [P.pogs_solve_batch([probs[k]], prm)[0] for k in pick]
+    reordered = P.pogs_solve_batch([probs[k] for k in reversed(range(48))], prm)[::-1]
+    for k, a in zip(pick, alone):
+        for got in (a, reordered[k]):
+            assert got[0].iters == mix[k][0].iters and got[0].obj == mix[k][0].obj
+            for u, v in zip(got[1:], mix[k][1:]):
+                assert np.array_equal(u, v)
+
+
+def test_batch_routes_large_instances_and_isolates_errors(P):
+    probs = [W.nnls(300, 100, seed=1), W.lasso(1500, 700, seed=2), W.huber(200, 60, seed=3), W.svm(400, 90, seed=4)]
+    probs[2].f.a[5] = 0.0           # invalid parameter in one instance only
+    res = P.pogs_solve_batch(probs, P.pogs_default_params(max_iter=5000))
+    assert res[2][0].status == -1
+    for k in (0, 1, 3):
+        assert res[k][0].status == 0
+        ref = _tight(probs[k])
+        assert abs(res[k][0].obj - ref.obj) <= 1e-3 * max(1.0, abs(ref.obj))
+
+
+def test_batch_of_device_inputs_equals_host_inputs(P):
+    import torch
+    probs = W.batch_mix(count=6, base_seed=72_000)
+    host = P.pogs_solve_batch(probs, P.pogs_default_params())
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    dprobs = [W.Problem(p.name, dev(p.A), W.FnParams(*(dev(getattr(p.f, k)) for k in "habcde")),
+                        W.FnParams(*(dev(getattr(p.g, k)) for k in "habcde")), p.meta) for p in probs]
+    devr = P.pogs_solve_batch(dprobs, P.pogs_default_params())
+    for a, b in zip(host, devr):
+        assert a[0].iters == b[0].iters and np.array_equal(a[1], b[1])
