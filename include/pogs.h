@@ -187,6 +187,49 @@ typedef struct {
 int pogs_solve_batch(int count, const pogs_problem* probs, const pogs_params* p, pogs_result* out,
                      void* stream);
 
+/* ---- continuous-batching server ---------------------------------------------------------- */
+
+typedef struct pogs_server pogs_server;
+
+/* A finished request: its tag, report and host timestamps (seconds, steady clock) of
+ * submission, admission and completion. */
+typedef struct {
+  int64_t tag;
+  pogs_info info;
+  double submit_s, admit_s, done_s;
+} pogs_server_done;
+
+/* Create a server that keeps admitted requests resident on the device within `hbm_budget`
+ * bytes (matrix, factor, scalings and ADMM state; an estimate of each request's footprint is
+ * charged at admission and released at completion).  Requests with min(m, n) <= 512 are
+ * stepped together by the batched engine, at most `max_resident` of them at a time; larger
+ * ones run on `large_workers` host threads with their own streams through the single-problem
+ * path.  `stream` carries the batched work.  Errors: ARG, OOM. */
+int pogs_server_create(size_t hbm_budget, int large_workers, int max_resident, const pogs_params* p,
+                       void* stream, pogs_server** out);
+
+/* Queue a request.  The problem's arrays and the output arrays (host or device, may be NULL)
+ * must stay valid until the request is returned by pogs_server_poll.  Errors: ARG, CAPACITY
+ * (a footprint above the whole budget). */
+int pogs_server_submit(pogs_server* s, const pogs_problem* prob, float* x, float* y, float* mu, float* nu,
+                       int64_t tag);
+
+/* One step of continuous batching: admit waiting requests (first come, first served) while
+ * the budget allows, set up the new ones, advance every resident batched request by up to
+ * `iters` iterations (Algorithm 1 with its adaptive rho, continued exactly from the previous
+ * step), and retire the finished ones (outputs copied).  Large requests progress on their own
+ * threads.  Returns when the step's device work is done.  Errors: ARG, OOM, CUDA. */
+int pogs_server_step(pogs_server* s, int iters);
+
+/* Move up to `max` finished requests into `out`; returns how many. */
+int pogs_server_poll(pogs_server* s, pogs_server_done* out, int max);
+
+/* Requests submitted and not yet finished. */
+int pogs_server_pending(pogs_server* s);
+
+/* Stop the workers (requests not yet admitted are dropped) and release everything. */
+void pogs_server_destroy(pogs_server* s);
+
 /* ---- step-level entry points (the same device code the solver runs) ---------------- */
 
 /* Elementwise parametric prox of Section 5 on device arrays of length k:

@@ -71,6 +71,11 @@ class pogs_result(C.Structure):
     _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("mu", C.c_void_p), ("nu", C.c_void_p), ("info", pogs_info)]
 
 
+class pogs_server_done(C.Structure):
+    _fields_ = [("tag", C.c_int64), ("info", pogs_info), ("submit_s", C.c_double), ("admit_s", C.c_double),
+                ("done_s", C.c_double)]
+
+
 _P = C.c_void_p
 lib.pogs_default_params.argtypes = [C.POINTER(pogs_params)]
 lib.pogs_default_params.restype = None
@@ -99,6 +104,18 @@ lib.pogs_gram_noalloc.argtypes = [_P, C.c_int64, C.c_int64, C.c_int64, C.c_int, 
 lib.pogs_gram_noalloc.restype = C.c_int
 lib.pogs_solve_batch.argtypes = [C.c_int, C.POINTER(pogs_problem), C.POINTER(pogs_params), C.POINTER(pogs_result), _P]
 lib.pogs_solve_batch.restype = C.c_int
+lib.pogs_server_create.argtypes = [C.c_size_t, C.c_int, C.c_int, C.POINTER(pogs_params), _P, C.POINTER(_P)]
+lib.pogs_server_create.restype = C.c_int
+lib.pogs_server_submit.argtypes = [_P, C.POINTER(pogs_problem), _P, _P, _P, _P, C.c_int64]
+lib.pogs_server_submit.restype = C.c_int
+lib.pogs_server_step.argtypes = [_P, C.c_int]
+lib.pogs_server_step.restype = C.c_int
+lib.pogs_server_poll.argtypes = [_P, C.POINTER(pogs_server_done), C.c_int]
+lib.pogs_server_poll.restype = C.c_int
+lib.pogs_server_pending.argtypes = [_P]
+lib.pogs_server_pending.restype = C.c_int
+lib.pogs_server_destroy.argtypes = [_P]
+lib.pogs_server_destroy.restype = None
 lib.pogs_kernel_launches.argtypes = []
 lib.pogs_kernel_launches.restype = C.c_longlong
 
@@ -314,3 +331,57 @@ def pogs_solve_batch(problems, params: pogs_params | None = None, stream=None):
                               _stream_ptr(stream))
     _check(rc, "pogs_solve_batch")
     return [(res[i].info, *outs[i]) for i in range(n_p)]
+
+
+class Server:
+    """Continuous-batching server (pogs_server_*): submit, step, poll.  Keeps each request's
+    input arrays and host output arrays alive until the request is polled."""
+
+    def __init__(self, budget_bytes: int, large_workers: int = 8, max_resident: int = 4096,
+                 params: pogs_params | None = None, stream=None):
+        self.params = params if params is not None else pogs_default_params()
+        h = _P()
+        _check(lib.pogs_server_create(int(budget_bytes), large_workers, max_resident, C.byref(self.params),
+                                      _stream_ptr(stream), C.byref(h)), "pogs_server_create")
+        self.h = h.value
+        self._live = {}
+
+    def submit(self, prob, tag: int):
+        keep: list = []
+        m, n = prob.A.shape
+        pr = pogs_problem()
+        pr.A = _ptr(prob.A, np.float32, keep)
+        pr.m, pr.n, pr.lda = m, n, n
+        pr.f = make_fn(prob.f, keep)
+        pr.g = make_fn(prob.g, keep)
+        outs = [np.empty(n, np.float32), np.empty(m, np.float32), np.empty(n, np.float32), np.empty(m, np.float32)]
+        _check(lib.pogs_server_submit(self.h, C.byref(pr), *(o.ctypes.data for o in outs), tag), "pogs_server_submit")
+        self._live[tag] = (keep, pr, outs)
+
+    def step(self, iters: int = 25):
+        _check(lib.pogs_server_step(self.h, iters), "pogs_server_step")
+
+    def poll(self, max_items: int = 4096):
+        buf = (pogs_server_done * max_items)()
+        k = lib.pogs_server_poll(self.h, buf, max_items)
+        _check(k, "pogs_server_poll")
+        res = []
+        for i in range(k):
+            d = buf[i]
+            _, _, outs = self._live.pop(d.tag)
+            res.append((d.tag, d.info, d.submit_s, d.admit_s, d.done_s, *outs))
+        return res
+
+    def pending(self) -> int:
+        return lib.pogs_server_pending(self.h)
+
+    def close(self):
+        if self.h:
+            lib.pogs_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

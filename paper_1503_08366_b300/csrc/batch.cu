@@ -49,7 +49,7 @@ __device__ __forceinline__ void bsum(double (&v)[NV], double* sh) {
 // Setup 1: Sinkhorn-Knopp (Algorithm 2, p = 2), Frobenius rescale (Section 4.1.2), A^ = D A E,
 // folded parameters (Eq. 12).
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) bsetup_equil_kernel(BInst* insts, BCfg cfg, BOut* out) {
+__global__ void __launch_bounds__(NT) bsetup_equil_kernel(BInst* insts, BCfg cfg) {
   __shared__ double sh[4 * NW];
   __shared__ int s_err;
   BInst I = insts[blockIdx.x];
@@ -134,17 +134,17 @@ __global__ void __launch_bounds__(NT) bsetup_equil_kernel(BInst* insts, BCfg cfg
     }
   }
   __syncthreads();
-  if (tid == 0) out[blockIdx.x].status = s_err;
+  if (tid == 0) I.out->status = s_err;
 }
 
 // ---------------------------------------------------------------------------------------------
 // Setup 2: H = I + G in FP64 (lower), G = A^T A (tall) or A A^T (fat), FP32 products, 32 x 32
 // tiles with 32-deep K chunks staged in shared memory.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) bsetup_gram_kernel(BInst* insts, BOut* out) {
+__global__ void __launch_bounds__(NT) bsetup_gram_kernel(BInst* insts) {
   __shared__ float Xs[32][33], Ys[32][33];
   BInst I = insts[blockIdx.x];
-  if (out[blockIdx.x].status != 0) return;
+  if (I.out->status != 0) return;
   const int q = I.q, K = I.tall ? I.m : I.n, lda = I.lda;
   const int T = (q + 31) / 32;
   const int tid = threadIdx.x;
@@ -194,12 +194,12 @@ __global__ void __launch_bounds__(NT) bsetup_gram_kernel(BInst* insts, BOut* out
 // Setup 3: right-looking blocked Cholesky of H (32-column panels): FP64 diagonal blocks and
 // panel solves; trailing update from the FP32-rounded panel in FP32 (mixed) or in FP64.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) bsetup_chol_kernel(BInst* insts, BOut* out, int mixed) {
+__global__ void __launch_bounds__(NT) bsetup_chol_kernel(BInst* insts, int mixed) {
   extern __shared__ float Pf[];            // [q][33] FP32 panel
   __shared__ double Ld[32][33], Xi[32][33];
   __shared__ int s_err;
   BInst I = insts[blockIdx.x];
-  if (out[blockIdx.x].status != 0) return;
+  if (I.out->status != 0) return;
   const int q = I.q;
   double* H = I.H;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -285,16 +285,16 @@ __global__ void __launch_bounds__(NT) bsetup_chol_kernel(BInst* insts, BOut* out
     }
     __syncthreads();
   }
-  if (tid == 0 && s_err != 0) out[blockIdx.x].status = s_err;
+  if (tid == 0 && s_err != 0) I.out->status = s_err;
 }
 
 // ---------------------------------------------------------------------------------------------
 // Setup 4: M = L^{-1} (FP32, dense lower, ld q), one column per thread by forward substitution
 // with FP64 accumulation.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) bsetup_inverse_kernel(BInst* insts, BOut* out) {
+__global__ void __launch_bounds__(NT) bsetup_inverse_kernel(BInst* insts) {
   BInst I = insts[blockIdx.x];
-  if (out[blockIdx.x].status != 0) return;
+  if (I.out->status != 0) return;
   const int q = I.q;
   const double* L = I.H;
   float* M = I.M;
@@ -313,10 +313,7 @@ __global__ void __launch_bounds__(NT) bsetup_inverse_kernel(BInst* insts, BOut* 
 // ---------------------------------------------------------------------------------------------
 // Iteration phases (one CTA).
 // ---------------------------------------------------------------------------------------------
-struct Loop {
-  double rho, pend;
-  int k, l, u, done, status;
-};
+using Loop = BLoop;
 
 __device__ __forceinline__ void zero_state(const BInst& I) {
   for (int j = threadIdx.x; j < I.n; j += NT) { I.x[j] = 0.0f; I.xt[j] = 0.0f; }
@@ -353,7 +350,8 @@ __device__ __forceinline__ void colsum3(const float* A, int lda, int m, int j, c
   t3 = s3;
 }
 
-__device__ void run_instance(const BInst& I, const BCfg& cfg, BOut* out, float* smemA, double* red, Loop* L) {
+__device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, double* red, Loop* L, int max_steps) {
+  BOut* out = I.out;
   const int m = I.m, n = I.n, q = I.q, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* A = I.A;
   int lda = I.lda;
@@ -363,14 +361,21 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, BOut* out, float* 
     A = smemA;
     lda = n;
   }
-  zero_state(I);
+  const bool resume = I.loop && I.loop->started;
+  if (!resume) zero_state(I);
   if (tid == 0) {
-    L->rho = cfg.rho0;
-    L->pend = 1.0;
-    L->k = L->l = L->u = L->done = 0;
-    L->status = POGS_MAX_ITER;
+    if (resume) {
+      *L = *I.loop;
+    } else {
+      L->rho = cfg.rho0;
+      L->pend = 1.0;
+      L->k = L->l = L->u = L->done = 0;
+      L->status = POGS_MAX_ITER;
+      L->started = 1;
+    }
   }
   __syncthreads();
+  int steps = 0;
   const float alpha = (float)cfg.alpha;
   while (true) {
     const float rho = (float)L->rho, pend = (float)L->pend;
@@ -546,8 +551,13 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, BOut* out, float* 
       }
     }
     __syncthreads();
-    if (L->done) break;
+    ++steps;
+    if (L->done || (max_steps > 0 && steps >= max_steps)) break;
   }
+  if (tid == 0 && I.loop) *I.loop = *L;
+  const bool finished = L->done != 0;
+  __syncthreads();
+  if (!finished) return;
   // returned tuple in the original variables (Section 5)
   for (int j = tid; j < n; j += NT) {
     I.ox[j] = I.E[j] * I.xh[j];
@@ -560,8 +570,8 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, BOut* out, float* 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(NT) batch_admm_kernel(BInst* insts, int count, BCfg cfg, BOut* out,
-                                                       int* queue, const int* order) {
+__global__ void __launch_bounds__(NT) batch_admm_kernel(BInst* insts, int count, BCfg cfg, int* queue,
+                                                       const int* order, int max_steps) {
   extern __shared__ float smemA[];
   __shared__ double red[6 * NW];
   __shared__ Loop L;
@@ -573,8 +583,10 @@ __global__ void __launch_bounds__(NT) batch_admm_kernel(BInst* insts, int count,
     __syncthreads();
     if (pos >= count) break;
     const int idx = order ? order[pos] : pos;
-    if (out[idx].status != 0 && out[idx].iters == 0) continue;   // setup failed: reported as is
-    run_instance(insts[idx], cfg, out + idx, smemA, red, &L);
+    const BInst& I = insts[idx];
+    if (I.out->status != 0 && I.out->iters == 0) continue;   // setup failed: reported as is
+    if (I.loop && I.loop->done) continue;                      // already finished
+    run_instance(I, cfg, smemA, red, &L, max_steps);
   }
 }
 
@@ -582,11 +594,11 @@ __global__ void __launch_bounds__(NT) batch_admm_kernel(BInst* insts, int count,
 
 int batch_max_smem() { return 200 * 1024; }
 
-int batch_setup(BInst* d_inst, int count, const BCfg& cfg, BOut* d_out, cudaStream_t s) {
+int batch_setup(BInst* d_inst, int count, const BCfg& cfg, cudaStream_t s) {
   if (count <= 0) return 0;
   count_launch(4);
-  bsetup_equil_kernel<<<count, NT, 0, s>>>(d_inst, cfg, d_out);
-  bsetup_gram_kernel<<<count, NT, 0, s>>>(d_inst, d_out);
+  bsetup_equil_kernel<<<count, NT, 0, s>>>(d_inst, cfg);
+  bsetup_gram_kernel<<<count, NT, 0, s>>>(d_inst);
   const int chol_smem = 512 * 33 * sizeof(float);
   static bool attr = false;
   if (!attr) {
@@ -594,16 +606,16 @@ int batch_setup(BInst* d_inst, int count, const BCfg& cfg, BOut* d_out, cudaStre
     cudaFuncSetAttribute(batch_admm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_max_smem());
     attr = true;
   }
-  bsetup_chol_kernel<<<count, NT, chol_smem, s>>>(d_inst, d_out, cfg.mixed_chol);
-  bsetup_inverse_kernel<<<count, NT, 0, s>>>(d_inst, d_out);
+  bsetup_chol_kernel<<<count, NT, chol_smem, s>>>(d_inst, cfg.mixed_chol);
+  bsetup_inverse_kernel<<<count, NT, 0, s>>>(d_inst);
   return cudaGetLastError() == cudaSuccess ? 0 : POGS_ERR_CUDA;
 }
 
-int batch_iterate(BInst* d_inst, int count, const BCfg& cfg, BOut* d_out, int* d_queue, const int* d_order,
-                  int grid, int smem_bytes, cudaStream_t s) {
+int batch_iterate(BInst* d_inst, int count, const BCfg& cfg, int* d_queue, const int* d_order, int grid,
+                  int smem_bytes, int max_steps, cudaStream_t s) {
   if (count <= 0) return 0;
   count_launch();
-  batch_admm_kernel<<<grid, NT, smem_bytes, s>>>(d_inst, count, cfg, d_out, d_queue, d_order);
+  batch_admm_kernel<<<grid, NT, smem_bytes, s>>>(d_inst, count, cfg, d_queue, d_order, max_steps);
   return cudaGetLastError() == cudaSuccess ? 0 : POGS_ERR_CUDA;
 }
 

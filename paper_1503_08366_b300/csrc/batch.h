@@ -4,6 +4,9 @@
 
 namespace pogs {
 
+struct BOut;
+struct BLoop;
+
 // One instance, all pointers into a device arena.  Pre-conditioned data (A^ = D A E, folded
 // function parameters) and the FP32 inverse factor M = L^{-1} (dense lower triangle, ld q).
 struct BInst {
@@ -18,6 +21,15 @@ struct BInst {
   float *fa, *fb, *fc, *fd, *fe, *ga, *gb, *gc, *gd, *ge;
   float *x, *y, *xt, *yt, *xh, *yh, *cx, *dy, *mu, *nu, *r, *z, *w;
   float *ox, *oy, *omu, *onu;                   // unscaled outputs
+  BOut* out;                                    // report
+  BLoop* loop;                                  // saved loop state (resumable runs) or null
+};
+
+// Loop state of an instance saved between launches of the iteration kernel (exact: the next
+// launch continues with the same rho, pending rescale and Algorithm 3 counters).
+struct BLoop {
+  double rho, pend;
+  int k, l, u, done, status, started;
 };
 
 // Per-instance report (mirrors pogs_info).
@@ -34,9 +46,11 @@ struct BCfg {
 constexpr int kBatchThreads = 256;   // fixed: per-instance arithmetic never depends on the batch
 
 // setup (one CTA per instance) and the persistent iteration kernel
-int batch_setup(BInst* d_inst, int count, const BCfg& cfg, BOut* d_out, cudaStream_t s);
-int batch_iterate(BInst* d_inst, int count, const BCfg& cfg, BOut* d_out, int* d_queue, const int* d_order,
-                  int grid, int smem_bytes, cudaStream_t s);
+int batch_setup(BInst* d_inst, int count, const BCfg& cfg, cudaStream_t s);
+// Run the iteration for the listed instances; max_steps > 0 stops each instance after that many
+// iterations in this launch (its loop state is saved in BInst::loop and resumed next launch).
+int batch_iterate(BInst* d_inst, int count, const BCfg& cfg, int* d_queue, const int* d_order, int grid,
+                  int smem_bytes, int max_steps, cudaStream_t s);
 int batch_max_smem();
 
 }  // namespace pogs

@@ -214,6 +214,8 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
     float** vecs[] = {&I.x, &I.y, &I.xt, &I.yt, &I.xh, &I.yh, &I.cx, &I.dy, &I.mu, &I.nu, &I.r, &I.z, &I.w,
                       &I.ox, &I.oy, &I.omu, &I.onu};
     for (int t = 0; t < 17; ++t) *vecs[t] = v + (size_t)t * vlen;
+    I.out = d_out + k;
+    I.loop = nullptr;
   }
   // ---- configuration ------------------------------------------------------------------------
   memset(&cfg, 0, sizeof(cfg));
@@ -238,7 +240,7 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
     return (int64_t)inst[a].m * inst[a].n > (int64_t)inst[b].m * inst[b].n;
   });
   BCK(cudaMemcpyAsync(d_inst, inst.data(), sizeof(BInst) * ns, cudaMemcpyHostToDevice, s));
-  rc = batch_setup(d_inst, ns, cfg, d_out, s);
+  rc = batch_setup(d_inst, ns, cfg, s);
   if (rc != 0) goto done;
   {
     // size class of this batch: log2 of the count, of the largest q and of the mean m n
@@ -275,7 +277,7 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
                             cudaMemcpyHostToDevice, s));
         BCK(cudaMemsetAsync(d_queue, 0, sizeof(int), s));
         BCK(cudaEventRecord(e0, s));
-        rc = batch_iterate(d_inst, ns, tc, d_out, d_queue, d_order, num_sms * c.grid_mult, c.smem, s);
+        rc = batch_iterate(d_inst, ns, tc, d_queue, d_order, num_sms * c.grid_mult, c.smem, 0, s);
         if (rc != 0) goto done;
         BCK(cudaEventRecord(e1, s));
         BCK(cudaEventSynchronize(e1));
@@ -304,7 +306,7 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
   BCK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
   ++g_capture_depth;
   cudaMemsetAsync(d_queue, 0, sizeof(int), cap);
-  rc = batch_iterate(d_inst, ns, cfg, d_out, d_queue, d_order, num_sms * lc.grid_mult, lc.smem, cap);
+  rc = batch_iterate(d_inst, ns, cfg, d_queue, d_order, num_sms * lc.grid_mult, lc.smem, 0, cap);
   --g_capture_depth;
   BCK(cudaStreamEndCapture(cap, &graph));
   if (rc != 0) goto done;

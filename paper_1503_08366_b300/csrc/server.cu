@@ -1,0 +1,433 @@
+// Continuous-batching server: requests are admitted against a device-memory budget, stay
+// resident on the device (matrix, factor, scalings and ADMM state), and advance together.
+//
+// Requests with min(m, n) <= 512 use the batched engine: each step launches the persistent
+// iteration kernel once over every resident request, advancing each by up to `iters`
+// iterations from its saved loop state; requests admitted between steps join at the next one
+// and finished ones retire (outputs copied, memory released) after it.  Larger requests run
+// through the single-problem path on worker threads with their own streams, concurrently with
+// the batched steps.  A request's result does not depend on what else is resident: the batched
+// engine's arithmetic is fixed per instance and exact across step boundaries.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "batch.h"
+#include "kernels.h"
+
+using namespace pogs;
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+bool is_dev(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+constexpr int kSmallMaxQ = 512;
+
+struct SReq {
+  int64_t tag = 0;
+  pogs_problem prob{};
+  float *x = nullptr, *y = nullptr, *mu = nullptr, *nu = nullptr;
+  bool small = false;
+  size_t bytes = 0;
+  double t_submit = 0, t_admit = 0;
+  int slot = -1;
+  char* arena = nullptr;
+  BInst inst{};
+};
+
+// Device bytes a request holds while resident.
+size_t small_bytes(int64_t m, int64_t n) {
+  const int64_t q = std::min(m, n), v = std::max(m, n), lda4 = (n + 3) / 4 * 4;
+  size_t b = al((size_t)m * lda4 * 4) + al((size_t)q * q * 4) + al((size_t)q * q * 8) + al((size_t)m * 4) +
+             al((size_t)n * 4) + al((size_t)17 * v * 4);
+  for (int t = 0; t < 24; ++t) b += al((size_t)((t % 12) < 6 ? m : n) * (((t % 6) == 0) ? 1 : 4));
+  return b;
+}
+size_t large_bytes(int64_t m, int64_t n) {
+  const int64_t q = std::min(m, n), p = std::max(m, n);
+  const int64_t T = (q + 127) / 128;
+  // matrix + tiles + vectors resident, plus the setup peak (Gram, FP64 factor, dense inverse,
+  // packed tensor-core operands)
+  return (size_t)m * ((n + 31) / 32 * 32) * 4 + (size_t)T * (T + 1) / 2 * 128 * 128 * 4 + (size_t)64 * (m + n) * 4 +
+         (size_t)q * q * (4 + 8 + 4 + 2) + (size_t)((q + 127) / 128 * 128) * ((p + 63) / 64 * 64) * 4;
+}
+
+}  // namespace
+
+struct pogs_server {
+  size_t budget = 0, used = 0;
+  pogs_params p{};
+  BCfg cfg{};
+  cudaStream_t stream = nullptr;
+  int num_sms = 148;
+  int cap = 0;                       // slots for resident small requests
+  BOut* d_outs = nullptr;
+  BLoop* d_loops = nullptr;
+  BInst* d_active = nullptr;
+  BInst* d_new = nullptr;
+  int* d_queue = nullptr;
+  std::vector<int> free_slots;
+  std::deque<SReq*> waiting;
+  std::vector<SReq*> active;
+  std::vector<pogs_server_done> done;
+  std::vector<BOut> h_outs;
+  std::vector<BLoop> h_loops;
+  // large requests
+  std::vector<std::thread> workers;
+  std::deque<SReq*> large_q;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  int large_inflight = 0;
+  int64_t submitted = 0, completed = 0;
+};
+
+namespace {
+
+void worker_main(pogs_server* S) {
+  cudaStream_t st;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    st = nullptr;
+  }
+  while (true) {
+    SReq* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait(lk, [&] { return S->stop || !S->large_q.empty(); });
+      if (S->large_q.empty()) break;
+      r = S->large_q.front();
+      S->large_q.pop_front();
+    }
+    pogs_server_done d;
+    memset(&d, 0, sizeof(d));
+    d.tag = r->tag;
+    d.submit_s = r->t_submit;
+    d.admit_s = r->t_admit;
+    pogs_handle* h = nullptr;
+    int rc = pogs_setup(r->prob.A, r->prob.m, r->prob.n, r->prob.lda, 'R', &S->p, st, &h);
+    if (rc == 0) {
+      rc = pogs_solve(h, &r->prob.f, &r->prob.g, &S->p, r->x, r->y, r->mu, r->nu, &d.info);
+      pogs_free(h);
+    }
+    d.info.status = rc;
+    d.done_s = now_s();
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->done.push_back(d);
+      S->used -= r->bytes;
+      --S->large_inflight;
+      ++S->completed;
+    }
+    delete r;
+  }
+  if (st) cudaStreamDestroy(st);
+}
+
+// Lay out a small request's arena and fill its descriptor (device pointers).
+void layout_small(SReq* r, BOut* out, BLoop* loop) {
+  const pogs_problem& pr = r->prob;
+  BInst& I = r->inst;
+  memset(&I, 0, sizeof(I));
+  char* a = r->arena;
+  size_t cur = 0;
+  auto take = [&](size_t bytes) {
+    char* p = a + cur;
+    cur = al(cur + bytes);
+    return p;
+  };
+  I.m = (int)pr.m;
+  I.n = (int)pr.n;
+  I.lda = (int)((pr.n + 3) / 4 * 4);
+  I.q = (int)std::min(pr.m, pr.n);
+  I.tall = pr.m >= pr.n;
+  I.A = (float*)take((size_t)pr.m * I.lda * 4);
+  I.M = (float*)take((size_t)I.q * I.q * 4);
+  I.H = (double*)take((size_t)I.q * I.q * 8);
+  I.D = (float*)take((size_t)pr.m * 4);
+  I.E = (float*)take((size_t)pr.n * 4);
+  void* raw[12];
+  for (int t = 0; t < 12; ++t) raw[t] = take((size_t)(t < 6 ? pr.m : pr.n) * ((t % 6) == 0 ? 1 : 4));
+  const void* src[12] = {pr.f.h, pr.f.a, pr.f.b, pr.f.c, pr.f.d, pr.f.e, pr.g.h, pr.g.a, pr.g.b, pr.g.c, pr.g.d, pr.g.e};
+  auto in = [&](int t) -> void* { return src[t] ? raw[t] : nullptr; };
+  I.fh0 = (const uint8_t*)in(0); I.fa0 = (const float*)in(1); I.fb0 = (const float*)in(2);
+  I.fc0 = (const float*)in(3); I.fd0 = (const float*)in(4); I.fe0 = (const float*)in(5);
+  I.gh0 = (const uint8_t*)in(6); I.ga0 = (const float*)in(7); I.gb0 = (const float*)in(8);
+  I.gc0 = (const float*)in(9); I.gd0 = (const float*)in(10); I.ge0 = (const float*)in(11);
+  void* fo[12];
+  for (int t = 0; t < 12; ++t) fo[t] = take((size_t)(t < 6 ? pr.m : pr.n) * ((t % 6) == 0 ? 1 : 4));
+  I.fh = (uint8_t*)fo[0]; I.fa = (float*)fo[1]; I.fb = (float*)fo[2]; I.fc = (float*)fo[3]; I.fd = (float*)fo[4];
+  I.fe = (float*)fo[5];
+  I.gh = (uint8_t*)fo[6]; I.ga = (float*)fo[7]; I.gb = (float*)fo[8]; I.gc = (float*)fo[9]; I.gd = (float*)fo[10];
+  I.ge = (float*)fo[11];
+  const int64_t v = std::max(pr.m, pr.n);
+  float* vec = (float*)take((size_t)17 * v * 4);
+  float** vecs[] = {&I.x, &I.y, &I.xt, &I.yt, &I.xh, &I.yh, &I.cx, &I.dy, &I.mu, &I.nu, &I.r, &I.z, &I.w,
+                    &I.ox, &I.oy, &I.omu, &I.onu};
+  for (int t = 0; t < 17; ++t) *vecs[t] = vec + (size_t)t * v;
+  I.out = out;
+  I.loop = loop;
+}
+
+int copy_inputs(SReq* r, cudaStream_t s) {
+  const pogs_problem& pr = r->prob;
+  const BInst& I = r->inst;
+  const cudaMemcpyKind kA = is_dev(pr.A) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (cudaMemcpy2DAsync(I.A, (size_t)I.lda * 4, pr.A, (size_t)pr.lda * 4, (size_t)pr.n * 4, pr.m, kA, s) !=
+      cudaSuccess)
+    return POGS_ERR_CUDA;
+  const void* src[12] = {pr.f.h, pr.f.a, pr.f.b, pr.f.c, pr.f.d, pr.f.e, pr.g.h, pr.g.a, pr.g.b, pr.g.c, pr.g.d, pr.g.e};
+  const void* dst[12] = {I.fh0, I.fa0, I.fb0, I.fc0, I.fd0, I.fe0, I.gh0, I.ga0, I.gb0, I.gc0, I.gd0, I.ge0};
+  for (int t = 0; t < 12; ++t) {
+    if (!src[t]) continue;
+    const size_t bytes = (size_t)(t < 6 ? pr.m : pr.n) * ((t % 6) == 0 ? 1 : 4);
+    if (cudaMemcpyAsync(const_cast<void*>(dst[t]), src[t], bytes,
+                        is_dev(src[t]) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return POGS_ERR_CUDA;
+  }
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pogs_server_create(size_t hbm_budget, int large_workers, int max_resident, const pogs_params* p, void* stream,
+                       pogs_server** out) {
+  if (!out || hbm_budget == 0 || large_workers < 0 || max_resident < 1) return POGS_ERR_ARG;
+  *out = nullptr;
+  pogs_server* S = new pogs_server();
+  pogs_default_params(&S->p);
+  if (p) S->p = *p;
+  S->budget = hbm_budget;
+  S->stream = static_cast<cudaStream_t>(stream);
+  S->cap = max_resident;
+  BCfg& c = S->cfg;
+  memset(&c, 0, sizeof(c));
+  c.abs_tol = S->p.abs_tol; c.rel_tol = S->p.rel_tol; c.rho0 = S->p.rho0; c.alpha = S->p.alpha; c.delta = S->p.delta;
+  c.tau = S->p.tau; c.gamma_scale = S->p.gamma; c.max_iter = S->p.max_iter; c.gap_stop = S->p.gap_stop;
+  c.adaptive = S->p.adaptive_rho; c.sk_sweeps = S->p.sk_sweeps; c.equil = S->p.equil;
+  c.mixed_chol = S->p.chol_prec == POGS_CHOL_MIXED;
+  int dev = 0;
+  bool ok = cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&S->num_sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaMalloc(&S->d_outs, sizeof(BOut) * S->cap) == cudaSuccess &&
+            cudaMalloc(&S->d_loops, sizeof(BLoop) * S->cap) == cudaSuccess &&
+            cudaMalloc(&S->d_active, sizeof(BInst) * S->cap) == cudaSuccess &&
+            cudaMalloc(&S->d_new, sizeof(BInst) * S->cap) == cudaSuccess &&
+            cudaMalloc(&S->d_queue, sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    pogs_server_destroy(S);
+    return POGS_ERR_OOM;
+  }
+  {
+    // keep freed request memory in the stream-ordered pool for the next admissions
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+  }
+  for (int i = S->cap - 1; i >= 0; --i) S->free_slots.push_back(i);
+  S->h_outs.resize(S->cap);
+  S->h_loops.resize(S->cap);
+  for (int i = 0; i < large_workers; ++i) S->workers.emplace_back(worker_main, S);
+  *out = S;
+  return 0;
+}
+
+int pogs_server_submit(pogs_server* S, const pogs_problem* prob, float* x, float* y, float* mu, float* nu,
+                       int64_t tag) {
+  if (!S || !prob || !prob->A || prob->m < 1 || prob->n < 1 || prob->lda < prob->n || !prob->f.h || !prob->g.h)
+    return POGS_ERR_ARG;
+  SReq* r = new SReq();
+  r->tag = tag;
+  r->prob = *prob;
+  r->x = x; r->y = y; r->mu = mu; r->nu = nu;
+  r->small = std::min(prob->m, prob->n) <= kSmallMaxQ;
+  r->bytes = r->small ? small_bytes(prob->m, prob->n) : large_bytes(prob->m, prob->n);
+  if (r->bytes > S->budget) {
+    delete r;
+    return POGS_ERR_CAPACITY;
+  }
+  r->t_submit = now_s();
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->waiting.push_back(r);
+  ++S->submitted;
+  return 0;
+}
+
+int pogs_server_step(pogs_server* S, int iters) {
+  if (!S || iters < 1) return POGS_ERR_ARG;
+  cudaStream_t s = S->stream;
+  // ---- admission: first come first served, within the memory budget and the slot count -----
+  std::vector<SReq*> fresh;
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->waiting.empty()) {
+      SReq* r = S->waiting.front();
+      if (S->used + r->bytes > S->budget) break;
+      if (r->small && S->free_slots.empty()) break;
+      S->waiting.pop_front();
+      S->used += r->bytes;
+      r->t_admit = now_s();
+      if (r->small) {
+        r->slot = S->free_slots.back();
+        S->free_slots.pop_back();
+        fresh.push_back(r);
+      } else {
+        ++S->large_inflight;
+        S->large_q.push_back(r);
+        S->cv.notify_one();
+      }
+    }
+  }
+  for (SReq* r : fresh) {
+    if (cudaMallocAsync((void**)&r->arena, r->bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      return POGS_ERR_OOM;
+    }
+    layout_small(r, S->d_outs + r->slot, S->d_loops + r->slot);
+    if (copy_inputs(r, s) != 0) return POGS_ERR_CUDA;
+    if (cudaMemsetAsync(S->d_outs + r->slot, 0, sizeof(BOut), s) != cudaSuccess ||
+        cudaMemsetAsync(S->d_loops + r->slot, 0, sizeof(BLoop), s) != cudaSuccess)
+      return POGS_ERR_CUDA;
+    S->active.push_back(r);
+  }
+  if (!fresh.empty()) {
+    std::vector<BInst> hn;
+    for (SReq* r : fresh) hn.push_back(r->inst);
+    if (cudaMemcpyAsync(S->d_new, hn.data(), sizeof(BInst) * hn.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return POGS_ERR_CUDA;
+    int rc = batch_setup(S->d_new, (int)hn.size(), S->cfg, s);
+    if (rc != 0) return rc;
+  }
+  if (S->active.empty()) return 0;
+  // ---- one launch advances every resident request ------------------------------------------
+  std::vector<BInst> ha;
+  std::vector<int> order;
+  for (SReq* r : S->active) ha.push_back(r->inst);
+  const int na = (int)ha.size();
+  if (cudaMemcpyAsync(S->d_active, ha.data(), sizeof(BInst) * na, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(S->d_queue, 0, sizeof(int), s) != cudaSuccess)
+    return POGS_ERR_CUDA;
+  int rc = batch_iterate(S->d_active, na, S->cfg, S->d_queue, nullptr, S->num_sms * 4, 0, iters, s);
+  if (rc != 0) return rc;
+  if (cudaMemcpyAsync(S->h_outs.data(), S->d_outs, sizeof(BOut) * S->cap, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(S->h_loops.data(), S->d_loops, sizeof(BLoop) * S->cap, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return POGS_ERR_CUDA;
+  }
+  // ---- retire finished requests ------------------------------------------------------------------
+  std::vector<SReq*> keep;
+  const double t = now_s();
+  for (SReq* r : S->active) {
+    const BOut& o = S->h_outs[r->slot];
+    const BLoop& L = S->h_loops[r->slot];
+    const bool setup_failed = o.status != 0 && o.iters == 0;
+    if (!setup_failed && !L.done) {
+      keep.push_back(r);
+      continue;
+    }
+    const BInst& I = r->inst;
+    const float* srcs[4] = {I.ox, I.oy, I.omu, I.onu};
+    float* dsts[4] = {r->x, r->y, r->mu, r->nu};
+    const int64_t lens[4] = {I.n, I.m, I.n, I.m};
+    if (!setup_failed)
+      for (int k = 0; k < 4; ++k)
+        if (dsts[k])
+          cudaMemcpyAsync(dsts[k], srcs[k], (size_t)lens[k] * 4,
+                          is_dev(dsts[k]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(r->arena, s);
+    pogs_server_done d;
+    memset(&d, 0, sizeof(d));
+    d.tag = r->tag;
+    d.submit_s = r->t_submit;
+    d.admit_s = r->t_admit;
+    d.done_s = t;
+    d.info.status = o.status;
+    d.info.iters = o.iters;
+    d.info.rho = o.rho;
+    d.info.r_pri = o.r_pri;
+    d.info.r_dual = o.r_dual;
+    d.info.eps_pri = o.eps_pri;
+    d.info.eps_dual = o.eps_dual;
+    d.info.gap = o.gap;
+    d.info.obj = o.obj;
+    d.info.r_pri_unscaled = o.r_pri_u;
+    d.info.r_dual_unscaled = o.r_dual_u;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->done.push_back(d);
+    S->used -= r->bytes;
+    S->free_slots.push_back(r->slot);
+    ++S->completed;
+    delete r;
+  }
+  S->active.swap(keep);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return POGS_ERR_CUDA;
+  }
+  return 0;
+}
+
+int pogs_server_poll(pogs_server* S, pogs_server_done* out, int max) {
+  if (!S || (max > 0 && !out)) return POGS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  const int k = std::min<int>(max, (int)S->done.size());
+  for (int i = 0; i < k; ++i) out[i] = S->done[i];
+  S->done.erase(S->done.begin(), S->done.begin() + k);
+  return k;
+}
+
+int pogs_server_pending(pogs_server* S) {
+  if (!S) return POGS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  return (int)(S->submitted - S->completed);
+}
+
+void pogs_server_destroy(pogs_server* S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  for (auto& t : S->workers) t.join();
+  if (S->stream) cudaStreamSynchronize(S->stream);
+  for (SReq* r : S->active) {
+    cudaFree(r->arena);
+    delete r;
+  }
+  for (SReq* r : S->waiting) delete r;
+  cudaFree(S->d_outs);
+  cudaFree(S->d_loops);
+  cudaFree(S->d_active);
+  cudaFree(S->d_new);
+  cudaFree(S->d_queue);
+  delete S;
+}
+
+}  // extern "C"
