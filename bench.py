@@ -399,6 +399,116 @@ def _traffic(kernel):
         return None
 
 
+# ----------------------------------------------------------------------------------------------
+# Extra workloads (not the default bench line): many small instances, and serving.
+# ----------------------------------------------------------------------------------------------
+def run_batch(args):
+    """2048 independent instances (Lasso / Huber / SVM / NNLS, m log-U[64, 2048], n log-U[32, 512])
+    in one pogs_solve_batch call, vs the plain single-problem path one instance at a time."""
+    import torch
+    import paper_1503_08366_b300 as P
+    import workloads as W
+    probs = W.batch_mix(count=args.count)
+    prm = P.pogs_default_params()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    dprobs = [W.Problem(p.name, dev(p.A), W.FnParams(*(dev(getattr(p.f, k)) for k in "habcde")),
+                        W.FnParams(*(dev(getattr(p.g, k)) for k in "habcde")), p.meta) for p in probs]
+    P.pogs_solve_batch(dprobs, prm)                     # tunes the launch configuration once
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = P.pogs_solve_batch(dprobs, prm)
+    torch.cuda.synchronize()
+    t_dev = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P.pogs_solve_batch(probs, prm)
+    t_host = time.perf_counter() - t0
+    st = [r[0].status for r in res]
+    # plain: the single-problem path, one instance at a time (a bounded sample, extrapolated)
+    k = min(args.plain_sample, len(probs))
+    t0 = time.perf_counter()
+    for pb in dprobs[:k]:
+        with P.Solver(pb.A, prm) as sv:
+            sv.solve(pb.f, pb.g, device_out=True)
+    torch.cuda.synchronize()
+    t_plain = (time.perf_counter() - t0) / k * len(probs)
+    print(json.dumps(dict(workload="batch", metric="solves/s", value=len(probs) / t_dev, unit="solves/s",
+                          e2e=dict(value=len(probs) / t_host, unit="solves/s"),
+                          plain=dict(value=len(probs) / t_plain, unit="solves/s", sample=k),
+                          statuses={str(s_): st.count(s_) for s_ in set(st)},
+                          iters_mean=float(np.mean([r[0].iters for r in res])),
+                          config=dict(count=len(probs), classes="lasso,huber,svm,nnls", m="log-U[64,2048]",
+                                      n="log-U[32,512]"))))
+
+
+def _pool(trace, size):
+    """Request payloads: `size` distinct problems drawn like the trace (class, m, n); request i
+    carries payload i mod size."""
+    return [trace[i].problem() for i in range(min(size, len(trace)))]
+
+
+def run_serve(args):
+    """Poisson arrivals at 2000 req/s, mixed Lasso / logistic / Huber / SVM / NNLS with
+    m log-U[100, 8000], n log-U[50, 4000], served with continuous batching under a 120 GB budget,
+    vs the same trace served one request at a time by the single-problem path."""
+    import torch
+    import paper_1503_08366_b300 as P
+    import workloads as W
+    trace = W.serve_trace(count=args.requests)
+    pool = _pool(trace, args.pool)
+    prm = P.pogs_default_params()
+    n_req = len(trace)
+
+    def served():
+        lat, iters, st = [], [], []
+        with P.Server(int(120e9), large_workers=args.workers, max_resident=8192, params=prm) as srv:
+            t0 = time.monotonic()
+            i = 0
+            while len(lat) < n_req:
+                now = time.monotonic() - t0
+                while i < n_req and trace[i].arrival_s <= now:
+                    srv.submit(pool[i % len(pool)], i)
+                    i += 1
+                if srv.pending() > 0:
+                    srv.step(args.step_iters)
+                else:
+                    time.sleep(min(1e-4, max(0.0, trace[i].arrival_s - now)) if i < n_req else 0)
+                for tag, info, _s, _a, done_s, *_ in srv.poll():
+                    lat.append(done_s - (t0 + trace[tag].arrival_s))
+                    iters.append(info.iters)
+                    st.append(info.status)
+            wall = time.monotonic() - t0
+        return wall, lat, iters, st
+
+    def plain(limit_s):
+        lat, st = [], []
+        t0 = time.monotonic()
+        for i, req in enumerate(trace):
+            now = time.monotonic() - t0
+            if now > limit_s:
+                break
+            if req.arrival_s > now:
+                time.sleep(req.arrival_s - now)
+            pb = pool[i % len(pool)]
+            with P.Solver(pb.A, prm) as sv:
+                info, *_ = sv.solve(pb.f, pb.g)
+            lat.append(time.monotonic() - (t0 + req.arrival_s))
+            st.append(info.status)
+        return time.monotonic() - t0, lat, st
+
+    wall, lat, iters, st = served()
+    pwall, plat, pst = plain(args.plain_limit)
+    pct = lambda v, q: float(np.percentile(np.asarray(v) * 1e3, q)) if v else None
+    print(json.dumps(dict(
+        workload="serve", metric="solves/s & p50/p99 latency at eps_rel=1e-3, served vs plain",
+        value=len(lat) / wall, unit="solves/s", latency_ms=dict(p50=pct(lat, 50), p99=pct(lat, 99)),
+        statuses={str(s_): st.count(s_) for s_ in set(st)}, iters_mean=float(np.mean(iters)),
+        plain=dict(value=len(plat) / pwall, unit="solves/s", served=len(plat), of=n_req,
+                   latency_ms=dict(p50=pct(plat, 50), p99=pct(plat, 99)), limit_s=args.plain_limit),
+        config=dict(requests=n_req, rate_hz=2000, budget_gb=120, payload_pool=len(pool), step_iters=args.step_iters,
+                    large_workers=args.workers, m="log-U[100,8000]", n="log-U[50,4000]",
+                    classes="lasso,logistic,huber,svm,nnls"))))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -406,12 +516,24 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve"])
+    ap.add_argument("--count", type=int, default=2048, help="batch workload: instances")
+    ap.add_argument("--plain-sample", type=int, default=128, help="batch workload: plain-path sample")
+    ap.add_argument("--requests", type=int, default=4000, help="serve workload: requests in the trace")
+    ap.add_argument("--pool", type=int, default=256, help="serve workload: distinct payloads")
+    ap.add_argument("--workers", type=int, default=8, help="serve workload: threads for large requests")
+    ap.add_argument("--step-iters", type=int, default=25, help="serve workload: iterations per step")
+    ap.add_argument("--plain-limit", type=float, default=60.0, help="serve workload: seconds for the plain run")
     ap.add_argument("--loop-mode", type=int, default=0,
                     help="0: one graph per solve (conditional WHILE node); 1: host-checked loop over a "
                          "captured iteration (for profilers that skip conditional graphs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -7,23 +7,34 @@ namespace pogs {
 
 POGS_DEV float sigmoidf(float z) { return 1.0f / (1.0f + expf(-z)); }
 
-// argmin_z log(1+e^z) + (r/2)(z - v)^2: the root of sigma(z) + r (z - v) = 0, which lies in
-// [v - 1/r, v].  Newton steps kept inside a shrinking bracket (bisection when a step
-// leaves it); the map is strictly increasing so the root is unique.
+// argmin_z log(1+e^z) + (r/2)(z - v)^2: the root of phi(z) = sigma(z) + r (z - v), which is
+// strictly increasing, negative at v - 1/r and positive at v.  Safeguarded Newton: a step is
+// replaced by bisection of the current bracket whenever it would leave the bracket or fails to
+// halve the step before it (plain Newton can bounce between the two flat tails of the sigmoid
+// without converging), so the bracket at least halves every other iteration.
 POGS_DEV float prox_logistic(float v, float r) {
   float lo = v - 1.0f / r, hi = v;
-  float z = v - sigmoidf(v) / (1.0f + r);   // one implicit-Euler guess, inside the bracket
+  float z = v - sigmoidf(v) / (1.0f + r);   // one implicit-Euler guess
   z = fminf(fmaxf(z, lo), hi);
+  float dx_old = hi - lo, dx = dx_old;
 #pragma unroll 1
-  for (int it = 0; it < 40; ++it) {
+  for (int it = 0; it < 64; ++it) {
     const float s = sigmoidf(z);
     const float phi = s + r * (z - v);
+    const float dphi = s * (1.0f - s) + r;
+    if (phi == 0.0f) break;
     if (phi > 0.0f) hi = z; else lo = z;
-    float zn = z - phi / (s * (1.0f - s) + r);
-    if (!(zn > lo && zn < hi)) zn = 0.5f * (lo + hi);
-    const bool stop = fabsf(zn - z) <= 1e-7f * (1.0f + fabsf(zn)) || hi - lo <= 1e-7f * (1.0f + fabsf(zn));
-    z = zn;
-    if (stop) break;
+    const bool newton_out = ((z - hi) * dphi - phi) * ((z - lo) * dphi - phi) > 0.0f;
+    const bool too_slow = fabsf(2.0f * phi) > fabsf(dx_old * dphi);
+    dx_old = dx;
+    if (newton_out || too_slow) {
+      dx = 0.5f * (hi - lo);
+      z = lo + dx;
+    } else {
+      dx = phi / dphi;
+      z = z - dx;
+    }
+    if (fabsf(dx) <= 1e-7f * (1.0f + fabsf(z)) || hi - lo <= 1e-7f * (1.0f + fabsf(z))) break;
   }
   return z;
 }

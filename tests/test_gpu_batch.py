@@ -71,3 +71,15 @@ def test_batch_of_device_inputs_equals_host_inputs(P):
     devr = P.pogs_solve_batch(dprobs, P.pogs_default_params())
     for a, b in zip(host, devr):
         assert a[0].iters == b[0].iters and np.array_equal(a[1], b[1])
+
+
+def test_batch_logistic_instances_converge_and_match_oracle(P):
+    """Logistic regression instances (the class whose prox is an inner root-find) in the batched
+    engine: every one converges under adaptive rho and matches the oracle."""
+    probs = W.batch_mix(count=24, base_seed=73_000, classes=("logistic",))
+    res = P.pogs_solve_batch(probs, P.pogs_default_params(max_iter=5000))
+    for k, (prob, (info, *_)) in enumerate(zip(probs, res)):
+        assert info.status == 0, (k, prob.A.shape, info.as_dict())
+        if k % 3 == 0:
+            ref = _tight(prob)
+            assert abs(info.obj - ref.obj) <= 1e-3 * max(1.0, abs(ref.obj)), (k, info.obj, ref.obj)

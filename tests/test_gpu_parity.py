@@ -64,6 +64,27 @@ def test_prox_eval_matches_oracle(P, code):
     assert err.max() <= 2e-5, (err.max(), int(err.argmax()))
 
 
+@pytest.mark.parametrize("code", [W.H[k] for k in ("LOGISTIC", "HUBER", "ABS", "MAXPOS")],
+                         ids=["LOGISTIC", "HUBER", "ABS", "MAXPOS"])
+def test_prox_eval_extreme_regimes(P, code):
+    """The unit base prox (a = c = 1, b = d = e = 0) at rho from 1e-6 to 1e4 and |v| up to 1e4.
+    For the logistic this is the regime where an unguarded Newton iteration bounces between the
+    two flat tails of the sigmoid (small rho, |v| of tens to thousands)."""
+    import torch
+    rng = np.random.default_rng(900 + code)
+    k = 60000
+    v = (rng.standard_normal(k) * 10 ** rng.uniform(-1, 4, k)).astype(np.float32)
+    rho = (10 ** rng.uniform(-6, 4, k)).astype(np.float32)
+    one, zero = np.ones(k, np.float32), np.zeros(k, np.float32)
+    fn = W.FnParams(np.full(k, code, np.uint8), one, zero, one, zero, zero)
+    dev = lambda x: torch.from_numpy(x).cuda()
+    fd = W.FnParams(dev(fn.h), dev(one), dev(zero), dev(one), dev(zero), dev(zero))
+    got = P.pogs_prox_eval(fd, dev(v), rho_vec=dev(rho)).cpu().numpy().astype(np.float64)
+    ref = OP.prox_f(fn, v.astype(np.float64), rho.astype(np.float64))
+    err = np.abs(got - ref) / (1 + np.abs(ref) + np.abs(v))
+    assert err.max() <= 2e-5, (err.max(), float(v[err.argmax()]), float(rho[err.argmax()]))
+
+
 # ---------------------------------------------------------------------------------------------
 SHAPES = [(700, 300), (300, 700), (1100, 1030), (2500, 130), (130, 2500), (257, 257)]
 
