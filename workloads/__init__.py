@@ -207,6 +207,16 @@ def lp(m: int, n: int, seed: int, density=0.1) -> Problem:
 CLASSES = dict(lasso=lasso, logistic=logistic, huber=huber, svm=svm, nnls=nnls, lp=lp)
 
 
+def nnls_precision_large(seed: int = 30_000) -> Problem:
+    """Dense NNLS, 30000 x 15000 (1.8 GB FP32), for the Gram-precision study."""
+    return nnls(30000, 15000, seed)
+
+
+def lp_precision_large(seed: int = 30_001) -> Problem:
+    """Inequality-form LP, 30000 x 15000, 10% nonzeros stored dense, for the Gram-precision study."""
+    return lp(30000, 15000, seed, density=0.1)
+
+
 def _log_uniform_int(rng, lo, hi) -> int:
     return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
 
