@@ -1,0 +1,501 @@
+// Mixed-precision blocked Cholesky of I + G and the FP32 inverse factor M = L^{-1}
+// (Section 3.5, factorization caching), built on one double-buffered SIMT SGEMM.
+//
+// Right-looking, 128-wide block columns (the tile edge of the packed inverse):
+//   diag   one CTA factors the 128 x 128 diagonal block of the FP64 Schur complement in FP32
+//          shared memory (32-wide sub-blocks) and inverts it; W_kk = L_kk^{-1} is also the
+//          diagonal tile of M;
+//   panel  L21 = H21 W_kk^T from the FP32-rounded Schur complement, stored FP32;
+//   update H22 <- H22 - L21 L21^T: FP32 products accumulated over the 128-wide panel, then
+//          subtracted from the Schur complement (lower tiles only).
+// The Schur complement is held in extended precision as an unevaluated sum hi + lo of two
+// FP32 numbers and every update is applied with error-free transformations (Knuth's TwoSum
+// followed by Dekker's Fast2Sum renormalisation), which carries about 48 significant bits
+// through the q/128 block steps using only the FP32 pipes -- B300's FP64 rate is a small
+// fraction of its FP32 rate, and an FP64 subtraction per element and block step would cost
+// as much as the products themselves.  Every O(q^3) product runs on the FP32 pipes.  I + G
+// has all eigenvalues >= 1, so no pivot of the factorization suffers cancellation.
+//
+// The inverse uses the 2 x 2 block identity
+//   inv([[L11, 0], [L21, L22]]) = [[M11, 0], [-M22 L21 M11, M22]]
+// recursively, splitting at multiples of 128 so that the leaves are the W_kk above.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace pogs {
+namespace {
+
+constexpr int kBM = 128, kBN = 128, kBK = 16;
+constexpr int kLDS = kBM + 4;   // shared k-row pitch (floats): 16-byte aligned rows
+
+enum { OUT_F32 = 0, OUT_SUB_DF = 1 };
+
+// (hi, lo) <- (hi, lo) - x exactly up to the final rounding of the pair: TwoSum of hi and -x
+// (the rounding error e of s = hi - x is recovered exactly), then Fast2Sum of s and lo + e.
+__device__ __forceinline__ void df_sub(float& hi, float& lo, float x) {
+  const float s = __fsub_rn(hi, x);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(-x, bb));
+  const float t = __fadd_rn(lo, e);
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+// Four consecutive elements r[0 .. 3] of a row whose remaining length is `left` (zero past
+// it).  The caller guarantees 16-byte alignment of r (ld % 4 == 0, k % 4 == 0).
+__device__ __forceinline__ float4 ld4(const float* __restrict__ r, int64_t left) {
+  if (left >= 4) return *reinterpret_cast<const float4*>(r);
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (left > 0) v.x = r[0];
+  if (left > 1) v.y = r[1];
+  if (left > 2) v.z = r[2];
+  return v;
+}
+// C = op(A) op(B) on 128 x 128 tiles, 256 threads, 8 x 8 outputs per thread (two 4-row by
+// two 4-column groups, 64 apart, so shared reads are float4 and conflict-free).
+//   A: M x K row-major.
+//   B: BT ? N x K row-major (C = A B^T) : K x N row-major (C = A B).
+//   OUT_F32:    Cf = alpha * (A op(B))
+//   OUT_SUB_DF: (Cf, Clo) -= A op(B) on the double-float pair, elements on or below the
+//               diagonal only when `lower`.
+// MINB: resident CTAs per SM the register budget is sized for.
+// `lower`: blockIdx.x enumerates the lower-triangular tiles (row of tiles by row of tiles).
+// `tri`: bit 0 -- op(B) lower triangular (rows k < j of column j are zero): skip k < col0;
+//        bit 1 -- A lower triangular (A[i][k] = 0 for k > i): stop at row0 + 128.
+// Global tiles are prefetched into registers while the previous shared tile is consumed.
+template <bool BT, int OUT, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    sgemm128_kernel(int M, int N, int K, const float* __restrict__ A, int64_t lda, const float* __restrict__ B,
+                    int64_t ldb, float alpha, float* __restrict__ Cf, float* __restrict__ Clo, int64_t ldc,
+                    int lower, int tri) {
+  __shared__ __align__(16) float As[2][kBK][kLDS];
+  __shared__ __align__(16) float Bs[2][kBK][kLDS];
+  int bi, bj;
+  if (lower) {
+    const int b = blockIdx.x;
+    int I = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
+    while ((I + 1) * (I + 2) / 2 <= b) ++I;
+    while (I * (I + 1) / 2 > b) --I;
+    bi = I;
+    bj = b - I * (I + 1) / 2;
+  } else {
+    bi = blockIdx.y;
+    bj = blockIdx.x;
+  }
+  const int row0 = bi * kBM, col0 = bj * kBN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  int kbeg = 0, kend = K;
+  if (tri & 1) kbeg = col0 < K ? col0 : K;
+  if (tri & 2) kend = row0 + kBM < K ? row0 + kBM : K;
+
+  // per-thread global sources: A rows r = tid/4 (+64), K offset 4*(tid%4); B likewise when
+  // BT, else K row tid/32 (+8) and columns 4*(tid%32)
+  const int r_ld = tid >> 2, kq = (tid & 3) * 4;
+  const float* ap[2];
+  const float* bp[2];
+  bool aok[2], bok[2];
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    const int ar = row0 + r_ld + 64 * l;
+    aok[l] = ar < M;
+    ap[l] = A + (int64_t)(aok[l] ? ar : 0) * lda + kq;
+    if (BT) {
+      const int br = col0 + r_ld + 64 * l;
+      bok[l] = br < N;
+      bp[l] = B + (int64_t)(bok[l] ? br : 0) * ldb + kq;
+    } else {
+      const int bc = col0 + (tid & 31) * 4;
+      bok[l] = bc < N;
+      bp[l] = B + (int64_t)((tid >> 5) + 8 * l) * ldb + (bok[l] ? bc : 0);
+    }
+  }
+  const int bc_left = N - (col0 + (tid & 31) * 4);
+
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+  float4 ra[2], rb[2];
+  auto gload = [&](int k0) {
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      ra[l] = aok[l] ? ld4(ap[l] + k0, K - (k0 + kq)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (BT) {
+        rb[l] = bok[l] ? ld4(bp[l] + k0, K - (k0 + kq)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        const int kr = k0 + (tid >> 5) + 8 * l;
+        rb[l] = (bok[l] && kr < K) ? ld4(bp[l] + (int64_t)k0 * ldb, bc_left) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      const int r = r_ld + 64 * l;
+      As[buf][kq + 0][r] = ra[l].x;
+      As[buf][kq + 1][r] = ra[l].y;
+      As[buf][kq + 2][r] = ra[l].z;
+      As[buf][kq + 3][r] = ra[l].w;
+      if (BT) {
+        Bs[buf][kq + 0][r] = rb[l].x;
+        Bs[buf][kq + 1][r] = rb[l].y;
+        Bs[buf][kq + 2][r] = rb[l].z;
+        Bs[buf][kq + 3][r] = rb[l].w;
+      } else {
+        *reinterpret_cast<float4*>(&Bs[buf][(tid >> 5) + 8 * l][(tid & 31) * 4]) = rb[l];
+      }
+    }
+  };
+
+  if (kbeg < kend) {
+    gload(kbeg);
+    sstore(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = kbeg; k0 < kend; k0 += kBK) {
+      const bool more = k0 + kBK < kend;
+      if (more) gload(k0 + kBK);
+#pragma unroll
+      for (int k = 0; k < kBK; ++k) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4 + 64]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 4]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 4 + 64]);
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+      if (more) sstore(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gi = row0 + ty * 4 + (i & 3) + (i >> 2) * 64;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int gj0 = col0 + tx * 4 + h * 64;
+      if (gj0 >= N) continue;
+      const float v0 = acc[i][h * 4 + 0], v1 = acc[i][h * 4 + 1], v2 = acc[i][h * 4 + 2], v3 = acc[i][h * 4 + 3];
+      if (OUT == OUT_F32) {
+        float* c = Cf + (int64_t)gi * ldc + gj0;
+        if (gj0 + 3 < N) {
+          *reinterpret_cast<float4*>(c) = make_float4(alpha * v0, alpha * v1, alpha * v2, alpha * v3);
+        } else {
+          c[0] = alpha * v0;
+          if (gj0 + 1 < N) c[1] = alpha * v1;
+          if (gj0 + 2 < N) c[2] = alpha * v2;
+        }
+      } else {
+        float* ch = Cf + (int64_t)gi * ldc + gj0;
+        float* cl = Clo + (int64_t)gi * ldc + gj0;
+        const int lim = min(N, lower ? gi + 1 : N) - gj0;   // elements of this group to update
+        if (lim >= 4) {
+          float4 h = *reinterpret_cast<float4*>(ch);
+          float4 l = *reinterpret_cast<float4*>(cl);
+          df_sub(h.x, l.x, v0);
+          df_sub(h.y, l.y, v1);
+          df_sub(h.z, l.z, v2);
+          df_sub(h.w, l.w, v3);
+          *reinterpret_cast<float4*>(ch) = h;
+          *reinterpret_cast<float4*>(cl) = l;
+        } else if (lim > 0) {
+          df_sub(ch[0], cl[0], v0);
+          if (lim > 1) df_sub(ch[1], cl[1], v1);
+          if (lim > 2) df_sub(ch[2], cl[2], v2);
+        }
+      }
+    }
+  }
+}
+
+template <bool BT, int OUT, int MINB>
+void sgemm_launch(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
+                  float alpha, float* Cf, float* Clo, int64_t ldc, bool lower, int tri, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return;
+  count_launch();   // sizes fit int: q <= 2^31 / 128 rows of 128-tiles
+  if (lower) {
+    const int64_t T = cdiv(M, kBM);
+    sgemm128_kernel<BT, OUT, MINB><<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(
+        (int)M, (int)N, (int)K, A, lda, B, ldb, alpha, Cf, Clo, ldc, 1, tri);
+  } else {
+    dim3 grid((unsigned)cdiv(N, kBN), (unsigned)cdiv(M, kBM));
+    sgemm128_kernel<BT, OUT, MINB><<<grid, 256, 0, s>>>((int)M, (int)N, (int)K, A, lda, B, ldb, alpha, Cf, Clo,
+                                                         ldc, 0, tri);
+  }
+}
+
+// ---- diagonal block ------------------------------------------------------------------------
+constexpr int kDB = 128;        // block edge
+constexpr int kDS = kDB + 1;    // shared row pitch (conflict-free column walks)
+
+// One CTA factors the nb x nb diagonal block Hkk (hi part, lower triangle read) in FP32 and
+// writes W = L_kk^{-1} (lower triangular, zero above the diagonal) to W (ld ldw).  Rows and
+// columns nb..127 are padded with the identity.  Four 32-wide sub-block steps: warp 0 factors
+// the 32 x 32 diagonal sub-block in registers (lane = row, pivot columns broadcast by
+// shuffles) and inverts it (lane = column, forward substitution on e_c); all warps then form
+// the panel below it, P = S_panel V^T, and update the trailing rows.  The off-diagonal blocks
+// of W follow by block forward substitution, W_ij = -W_ii sum_{k=j}^{i-1} L_ik W_kj.
+__global__ void __launch_bounds__(256) chol_diag_kernel(const float* __restrict__ Hkk, int64_t ldh, int nb,
+                                                        float* __restrict__ W, int64_t ldw, int* err) {
+  extern __shared__ float sm[];
+  float* S = sm;               // [128][129]: Schur block, then L
+  float* V = S + kDB * kDS;    // [128][129]: W in the lower triangle; panel and T scratch
+  float* Dv = V + kDB * kDS;   // [128]: 1 / L_jj
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < kDB * kDB; e += 256) {
+    const int i = e >> 7, k = e & 127;
+    float v = 0.0f;
+    if (i < nb && k <= i) v = Hkk[(int64_t)i * ldh + k];
+    else if (i == k) v = 1.0f;
+    S[i * kDS + k] = v;
+    V[i * kDS + k] = 0.0f;
+  }
+  __syncthreads();
+  bool bad = false;
+  for (int jb = 0; jb < 4; ++jb) {
+    const int o = jb * 32;
+    if (warp == 0) {
+      // 32 x 32 sub-block: lane = row, pivot column broadcast by shuffles.  1/L_jj comes from
+      // rsqrt of the pivot (no divide), L_jj = pivot * (1/L_jj); Dv keeps 1/L_jj for the
+      // inverse.
+      float* Sd = S + o * kDS + o;
+      float r[32];
+      float dinv = 1.0f;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) r[k] = k <= lane ? Sd[lane * kDS + k] : 0.0f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        float piv = __shfl_sync(0xffffffffu, r[j], j);
+        if (!(piv > 0.0f) || !isfinite(piv)) {
+          bad = true;
+          piv = 1.0f;
+        }
+        const float rs = rsqrtf(piv);
+        if (lane == j) {
+          r[j] = piv * rs;
+          dinv = rs;
+        } else if (lane > j) {
+          r[j] *= rs;
+        }
+#pragma unroll
+        for (int k = 1; k < 32; ++k) {   // uniform bounds keep r[] in registers (full unroll)
+          const float lkj = __shfl_sync(0xffffffffu, r[j], k);
+          if (k > j && lane >= k) r[k] = fmaf(-r[j], lkj, r[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if (k <= lane) Sd[lane * kDS + k] = r[k];
+      Dv[o + lane] = dinv;
+      __syncwarp();
+      // inverse of the 32 x 32 factor, lane = column c: v_i = -(sum_{k<i} L_ik v_k) / L_ii
+      float* Vd = V + o * kDS + o;
+      float v[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        float a = 0.0f;
+#pragma unroll
+        for (int k = 0; k < i; ++k) a = fmaf(Sd[i * kDS + k], v[k], a);
+        const float di = Dv[o + i];
+        v[i] = i < lane ? 0.0f : (i == lane ? di : -a * di);
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) Vd[i * kDS + lane] = v[i];
+    }
+    __syncthreads();
+    const int rows = kDB - o - 32;   // 96, 64, 32, 0: whole warps
+    // panel P = S_panel V_jj^T into the (still unused) lower part of V; task = one element
+    for (int t = tid; t < rows * 32; t += 256) {
+      const int rr = o + 32 + (t % rows), cc = t / rows;
+      const float* Sr = S + rr * kDS + o;
+      const float* Vc = V + (o + cc) * kDS + o;
+      float a0 = 0.0f, a1 = 0.0f;
+      int k = 0;
+      for (; k + 1 <= cc; k += 2) {
+        a0 = fmaf(Sr[k], Vc[k], a0);
+        a1 = fmaf(Sr[k + 1], Vc[k + 1], a1);
+      }
+      if (k <= cc) a0 = fmaf(Sr[k], Vc[k], a0);
+      V[rr * kDS + o + cc] = a0 + a1;
+    }
+    __syncthreads();
+    if (rows > 0) {
+      // P back into S (the factor's panel), and S[i][k] -= sum_c P[i][c] P[k][c] for
+      // o+32 <= k <= i < 128 in 4 x 4 register blocks
+      for (int e = tid; e < rows * 32; e += 256) {
+        const int rr = o + 32 + (e >> 5), cc = o + (e & 31);
+        S[rr * kDS + cc] = V[rr * kDS + cc];
+      }
+      const int nbk = rows / 4;
+      for (int b = tid; b < nbk * nbk; b += 256) {
+        const int bi = b / nbk, bk = b - bi * nbk;
+        if (bk > bi) continue;
+        const int i0 = o + 32 + bi * 4, k0 = o + 32 + bk * 4;
+        float a[4][4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a[t][u] = 0.0f;
+#pragma unroll 4
+        for (int cc = 0; cc < 32; ++cc) {
+          float pi[4], pk[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            pi[t] = V[(i0 + t) * kDS + o + cc];
+            pk[t] = V[(k0 + t) * kDS + o + cc];
+          }
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[t][u] = fmaf(pi[t], pk[u], a[t][u]);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (k0 + u <= i0 + t) S[(i0 + t) * kDS + k0 + u] -= a[t][u];
+      }
+    }
+    __syncthreads();
+  }
+  // Off-diagonal 32-blocks of W, block row by block row.  T_j = sum_k L_{bi,k} W_{k,j} goes to
+  // the (j, bi) block of V (strictly above the block diagonal, never part of W), then
+  // W_{bi,j} = -V_{bi} T_j.  Task = 4 x 4 outputs.
+  for (int bi = 1; bi < 4; ++bi) {
+    for (int t = tid; t < bi * 64; t += 256) {
+      const int j = t >> 6, r0 = ((t >> 3) & 7) * 4, c0 = (t & 7) * 4;
+      float a[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) a[x][y] = 0.0f;
+      for (int kk = j * 32; kk < bi * 32; ++kk) {
+        float l[4], w[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) l[x] = S[(bi * 32 + r0 + x) * kDS + kk];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) w[y] = V[kk * kDS + j * 32 + c0 + y];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) a[x][y] = fmaf(l[x], w[y], a[x][y]);
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) V[(j * 32 + r0 + x) * kDS + bi * 32 + c0 + y] = a[x][y];
+    }
+    __syncthreads();
+    for (int t = tid; t < bi * 64; t += 256) {
+      const int j = t >> 6, r0 = ((t >> 3) & 7) * 4, c0 = (t & 7) * 4;
+      float a[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) a[x][y] = 0.0f;
+      for (int tt = 0; tt < r0 + 4; ++tt) {   // V_bi is lower triangular: rows r0..r0+3 need tt <= r0+3
+        float vv[4], tv[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) vv[x] = V[(bi * 32 + r0 + x) * kDS + bi * 32 + tt];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) tv[y] = V[(j * 32 + tt) * kDS + bi * 32 + c0 + y];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) a[x][y] = fmaf(vv[x], tv[y], a[x][y]);
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) V[(bi * 32 + r0 + x) * kDS + j * 32 + c0 + y] = -a[x][y];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nb * nb; e += 256) {
+    const int i = e / nb, k = e - (e / nb) * nb;
+    W[(int64_t)i * ldw + k] = k <= i ? V[i * kDS + k] : 0.0f;
+  }
+  if (bad && lane == 0) atomicCAS(err, 0, POGS_ERR_NUMERIC);
+}
+
+constexpr size_t kDiagSmem = (size_t)(2 * kDB * kDS + kDB) * sizeof(float);
+
+// Recursive 2 x 2 block inverse on the FP32 factor (leaves already in M).
+void inv_rec(const float* L, int64_t ldl, float* M, int64_t ldm, int64_t r0, int64_t nsz, float* work,
+             cudaStream_t s) {
+  if (nsz <= kTile) return;
+  const int64_t nblk = cdiv(nsz, kTile);
+  const int64_t n1 = (nblk / 2) * kTile, n2 = nsz - n1;
+  inv_rec(L, ldl, M, ldm, r0, n1, work, s);
+  inv_rec(L, ldl, M, ldm, r0 + n1, n2, work, s);
+  // T = L21 M11 (M11 lower triangular), then M21 = -M22 T (M22 lower triangular)
+  sgemm_launch<false, OUT_F32, 1>(n2, n1, n1, L + (r0 + n1) * ldl + r0, ldl, M + r0 * ldm + r0, ldm, 1.0f, work,
+                                  nullptr, n1, false, 1, s);
+  sgemm_launch<false, OUT_F32, 1>(n2, n1, n2, M + (r0 + n1) * ldm + r0 + n1, ldm, work, n1, -1.0f,
+                                  M + (r0 + n1) * ldm + r0, nullptr, ldm, false, 2, s);
+}
+
+// I + G as the double-float pair (G in place becomes hi; lo receives the rounding error of the
+// diagonal 1 + G_ii), lower triangle, zero above.
+__global__ void gram_to_df_kernel(float* G, int64_t ld, int64_t q, float* lo) {
+  const int64_t total = q * q;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / q, j = e - i * q;
+    float h = 0.0f, l = 0.0f;
+    if (j < i) {
+      h = G[i * ld + j];
+    } else if (j == i) {
+      const float g = G[i * ld + j];
+      h = __fadd_rn(g, 1.0f);
+      const float bb = __fsub_rn(h, g);
+      l = __fadd_rn(__fsub_rn(g, __fsub_rn(h, bb)), __fsub_rn(1.0f, bb));   // TwoSum error, exact
+    }
+    G[i * ld + j] = h;
+    lo[i * ld + j] = l;
+  }
+}
+
+}  // namespace
+
+int chol_mixed(float* G, float* Hlo, int64_t ldh, int64_t q, float* Lf, int64_t ldf, float* Md, int64_t ldm,
+               int* err, cudaStream_t s) {
+  if ((ldh | ldf | ldm) & 3) return POGS_ERR_ARG;   // 16-byte rows for the vector loads
+  if (cudaFuncSetAttribute(chol_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiagSmem) !=
+      cudaSuccess)
+    return POGS_ERR_CUDA;
+  count_launch();
+  gram_to_df_kernel<<<(int)std::min<int64_t>(cdiv(q * q, 256), 148 * 16), 256, 0, s>>>(G, ldh, q, Hlo);
+  float* Hhi = G;
+  for (int64_t k0 = 0; k0 < q; k0 += kDB) {
+    const int nb = (int)std::min<int64_t>(kDB, q - k0);
+    count_launch();
+    chol_diag_kernel<<<1, 256, kDiagSmem, s>>>(Hhi + k0 * ldh + k0, ldh, nb, Md + k0 * ldm + k0, ldm, err);
+    const int64_t rest = q - k0 - nb;
+    if (rest > 0) {
+      // L21 = H21 W_kk^T (from the hi part: the pair rounds to hi)
+      sgemm_launch<true, OUT_F32, 2>(rest, kDB, kDB, Hhi + (k0 + kDB) * ldh + k0, ldh, Md + k0 * ldm + k0, ldm,
+                                     1.0f, Lf + (k0 + kDB) * ldf + k0, nullptr, ldf, false, 0, s);
+      // H22 -= L21 L21^T (lower tiles, double-float)
+      const float* P = Lf + (k0 + kDB) * ldf + k0;
+      sgemm_launch<true, OUT_SUB_DF, 2>(rest, rest, kDB, P, ldf, P, ldf, 1.0f, Hhi + (k0 + kDB) * ldh + k0 + kDB,
+                                        Hlo + (k0 + kDB) * ldh + k0 + kDB, ldh, true, 0, s);
+    }
+  }
+  return 0;
+}
+
+void tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ldm, float* work, cudaStream_t s) {
+  inv_rec(L, ldl, M, ldm, 0, q, work, s);
+}
+
+}  // namespace pogs

@@ -99,12 +99,15 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, c
 void launch_gram_to_f64(const float* G, int64_t ldg, int64_t q, double* H, int64_t ldh, cudaStream_t s);
 // FP64 products of FP32-rounded inputs: C (FP64) = alpha op(A) op(B) + beta C with the
 // products and their sum over K formed in FP32.
-void gemm_f64_f32prod(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
-                      int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
-                      bool lower_only, cudaStream_t s);
 // Right-looking blocked Cholesky of H (lower, in place).  mixed: trailing products in FP32
 // (FP64 diagonal blocks, panel solves and Schur complement).
-int chol_f64(double* H, int64_t ldh, int64_t q, double* work, int* err, bool mixed, cudaStream_t s);
+int chol_f64(double* H, int64_t ldh, int64_t q, double* work, int* err, cudaStream_t s);
+// Mixed-precision factorization (chol.cu) of I + G: G (lower triangle, ld ldh) is overwritten
+// with the hi part of the double-float Schur complement, Hlo (same layout) receives the lo
+// part; the FP32 off-diagonal panels of L go to Lf and the diagonal 128-blocks of L^{-1} to
+// Md.  ldh, ldf, ldm must be multiples of 4.
+int chol_mixed(float* G, float* Hlo, int64_t ldh, int64_t q, float* Lf, int64_t ldf, float* Md, int64_t ldm,
+               int* err, cudaStream_t s);
 void launch_leaf_inverse(const double* L, int64_t ldl, int64_t q, float* Minv, int64_t ldm, cudaStream_t s);
 void launch_l_to_f32(const double* L, int64_t ldl, int64_t q, float* Lf, int64_t ldf, cudaStream_t s);
 void tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ldm, float* work,

@@ -1,7 +1,8 @@
 // One-time setup kernels: ingest of A, Sinkhorn-Knopp finish + Frobenius rescale
-// (Algorithm 2, Section 4.1.2), the dense SIMT GEMM used for the FP32 Gram mode, the FP64
-// blocked Cholesky of I + G (Section 3.5, factorization caching) and the FP32 triangular
-// inverse M = L^{-1} that the iteration applies, packed into 128 x 128 tiles.
+// (Algorithm 2, Section 4.1.2), the dense SIMT GEMM used for the FP32 Gram mode, the all-FP64
+// blocked Cholesky of I + G (Section 3.5, factorization caching; the mixed-precision default
+// is in chol.cu), the FP64 leaf inverses it needs, and the packing of M = L^{-1} into
+// 128 x 128 tiles.
 #include <algorithm>
 #include <cstdio>
 
@@ -202,12 +203,6 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, c
   gemm_launch<double, double, 64, 64, 8, 4, 4>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, 0,
                                                s);
 }
-void gemm_f64_f32prod(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
-                      int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
-                      bool lower_only, cudaStream_t s) {
-  gemm_launch<double, float, 128, 128, 8, 8, 8>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only,
-                                                0, s);
-}
 
 // H = I + G (lower triangle, FP64), zero above the diagonal.
 __global__ void gram_to_f64_kernel(const float* G, int64_t ldg, int64_t q, double* H, int64_t ldh) {
@@ -280,7 +275,7 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* Hk, int64_t ldh
   }
 }
 
-int chol_f64(double* H, int64_t ldh, int64_t q, double* work, int* err, bool mixed, cudaStream_t s) {
+int chol_f64(double* H, int64_t ldh, int64_t q, double* work, int* err, cudaStream_t s) {
   for (int64_t k0 = 0; k0 < q; k0 += kNB) {
     const int nb = (int)std::min<int64_t>(kNB, q - k0);
     count_launch();
@@ -290,13 +285,8 @@ int chol_f64(double* H, int64_t ldh, int64_t q, double* work, int* err, bool mix
       double* P = H + (k0 + nb) * ldh + k0;
       // panel: P <- P L_kk^{-T} (in place: one block column covers all nb <= 64 columns)
       gemm_f64(false, true, rest, nb, nb, 1.0, P, ldh, work, kNB, 0.0, P, ldh, false, s);
-      // trailing update: H22 <- H22 - P P^T (lower tiles), FP64 Schur complement; the mixed
-      // variant forms the products from the FP32-rounded panel in FP32
-      if (mixed)
-        gemm_f64_f32prod(false, true, rest, rest, nb, -1.0, P, ldh, P, ldh, 1.0, H + (k0 + nb) * ldh + (k0 + nb), ldh,
-                         true, s);
-      else
-        gemm_f64(false, true, rest, rest, nb, -1.0, P, ldh, P, ldh, 1.0, H + (k0 + nb) * ldh + (k0 + nb), ldh, true, s);
+      // trailing update: H22 <- H22 - P P^T (lower tiles), all in FP64
+      gemm_f64(false, true, rest, rest, nb, -1.0, P, ldh, P, ldh, 1.0, H + (k0 + nb) * ldh + (k0 + nb), ldh, true, s);
     }
   }
   return 0;
@@ -352,27 +342,6 @@ void launch_l_to_f32(const double* L, int64_t ldl, int64_t q, float* Lf, int64_t
   int64_t g = std::min<int64_t>((q * q + 255) / 256, 148 * 16);
   count_launch();
   l_to_f32_kernel<<<(int)g, 256, 0, s>>>(L, ldl, q, Lf, ldf);
-}
-
-// Recursive 2 x 2 block inverse of a lower-triangular matrix:
-//   inv([[L11, 0], [L21, L22]]) = [[M11, 0], [-M22 L21 M11, M22]],
-// splitting at multiples of 128 so the leaves are the FP64-inverted diagonal blocks.
-static void inv_rec(const float* L, int64_t ldl, float* M, int64_t ldm, int64_t r0, int64_t nsz, float* work,
-                    cudaStream_t s) {
-  if (nsz <= kTile) return;
-  const int64_t nblk = cdiv(nsz, kTile);
-  const int64_t n1 = (nblk / 2) * kTile, n2 = nsz - n1;
-  inv_rec(L, ldl, M, ldm, r0, n1, work, s);
-  inv_rec(L, ldl, M, ldm, r0 + n1, n2, work, s);
-  // T = L21 M11 (M11 lower triangular), then M21 = -M22 T (M22 lower triangular)
-  gemm_f32(false, false, n2, n1, n1, 1.0f, L + (r0 + n1) * ldl + r0, ldl, M + r0 * ldm + r0, ldm, 0.0f, work, n1,
-           false, s, 1);
-  gemm_f32(false, false, n2, n1, n2, -1.0f, M + (r0 + n1) * ldm + r0 + n1, ldm, work, n1, 0.0f,
-           M + (r0 + n1) * ldm + r0, ldm, false, s, 2);
-}
-
-void tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ldm, float* work, cudaStream_t s) {
-  inv_rec(L, ldl, M, ldm, 0, q, work, s);
 }
 
 // Pack the lower triangle of M (dense, ld ldm) into 128 x 128 tiles, zero outside.

@@ -351,48 +351,58 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order) {
   CK(cudaGetLastError());
   phase("equil");
   // ---- Gram -----------------------------------------------------------------------------
+  // square work matrices share one 128-byte-aligned pitch (vector loads in the factorization)
+  const int64_t ldq = round_up(q, 32);
   float* G = nullptr;
-  TRY(scr.get(&G, (size_t)(q * q), s));
+  TRY(scr.get(&G, (size_t)(ldq * ldq), s));
   int used = -1;
   if (h->sp.gram_prec != POGS_GRAM_FP32) {
     size_t need = 0;
-    int rc = gram_tensor(h->sp.gram_prec, h->A, h->lda, m, n, h->tall, G, q, nullptr, 0, &need, err, s);
+    int rc = gram_tensor(h->sp.gram_prec, h->A, h->lda, m, n, h->tall, G, ldq, nullptr, 0, &need, err, s);
     if (rc == 0 && need > 0) {
       void* ws = nullptr;
       char* wsc = nullptr;
       TRY(scr.get(&wsc, need, s));
       ws = wsc;
-      rc = gram_tensor(h->sp.gram_prec, h->A, h->lda, m, n, h->tall, G, q, ws, need, &need, err, s);
+      rc = gram_tensor(h->sp.gram_prec, h->A, h->lda, m, n, h->tall, G, ldq, ws, need, &need, err, s);
       if (rc == 0) used = h->sp.gram_prec;
     }
   }
   if (used < 0) {
-    if (h->tall) gemm_f32(true, false, q, q, m, 1.0f, h->A, h->lda, h->A, h->lda, 0.0f, G, q, true, s);
-    else gemm_f32(false, true, q, q, n, 1.0f, h->A, h->lda, h->A, h->lda, 0.0f, G, q, true, s);
+    if (h->tall) gemm_f32(true, false, q, q, m, 1.0f, h->A, h->lda, h->A, h->lda, 0.0f, G, ldq, true, s);
+    else gemm_f32(false, true, q, q, n, 1.0f, h->A, h->lda, h->A, h->lda, 0.0f, G, ldq, true, s);
     used = POGS_GRAM_FP32;
   }
   h->gram_used = used;
   CK(cudaGetLastError());
   phase("gram");
-  // ---- FP64 Cholesky of I + G -------------------------------------------------------------
-  double* H = nullptr;
-  TRY(scr.get(&H, (size_t)(q * q), s));
-  launch_gram_to_f64(G, q, q, H, q, s);
-  double* work = nullptr;
-  TRY(scr.get(&work, 64 * 64, s));
-  chol_f64(H, q, q, work, err, h->sp.chol_prec == POGS_CHOL_MIXED, s);
+  // ---- Cholesky of I + G -------------------------------------------------------------------
+  float *Md = nullptr, *Lf = nullptr;
+  TRY(scr.get(&Md, (size_t)(ldq * ldq), s));
+  TRY(scr.get(&Lf, (size_t)(ldq * ldq), s));
+  if (h->sp.chol_prec == POGS_CHOL_MIXED) {
+    // double-float Schur complement (G becomes its hi part); also writes the diagonal blocks of M
+    float* Hlo = nullptr;
+    TRY(scr.get(&Hlo, (size_t)(ldq * ldq), s));
+    TRY(chol_mixed(G, Hlo, ldq, q, Lf, ldq, Md, ldq, err, s));
+  } else {
+    double* H = nullptr;
+    TRY(scr.get(&H, (size_t)(ldq * ldq), s));
+    launch_gram_to_f64(G, ldq, q, H, ldq, s);
+    double* work = nullptr;
+    TRY(scr.get(&work, 64 * 64, s));
+    chol_f64(H, ldq, q, work, err, s);
+    launch_leaf_inverse(H, ldq, q, Md, ldq, s);
+    launch_l_to_f32(H, ldq, q, Lf, ldq, s);
+  }
   CK(cudaGetLastError());
   phase("cholesky");
   // ---- M = L^{-1} (FP32), packed tiles --------------------------------------------------
-  float *Lf = nullptr, *Md = nullptr, *wk = nullptr;
-  TRY(scr.get(&Md, (size_t)(q * q), s));
-  launch_leaf_inverse(H, q, q, Md, q, s);
-  Lf = G;   // G is no longer needed: reuse its storage for the FP32 factor
-  launch_l_to_f32(H, q, q, Lf, q, s);
+  float* wk = nullptr;
   TRY(scr.get(&wk, (size_t)(q * (q / 2 + kTile)), s));
-  tri_inverse_f32(Lf, q, q, Md, q, wk, s);
+  tri_inverse_f32(Lf, ldq, q, Md, ldq, wk, s);
   TRY(dalloc(h, &h->Mt, (size_t)h->T * (h->T + 1) / 2 * kTile * kTile));
-  launch_pack_tiles(Md, q, q, h->T, h->Mt, s);
+  launch_pack_tiles(Md, ldq, q, h->T, h->Mt, s);
   CK(cudaGetLastError());
   phase("inverse");
   CK(cudaStreamSynchronize(s));

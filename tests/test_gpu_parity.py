@@ -238,11 +238,12 @@ def test_degenerate_sizes(P):
         assert info.status in (0, 1) and np.all(np.isfinite(x))
 
 
-@pytest.mark.parametrize("shape", [(1100, 1030), (300, 700)])
+@pytest.mark.parametrize("shape", [(1100, 1030), (300, 700), (7000, 3333), (2100, 4100)])
 @pytest.mark.parametrize("chol", ["FP64", "MIXED"])
 def test_projection_both_cholesky_precisions(P, shape, chol):
-    """Pure FP64 and mixed (FP32 trailing products, FP64 Schur complement) factorizations
-    both reproduce the FP64 projection of the same input within 1e-5."""
+    """Pure FP64 and mixed (FP32 diagonal blocks and products, FP64 Schur complement)
+    factorizations both reproduce the FP64 projection of the same input within 1e-5, up to
+    q = 4100 (33 block columns, ragged last block)."""
     m, n = shape
     prob = W.huber(m, n, seed=17)
     prm = P.pogs_default_params(gram_prec="FP32", chol_prec=chol)
