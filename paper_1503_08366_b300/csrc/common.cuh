@@ -53,6 +53,64 @@ POGS_DEV double warp_sum(double v) {
   return v;
 }
 
+// ---- double-float accumulation -------------------------------------------------------------
+// Sums that must keep more digits than FP32 (norms, gap terms, objective partials) are carried
+// as an unevaluated pair hi + lo of FP32 numbers and updated with error-free transformations:
+// Knuth's TwoSum for additions and the exact rounding error of a product recovered with one
+// FMA.  That keeps about 48 significant bits using only the FP32 pipes (B300's FP64 rate is a
+// small fraction of its FP32 rate); per-warp results are converted to FP64 once.
+struct Df {
+  float hi, lo;
+};
+POGS_DEV void df_add(Df& a, float x) {
+  const float s = __fadd_rn(a.hi, x);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, e);
+}
+POGS_DEV void df_add(Df& a, const Df& b) {
+  df_add(a, b.hi);
+  a.lo = __fadd_rn(a.lo, b.lo);
+}
+POGS_DEV void df_add_prod(Df& a, float x, float y) {   // a += x y
+  const float p = __fmul_rn(x, y);
+  const float pe = __fmaf_rn(x, y, -p);   // exact: x y - p
+  df_add(a, p);
+  a.lo = __fadd_rn(a.lo, pe);
+}
+POGS_DEV double df_value(const Df& a) { return (double)a.hi + (double)a.lo; }
+
+// Block-wide sum of NV double-float values per thread: a fixed xor-shuffle tree on the FP32
+// pipes inside each warp, then the per-warp results in FP64 in warp order; `out` valid in
+// thread 0; `sh` holds NV * (blockDim/32) doubles.  Deterministic.
+template <int NV>
+POGS_DEV void block_sum_df(Df (&v)[NV], double (&out)[NV], double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const Df b{__shfl_xor_sync(0xffffffffu, v[t].hi, o), __shfl_xor_sync(0xffffffffu, v[t].lo, o)};
+      df_add(v[t], b);
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int t = 0; t < NV; ++t) sh[t * nw + wid] = df_value(v[t]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sh[t * nw + w];
+      out[t] = s;
+    }
+  }
+  __syncthreads();
+}
+
 // Block-wide FP64 sum of NV values per thread; result valid in thread 0. `sh` holds
 // NV * (blockDim/32) doubles. Deterministic (fixed shuffle tree + fixed warp order).
 template <int NV>

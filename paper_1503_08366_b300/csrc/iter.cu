@@ -32,13 +32,13 @@ __global__ void __launch_bounds__(256) prox_step_kernel(
     float* __restrict__ cx, float* __restrict__ mu, const float* __restrict__ y,
     float* __restrict__ yt, float* __restrict__ yh, float* __restrict__ dy,
     float* __restrict__ nu, FnDev g, FnDev f, const DevState* __restrict__ st,
-    const DevCfg* __restrict__ cfg, double* __restrict__ part) {
+    const DevCfg* __restrict__ cfg, Df* __restrict__ part) {
   __shared__ double sh[6 * 8];
   if (st->done) return;
   const float rho = (float)st->rho;
   const float pend = (float)st->pend;
   const float alpha = (float)cfg->alpha;
-  double acc[6] = {0, 0, 0, 0, 0, 0};   // ||mu||^2, x.mu, g(x), ||y||^2, y.nu, f(y)
+  Df acc[6] = {};   // ||mu||^2, x.mu, g(x), ||y||^2, y.nu, f(y)
   const int total = n + m;
   const bool rescale = pend != 1.0f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -54,9 +54,9 @@ __global__ void __launch_bounds__(256) prox_step_kernel(
       xh[j] = xhj;
       cx[j] = xr;
       mu[j] = muj;
-      acc[0] += (double)muj * muj;
-      acc[1] += (double)xhj * muj;
-      acc[2] += (double)f_param(h, a, b, c, d, e, xhj);
+      df_add_prod(acc[0], muj, muj);
+      df_add_prod(acc[1], xhj, muj);
+      df_add(acc[2], f_param(h, a, b, c, d, e, xhj));
     } else {
       const int k = i - n;
       const float ytk = pend * yt[k], yk = y[k], v = yk - ytk;
@@ -69,21 +69,25 @@ __global__ void __launch_bounds__(256) prox_step_kernel(
       yh[k] = yhk;
       dy[k] = yr;
       nu[k] = nuk;
-      acc[3] += (double)yhk * yhk;
-      acc[4] += (double)yhk * nuk;
-      acc[5] += (double)f_param(h, a, b, c, d, e, yhk);
+      df_add_prod(acc[3], yhk, yhk);
+      df_add_prod(acc[4], yhk, nuk);
+      df_add(acc[5], f_param(h, a, b, c, d, e, yhk));
     }
   }
-  block_sum<6>(acc, sh);
+  double tot[6];
+  block_sum_df<6>(acc, tot, sh);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int t = 0; t < 6; ++t) part[blockIdx.x * 6 + t] = acc[t];
+    for (int t = 0; t < 6; ++t) {
+      const float hi = (float)tot[t];
+      part[blockIdx.x * 6 + t] = Df{hi, (float)(tot[t] - (double)hi)};
+    }
   }
 }
 
 void launch_prox_step(int n, int m, const float* x, float* xt, float* xh, float* cx, float* mu,
                       const float* y, float* yt, float* yh, float* dy, float* nu, FnDev g, FnDev f,
-                      const DevState* st, const DevCfg* cfg, double* part, int nblocks, cudaStream_t s) {
+                      const DevState* st, const DevCfg* cfg, Df* part, int nblocks, cudaStream_t s) {
   count_launch();
   prox_step_kernel<<<nblocks, 256, 0, s>>>(n, m, x, xt, xh, cx, mu, y, yt, yh, dy, nu, g, f, st, cfg, part);
 }
@@ -95,7 +99,7 @@ void launch_prox_step(int n, int m, const float* x, float* xt, float* xh, float*
 // order and applies the epilogue.
 // ------------------------------------------------------------------------------------------
 template <int EPI>
-__device__ __forceinline__ void epi_t(const EpiArgs& ep, int j, float t1, float t2, float t3, double* res) {
+__device__ __forceinline__ void epi_t(const EpiArgs& ep, int j, float t1, float t2, float t3, Df* res) {
   if constexpr (EPI == EPT_RAW) {
     ep.out1[j] = t1;
     if (ep.out2) ep.out2[j] = t2;
@@ -103,18 +107,18 @@ __device__ __forceinline__ void epi_t(const EpiArgs& ep, int j, float t1, float 
     ep.r[j] = ep.cx[j] + t1;
     ep.xt[j] = -t3;                     // x~ re-derived as -A^T y~ (Section 3.3 invariant)
     const float dr = t2 + ep.mu[j];
-    res[0] += (double)dr * dr;
+    df_add_prod(res[0], dr, dr);
     const float du = dr / ep.E[j];
-    res[1] += (double)du * du;
+    df_add_prod(res[1], du, du);
   } else if constexpr (EPI == EPT_FAT_X) {
     const float c = ep.cx[j];
     const float xp = c + t1;
     ep.x[j] = xp;
     ep.xt[j] = -t3;                     // x~^{k+1} = -A^T y~^{k+1} (Section 3.3 invariant)
     const float dr = t2 + ep.mu[j];
-    res[0] += (double)dr * dr;
+    df_add_prod(res[0], dr, dr);
     const float du = dr / ep.E[j];
-    res[1] += (double)du * du;
+    df_add_prod(res[1], du, du);
   } else if constexpr (EPI == EPT_SK_COL) {
     // sk_num < 0: keep e (Frobenius norm only, no Sinkhorn-Knopp update)
     float ej;
@@ -124,7 +128,7 @@ __device__ __forceinline__ void epi_t(const EpiArgs& ep, int j, float t1, float 
     } else {
       ej = ep.sk_vec[j];
     }
-    res[0] += (double)ej * (double)t1;   // sum_ij d_i A_ij^2 e_j = ||D A E||_F^2 (p = 2)
+    df_add_prod(res[0], ej, t1);   // sum_ij d_i A_ij^2 e_j = ||D A E||_F^2 (p = 2)
   } else if constexpr (EPI == EPT_REFINE) {
     ep.out1[j] = ep.in1[j] - ep.in2[j] - t1;
   }
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(const float* __restrict__ A
           make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
   }
   if (!arrive_last(cnt + blockIdx.x, gridDim.y)) return;
-  double res[2] = {0.0, 0.0};
+  Df res[2] = {};
   if (active) {
     float s[NRHS][4];
 #pragma unroll
@@ -214,10 +218,14 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(const float* __restrict__ A
       if (j < n) epi_t<EPI>(ep, (int)j, s[0][u], NRHS >= 2 ? s[1][u] : 0.0f, NRHS == 3 ? s[NRHS - 1][u] : 0.0f, res);
     }
   }
-  block_sum<2>(res, sh);
+  double tot[2];
+  block_sum_df<2>(res, tot, sh);
   if (threadIdx.x == 0 && ep.res_part) {
-    ep.res_part[2 * blockIdx.x] = res[0];
-    ep.res_part[2 * blockIdx.x + 1] = res[1];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const float hi = (float)tot[t];
+      ep.res_part[2 * blockIdx.x + t] = Df{hi, (float)(tot[t] - (double)hi)};
+    }
   }
 }
 
@@ -228,7 +236,7 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(const float* __restrict__ A
 // reduces in a fixed order and applies the epilogue.
 // ------------------------------------------------------------------------------------------
 template <int EPI>
-__device__ __forceinline__ void epi_n(const EpiArgs& ep, int i, float u1, float u2, double* res) {
+__device__ __forceinline__ void epi_n(const EpiArgs& ep, int i, float u1, float u2, Df* res) {
   if constexpr (EPI == EPN_RAW) {
     ep.out1[i] = u1;
     if (ep.out2) ep.out2[i] = u2;
@@ -236,15 +244,15 @@ __device__ __forceinline__ void epi_n(const EpiArgs& ep, int i, float u1, float 
     ep.y[i] = u1;
     ep.yt[i] += ep.dy[i] - u1;          // y~ <- y~ + y_r - y^{k+1}
     const float pr = u2 - ep.yh[i];
-    res[0] += (double)pr * pr;
+    df_add_prod(res[0], pr, pr);
     const float pu = pr / ep.D[i];
-    res[1] += (double)pu * pu;
+    df_add_prod(res[1], pu, pu);
   } else if constexpr (EPI == EPN_FAT_R) {
     ep.r[i] = u1 - ep.dy[i];
     const float pr = u2 - ep.yh[i];
-    res[0] += (double)pr * pr;
+    df_add_prod(res[0], pr, pr);
     const float pu = pr / ep.D[i];
-    res[1] += (double)pu * pu;
+    df_add_prod(res[1], pu, pu);
   } else if constexpr (EPI == EPN_SK_ROW) {
     ep.sk_vec[i] = ep.sk_num / (u1 + ep.sk_reg);
   } else if constexpr (EPI == EPN_REFINE) {
@@ -311,7 +319,7 @@ __global__ void __launch_bounds__(256) gemv_n_kernel(const float* __restrict__ A
     }
   }
   if (!arrive_last(cnt + blockIdx.x, gridDim.y)) return;
-  double res[2] = {0.0, 0.0};
+  Df res[2] = {};
   for (int row = r0 + tid; row < r1; row += blockDim.x) {
     float u1 = 0.0f, u2 = 0.0f;
     for (int sp = 0; sp < (int)gridDim.y; ++sp) {
@@ -320,10 +328,14 @@ __global__ void __launch_bounds__(256) gemv_n_kernel(const float* __restrict__ A
     }
     epi_n<EPI>(ep, row, u1, u2, res);
   }
-  block_sum<2>(res, sh);
+  double tot[2];
+  block_sum_df<2>(res, tot, sh);
   if (threadIdx.x == 0 && ep.res_part) {
-    ep.res_part[2 * blockIdx.x] = res[0];
-    ep.res_part[2 * blockIdx.x + 1] = res[1];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const float hi = (float)tot[t];
+      ep.res_part[2 * blockIdx.x + t] = Df{hi, (float)(tot[t] - (double)hi)};
+    }
   }
 }
 
@@ -430,31 +442,30 @@ __global__ void __launch_bounds__(256) trmv_kernel(const float* __restrict__ Mt,
 // Stopping test (Section 3.4 + half-tuple gap) and Algorithm 3, single block.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) check_kernel(DevState* st, const DevCfg* __restrict__ cfg,
-                                                    const double* __restrict__ prox_part, int nprox,
-                                                    const double* __restrict__ pri_part, int npri,
-                                                    const double* __restrict__ dual_part, int ndual,
+                                                    const Df* __restrict__ prox_part, int nprox,
+                                                    const Df* __restrict__ pri_part, int npri,
+                                                    const Df* __restrict__ dual_part, int ndual,
                                                     cudaGraphConditionalHandle h, int use_cond) {
   __shared__ double sh[10 * 8];
   if (st->done) {
     if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
     return;
   }
-  double v[10];
-#pragma unroll
-  for (int t = 0; t < 10; ++t) v[t] = 0.0;
+  Df a[10] = {};
   for (int i = threadIdx.x; i < nprox; i += blockDim.x) {
 #pragma unroll
-    for (int t = 0; t < 6; ++t) v[t] += prox_part[6 * i + t];
+    for (int t = 0; t < 6; ++t) df_add(a[t], prox_part[6 * i + t]);
   }
   for (int i = threadIdx.x; i < npri; i += blockDim.x) {
-    v[6] += pri_part[2 * i];
-    v[7] += pri_part[2 * i + 1];
+    df_add(a[6], pri_part[2 * i]);
+    df_add(a[7], pri_part[2 * i + 1]);
   }
   for (int i = threadIdx.x; i < ndual; i += blockDim.x) {
-    v[8] += dual_part[2 * i];
-    v[9] += dual_part[2 * i + 1];
+    df_add(a[8], dual_part[2 * i]);
+    df_add(a[9], dual_part[2 * i + 1]);
   }
-  block_sum<10>(v, sh);
+  double v[10];
+  block_sum_df<10>(a, v, sh);
   if (threadIdx.x != 0) return;
   const double mu2 = v[0], xmu = v[1], gobj = v[2], yh2 = v[3], ynu = v[4], fobj = v[5];
   const double r_pri = sqrt(v[6]), r_pri_u = sqrt(v[7]), r_dual = sqrt(v[8]), r_dual_u = sqrt(v[9]);
@@ -595,10 +606,9 @@ GemvGeom choose_geometry(int64_t m, int64_t n, int64_t lda, int num_sms) {
   // column sums: 1024-column slabs, rows split so that the grid covers ~4 blocks per SM
   g.t_cols_per_blk = 1024;
   g.t_ncolblk = (int)cdiv(lda, 1024);
-  int64_t target = (int64_t)num_sms * 4;
+  int64_t target = (int64_t)num_sms * 5;   // 5 resident 256-thread blocks per SM at the kernel's register count
   int64_t nsplit = cdiv(target, g.t_ncolblk);
-  int64_t rows = cdiv(m, nsplit);
-  rows = rows < 8 ? 8 : rows;
+  int64_t rows = round_up(cdiv(m, nsplit), 8);   // whole 8-row steps
   g.t_rows = (int)rows;
   g.t_nsplit = (int)cdiv(m, rows);
   // row dots: column chunks of <= 4096 floats; rows per block chosen for ~8 blocks per SM
@@ -608,8 +618,9 @@ GemvGeom choose_geometry(int64_t m, int64_t n, int64_t lda, int num_sms) {
   g.n_ncolsplit = (int)cdiv(lda, cols);
   int64_t tgt = (int64_t)num_sms * 8;
   int64_t nrb = cdiv(tgt, g.n_ncolsplit);
-  int64_t rb = cdiv(m, nrb);
-  rb = rb < 8 ? 8 : (rb > 256 ? 256 : rb);
+  // a multiple of 8 rows per block, so that each of the 8 warps gets the same number of rows
+  int64_t rb = round_up(cdiv(m, nrb), 8);
+  rb = rb > 256 ? 256 : rb;
   g.n_rows = (int)rb;
   g.n_nrowblk = (int)cdiv(m, rb);
   return g;
@@ -690,8 +701,8 @@ void launch_trmv(bool trans, int epi, const float* Mt, int T, int q, const float
 #undef POGS_R
 }
 
-void launch_check(DevState* st, const DevCfg* cfg, const double* prox_part, int nprox, const double* pri_part,
-                  int npri, const double* dual_part, int ndual, unsigned long long cond_handle, int use_cond,
+void launch_check(DevState* st, const DevCfg* cfg, const Df* prox_part, int nprox, const Df* pri_part,
+                  int npri, const Df* dual_part, int ndual, unsigned long long cond_handle, int use_cond,
                   cudaStream_t s) {
   count_launch();
   check_kernel<<<1, 256, 0, s>>>(st, cfg, prox_part, nprox, pri_part, npri, dual_part, ndual,

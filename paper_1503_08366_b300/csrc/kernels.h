@@ -37,7 +37,7 @@ struct EpiArgs {
   const float *D, *E;                 // diagonal scalings (unscaled residuals)
   float* sk_vec;                      // SK output vector (d or e)
   float sk_num, sk_reg;               // n and gamma/m (rows) or m and gamma/n (cols)
-  double* res_part;                   // 2 doubles per block: residual^2, unscaled residual^2
+  Df* res_part;                       // 2 per block: residual^2, unscaled residual^2 (double-float)
 };
 
 // Loop parameters in device memory (so a captured graph survives parameter changes).
@@ -57,7 +57,7 @@ GemvGeom choose_geometry(int64_t m, int64_t n, int64_t lda, int num_sms);
 // ---- iteration kernels (iter.cu) --------------------------------------------------------
 void launch_prox_step(int n, int m, const float* x, float* xt, float* xh, float* cx, float* mu,
                       const float* y, float* yt, float* yh, float* dy, float* nu,
-                      FnDev g, FnDev f, const DevState* st, const DevCfg* cfg, double* part,
+                      FnDev g, FnDev f, const DevState* st, const DevCfg* cfg, Df* part,
                       int nblocks, cudaStream_t s);
 void launch_gemv_t(int nrhs, bool sq, int epi, const float* A, int64_t lda, int m, int n,
                    const float* v1, const float* v2, const float* v3, const GemvGeom& g, float* part,
@@ -68,8 +68,8 @@ void launch_gemv_n(int nrhs, bool sq, int epi, const float* A, int64_t lda, int 
                    const EpiArgs& ep, const DevState* guard, cudaStream_t s);
 void launch_trmv(bool trans, int epi, const float* Mt, int T, int q, const float* vin, float* part,
                  unsigned* cnt, const EpiArgs& ep, const DevState* guard, cudaStream_t s);
-void launch_check(DevState* st, const DevCfg* cfg, const double* prox_part, int nprox,
-                  const double* pri_part, int npri, const double* dual_part, int ndual,
+void launch_check(DevState* st, const DevCfg* cfg, const Df* prox_part, int nprox,
+                  const Df* pri_part, int npri, const Df* dual_part, int ndual,
                   unsigned long long cond_handle, int use_cond, cudaStream_t s);
 void launch_prox_eval(FnDev fn, int64_t k, const float* v, const float* rho_vec, float rho, float* out,
                       cudaStream_t s);
@@ -86,7 +86,7 @@ void launch_copy_in(const float* src, int64_t m, int64_t n, int64_t lds, bool co
                     int64_t lda, int* err, cudaStream_t s);
 void launch_scale(float* A, int64_t lda, int64_t m, int64_t n, const float* D, const float* E,
                   cudaStream_t s);
-void launch_sk_finish(const float* dvec, const float* evec, int64_t m, int64_t n, const double* frob_part,
+void launch_sk_finish(const float* dvec, const float* evec, int64_t m, int64_t n, const Df* frob_part,
                       int nfrob, int64_t q, float* D, float* E, cudaStream_t s);
 // C[M x N] = alpha op(A) op(B) + beta C (row-major, SIMT); lower_only skips tiles above
 // the diagonal of C.

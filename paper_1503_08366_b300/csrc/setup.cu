@@ -81,12 +81,12 @@ void launch_scale(float* A, int64_t lda, int64_t m, int64_t n, const float* D, c
 
 // D = sqrt(d / s), E = sqrt(e / s) with s = ||diag(d)^{1/2} A diag(e)^{1/2}||_F / sqrt(q):
 // Algorithm 2's D = diag(d)^{1/p}, E = diag(e)^{1/p} (p = 2) rescaled evenly (Section 4.1.2).
-__global__ void sk_finish_kernel(const float* dvec, const float* evec, int64_t m, int64_t n, const double* frob_part,
+__global__ void sk_finish_kernel(const float* dvec, const float* evec, int64_t m, int64_t n, const Df* frob_part,
                                  int nfrob, int64_t q, float* D, float* E) {
   __shared__ double sh[32];
   __shared__ double s_inv;
   double v[1] = {0.0};
-  for (int i = threadIdx.x; i < nfrob; i += blockDim.x) v[0] += frob_part[2 * i];
+  for (int i = threadIdx.x; i < nfrob; i += blockDim.x) v[0] += df_value(frob_part[2 * i]);
   block_sum<1>(v, sh);
   if (threadIdx.x == 0) s_inv = 1.0 / sqrt(v[0] / (double)q);
   __syncthreads();
@@ -95,7 +95,7 @@ __global__ void sk_finish_kernel(const float* dvec, const float* evec, int64_t m
   for (int64_t j = threadIdx.x; j < n; j += blockDim.x) E[j] = (float)sqrt((double)evec[j] * si);
 }
 
-void launch_sk_finish(const float* dvec, const float* evec, int64_t m, int64_t n, const double* frob_part, int nfrob,
+void launch_sk_finish(const float* dvec, const float* evec, int64_t m, int64_t n, const Df* frob_part, int nfrob,
                       int64_t q, float* D, float* E, cudaStream_t s) {
   count_launch();
   sk_finish_kernel<<<1, 1024, 0, s>>>(dvec, evec, m, n, frob_part, nfrob, q, D, E);

@@ -41,7 +41,7 @@ struct pogs_handle {
   float *fa, *fb, *fc, *fd, *fe, *ga, *gb, *gc, *gd, *ge, *ra, *rb, *rc, *rd, *re;
   float *part_t = nullptr, *part_n = nullptr, *part_tr = nullptr;
   unsigned *cnt_t = nullptr, *cnt_n = nullptr, *cnt_tr = nullptr;
-  double *prox_part = nullptr, *pri_part = nullptr, *dual_part = nullptr;
+  Df *prox_part = nullptr, *pri_part = nullptr, *dual_part = nullptr;   // block partials (double-float)
   DevState* st = nullptr;
   DevCfg* cfg = nullptr;
   DevState* st_host = nullptr;     // pinned mirror
