@@ -289,8 +289,11 @@ def run_ours(args):
     d2h = sum(4 * 2 * (p.m + p.n) for p in probs) + 2 * 112
 
     # ---- per-kernel breakdown and the dominant kernel's roofline --------------------------------
+    # Each iteration kernel is timed live with CUDA events on the launching stream (20 launches
+    # back to back on the solved state, after the timed region); setup phases come from the
+    # setup's own events.  Shares are of one step: per-launch time x launches per solve.
     peaks = _peaks()
-    comp = {}
+    comp = {}        # (kernel, problem index) -> dict(total ms, per-launch ms, bytes per launch, launches)
     per_problem = []
     proj = []
     for i, p in enumerate(probs):
@@ -301,62 +304,61 @@ def run_ours(args):
         kt = P.pogs_time_kernels(h, reps=20)
         P.pogs_free(h)
         it = info.iters
-        q = min(p.m, p.n)
+        tall = p.m >= p.n
+        names = dict(prox="prox", A_pass1="gemv_t" if tall else "gemv_n", Linv="trmv", LinvT="trmv_t",
+                     A_pass2="gemv_n" if tall else "gemv_t", check="check")
         for name, t in (("equil", rep.equil_ms), ("gram", rep.gram_ms), ("factor", rep.factor_ms),
                         ("inverse", rep.inverse_ms), ("ingest", rep.ingest_ms)):
-            comp.setdefault(name, []).append((t, i))
-        for k in ("prox", "A_pass1", "Linv", "LinvT", "A_pass2", "check"):
-            comp.setdefault(k, []).append((kt[k][0] * it, i, kt[k][0], kt[k][1]))
+            comp[(name, i)] = dict(total=t, ms=t, bytes=None, launches=1)
+        for k, name in names.items():
+            comp[(name, i)] = dict(total=kt[k][0] * it, ms=kt[k][0], bytes=kt[k][1], launches=it)
         proj_ms = sum(kt[k][0] for k in ("A_pass1", "Linv", "LinvT", "A_pass2"))
         proj_b = sum(kt[k][1] for k in ("A_pass1", "Linv", "LinvT", "A_pass2"))
         proj.append(dict(shape=[p.m, p.n], ms=proj_ms, bytes=proj_b, gbs=proj_b / proj_ms / 1e6,
                          frac=proj_b / proj_ms / 1e6 / peaks["hbm"]))
         per_problem.append(dict(shape=[p.m, p.n], cls=p.name, iters=it, obj=info.obj, setup_ms=info.setup_ms,
                                 solve_ms=info.solve_ms, setup=rep.as_dict(),
-                                kernels={k: dict(ms=v[0], bytes=v[1]) for k, v in kt.items()}))
-    totals = {k: sum(x[0] for x in v) for k, v in comp.items()}
-    dom = max(totals, key=totals.get)
+                                kernels={names[k]: dict(ms=v[0], bytes=v[1]) for k, v in kt.items() if k in names}))
+    totals = {}
+    for (name, i), r in comp.items():
+        totals[name] = totals.get(name, 0.0) + r["total"]
+    (dom, di) = max(comp, key=lambda key: comp[key]["total"])
+    rec = comp[(dom, di)]
+    pm, pn = probs[di].m, probs[di].n
+    p_, q_ = max(pm, pn), min(pm, pn)
+    shape = f"{pm}x{pn}"
     step_ms = t_ms / args.steps
-    if dom in ("A_pass1", "A_pass2", "Linv", "LinvT", "prox"):
-        # the largest-share launch of that kernel (problem with most time in it)
-        rec = max(comp[dom], key=lambda x: x[0])
-        achieved = rec[3] / rec[2] / 1e6
-        roof = dict(kernel=dom, problem=probs[rec[1]].name, bound="hbm", achieved=achieved, peak=peaks["hbm"],
-                    unit="GB/s", frac=achieved / peaks["hbm"], peak_src=peaks["src"] + " hbm_gbs")
-    elif dom == "factor":
-        i = max(comp[dom], key=lambda x: x[0])[1]
-        q = min(probs[i].m, probs[i].n)
-        fl = q ** 3 / 3.0
-        t = comp[dom][[x[1] for x in comp[dom]].index(i)][0]
-        achieved = fl / t / 1e9
+    if rec["bytes"] is not None:
+        achieved = rec["bytes"] / rec["ms"] / 1e6
+        roof = dict(kernel=dom, shape=shape, bound="hbm", achieved=achieved, peak=peaks["hbm"], unit="GB/s",
+                    frac=achieved / peaks["hbm"], bytes_per_launch=rec["bytes"], ms_per_launch=rec["ms"],
+                    launches_per_step=rec["launches"], peak_src=peaks["src"] + " hbm_gbs (burst copy)")
+    elif dom in ("factor", "inverse"):
+        fl = q_ ** 3 / 3.0   # Cholesky: q^3/3 flop; triangular inverse: q^3/3 flop
         mixed = prm.chol_prec == P.CHOL["MIXED"]
-        peak = FP32_SIMT_TFLOPS if mixed else FP64_TFLOPS
-        roof = dict(kernel="cholesky", problem=probs[i].name, bound="alu", achieved=achieved, peak=peak,
-                    unit="TFLOP/s", frac=achieved / peak,
-                    peak_src=("FP32 SIMT" if mixed else "FP64") + " from unit counts and clocks")
-    else:
-        i = max(comp[dom], key=lambda x: x[0])[1]
-        pm, pn = probs[i].m, probs[i].n
-        p_, q_ = max(pm, pn), min(pm, pn)
-        t = comp[dom][[x[1] for x in comp[dom]].index(i)][0]
-        if dom == "gram":
-            fl = float(p_) * q_ * q_   # lower triangle of G: q(q+1)/2 dot products of length p
-            used = per_problem[i]["setup"]["gram_prec_used"]
-            if used == P.GRAM["FP32"]:
-                roof = dict(kernel="gram", bound="alu", achieved=fl / t / 1e9, peak=FP32_SIMT_TFLOPS, unit="TFLOP/s",
-                            peak_src="FP32 SIMT from unit counts and clocks")
-            else:
-                eff = fl * (3 if used == P.GRAM["BF16X3"] else 1)
-                pk = peaks["bf16"] * (0.5 if used == P.GRAM["TF32"] else 1.0)
-                roof = dict(kernel="gram", bound="tensor", achieved=eff / t / 1e9, peak=pk, unit="TFLOP/s",
-                            peak_src=peaks["src"] + " bf16 burst" + (" x 1/2 (tf32 nominal ratio)" if used == 1 else ""))
-            roof["frac"] = roof["achieved"] / roof["peak"]
-            roof["problem"] = probs[i].name
+        peak = FP32_SIMT_TFLOPS if (mixed or dom == "inverse") else FP64_TFLOPS
+        roof = dict(kernel=dom, shape=shape, bound="alu", achieved=fl / rec["ms"] / 1e9, peak=peak,
+                    unit="TFLOP/s", peak_src=("FP32 SIMT" if peak == FP32_SIMT_TFLOPS else "FP64")
+                    + " from unit counts and clocks")
+        roof["frac"] = roof["achieved"] / peak
+    elif dom == "gram":
+        fl = float(p_) * q_ * q_   # lower triangle of G: q(q+1)/2 dot products of length p
+        used = per_problem[di]["setup"]["gram_prec_used"]
+        if used == P.GRAM["FP32"]:
+            roof = dict(kernel="gram", shape=shape, bound="alu", achieved=fl / rec["ms"] / 1e9,
+                        peak=FP32_SIMT_TFLOPS, unit="TFLOP/s", peak_src="FP32 SIMT from unit counts and clocks")
         else:
-            by = 2 * 4.0 * pm * pn if dom in ("equil", "ingest") else 4.0 * q_ * q_
-            roof = dict(kernel=dom, problem=probs[i].name, bound="hbm", achieved=by / t / 1e6, peak=peaks["hbm"],
-                        unit="GB/s", frac=by / t / 1e6 / peaks["hbm"], peak_src=peaks["src"] + " hbm_gbs")
-    roof["traffic"] = _traffic(roof["kernel"])
+            eff = fl * (3 if used == P.GRAM["BF16X3"] else 1)
+            pk = peaks["bf16"] * (0.5 if used == P.GRAM["TF32"] else 1.0)
+            roof = dict(kernel="gram", shape=shape, bound="tensor", achieved=eff / rec["ms"] / 1e9, peak=pk,
+                        unit="TFLOP/s", peak_src=peaks["src"] + " bf16 burst"
+                        + (" x 1/2 (tf32 nominal ratio)" if used == P.GRAM["TF32"] else ""))
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    else:
+        by = 2 * 4.0 * pm * pn * (2 * 10 + 1) if dom == "equil" else 2 * 4.0 * pm * pn
+        roof = dict(kernel=dom, shape=shape, bound="hbm", achieved=by / rec["ms"] / 1e6, peak=peaks["hbm"],
+                    unit="GB/s", frac=by / rec["ms"] / 1e6 / peaks["hbm"], peak_src=peaks["src"] + " hbm_gbs")
+    roof["traffic"] = _traffic(dom, shape)
     shares = {k: v / sum(totals.values()) for k, v in sorted(totals.items(), key=lambda kv: -kv[1])}
 
     cpu = None
@@ -383,12 +385,13 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _traffic(kernel):
-    """DRAM bytes per launch from a committed ncu capture, if the kernel is unchanged since."""
+def _traffic(kernel, shape):
+    """DRAM bytes (read + write) per launch of `kernel` on `shape` from the committed ncu summary,
+    or None if the kernel's source changed since the counters were taken."""
     try:
         import hashlib
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            rec = json.load(f).get(kernel)
+            rec = json.load(f).get(f"{kernel}@{shape}")
         if not rec:
             return None
         src = open(os.path.join(ROOT, "paper_1503_08366_b300", "csrc", rec["source"]), "rb").read()
