@@ -512,6 +512,76 @@ def run_serve(args):
                     classes="lasso,logistic,huber,svm,nnls"))))
 
 
+def _precision_refs(name, m, n):
+    """Oracle reference results for the precision study, written by tests/golden/make_precision_refs.py."""
+    path = os.path.join(ROOT, "tests", "golden", f"precision_{name}_{m}x{n}.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def run_precision(args):
+    """Gram precision x refinement on dense NNLS and inequality-form LP, 30000 x 15000.
+
+    Per (class, gram mode, refinement): the solve (setup and iteration times, iterations,
+    status, objective, residuals), its objective error against the stored FP64 oracle results
+    (the oracle stopped by the same test, and a much tighter oracle run standing in for p*),
+    and the accuracy of one projection of seeded (c, d), measured as the FP64 residual of the
+    normal equations the exact projection satisfies, (c + A^T d) - (I + A^T A) x and y - A x
+    (tall case), relative to ||c + A^T d||."""
+    import torch
+    import workloads as W
+    import paper_1503_08366_b300 as P
+
+    torch.cuda.set_device(0)
+    modes = [("BF16", 0), ("BF16", 1), ("TF32", 0), ("TF32", 1), ("BF16X3", 0)]
+    out = []
+    for gen in (W.nnls_precision_large, W.lp_precision_large):
+        prob = gen()
+        m, n = prob.A.shape
+        refs = _precision_refs(prob.name, m, n) or {}
+        Adev = torch.from_numpy(prob.A).cuda()
+        rng = np.random.default_rng(77)
+        c = rng.standard_normal(n).astype(np.float32)
+        d = rng.standard_normal(m).astype(np.float32)
+        for gram, refine in modes:
+            prm = P.pogs_default_params(gram_prec=gram, refine_steps=refine, max_iter=5000)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with P.Solver(Adev, prm) as s:
+                torch.cuda.synchronize()
+                setup_s = time.perf_counter() - t0
+                rep = P.pogs_get_setup_report(s.handle)
+                info, x, y, mu, nu = s.solve(prob.f, prob.g)
+                xp, yp = s.project(c, d, prm)
+                Ah = s.ahat().astype(np.float64)
+            rhs = c.astype(np.float64) + Ah.T @ d.astype(np.float64)
+            xp64, yp64 = xp.astype(np.float64), yp.astype(np.float64)
+            kkt = rhs - (xp64 + Ah.T @ (Ah @ xp64))
+            rec = dict(cls=prob.name, gram=gram, refine=refine, gram_used=rep.gram_prec_used, status=info.status,
+                       iters=info.iters, obj=info.obj, r_pri=info.r_pri, r_dual=info.r_dual, eps_pri=info.eps_pri,
+                       eps_dual=info.eps_dual, r_pri_unscaled=info.r_pri_unscaled,
+                       r_dual_unscaled=info.r_dual_unscaled, setup_ms=info.setup_ms, solve_ms=info.solve_ms,
+                       gram_ms=rep.gram_ms, factor_ms=rep.factor_ms,
+                       proj_kkt_rel=float(np.linalg.norm(kkt) / np.linalg.norm(rhs)),
+                       proj_graph_rel=float(np.linalg.norm(yp64 - Ah @ xp64) / max(np.linalg.norm(yp64), 1e-30)))
+            for key in ("same_tol", "tight"):
+                if key in refs:
+                    po = refs[key]["obj"]
+                    rec[f"obj_relerr_vs_oracle_{key}"] = abs(info.obj - po) / max(1.0, abs(po))
+            out.append(rec)
+            del Ah
+        del Adev
+    line = dict(workload="precision", metric="relative objective error vs FP64 oracle and projection accuracy",
+                config=dict(shape=[30000, 15000], classes="nnls, lp (10% nonzeros stored dense)",
+                            eps_abs=1e-4, eps_rel=1e-3, chol_prec="MIXED",
+                            oracle="stored oracle results: tests/golden/precision_<class>_30000x15000.json"),
+                results=out)
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -519,7 +589,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve"])
+    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve", "precision"])
     ap.add_argument("--count", type=int, default=2048, help="batch workload: instances")
     ap.add_argument("--plain-sample", type=int, default=128, help="batch workload: plain-path sample")
     ap.add_argument("--requests", type=int, default=4000, help="serve workload: requests in the trace")
@@ -537,6 +607,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 
