@@ -138,11 +138,15 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
   int num_sms = 148, dev = 0;
   std::vector<int> order_big(ns), order_in(ns);
   bool any_host_in = false;
-  BCK(cudaMalloc(&arena, total));
-  BCK(cudaMalloc(&d_inst, sizeof(BInst) * ns));
-  BCK(cudaMalloc(&d_out, sizeof(BOut) * ns));
-  BCK(cudaMalloc(&d_queue, sizeof(int)));
-  BCK(cudaMalloc(&d_order, sizeof(int) * ns));
+  // stream-ordered allocations from the library's pool (no device-wide synchronisation)
+  if (pool_alloc(reinterpret_cast<void**>(&arena), total, s) != 0 ||
+      pool_alloc(reinterpret_cast<void**>(&d_inst), sizeof(BInst) * ns, s) != 0 ||
+      pool_alloc(reinterpret_cast<void**>(&d_out), sizeof(BOut) * ns, s) != 0 ||
+      pool_alloc(reinterpret_cast<void**>(&d_queue), sizeof(int), s) != 0 ||
+      pool_alloc(reinterpret_cast<void**>(&d_order), sizeof(int) * ns, s) != 0) {
+    rc = POGS_ERR_OOM;
+    goto done;
+  }
   BCK(cudaMemsetAsync(d_out, 0, sizeof(BOut) * ns, s));
   // ---- ingest -------------------------------------------------------------------------------
   for (int k = 0; k < ns && !any_host_in; ++k) any_host_in = !is_dev(probs[small[k]].A);
@@ -348,11 +352,11 @@ done:
   if (gexec) cudaGraphExecDestroy(gexec);
   if (graph) cudaGraphDestroy(graph);
   if (cap) cudaStreamDestroy(cap);
+  if (arena) cudaFreeAsync(arena, s);
+  if (d_inst) cudaFreeAsync(d_inst, s);
+  if (d_out) cudaFreeAsync(d_out, s);
+  if (d_queue) cudaFreeAsync(d_queue, s);
+  if (d_order) cudaFreeAsync(d_order, s);
   cudaStreamSynchronize(s);
-  cudaFree(arena);
-  cudaFree(d_inst);
-  cudaFree(d_out);
-  cudaFree(d_queue);
-  cudaFree(d_order);
   return rc;
 }

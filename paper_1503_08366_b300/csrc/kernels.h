@@ -102,6 +102,9 @@ void launch_gram_to_f64(const float* G, int64_t ldg, int64_t q, double* H, int64
 // Right-looking blocked Cholesky of H (lower, in place).  mixed: trailing products in FP32
 // (FP64 diagonal blocks, panel solves and Schur complement).
 int chol_f64(double* H, int64_t ldh, int64_t q, double* work, int* err, cudaStream_t s);
+// Stream-ordered allocation from the library's per-device pool (solver.cu); free with
+// cudaFreeAsync on a stream ordered after the last use.  Returns 0 or POGS_ERR_OOM / _CUDA.
+int pool_alloc(void** q, size_t bytes, cudaStream_t s);
 // Mixed-precision factorization (chol.cu) of I + G: G (lower triangle, ld ldh) is overwritten
 // with the hi part of the double-float Schur complement, Hlo (same layout) receives the lo
 // part; the FP32 off-diagonal panels of L go to Lf and the diagonal 128-blocks of L^{-1} to

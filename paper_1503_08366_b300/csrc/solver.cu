@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <mutex>
 #include <vector>
 
 #include "kernels.h"
@@ -59,6 +60,45 @@ struct pogs_handle {
 std::atomic<long long> pogs::g_launch_count{0};
 thread_local int pogs::g_capture_depth = 0;
 
+// Stream-ordered device memory: one pool per device that keeps freed memory cached up to a
+// threshold, so that setup, solve and free on one stream never synchronise the device (plain
+// cudaMalloc / cudaFree do, which would serialise concurrent solves on other streams).
+int pogs::pool_alloc(void** q, size_t bytes, cudaStream_t s) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  *q = nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return POGS_ERR_CUDA;
+  }
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t p = nullptr;
+      if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return POGS_ERR_CUDA;
+      }
+      uint64_t keep = 16ull << 30;   // bytes kept cached across synchronisations
+      cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+      pools[dev] = p;
+    }
+    pool = pools[dev];
+  }
+  if (cudaMallocFromPoolAsync(q, bytes, pool, s) != cudaSuccess) {
+    cudaGetLastError();
+    *q = nullptr;
+    return POGS_ERR_OOM;
+  }
+  return 0;
+}
+
 namespace {
 
 #define CK(call)                                                                      \
@@ -86,11 +126,8 @@ int dalloc(pogs_handle* h, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return POGS_ERR_OOM;
-  }
+  const int rc = pool_alloc(&q, count * sizeof(T), h->stream);
+  if (rc != 0) return rc;
   h->allocs.push_back(q);
   h->device_bytes += (int64_t)(count * sizeof(T));
   *p = static_cast<T*>(q);
@@ -98,22 +135,50 @@ int dalloc(pogs_handle* h, T** p, size_t count) {
   return 0;
 }
 
-// Scratch that lives only during setup.
+// Pinned host slots for each handle's status / parameter mirror, allocated in chunks and
+// recycled (never released while the library is loaded: cudaFreeHost synchronises the device).
+constexpr size_t kPinSlot = 512;
+static_assert(sizeof(DevState) + sizeof(DevCfg) <= kPinSlot, "pinned slot too small");
+std::mutex g_pin_mu;
+std::vector<void*> g_pin_free;
+
+void* pin_slot_get() {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  if (g_pin_free.empty()) {
+    void* chunk = nullptr;
+    if (cudaMallocHost(&chunk, 64 * kPinSlot) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (int i = 63; i >= 0; --i) g_pin_free.push_back(static_cast<char*>(chunk) + i * kPinSlot);
+  }
+  void* p = g_pin_free.back();
+  g_pin_free.pop_back();
+  memset(p, 0, kPinSlot);
+  return p;
+}
+void pin_slot_put(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(p);
+}
+
+// Scratch that lives only during setup (stream-ordered: freed on the setup stream).
 struct Scratch {
+  cudaStream_t s = nullptr;
   std::vector<void*> ptrs;
   ~Scratch() {
-    for (void* p : ptrs) cudaFree(p);
+    for (void* p : ptrs) cudaFreeAsync(p, s);
   }
   template <class T>
-  int get(T** p, size_t count, cudaStream_t s) {
+  int get(T** p, size_t count, cudaStream_t st) {
+    s = st;
     void* q = nullptr;
-    if (cudaMalloc(&q, (count ? count : 1) * sizeof(T)) != cudaSuccess) {
-      cudaGetLastError();
-      return POGS_ERR_OOM;
-    }
+    const int rc = pool_alloc(&q, (count ? count : 1) * sizeof(T), st);
+    if (rc != 0) return rc;
     ptrs.push_back(q);
     *p = static_cast<T*>(q);
-    if (cudaMemsetAsync(q, 0, (count ? count : 1) * sizeof(T), s) != cudaSuccess) return POGS_ERR_CUDA;
+    if (cudaMemsetAsync(q, 0, (count ? count : 1) * sizeof(T), st) != cudaSuccess) return POGS_ERR_CUDA;
     return 0;
   }
 };
@@ -440,8 +505,8 @@ int alloc_state(pogs_handle* h) {
   TRY(dalloc(h, &h->dual_part, (size_t)g.t_ncolblk * 2));
   TRY(dalloc(h, &h->st, 1));
   TRY(dalloc(h, &h->cfg, 1));
-  void* pin = nullptr;
-  CK(cudaMallocHost(&pin, sizeof(DevState) + sizeof(DevCfg)));
+  void* pin = pin_slot_get();
+  if (!pin) return POGS_ERR_OOM;
   h->st_host = static_cast<DevState*>(pin);
   h->cfg_host = reinterpret_cast<DevCfg*>(static_cast<char*>(pin) + sizeof(DevState));
   return 0;
@@ -451,8 +516,8 @@ void release(pogs_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  for (void* p : h->allocs) cudaFree(p);
-  if (h->st_host) cudaFreeHost(h->st_host);
+  for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
+  pin_slot_put(h->st_host);
   if (h->cap) cudaStreamDestroy(h->cap);
   for (cudaEvent_t e : h->ev)
     if (e) cudaEventDestroy(e);
@@ -597,7 +662,9 @@ int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order, co
   int rc = alloc_state(h);
   if (rc == 0) rc = setup_impl(h, A, lda, order);
   if (rc == 0) {
-    if (cudaMemcpy(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess) rc = POGS_ERR_CUDA;
+    if (cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      rc = POGS_ERR_CUDA;
     else if (h->st_host->err != 0) rc = h->st_host->err;
   }
   if (rc != 0) {
@@ -685,10 +752,7 @@ int pogs_prox_eval(const pogs_fn* fn, int64_t k, const float* v, const float* rh
   float* tmp = nullptr;
   const bool need = !fn->a || !fn->b || !fn->c || !fn->d || !fn->e;
   if (need) {
-    if (cudaMalloc(&tmp, (size_t)k * 2 * sizeof(float)) != cudaSuccess) {
-      cudaGetLastError();
-      return POGS_ERR_OOM;
-    }
+    if (pool_alloc(reinterpret_cast<void**>(&tmp), (size_t)k * 2 * sizeof(float), s) != 0) return POGS_ERR_OOM;
     launch_fill(tmp, k, 1.0f, s);
     launch_fill(tmp + k, k, 0.0f, s);
     if (!d.a) d.a = tmp;
@@ -699,10 +763,7 @@ int pogs_prox_eval(const pogs_fn* fn, int64_t k, const float* v, const float* rh
   }
   launch_prox_eval(d, k, v, rho_vec, rho, out, s);
   cudaError_t e = cudaGetLastError();
-  if (tmp) {
-    cudaStreamSynchronize(s);
-    cudaFree(tmp);
-  }
+  if (tmp) cudaFreeAsync(tmp, s);
   return e == cudaSuccess ? 0 : POGS_ERR_CUDA;
 }
 
@@ -886,7 +947,7 @@ extern "C" int pogs_gram(const float* A, int64_t m, int64_t n, int64_t lda, int 
   const bool tall = m >= n;
   const int64_t q = tall ? n : m;
   int* err = nullptr;
-  CK(cudaMalloc(&err, sizeof(int)));
+  if (pool_alloc(reinterpret_cast<void**>(&err), sizeof(int), s) != 0) return POGS_ERR_OOM;
   CK(cudaMemsetAsync(err, 0, sizeof(int), s));
   int rc = 0;
   if (gram_prec == POGS_GRAM_FP32) {
@@ -896,19 +957,15 @@ extern "C" int pogs_gram(const float* A, int64_t m, int64_t n, int64_t lda, int 
     size_t need = 0;
     rc = gram_tensor(gram_prec, A, lda, m, n, tall, G, q, nullptr, 0, &need, err, s);
     void* ws = nullptr;
-    if (rc == 0 && cudaMalloc(&ws, need) != cudaSuccess) {
-      cudaGetLastError();
-      rc = POGS_ERR_OOM;
-    }
+    if (rc == 0 && pool_alloc(&ws, need, s) != 0) rc = POGS_ERR_OOM;
     if (rc == 0 && gram_tensor(gram_prec, A, lda, m, n, tall, G, q, ws, need, &need, err, s) != 0) rc = POGS_ERR_CUDA;
-    cudaStreamSynchronize(s);
-    if (ws) cudaFree(ws);
+    if (ws) cudaFreeAsync(ws, s);
   }
   int herr = 0;
   if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     rc = POGS_ERR_CUDA;
-  cudaFree(err);
+  cudaFreeAsync(err, s);
   if (rc == 0 && herr != 0) rc = herr;
   if (rc == 0 && cudaGetLastError() != cudaSuccess) rc = POGS_ERR_CUDA;
   return rc;
