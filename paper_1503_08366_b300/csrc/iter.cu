@@ -468,9 +468,12 @@ __global__ void __launch_bounds__(256) check_kernel(DevState* st, const DevCfg* 
   block_sum_df<10>(a, v, sh);
   if (threadIdx.x != 0) return;
   const double mu2 = v[0], xmu = v[1], gobj = v[2], yh2 = v[3], ynu = v[4], fobj = v[5];
-  const double r_pri = sqrt(v[6]), r_pri_u = sqrt(v[7]), r_dual = sqrt(v[8]), r_dual_u = sqrt(v[9]);
-  const double eps_pri = cfg->abs_tol + cfg->rel_tol * sqrt(yh2);
-  const double eps_dual = cfg->abs_tol + cfg->rel_tol * sqrt(mu2);
+  // square roots of the FP64 sums in FP32 (the FP64 square root is a long sequence on the
+  // FP64 pipe; seven significant digits are far more than the tolerance test needs)
+  auto rt = [](double a) { return (double)sqrtf((float)a); };
+  const double r_pri = rt(v[6]), r_pri_u = rt(v[7]), r_dual = rt(v[8]), r_dual_u = rt(v[9]);
+  const double eps_pri = cfg->abs_tol + cfg->rel_tol * rt(yh2);
+  const double eps_dual = cfg->abs_tol + cfg->rel_tol * rt(mu2);
   const double gap = ynu + xmu;
   const double obj = fobj + gobj;
   const double eps_gap = cfg->abs_tol + cfg->rel_tol * fabs(obj);
@@ -498,12 +501,13 @@ __global__ void __launch_bounds__(256) check_kernel(DevState* st, const DevCfg* 
     double rho_new = rho;
     if (r_dual < eps_dual && cfg->tau * k > st->l) {
       rho_new = cfg->delta * rho;
+      pend = cfg->inv_delta;        // rho^k / rho^{k+1}
       st->u = k;
     } else if (r_pri < eps_pri && cfg->tau * k > st->u) {
-      rho_new = rho / cfg->delta;
+      rho_new = rho * cfg->inv_delta;
+      pend = cfg->delta;
       st->l = k;
     }
-    pend = rho / rho_new;
     st->rho = rho_new;
   }
   st->pend = pend;
@@ -608,7 +612,10 @@ GemvGeom choose_geometry(int64_t m, int64_t n, int64_t lda, int num_sms) {
   g.t_ncolblk = (int)cdiv(lda, 1024);
   int64_t target = (int64_t)num_sms * 5;   // 5 resident 256-thread blocks per SM at the kernel's register count
   int64_t nsplit = cdiv(target, g.t_ncolblk);
-  int64_t rows = round_up(cdiv(m, nsplit), 8);   // whole 8-row steps
+  // whole 8-row steps, and at least 64 rows per split: the slab's last block sums the splits
+  // serially, which dominates the launch for small matrices split too finely
+  int64_t rows = round_up(cdiv(m, nsplit), 8);
+  if (rows < 64) rows = std::min<int64_t>(64, round_up(m, 8));
   g.t_rows = (int)rows;
   g.t_nsplit = (int)cdiv(m, rows);
   // row dots: column chunks of <= 4096 floats; rows per block chosen for ~8 blocks per SM

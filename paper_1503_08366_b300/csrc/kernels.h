@@ -42,7 +42,7 @@ struct EpiArgs {
 
 // Loop parameters in device memory (so a captured graph survives parameter changes).
 struct DevCfg {
-  double abs_tol, rel_tol, alpha, delta, tau;
+  double abs_tol, rel_tol, alpha, delta, inv_delta, tau;
   int max_iter, gap_stop, adaptive, pad_;
 };
 

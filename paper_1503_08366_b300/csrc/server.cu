@@ -77,6 +77,8 @@ struct pogs_server {
   pogs_params p{};
   BCfg cfg{};
   cudaStream_t stream = nullptr;
+  bool own_stream = false;           // internal highest-priority stream (caller passed none)
+  cudaEvent_t ev_in = nullptr;       // orders the internal stream after the legacy stream
   int num_sms = 148;
   int cap = 0;                       // slots for resident small requests
   BOut* d_outs = nullptr;
@@ -103,8 +105,12 @@ struct pogs_server {
 namespace {
 
 void worker_main(pogs_server* S) {
+  // large requests run at the lowest stream priority, so that the block scheduler places the
+  // batched engine's CTAs first when both are pending
   cudaStream_t st;
-  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, lo) != cudaSuccess) {
     cudaGetLastError();
     st = nullptr;
   }
@@ -219,6 +225,18 @@ int pogs_server_create(size_t hbm_budget, int large_workers, int max_resident, c
   if (p) S->p = *p;
   S->budget = hbm_budget;
   S->stream = static_cast<cudaStream_t>(stream);
+  if (!S->stream) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&S->stream, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (S->stream) cudaStreamDestroy(S->stream);
+      delete S;
+      return POGS_ERR_CUDA;
+    }
+    S->own_stream = true;
+  }
   S->cap = max_resident;
   BCfg& c = S->cfg;
   memset(&c, 0, sizeof(c));
@@ -260,6 +278,12 @@ int pogs_server_submit(pogs_server* S, const pogs_problem* prob, float* x, float
                        int64_t tag) {
   if (!S || !prob || !prob->A || prob->m < 1 || prob->n < 1 || prob->lda < prob->n || !prob->f.h || !prob->g.h)
     return POGS_ERR_ARG;
+  if (S->own_stream) {
+    // device inputs written on the legacy default stream are ordered before their use on the
+    // server's internal (non-blocking) stream
+    cudaEventRecord(S->ev_in, 0);
+    cudaStreamWaitEvent(S->stream, S->ev_in, 0);
+  }
   SReq* r = new SReq();
   r->tag = tag;
   r->prob = *prob;
@@ -427,6 +451,8 @@ void pogs_server_destroy(pogs_server* S) {
   cudaFree(S->d_active);
   cudaFree(S->d_new);
   cudaFree(S->d_queue);
+  if (S->ev_in) cudaEventDestroy(S->ev_in);
+  if (S->own_stream) cudaStreamDestroy(S->stream);
   delete S;
 }
 

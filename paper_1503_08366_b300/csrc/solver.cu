@@ -569,6 +569,7 @@ int reset_state(pogs_handle* h, const pogs_params* p) {
   DevCfg c;
   memset(&c, 0, sizeof(c));
   c.abs_tol = p->abs_tol; c.rel_tol = p->rel_tol; c.alpha = p->alpha; c.delta = p->delta; c.tau = p->tau;
+  c.inv_delta = 1.0 / p->delta;
   c.max_iter = p->max_iter; c.gap_stop = p->gap_stop; c.adaptive = p->adaptive_rho;
   *h->cfg_host = c;
   CK(cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
