@@ -48,10 +48,17 @@ FP32_SIMT_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 FP64_TFLOPS = 1.25
 
 
+def problem_seeds(rank: int):
+    """Seeds of the two large solves a rank runs: rank 0 runs the named workload (seeds 10000,
+    10001); every other rank runs its own independent replica of it."""
+    return 10_000 + 100 * rank, 10_001 + 100 * rank
+
+
 def problems(rank: int):
     import workloads as W
-    a = W.lasso(40000, 10000, seed=10_000 + 100 * rank, nnz_frac=0.1, noise_std=0.01, lam_frac=0.1)
-    b = W.logistic(2000, 40000, seed=10_001 + 100 * rank, nnz_frac=0.05, lam_frac=0.05)
+    sa, sb = problem_seeds(rank)
+    a = W.lasso(40000, 10000, seed=sa, nnz_frac=0.1, noise_std=0.01, lam_frac=0.1)
+    b = W.logistic(2000, 40000, seed=sb, nnz_frac=0.05, lam_frac=0.05)
     return [a, b]
 
 
@@ -103,10 +110,15 @@ class Clocks:
 
 
 def _dist():
+    """(dist, rank, world size, local rank).  One process per GPU under torchrun: NCCL when a GPU
+    is present, gloo otherwise (POGS_DIST_BACKEND overrides).  The replicas exchange only the
+    barrier and the maximum of their timed intervals -- the path itself has no collective."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        backend = os.environ.get("POGS_DIST_BACKEND") or ("nccl" if torch.cuda.is_available() else "gloo")
+        dist.init_process_group(backend)
         return dist, dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
     return None, 0, 1, 0
 
@@ -115,7 +127,8 @@ def _max_over_ranks(dist, v: float) -> float:
     if dist is None:
         return v
     import torch
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -123,6 +136,11 @@ def _max_over_ranks(dist, v: float) -> float:
 def _barrier(dist):
     if dist is not None:
         dist.barrier()
+
+
+def job_rate(units_per_rank: int, world_size: int, t_ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world_size / (t_ms_max / 1000.0)
 
 
 # ----------------------------------------------------------------------------------------------
@@ -270,7 +288,7 @@ def run_ours(args):
     clk = clocks.stop()
     t_ms = _max_over_ranks(dist, e_start.elapsed_time(e_end))
     solves = len(probs) * args.steps * ws
-    value = solves / (t_ms / 1000.0)
+    value = job_rate(len(probs) * args.steps, ws, t_ms)
     lats = sorted(a.elapsed_time(b) for a, b in lat_events)
     p50 = float(np.percentile(lats, 50))
     p99 = float(np.percentile(lats, 99))
