@@ -78,7 +78,7 @@ def _identity_equil(A):
 
 
 def solve(A, f, g, params: Params | None = None, eq: Equilibration | None = None,
-          record: bool = False) -> Result:
+          record: bool = False, x0=None, nu0=None) -> Result:
     p = params or Params()
     A = np.asarray(A, np.float64)
     m, n = A.shape
@@ -94,6 +94,18 @@ def solve(A, f, g, params: Params | None = None, eq: Equilibration | None = None
     x, xt = np.zeros(n), np.zeros(n)
     y, yt = np.zeros(m), np.zeros(m)
     rho = float(p.rho0)
+    # Warm start (Section 5): an initial x^0 and/or nu^0 in the original variables.  In the
+    # pre-conditioned problem x^ = E^-1 x and nu^ = D^-1 nu (the inverse of the unscaling of the
+    # returned tuple).  The graph point starts at (x^0, A^ x^0); the scaled duals at
+    # y~ = -nu^0 / rho and x~ = -A^T y~, which keeps the Section 3.3 invariant.  A part that is
+    # not given starts at zero, and the first prox step estimates it: it returns nu^{1/2} in the
+    # subdifferential of f at y^{1/2} (mu^{1/2} likewise for g).
+    if x0 is not None:
+        x = np.asarray(x0, np.float64) / E
+        y = Ah @ x
+    if nu0 is not None:
+        yt = -(np.asarray(nu0, np.float64) / D) / rho
+        xt = -(Ah.T @ yt)
     l = u = 0
     hist = []
     status, iters = 1, p.max_iter

@@ -142,3 +142,39 @@ def test_small_lasso_converges_with_default_tolerances():
     assert r.r_pri < r.eps_pri and r.r_dual < r.eps_dual
     rt = OA.solve(P.A, P.f, P.g, TIGHT)
     assert abs(r.obj - rt.obj) <= 1e-3 * max(1, abs(rt.obj))
+
+
+# ---- warm start (Section 5) -----------------------------------------------------------------
+@pytest.mark.parametrize("cls,shape", [("lasso", (120, 60)), ("logistic", (80, 150)), ("nnls", (90, 40))])
+def test_warm_start_at_the_solution_is_a_fixed_point(cls, shape):
+    """Started from the optimal (x*, nu*) of a tight solve, the first iteration reproduces them:
+    x* = prox_g(x* + mu*/rho) and y* = prox_f(y* + nu*/rho) are exactly the optimality
+    conditions.  A wrong sign or a missing D/E scaling of the warm start breaks this."""
+    prob = W.CLASSES[cls](*shape, seed=13)
+    tight = OA.solve(prob.A, prob.f, prob.g, OA.Params(abs_tol=1e-10, rel_tol=1e-9, max_iter=50000))
+    assert tight.status == 0
+    warm = OA.solve(prob.A, prob.f, prob.g, OA.Params(max_iter=1, adaptive_rho=False), x0=tight.x, nu0=tight.nu)
+    assert np.linalg.norm(warm.x - tight.x) <= 1e-6 * max(1.0, np.linalg.norm(tight.x))
+    assert np.linalg.norm(warm.nu - tight.nu) <= 1e-6 * max(1.0, np.linalg.norm(tight.nu))
+    # and a perturbed start converges to the same optimum
+    rng = np.random.default_rng(1)
+    pert = OA.solve(prob.A, prob.f, prob.g, OA.Params(abs_tol=1e-8, rel_tol=1e-7, max_iter=50000),
+                    x0=tight.x + 0.1 * rng.standard_normal(prob.n), nu0=tight.nu + 0.1 * rng.standard_normal(prob.m))
+    assert abs(pert.obj - tight.obj) <= 1e-5 * max(1.0, abs(tight.obj))
+
+
+@pytest.mark.parametrize("which", ["x0", "nu0"])
+def test_warm_start_with_one_part_estimates_the_other(which):
+    """Only x^0 (or only nu^0) of the optimum: the solve converges to the same optimum, no slower
+    than from zero (strictly faster from x^0), and the invariant x~ + A^T y~ = 0 holds from the
+    first iteration."""
+    prob = W.lasso(150, 70, seed=21)
+    prm = OA.Params(abs_tol=1e-7, rel_tol=1e-6, max_iter=50000)
+    cold = OA.solve(prob.A, prob.f, prob.g, prm, record=True)
+    kw = dict(x0=cold.x) if which == "x0" else dict(nu0=cold.nu)
+    warm = OA.solve(prob.A, prob.f, prob.g, prm, record=True, **kw)
+    assert warm.status == 0 and warm.iters <= cold.iters
+    if which == "x0":
+        assert warm.iters < cold.iters
+    assert abs(warm.obj - cold.obj) <= 1e-5 * max(1.0, abs(cold.obj))
+    assert max(h["dual_inv"] for h in warm.history) < 1e-9
