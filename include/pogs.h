@@ -154,6 +154,19 @@ int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order,
 int pogs_solve(pogs_handle* hdl, const pogs_fn* f, const pogs_fn* g, const pogs_params* p,
                float* x, float* y, float* mu, float* nu, pogs_info* info);
 
+/* pogs_solve from a warm start (Section 5): an initial guess x0 (n, host or device) and/or
+ * nu0 (m, host or device), in the original variables; either may be NULL.  The iteration
+ * starts on the graph at (x0, A x0) with scaled duals y~ = -nu0 / rho0 and x~ = -A^T y~ (in
+ * the pre-conditioned variables: x0 / E, nu0 / D), which keeps x~ + A^T y~ = 0.  A part that
+ * is not given starts at zero and the first prox step estimates it (nu^{1/2} is a subgradient
+ * of f at y^{1/2}, mu^{1/2} of g at x^{1/2}).  With the handle's cached factor this solves
+ * further problems with the same A (new f, g, or a new regularisation weight) from the
+ * previous solution.  Outputs, errors and parameters as pogs_solve; pogs_solve is
+ * pogs_solve_warm with x0 = nu0 = NULL. */
+int pogs_solve_warm(pogs_handle* hdl, const pogs_fn* f, const pogs_fn* g, const pogs_params* p,
+                    const float* x0, const float* nu0, float* x, float* y, float* mu, float* nu,
+                    pogs_info* info);
+
 /* Release everything the handle owns.  pogs_free(NULL) is a no-op. */
 void pogs_free(pogs_handle* hdl);
 

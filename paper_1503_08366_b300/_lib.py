@@ -84,6 +84,9 @@ lib.pogs_setup.restype = C.c_int
 lib.pogs_solve.argtypes = [_P, C.POINTER(pogs_fn), C.POINTER(pogs_fn), C.POINTER(pogs_params), _P, _P, _P, _P,
                            C.POINTER(pogs_info)]
 lib.pogs_solve.restype = C.c_int
+lib.pogs_solve_warm.argtypes = [_P, C.POINTER(pogs_fn), C.POINTER(pogs_fn), C.POINTER(pogs_params), _P, _P, _P, _P, _P,
+                                _P, C.POINTER(pogs_info)]
+lib.pogs_solve_warm.restype = C.c_int
 lib.pogs_free.argtypes = [_P]
 lib.pogs_free.restype = None
 lib.pogs_prox_eval.argtypes = [C.POINTER(pogs_fn), C.c_int64, _P, _P, C.c_float, _P, _P]
@@ -213,6 +216,19 @@ def pogs_solve(handle, f, g, params: pogs_params | None = None, x=None, y=None, 
     rc = lib.pogs_solve(handle, C.byref(fs), C.byref(gs), C.byref(params) if params is not None else None,
                         _outptr(x), _outptr(y), _outptr(mu), _outptr(nu), C.byref(info))
     _check(rc, "pogs_solve")
+    return info
+
+
+def pogs_solve_warm(handle, f, g, params: pogs_params | None = None, x0=None, nu0=None, x=None, y=None, mu=None,
+                    nu=None) -> pogs_info:
+    """pogs_solve from an initial x0 (length n) and/or nu0 (length m), host or device, either None."""
+    keep: list = []
+    fs, gs = make_fn(f, keep), make_fn(g, keep)
+    info = pogs_info()
+    rc = lib.pogs_solve_warm(handle, C.byref(fs), C.byref(gs), C.byref(params) if params is not None else None,
+                             _ptr(x0, np.float32, keep), _ptr(nu0, np.float32, keep), _outptr(x), _outptr(y),
+                             _outptr(mu), _outptr(nu), C.byref(info))
+    _check(rc, "pogs_solve_warm")
     return info
 
 

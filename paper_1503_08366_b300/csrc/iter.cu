@@ -588,6 +588,23 @@ void launch_fold(FnDev raw, int64_t k, const float* scale, int is_f, uint8_t* h,
   count_launch();
   fold_kernel<<<grid_for(k), 256, 0, s>>>(raw, k, scale, is_f, h, a, b, c, d, e, err);
 }
+// Warm start (Section 5) into the pre-conditioned variables: v = src / scale * factor;
+// out_pos = v, out_neg = -v (when given).  x^0: x^ = x0 / E.  nu^0: w = nu0 / D / rho and
+// y~ = -w (x~ = A^T w follows with a column-sum pass).
+__global__ void warm_kernel(const float* __restrict__ src, const float* __restrict__ scale, int64_t k, float factor,
+                            float* __restrict__ out_pos, float* __restrict__ out_neg) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = src[i] / scale[i] * factor;
+    out_pos[i] = v;
+    if (out_neg) out_neg[i] = -v;
+  }
+}
+void launch_warm(const float* src, const float* scale, int64_t k, float factor, float* out_pos, float* out_neg,
+                 cudaStream_t s) {
+  count_launch();
+  warm_kernel<<<grid_for(k), 256, 0, s>>>(src, scale, k, factor, out_pos, out_neg);
+}
+
 void launch_fill(float* p, int64_t k, float v, cudaStream_t s) {
   count_launch();
   fill_kernel<<<grid_for(k), 256, 0, s>>>(p, k, v);

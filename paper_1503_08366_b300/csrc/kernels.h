@@ -76,6 +76,8 @@ void launch_prox_eval(FnDev fn, int64_t k, const float* v, const float* rho_vec,
 void launch_fold(FnDev raw, int64_t k, const float* scale, int is_f, uint8_t* h, float* a, float* b,
                  float* c, float* d, float* e, int* err, cudaStream_t s);
 void launch_fill(float* p, int64_t k, float v, cudaStream_t s);
+void launch_warm(const float* src, const float* scale, int64_t k, float factor, float* out_pos, float* out_neg,
+                 cudaStream_t s);
 void launch_unscale(int n, int m, const float* xh, const float* mu, const float* yh, const float* nu,
                     const float* D, const float* E, float* x, float* muo, float* y, float* nuo,
                     cudaStream_t s);

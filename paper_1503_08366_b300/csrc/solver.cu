@@ -685,8 +685,36 @@ int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order, co
   return 0;
 }
 
-int pogs_solve(pogs_handle* h, const pogs_fn* f, const pogs_fn* g, const pogs_params* p, float* x, float* y,
-               float* mu, float* nu, pogs_info* info) {
+// Warm start (Section 5): the graph point (x^0 / E, A^ x^0 / E) and the scaled duals
+// y~ = -(nu^0 / D) / rho^0, x~ = -A^T y~ (Section 3.3 invariant); a part not given stays zero and
+// the first prox step estimates it.
+int warm_start(pogs_handle* h, const float* x0, const float* nu0, double rho0) {
+  cudaStream_t s = h->stream;
+  const GemvGeom& g = h->geom;
+  const int m = (int)h->m, n = (int)h->n;
+  if (x0) {
+    const float* src = nullptr;
+    TRY(stage_in(x0, h->tn, h->n, s, &src));
+    launch_warm(src, h->E, h->n, 1.0f, h->x, nullptr, s);
+    EpiArgs e = epi0();
+    e.out1 = h->y;
+    launch_gemv_n(1, false, EPN_RAW, h->A, h->lda, m, n, h->x, nullptr, g, h->part_n, h->cnt_n, e, nullptr, s);
+  }
+  if (nu0) {
+    const float* src = nullptr;
+    TRY(stage_in(nu0, h->oy, h->m, s, &src));
+    launch_warm(src, h->D, h->m, (float)(1.0 / rho0), h->w, h->yt, s);
+    EpiArgs e = epi0();
+    e.out1 = h->xt;
+    launch_gemv_t(1, false, EPT_RAW, h->A, h->lda, m, n, h->w, nullptr, nullptr, g, h->part_t, h->cnt_t, e, nullptr,
+                  s);
+  }
+  CK(cudaGetLastError());
+  return 0;
+}
+
+int pogs_solve_warm(pogs_handle* h, const pogs_fn* f, const pogs_fn* g, const pogs_params* p, const float* x0,
+                    const float* nu0, float* x, float* y, float* mu, float* nu, pogs_info* info) {
   if (!h || !f || !g) return POGS_ERR_ARG;
   if (!p) p = &h->sp;
   if (validate_params(p) != 0) return POGS_ERR_ARG;
@@ -695,6 +723,7 @@ int pogs_solve(pogs_handle* h, const pogs_fn* f, const pogs_fn* g, const pogs_pa
   TRY(reset_state(h, p));
   TRY(upload_fn(h, f, h->m, 1));
   TRY(upload_fn(h, g, h->n, 0));
+  if (x0 || nu0) TRY(warm_start(h, x0, nu0, p->rho0));
   const int refine = p->refine_steps;
   TRY(build_graph(h, refine, p->loop_mode));
   if (p->loop_mode == 0) {
@@ -739,6 +768,11 @@ int pogs_solve(pogs_handle* h, const pogs_fn* f, const pogs_fn* g, const pogs_pa
     info->solve_ms = now_ms() - t0;
   }
   return status;
+}
+
+int pogs_solve(pogs_handle* h, const pogs_fn* f, const pogs_fn* g, const pogs_params* p, float* x, float* y,
+               float* mu, float* nu, pogs_info* info) {
+  return pogs_solve_warm(h, f, g, p, nullptr, nullptr, x, y, mu, nu, info);
 }
 
 void pogs_free(pogs_handle* h) { release(h); }

@@ -14,8 +14,9 @@ class Solver:
         self.params = params if params is not None else L.pogs_default_params()
         self.handle = L.pogs_setup(A, self.params, stream=stream, order=order)
 
-    def solve(self, f, g, params: L.pogs_params | None = None, device_out: bool = False):
-        """Returns (info, x, y, mu, nu) -- the unscaled half-step tuple."""
+    def solve(self, f, g, params: L.pogs_params | None = None, device_out: bool = False, x0=None, nu0=None):
+        """Returns (info, x, y, mu, nu) -- the unscaled half-step tuple.  x0 / nu0: optional warm
+        start (Section 5), host or device float32 arrays of length n / m."""
         if device_out:
             import torch
             x = torch.empty(self.n, dtype=torch.float32, device="cuda")
@@ -25,7 +26,11 @@ class Solver:
         else:
             x, mu = np.empty(self.n, np.float32), np.empty(self.n, np.float32)
             y, nu = np.empty(self.m, np.float32), np.empty(self.m, np.float32)
-        info = L.pogs_solve(self.handle, f, g, params if params is not None else self.params, x, y, mu, nu)
+        prm = params if params is not None else self.params
+        if x0 is None and nu0 is None:
+            info = L.pogs_solve(self.handle, f, g, prm, x, y, mu, nu)
+        else:
+            info = L.pogs_solve_warm(self.handle, f, g, prm, x0, nu0, x, y, mu, nu)
         return info, x, y, mu, nu
 
     def equil(self):
