@@ -14,8 +14,8 @@ from __future__ import annotations
 import numpy as np
 from scipy.special import expit
 
-ZERO, ABS, SQUARE, HUBER, LOGISTIC, HINGE, MAXPOS, IND_GE0, IND_LE0, IND_EQ0, IND_BOX01 = range(11)
-ALL_H = (ZERO, ABS, SQUARE, HUBER, LOGISTIC, HINGE, MAXPOS, IND_GE0, IND_LE0, IND_EQ0, IND_BOX01)
+ZERO, ABS, SQUARE, HUBER, LOGISTIC, HINGE, MAXPOS, IND_GE0, IND_LE0, IND_EQ0, IND_BOX01, XLOGX = range(12)
+ALL_H = (ZERO, ABS, SQUARE, HUBER, LOGISTIC, HINGE, MAXPOS, IND_GE0, IND_LE0, IND_EQ0, IND_BOX01, XLOGX)
 INDICATORS = (IND_GE0, IND_LE0, IND_EQ0, IND_BOX01)
 
 
@@ -46,7 +46,34 @@ def h_value(h: int, z: np.ndarray, tol: float = 0.0) -> np.ndarray:
         return np.where(np.abs(z) <= tol, 0.0, inf)
     if h == IND_BOX01:
         return np.where((z >= -tol) & (z <= 1.0 + tol), 0.0, inf)
+    if h == XLOGX:
+        # z log z (entropy term, Appendix A.2): 0 at z = 0, +inf for z < 0
+        with np.errstate(divide="ignore", invalid="ignore"):
+            val = np.where(z > 0.0, z * np.log(np.where(z > 0.0, z, 1.0)), 0.0)
+        return np.where(z >= -tol, val, inf)
     raise ValueError(f"unknown h code {h}")
+
+
+def _prox_xlogx(v: np.ndarray, rho: np.ndarray) -> np.ndarray:
+    """argmin_{z > 0} z log z + (rho/2)(z-v)^2.
+
+    Optimality: log z + 1 + rho (z - v) = 0.  In t = log z the left side
+    psi(t) = t + 1 + rho e^t - rho v is increasing; with hi = max(v, 1), psi(log hi) > 0 and
+    psi(rho (v - hi) - 1) = rho (e^{rho(v-hi)-1} - hi) < 0, so the root is bracketed there;
+    plain bisection in t to full FP64 resolution, then z = e^t.
+    """
+    hi_z = np.maximum(v, 1.0)
+    hi = np.log(hi_z)
+    lo = rho * (v - hi_z) - 1.0
+    for _ in range(400):
+        mid = 0.5 * (lo + hi)
+        psi = mid + 1.0 + rho * np.exp(mid) - rho * v
+        neg = psi < 0.0
+        lo = np.where(neg, mid, lo)
+        hi = np.where(neg, hi, mid)
+        if np.all((hi - lo) <= 1e-15 * (1.0 + np.abs(hi))):
+            break
+    return np.exp(0.5 * (lo + hi))
 
 
 def _prox_logistic(v: np.ndarray, rho: np.ndarray) -> np.ndarray:
@@ -99,6 +126,8 @@ def prox_h(h: int, v: np.ndarray, rho) -> np.ndarray:
         return np.zeros_like(v)
     if h == IND_BOX01:
         return np.clip(v, 0.0, 1.0)
+    if h == XLOGX:
+        return _prox_xlogx(v, rho)
     raise ValueError(f"unknown h code {h}")
 
 

@@ -35,6 +35,10 @@ def base_value(code: int, z: float) -> float:
         return 0.0 if z == 0 else math.inf
     if code == 10:
         return 0.0 if 0 <= z <= 1 else math.inf
+    if code == 11:
+        if z < 0:
+            return math.inf
+        return 0.0 if z == 0 else z * math.log(z)
     raise ValueError(code)
 
 
@@ -85,7 +89,14 @@ def prox_bruteforce(code, a, b, c, d, e, rho, v):
         return (c * base_value(code, a * y - b) if c > 0 else 0.0) + smooth(y)
     # the minimiser lies within a window around v scaled by the slopes involved
     span = 10 * (1 + abs(v) + abs(d) / rho + c * abs(a) / rho + abs(b / a))
-    return _golden(phi, v - span, v + span)
+    lo, hi = v - span, v + span
+    if code == 11 and c > 0:
+        # domain a y - b >= 0, and log z grows only slowly: widen the window on that side
+        edge = b / a
+        span = 10 * (1 + abs(v) + abs(d) / rho + c * abs(a) / rho * (1 + abs(math.log(1 + abs(v) + abs(edge))))
+                     + abs(edge))
+        lo, hi = (edge, max(edge, v) + span) if a > 0 else (min(edge, v) - span, edge)
+    return _golden(phi, lo, hi)
 
 
 def f_scalar(code, a, b, c, d, e, y, tol=0.0):

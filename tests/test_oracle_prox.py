@@ -68,6 +68,17 @@ def test_textbook_values():
     assert abs(z - (-0.4010577)) < 1e-6
 
 
+def test_xlogx_prox_is_lambert_w():
+    """log z + 1 + rho (z - v) = 0 has the closed form rho z = W(rho e^{rho v - 1}) with the
+    principal branch of Lambert's W (scipy), a pin independent of the oracle's bisection."""
+    from scipy.special import lambertw
+    v = np.linspace(-6.0, 8.0, 57)
+    for rho in (0.05, 0.7, 3.0, 40.0):
+        ref = np.real(lambertw(rho * np.exp(rho * v - 1.0))) / rho
+        got = OP.prox_h(OP.XLOGX, v, rho)
+        assert np.allclose(got, ref, rtol=1e-11, atol=1e-300), rho
+
+
 def test_value_matches_bruteforce_table():
     rng = np.random.default_rng(7)
     for code in OP.ALL_H:

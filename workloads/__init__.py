@@ -36,6 +36,7 @@ H = dict(
     IND_LE0=8,     # indicator of z <= 0
     IND_EQ0=9,     # indicator of z == 0
     IND_BOX01=10,  # indicator of 0 <= z <= 1
+    XLOGX=11,      # z log z (0 at z = 0, +inf for z < 0)
 )
 H_NAMES = {v: k for k, v in H.items()}
 
@@ -204,7 +205,55 @@ def lp(m: int, n: int, seed: int, density=0.1) -> Problem:
     return Problem("lp", A, f, g, dict(seed=seed))
 
 
-CLASSES = dict(lasso=lasso, logistic=logistic, huber=huber, svm=svm, nnls=nnls, lp=lp)
+def basis_pursuit(m: int, n: int, seed: int) -> Problem:
+    """Basis pursuit (Appendix A.1): minimize ||x||_1 s.t. A x = b, in graph form
+    f = indicator(y = b), g = |x|.  A ~ N(0, 1/n); v has each entry 0 with probability 1/2,
+    else N(0, 1/n); b = A v.  Underdetermined (m < n), as the problem is described."""
+    rng = _rng(seed)
+    A = _normal32(rng, (m, n), std=1.0 / math.sqrt(n))
+    v = np.where(rng.random(n) < 0.5, 0.0, rng.standard_normal(n) / math.sqrt(n))
+    b = (A.astype(np.float64) @ v).astype(np.float32)
+    f = FnParams.make(m, H["IND_EQ0"], b=b)
+    g = FnParams.make(n, H["ABS"])
+    return Problem("basis_pursuit", A, f, g, dict(seed=seed))
+
+
+def entropy(m: int, n: int, seed: int) -> Problem:
+    """Entropy maximization (Appendix A.2): minimize sum_j x_j log x_j s.t. F x <= b,
+    1^T x = 1.  Graph form with the (m+1) x n matrix [F; 1^T]: f_i = indicator(y_i <= b_i)
+    for i < m, f_m = indicator(y_m = 1), g_j = x_j log x_j.  F ~ N(0, 1/n); v ~ U[0, 1]^n;
+    b = F v / (1^T v), so x = v / (1^T v) is feasible.  m < n."""
+    rng = _rng(seed)
+    F = _normal32(rng, (m, n), std=1.0 / math.sqrt(n))
+    v = rng.uniform(0.0, 1.0, n)
+    b = (F.astype(np.float64) @ v / v.sum()).astype(np.float32)
+    A = np.vstack([F, np.ones((1, n), np.float32)])
+    f = FnParams.make(m + 1, H["IND_LE0"], b=np.concatenate([b, [1.0]]).astype(np.float32))
+    f.h[m] = H["IND_EQ0"]
+    g = FnParams.make(n, H["XLOGX"])
+    return Problem("entropy", A, f, g, dict(seed=seed))
+
+
+def portfolio(n: int, k: int, seed: int, gamma: float = 1.0) -> Problem:
+    """Portfolio optimization with a k-factor risk model (Appendix A.7): maximize
+    mu^T x - gamma x^T (F F^T + D) x s.t. x >= 0, 1^T x = 1.  Graph form with the (k+1) x n
+    matrix [F^T; 1^T]: f_i = gamma y_i^2 (SQUARE with c = 2 gamma) for i < k,
+    f_k = indicator(y_k = 1), g_j(x) = -mu_j x + gamma D_jj x^2 + indicator(x >= 0).
+    F ~ N(0, 1), D_jj ~ U[0, sqrt(k)], mu ~ N(0, 1), gamma = 1; n > k."""
+    rng = _rng(seed)
+    F = _normal32(rng, (n, k))
+    Dd = rng.uniform(0.0, math.sqrt(k), n)
+    mu = rng.standard_normal(n)
+    A = np.vstack([np.ascontiguousarray(F.T), np.ones((1, n), np.float32)])
+    f = FnParams.make(k + 1, H["SQUARE"], c=2.0 * gamma, b=np.concatenate([np.zeros(k), [1.0]]).astype(np.float32))
+    f.h[k] = H["IND_EQ0"]
+    f.c[k] = 1.0
+    g = FnParams.make(n, H["IND_GE0"], d=(-mu).astype(np.float32), e=(2.0 * gamma * Dd).astype(np.float32))
+    return Problem("portfolio", A, f, g, dict(seed=seed, gamma=gamma))
+
+
+CLASSES = dict(lasso=lasso, logistic=logistic, huber=huber, svm=svm, nnls=nnls, lp=lp,
+               basis_pursuit=basis_pursuit, entropy=entropy, portfolio=portfolio)
 
 
 def nnls_precision_large(seed: int = 30_000) -> Problem:
