@@ -47,7 +47,8 @@ typedef enum {
   POGS_IND_GE0 = 7,   /* indicator of z >= 0                 */
   POGS_IND_LE0 = 8,   /* indicator of z <= 0                 */
   POGS_IND_EQ0 = 9,   /* indicator of z == 0                 */
-  POGS_IND_BOX01 = 10 /* indicator of 0 <= z <= 1            */
+  POGS_IND_BOX01 = 10, /* indicator of 0 <= z <= 1           */
+  POGS_XLOGX = 11      /* z log z (0 at z = 0, +inf for z < 0) */
 } pogs_h;
 
 /* Status / error codes. */

@@ -19,7 +19,7 @@ lib = C.CDLL(LIB_PATH)
 
 # ---- enums -----------------------------------------------------------------------------
 H = dict(ZERO=0, ABS=1, SQUARE=2, HUBER=3, LOGISTIC=4, HINGE=5, MAXPOS=6, IND_GE0=7, IND_LE0=8,
-         IND_EQ0=9, IND_BOX01=10)
+         IND_EQ0=9, IND_BOX01=10, XLOGX=11)
 OK, MAX_ITER = 0, 1
 ERR = {-1: "ARG", -2: "OOM", -3: "NONFINITE", -4: "NUMERIC", -5: "TIMEOUT", -6: "CUDA", -7: "CAPACITY"}
 GRAM = dict(BF16=0, TF32=1, BF16X3=2, FP32=3)

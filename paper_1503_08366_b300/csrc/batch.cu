@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(NT) bsetup_equil_kernel(BInst* insts, BCfg cfg
     const int hv = h0[i];
     const float av = a0 ? a0[i] : 1.0f, bv = b0 ? b0[i] : 0.0f, cv = c0 ? c0[i] : 1.0f;
     const float dv = d0 ? d0[i] : 0.0f, ev = e0 ? e0[i] : 0.0f;
-    if (hv < 0 || hv > POGS_IND_BOX01 || !(av != 0.0f) || !(cv >= 0.0f) || !(ev >= 0.0f) || !isfinite(av) ||
+    if (hv < 0 || hv > POGS_XLOGX || !(av != 0.0f) || !(cv >= 0.0f) || !(ev >= 0.0f) || !isfinite(av) ||
         !isfinite(bv) || !isfinite(cv) || !isfinite(dv) || !isfinite(ev))
       atomicCAS(&s_err, 0, POGS_ERR_ARG);
     const float sc = isf ? 1.0f / d[i] : e[i];

@@ -533,7 +533,7 @@ __global__ void fold_kernel(FnDev raw, int64_t k, const float* scale, int is_f, 
     const int hv = raw.h[i];
     const float av = raw.a ? raw.a[i] : 1.0f, bv = raw.b ? raw.b[i] : 0.0f;
     const float cv = raw.c ? raw.c[i] : 1.0f, dv = raw.d ? raw.d[i] : 0.0f, ev = raw.e ? raw.e[i] : 0.0f;
-    if (hv < 0 || hv > POGS_IND_BOX01 || !(av != 0.0f) || !(cv >= 0.0f) || !(ev >= 0.0f) ||
+    if (hv < 0 || hv > POGS_XLOGX || !(av != 0.0f) || !(cv >= 0.0f) || !(ev >= 0.0f) ||
         !isfinite(av) || !isfinite(bv) || !isfinite(cv) || !isfinite(dv) || !isfinite(ev))
       atomicCAS(err, 0, POGS_ERR_ARG);   // first error wins
     const float s = scale[i];

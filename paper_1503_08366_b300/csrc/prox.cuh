@@ -39,6 +39,38 @@ POGS_DEV float prox_logistic(float v, float r) {
   return z;
 }
 
+// argmin_{z > 0} z log z + (r/2)(z - v)^2: the root of psi(t) = t + 1 + r e^t - r v in
+// t = log z.  psi is increasing and convex; with hi = max(v, 1) the root lies in
+// [r (v - hi) - 1, log hi].  Newton from the right end (psi > 0) descends monotonically on a
+// convex increasing function; as in the logistic prox, a step that leaves the bracket or
+// fails to halve the previous one is replaced by bisection.
+POGS_DEV float prox_xlogx(float v, float r) {
+  const float zhi = fmaxf(v, 1.0f);
+  float hi = logf(zhi), lo = r * (v - zhi) - 1.0f;
+  float t = hi;
+  float dx_old = hi - lo, dx = dx_old;
+#pragma unroll 1
+  for (int it = 0; it < 64; ++it) {
+    const float et = expf(t);
+    const float psi = t + 1.0f + r * et - r * v;
+    const float dpsi = 1.0f + r * et;
+    if (psi == 0.0f) break;
+    if (psi > 0.0f) hi = t; else lo = t;
+    const bool newton_out = ((t - hi) * dpsi - psi) * ((t - lo) * dpsi - psi) > 0.0f;
+    const bool too_slow = fabsf(2.0f * psi) > fabsf(dx_old * dpsi);
+    dx_old = dx;
+    if (newton_out || too_slow) {
+      dx = 0.5f * (hi - lo);
+      t = lo + dx;
+    } else {
+      dx = psi / dpsi;
+      t = t - dx;
+    }
+    if (fabsf(dx) <= 1e-7f * (1.0f + fabsf(t)) || hi - lo <= 1e-7f * (1.0f + fabsf(t))) break;
+  }
+  return expf(t);
+}
+
 // argmin_z h(z) + (r/2)(z - v)^2 for the base functions of the library.
 POGS_DEV float prox_h(int h, float v, float r) {
   const float ir = 1.0f / r;
@@ -54,6 +86,7 @@ POGS_DEV float prox_h(int h, float v, float r) {
     case POGS_IND_LE0: return fminf(v, 0.0f);
     case POGS_IND_EQ0: return 0.0f;
     case POGS_IND_BOX01: return fminf(fmaxf(v, 0.0f), 1.0f);
+    case POGS_XLOGX: return prox_xlogx(v, r);
     default: return v;
   }
 }
@@ -68,6 +101,7 @@ POGS_DEV float h_value(int h, float z) {
     case POGS_LOGISTIC: return fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z)));
     case POGS_HINGE: return fmaxf(0.0f, 1.0f - z);
     case POGS_MAXPOS: return fmaxf(0.0f, z);
+    case POGS_XLOGX: return z > 0.0f ? z * logf(z) : 0.0f;
     default: return 0.0f;
   }
 }

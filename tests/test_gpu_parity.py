@@ -64,12 +64,13 @@ def test_prox_eval_matches_oracle(P, code):
     assert err.max() <= 2e-5, (err.max(), int(err.argmax()))
 
 
-@pytest.mark.parametrize("code", [W.H[k] for k in ("LOGISTIC", "HUBER", "ABS", "MAXPOS")],
-                         ids=["LOGISTIC", "HUBER", "ABS", "MAXPOS"])
+@pytest.mark.parametrize("code", [W.H[k] for k in ("LOGISTIC", "HUBER", "ABS", "MAXPOS", "XLOGX")],
+                         ids=["LOGISTIC", "HUBER", "ABS", "MAXPOS", "XLOGX"])
 def test_prox_eval_extreme_regimes(P, code):
     """The unit base prox (a = c = 1, b = d = e = 0) at rho from 1e-6 to 1e4 and |v| up to 1e4.
     For the logistic this is the regime where an unguarded Newton iteration bounces between the
-    two flat tails of the sigmoid (small rho, |v| of tens to thousands)."""
+    two flat tails of the sigmoid (small rho, |v| of tens to thousands); for z log z it spans
+    roots from far below the FP32 range (returned as 0) to ~1e4."""
     import torch
     rng = np.random.default_rng(900 + code)
     k = 60000
@@ -128,7 +129,15 @@ def _tight(prob):
 
 
 CASES = [("lasso", (200, 100)), ("huber", (600, 200)), ("svm", (500, 150)), ("nnls", (600, 250)),
-         ("logistic", (500, 120)), ("lasso", (150, 600)), ("logistic", (200, 700)), ("nnls", (1300, 1300))]
+         ("logistic", (500, 120)), ("lasso", (150, 600)), ("logistic", (200, 700)), ("nnls", (1300, 1300)),
+         ("basis_pursuit", (60, 150)), ("entropy", (60, 200)), ("portfolio", (300, 12))]
+
+
+# Classes whose f carries a dense equality or many inequality indicators (the LP's A x <= b,
+# the portfolio's budget 1^T x = 1): at eps_rel = 1e-3 the residual test bounds their objective
+# only loosely -- the FP64 oracle stopped by the same test lands ~1e-3 from p* on them -- so the
+# objective bound is 1e-2 there; both residuals must still meet their tolerances.
+OBJ_TOL = {"portfolio": 1e-2}
 
 
 @pytest.mark.parametrize("cls,shape", CASES)
@@ -140,10 +149,11 @@ def test_solve_matches_oracle_objective(P, cls, shape):
     assert info.status == 0, info.as_dict()
     assert info.r_pri < info.eps_pri and info.r_dual < info.eps_dual
     ref = _tight(prob)
-    assert abs(info.obj - ref.obj) <= 1e-3 * max(1.0, abs(ref.obj)), (info.obj, ref.obj)
+    tol = OBJ_TOL.get(cls, 1e-3)
+    assert abs(info.obj - ref.obj) <= tol * max(1.0, abs(ref.obj)), (info.obj, ref.obj)
     # the objective recomputed in FP64 from the returned (unscaled) tuple agrees too
     obj64 = OA.objective(prob.A, prob.f, prob.g, x.astype(float), y.astype(float), tol=1e-4)
-    assert abs(obj64 - ref.obj) <= 2e-3 * max(1.0, abs(ref.obj))
+    assert abs(obj64 - ref.obj) <= 2 * tol * max(1.0, abs(ref.obj))
 
 
 def test_lp_solution_matches_linprog(P):
