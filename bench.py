@@ -602,6 +602,74 @@ def run_precision(args):
     print(json.dumps(line))
 
 
+def run_next(args):
+    """Rows beyond the single-solve path: (1) warm start and factor reuse -- a Lasso
+    regularisation path of 10 weights on one handle (one setup), each solve started from the
+    previous solution, against the same path started cold; (2) the wider prox library and
+    classes -- basis pursuit, entropy maximization and portfolio optimization solves."""
+    import torch
+    import workloads as W
+    import paper_1503_08366_b300 as P
+
+    torch.cuda.set_device(0)
+    out = {}
+    # (1) regularisation path, 20000 x 8000 Lasso
+    base = W.lasso(20000, 8000, seed=50_000)
+    A = torch.from_numpy(base.A).cuda()
+    lam_max = float(np.max(np.abs(base.A.astype(np.float64).T @ base.f.b.astype(np.float64))))
+    fracs = [0.5, 0.35, 0.25, 0.18, 0.12, 0.09, 0.06, 0.045, 0.03, 0.02]
+    prm = P.pogs_default_params(max_iter=20000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with P.Solver(A, prm) as s:
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        runs = {}
+        for mode in ("cold", "warm"):
+            x0 = nu0 = None
+            iters, objs = [], []
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            for frac in fracs:
+                g = W.FnParams.make(base.n, W.H["ABS"], c=frac * lam_max)
+                info, x, y, mu, nu = s.solve(base.f, g, x0=x0, nu0=nu0)
+                if info.status != 0:
+                    raise RuntimeError(f"path solve did not converge: {info.as_dict()}")
+                iters.append(info.iters)
+                objs.append(info.obj)
+                if mode == "warm":
+                    x0, nu0 = x, nu
+            torch.cuda.synchronize()
+            runs[mode] = dict(seconds=time.perf_counter() - t1, iters=iters, objs=objs)
+    out["lasso_path"] = dict(shape=[20000, 8000], weights=len(fracs), setup_s=setup_s,
+                             cold=dict(solves_per_s=len(fracs) / runs["cold"]["seconds"], iters=runs["cold"]["iters"]),
+                             warm=dict(solves_per_s=len(fracs) / runs["warm"]["seconds"], iters=runs["warm"]["iters"]),
+                             max_obj_rel_diff=float(max(abs(a - b) / max(1.0, abs(b)) for a, b in
+                                                        zip(runs["warm"]["objs"], runs["cold"]["objs"]))))
+    del A
+    # (2) the remaining Appendix A classes
+    cls = []
+    for name, gen, shape in (("basis_pursuit", W.basis_pursuit, (2000, 8000)), ("entropy", W.entropy, (2000, 20000)),
+                             ("portfolio", W.portfolio, (20000, 100))):
+        prob = gen(*shape, seed=51_000)
+        prm = P.pogs_default_params(max_iter=20000)
+        Ad = torch.from_numpy(np.ascontiguousarray(prob.A)).cuda()
+        reps = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            with P.Solver(Ad, prm) as s:
+                info, x, *_ = s.solve(prob.f, prob.g)
+            torch.cuda.synchronize()
+            reps.append(time.perf_counter() - t1)
+        cls.append(dict(cls=name, shape=list(prob.A.shape), status=info.status, iters=info.iters, obj=info.obj,
+                        r_pri=info.r_pri, eps_pri=info.eps_pri, r_dual=info.r_dual, eps_dual=info.eps_dual,
+                        setup_ms=info.setup_ms, solve_ms=info.solve_ms, wall_s_median=float(np.median(reps))))
+        del Ad
+    out["classes"] = cls
+    print(json.dumps(dict(workload="next", metric="warm-start path solves/s and iterations; class solves", **out)))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -609,7 +677,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve", "precision"])
+    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve", "precision", "next"])
     ap.add_argument("--count", type=int, default=2048, help="batch workload: instances")
     ap.add_argument("--plain-sample", type=int, default=128, help="batch workload: plain-path sample")
     ap.add_argument("--requests", type=int, default=4000, help="serve workload: requests in the trace")
@@ -629,6 +697,8 @@ def main():
         run_serve(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "next":
+        run_next(args)
     else:
         run_ours(args)
 
