@@ -260,7 +260,9 @@ __device__ __forceinline__ void epi_n(const EpiArgs& ep, int i, float u1, float 
   }
 }
 
-template <int NRHS, bool SQ, int EPI>
+// U: float4 loads in flight per lane.  8 when a block holds at least 32 rows (long-running
+// blocks, where per-warp memory parallelism matters more than resident blocks), else 4.
+template <int NRHS, bool SQ, int EPI, int U>
 __global__ void __launch_bounds__(256) gemv_n_kernel(const float* __restrict__ A, int64_t lda, int m, int n,
                                                      const float* __restrict__ x1,
                                                      const float* __restrict__ x2, int rows, int cols,
@@ -285,12 +287,12 @@ __global__ void __launch_bounds__(256) gemv_n_kernel(const float* __restrict__ A
     const float4* Ar = reinterpret_cast<const float4*>(A + (int64_t)row * lda + cbeg);
     float s1 = 0.0f, s2 = 0.0f;
     int qq = lane;
-    for (; qq + 96 < nq; qq += 128) {
-      float4 a[4];
+    for (; qq + 32 * (U - 1) < nq; qq += 32 * U) {
+      float4 a[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = ldg_stream(Ar + qq + 32 * u);
+      for (int u = 0; u < U; ++u) a[u] = ldg_stream(Ar + qq + 32 * u);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < U; ++u) {
         float4 av = a[u];
         if (SQ) { av.x *= av.x; av.y *= av.y; av.z *= av.z; av.w *= av.w; }
         const float4 xv = sx[qq + 32 * u];
@@ -635,12 +637,14 @@ GemvGeom choose_geometry(int64_t m, int64_t n, int64_t lda, int num_sms) {
   if (rows < 64) rows = std::min<int64_t>(64, round_up(m, 8));
   g.t_rows = (int)rows;
   g.t_nsplit = (int)cdiv(m, rows);
-  // row dots: column chunks of <= 4096 floats; rows per block chosen for ~8 blocks per SM
+  // row dots: column chunks of <= 4096 floats; rows per block chosen for ~5 blocks per SM
+  // (measured on both large shapes against 2, 3, 4 and 8: fewer, longer-running blocks with
+  // eight loads in flight per lane stream closest to the copy bandwidth)
   int64_t nchunk = cdiv(lda, 4096);
   int64_t cols = round_up(cdiv(lda, nchunk), 128);
   g.n_cols = (int)cols;
   g.n_ncolsplit = (int)cdiv(lda, cols);
-  int64_t tgt = (int64_t)num_sms * 8;
+  int64_t tgt = (int64_t)num_sms * 5;
   int64_t nrb = cdiv(tgt, g.n_ncolsplit);
   // a multiple of 8 rows per block, so that each of the 8 warps gets the same number of rows
   int64_t rb = round_up(cdiv(m, nrb), 8);
@@ -684,8 +688,15 @@ static void gemv_n_dispatch(int epi, const float* A, int64_t lda, int m, int n, 
   count_launch();
   const size_t smem = (size_t)NRHS * g.n_cols * sizeof(float);
   // smem <= 2 x 4096 floats = 32 KB: no opt-in needed (and nothing to set during capture)
-#define POGS_N(E) \
-  gemv_n_kernel<NRHS, SQ, E><<<grid, 256, smem, s>>>(A, lda, m, n, x1, x2, g.n_rows, g.n_cols, part, cnt, ep, guard)
+#define POGS_N(E)                                                                                         \
+  do {                                                                                                    \
+    if (g.n_rows >= 32)                                                                                   \
+      gemv_n_kernel<NRHS, SQ, E, 8><<<grid, 256, smem, s>>>(A, lda, m, n, x1, x2, g.n_rows, g.n_cols, part, \
+                                                            cnt, ep, guard);                               \
+    else                                                                                                  \
+      gemv_n_kernel<NRHS, SQ, E, 4><<<grid, 256, smem, s>>>(A, lda, m, n, x1, x2, g.n_rows, g.n_cols, part, \
+                                                            cnt, ep, guard);                               \
+  } while (0)
   switch (epi) {
     case EPN_RAW: POGS_N(EPN_RAW); break;
     case EPN_TALL_Y: POGS_N(EPN_TALL_Y); break;
