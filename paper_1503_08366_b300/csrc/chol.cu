@@ -476,22 +476,74 @@ int chol_mixed(float* G, float* Hlo, int64_t ldh, int64_t q, float* Lf, int64_t 
   count_launch();
   gram_to_df_kernel<<<(int)std::min<int64_t>(cdiv(q * q, 256), 148 * 16), 256, 0, s>>>(G, ldh, q, Hlo);
   float* Hhi = G;
-  for (int64_t k0 = 0; k0 < q; k0 += kDB) {
-    const int nb = (int)std::min<int64_t>(kDB, q - k0);
-    count_launch();
-    chol_diag_kernel<<<1, 256, kDiagSmem, s>>>(Hhi + k0 * ldh + k0, ldh, nb, Md + k0 * ldm + k0, ldm, err);
-    const int64_t rest = q - k0 - nb;
-    if (rest > 0) {
+  // Lookahead: stream `ca` (highest priority) runs the critical chain -- diagonal block k,
+  // panel k, and the update of block column k+1 by panel k; stream `cb` (lowest priority)
+  // updates the remaining columns (>= k+2) by panel k, overlapping the next diagonal block and
+  // panel.  Both write block column k+1 (cb with panel k-1, ca with panel k), so the critical
+  // update of step k waits for cb's update of step k-1; every other pair touches disjoint
+  // blocks or is ordered within one stream.
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  cudaStream_t ca = nullptr, cb = nullptr;
+  cudaEvent_t e_fork = nullptr, e_panel = nullptr, e_rest = nullptr, e_a = nullptr, e_b = nullptr;
+  int rc = 0;
+  if (cudaStreamCreateWithPriority(&ca, cudaStreamNonBlocking, hi) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&cb, cudaStreamNonBlocking, lo) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e_panel, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e_rest, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e_a, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e_b, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    rc = POGS_ERR_CUDA;
+  }
+  if (rc == 0) {
+    cudaEventRecord(e_fork, s);
+    cudaStreamWaitEvent(ca, e_fork, 0);
+    cudaStreamWaitEvent(cb, e_fork, 0);
+    bool rest_pending = false;
+    for (int64_t k0 = 0; k0 < q; k0 += kDB) {
+      const int nb = (int)std::min<int64_t>(kDB, q - k0);
+      count_launch();
+      chol_diag_kernel<<<1, 256, kDiagSmem, ca>>>(Hhi + k0 * ldh + k0, ldh, nb, Md + k0 * ldm + k0, ldm, err);
+      const int64_t rest = q - k0 - nb;
+      if (rest <= 0) break;
       // L21 = H21 W_kk^T (from the hi part: the pair rounds to hi)
       sgemm_launch<true, OUT_F32, 2>(rest, kDB, kDB, Hhi + (k0 + kDB) * ldh + k0, ldh, Md + k0 * ldm + k0, ldm,
-                                     1.0f, Lf + (k0 + kDB) * ldf + k0, nullptr, ldf, false, 0, s);
-      // H22 -= L21 L21^T (lower tiles, double-float)
+                                     1.0f, Lf + (k0 + kDB) * ldf + k0, nullptr, ldf, false, 0, ca);
+      cudaEventRecord(e_panel, ca);
       const float* P = Lf + (k0 + kDB) * ldf + k0;
-      sgemm_launch<true, OUT_SUB_DF, 2>(rest, rest, kDB, P, ldf, P, ldf, 1.0f, Hhi + (k0 + kDB) * ldh + k0 + kDB,
-                                        Hlo + (k0 + kDB) * ldh + k0 + kDB, ldh, true, 0, s);
+      const int64_t nb1 = std::min<int64_t>(kDB, rest);
+      // critical: block column k+1 (all rows below k) by panel k, after cb's update by panel k-1
+      if (rest_pending) cudaStreamWaitEvent(ca, e_rest, 0);
+      sgemm_launch<true, OUT_SUB_DF, 2>(rest, nb1, kDB, P, ldf, P, ldf, 1.0f, Hhi + (k0 + kDB) * ldh + k0 + kDB,
+                                        Hlo + (k0 + kDB) * ldh + k0 + kDB, ldh, false, 0, ca);
+      // the rest: columns >= k+2 (lower tiles) by panel k, overlapped
+      const int64_t rest2 = rest - nb1;
+      if (rest2 > 0) {
+        cudaStreamWaitEvent(cb, e_panel, 0);
+        const float* P2 = P + nb1 * ldf;
+        sgemm_launch<true, OUT_SUB_DF, 2>(rest2, rest2, kDB, P2, ldf, P2, ldf, 1.0f,
+                                          Hhi + (k0 + kDB + nb1) * ldh + k0 + kDB + nb1,
+                                          Hlo + (k0 + kDB + nb1) * ldh + k0 + kDB + nb1, ldh, true, 0, cb);
+        cudaEventRecord(e_rest, cb);
+        rest_pending = true;
+      } else {
+        rest_pending = false;
+      }
     }
+    // join both streams back into the caller's stream
+    cudaEventRecord(e_a, ca);
+    cudaEventRecord(e_b, cb);
+    cudaStreamWaitEvent(s, e_a, 0);
+    cudaStreamWaitEvent(s, e_b, 0);
+    if (cudaGetLastError() != cudaSuccess) rc = POGS_ERR_CUDA;
   }
-  return 0;
+  for (cudaEvent_t e : {e_fork, e_panel, e_rest, e_a, e_b})
+    if (e) cudaEventDestroy(e);
+  if (ca) cudaStreamDestroy(ca);
+  if (cb) cudaStreamDestroy(cb);
+  return rc;
 }
 
 void tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ldm, float* work, cudaStream_t s) {
