@@ -28,7 +28,7 @@ import dataclasses
 import numpy as np
 
 from .equil import Equilibration, equilibrate, fold_f, fold_g, default_gamma
-from .project import Projector
+from .project import Projector, cgls
 from .prox import prox_f, f_value
 
 
@@ -46,6 +46,9 @@ class Params:
     adaptive_rho: bool = True
     gap_stop: bool = True
     equil: bool = True
+    proj: str = "direct"           # "direct" (cached Cholesky) or "cgls" (indirect, Section 3.5)
+    cg_iters: int = 50             # CGLS step cap per projection
+    cg_tol: float = 1e-6           # CGLS stop: ||B^T r|| <= cg_tol ||B^T b||
 
 
 @dataclasses.dataclass
@@ -89,7 +92,8 @@ def solve(A, f, g, params: Params | None = None, eq: Equilibration | None = None
             eq = _identity_equil(A)
     Ah, D, E = eq.Ahat, eq.D, eq.E
     fh, gh = fold_f(f, D), fold_g(g, E)
-    proj = Projector(Ah)
+    proj = Projector(Ah) if p.proj == "direct" else None
+    u_cg = None   # CGLS warm start: the previous projection's least-squares variable
 
     x, xt = np.zeros(n), np.zeros(n)
     y, yt = np.zeros(m), np.zeros(m)
@@ -123,7 +127,10 @@ def solve(A, f, g, params: Params | None = None, eq: Equilibration | None = None
         xr = p.alpha * xh + (1.0 - p.alpha) * x
         yr = p.alpha * yh + (1.0 - p.alpha) * y
         # Algorithm 1, projection and dual update
-        xn, yn = proj(xr + xt, yr + yt)
+        if proj is not None:
+            xn, yn = proj(xr + xt, yr + yt)
+        else:
+            xn, yn, u_cg, _ = cgls(Ah, xr + xt, yr + yt, u0=u_cg, iters=p.cg_iters, tol=p.cg_tol)
         xt = xt + xr - xn
         yt = yt + yr - yn
         x, y = xn, yn

@@ -53,3 +53,45 @@ class Projector:
             y = d + self.solve(A @ c - d)
             x = c + A.T @ (d - y)
         return x, y
+
+
+def cgls(A: np.ndarray, c: np.ndarray, d: np.ndarray, u0=None, iters: int = 50, tol: float = 0.0):
+    """Indirect projection (Section 3.5): CGLS on the reduced least-squares problem, started
+    from a previous iterate u0 (the paper's suggestion for very large problems).
+
+        m >= n:  x = argmin_u ||A u - d||^2 + ||u - c||^2,  y = A x;
+        m <  n:  z = argmin_u ||A^T u - c||^2 + ||u + d||^2, y = d + z, x = c - A^T z
+    (the normal equations of these are the two reduced updates).  Both are min ||B u - b||
+    with B = [M; I]; the iteration is textbook CGLS (Hestenes-Stiefel conjugate gradients on
+    the least-squares problem, residual kept as r = b - B u), run until
+    ||B^T r|| <= tol ||B^T b|| or `iters` steps.  Returns (x, y, u, steps)."""
+    A = np.asarray(A, np.float64)
+    c = np.asarray(c, np.float64)
+    d = np.asarray(d, np.float64)
+    m, n = A.shape
+    tall = m >= n
+    M, top, bot = (A, d, c) if tall else (A.T, c, -d)   # min ||M u - top||^2 + ||u - bot||^2
+    u = np.zeros(M.shape[1]) if u0 is None else np.array(u0, np.float64)
+    r_top = top - M @ u
+    r_bot = bot - u
+    s = M.T @ r_top + r_bot
+    p = s.copy()
+    gamma = float(s @ s)
+    stop = tol * float(np.linalg.norm(M.T @ top + bot))
+    steps = 0
+    while steps < iters and gamma > 0.0 and np.sqrt(gamma) > stop:
+        q = M @ p
+        alpha = gamma / float(q @ q + p @ p)
+        u = u + alpha * p
+        r_top = r_top - alpha * q
+        r_bot = r_bot - alpha * p
+        s = M.T @ r_top + r_bot
+        gamma_new = float(s @ s)
+        p = s + (gamma_new / gamma) * p
+        gamma = gamma_new
+        steps += 1
+    if tall:
+        x, y = u, A @ u
+    else:
+        x, y = c - A.T @ u, d + u
+    return x, y, u, steps
