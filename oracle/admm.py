@@ -48,7 +48,7 @@ class Params:
     equil: bool = True
     proj: str = "direct"           # "direct" (cached Cholesky) or "cgls" (indirect, Section 3.5)
     cg_iters: int = 50             # CGLS step cap per projection
-    cg_tol: float = 1e-6           # CGLS stop: ||B^T r|| <= cg_tol ||B^T b||
+    cg_tol: float = 1e-6           # CGLS stop: ||B^T r|| <= cg_tol ||r||
 
 
 @dataclasses.dataclass

@@ -63,8 +63,10 @@ def cgls(A: np.ndarray, c: np.ndarray, d: np.ndarray, u0=None, iters: int = 50, 
         m <  n:  z = argmin_u ||A^T u - c||^2 + ||u + d||^2, y = d + z, x = c - A^T z
     (the normal equations of these are the two reduced updates).  Both are min ||B u - b||
     with B = [M; I]; the iteration is textbook CGLS (Hestenes-Stiefel conjugate gradients on
-    the least-squares problem, residual kept as r = b - B u), run until
-    ||B^T r|| <= tol ||B^T b|| or `iters` steps.  Returns (x, y, u, steps)."""
+    the least-squares problem, residual kept as r = b - B u), run until the least-squares
+    optimality test ||B^T r|| <= tol ||r|| (LSQR's first stopping rule with ||B|| taken as 1,
+    the scale of an equilibrated matrix; ||r|| is the distance of (c, d) from the graph and
+    stays away from zero) or `iters` steps.  Returns (x, y, u, steps)."""
     A = np.asarray(A, np.float64)
     c = np.asarray(c, np.float64)
     d = np.asarray(d, np.float64)
@@ -77,9 +79,8 @@ def cgls(A: np.ndarray, c: np.ndarray, d: np.ndarray, u0=None, iters: int = 50, 
     s = M.T @ r_top + r_bot
     p = s.copy()
     gamma = float(s @ s)
-    stop = tol * float(np.linalg.norm(M.T @ top + bot))
     steps = 0
-    while steps < iters and gamma > 0.0 and np.sqrt(gamma) > stop:
+    while steps < iters and gamma > 0.0 and np.sqrt(gamma) > tol * np.sqrt(float(r_top @ r_top + r_bot @ r_bot)):
         q = M @ p
         alpha = gamma / float(q @ q + p @ p)
         u = u + alpha * p
