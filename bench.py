@@ -667,7 +667,30 @@ def run_next(args):
                         setup_ms=info.setup_ms, solve_ms=info.solve_ms, wall_s_median=float(np.median(reps))))
         del Ad
     out["classes"] = cls
-    print(json.dumps(dict(workload="next", metric="warm-start path solves/s and iterations; class solves", **out)))
+    # (3) indirect projection (CGLS, no Gram and no factorization) against the direct one
+    ind = []
+    for name, gen, shape in (("lasso", W.lasso, (40000, 10000)), ("logistic", W.logistic, (10000, 40000))):
+        prob = gen(*shape, seed=52_000)
+        Ad = torch.from_numpy(np.ascontiguousarray(prob.A)).cuda()
+        row = dict(cls=name, shape=list(prob.A.shape))
+        for mode in ("DIRECT", "CGLS"):
+            prm = P.pogs_default_params(max_iter=20000, proj_mode=mode)
+            reps = []
+            for _ in range(2):
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                with P.Solver(Ad, prm) as s:
+                    info, x, *_ = s.solve(prob.f, prob.g)
+                torch.cuda.synchronize()
+                reps.append(time.perf_counter() - t1)
+            row[mode.lower()] = dict(status=info.status, iters=info.iters, obj=info.obj, setup_ms=info.setup_ms,
+                                     solve_ms=info.solve_ms, wall_s_median=float(np.median(reps)))
+        row["obj_rel_diff"] = abs(row["cgls"]["obj"] - row["direct"]["obj"]) / max(1.0, abs(row["direct"]["obj"]))
+        ind.append(row)
+        del Ad
+    out["indirect"] = ind
+    print(json.dumps(dict(workload="next", metric="warm-start path solves/s and iterations; class solves; "
+                          "indirect vs direct projection", **out)))
 
 
 def main():

@@ -103,7 +103,16 @@ typedef struct {
                         check_every iterations                                         */
   int check_every;   /* loop_mode 1 only (default 10)                                  */
   int chol_prec;     /* POGS_CHOL_* (default POGS_CHOL_MIXED)                           */
+  int proj_mode;     /* POGS_PROJ_DIRECT (default): cached factor of I + A^T A (or I + A A^T);
+                        POGS_PROJ_CGLS: indirect projection (Section 3.5), no Gram and no
+                        factorization -- CGLS on the reduced least-squares problem, started
+                        from the previous projection; fixed at setup                     */
+  int cg_max_iter;   /* CGLS steps per projection, at most (default 30)                 */
+  double cg_tol;     /* CGLS stop: ||B^T r|| <= cg_tol ||r||, B = [A; I] or [A^T; I]
+                        (LSQR's first test with ||B|| = 1; default 1e-4)                */
 } pogs_params;
+
+enum { POGS_PROJ_DIRECT = 0, POGS_PROJ_CGLS = 1 };
 
 /* Arithmetic of the Cholesky factorization of I + G (Section 3.5). */
 enum {

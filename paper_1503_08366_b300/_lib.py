@@ -24,6 +24,7 @@ OK, MAX_ITER = 0, 1
 ERR = {-1: "ARG", -2: "OOM", -3: "NONFINITE", -4: "NUMERIC", -5: "TIMEOUT", -6: "CUDA", -7: "CAPACITY"}
 GRAM = dict(BF16=0, TF32=1, BF16X3=2, FP32=3)
 CHOL = dict(FP64=0, MIXED=1)
+PROJ = dict(DIRECT=0, CGLS=1)
 
 
 class pogs_fn(C.Structure):
@@ -37,7 +38,7 @@ class pogs_params(C.Structure):
                 ("sk_sweeps", C.c_int), ("gamma", C.c_double), ("gram_prec", C.c_int),
                 ("refine_steps", C.c_int), ("gap_stop", C.c_int), ("adaptive_rho", C.c_int),
                 ("equil", C.c_int), ("verbose", C.c_int), ("loop_mode", C.c_int), ("check_every", C.c_int),
-                ("chol_prec", C.c_int)]
+                ("chol_prec", C.c_int), ("proj_mode", C.c_int), ("cg_max_iter", C.c_int), ("cg_tol", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -180,6 +181,8 @@ def pogs_default_params(**overrides) -> pogs_params:
             v = GRAM[v.upper()]
         if isinstance(v, str) and k == "chol_prec":
             v = CHOL[v.upper()]
+        if isinstance(v, str) and k == "proj_mode":
+            v = PROJ[v.upper()]
         setattr(p, k, v)
     return p
 

@@ -98,6 +98,32 @@ void launch_prox_step(int n, int m, const float* x, float* xt, float* xh, float*
 // sums go to part[by][rhs][col]; the last block of each slab reduces the splits in a fixed
 // order and applies the epilogue.
 // ------------------------------------------------------------------------------------------
+// CGLS epilogues (indirect projection), shared by both GEMV orientations with one right-hand
+// side: i indexes the output vector, u = (M v)_i.  Codes 5..8 of EpiT / EpiN.
+template <int E>
+__device__ __forceinline__ void epi_cg(const EpiArgs& ep, int i, float u, Df* res) {
+  if constexpr (E == 5) {            // r_top = top - M u0
+    const float r = ep.cg_top[i] - u;
+    ep.cg_rt[i] = r;
+    df_add_prod(res[0], r, r);
+  } else if constexpr (E == 6) {     // r_bot = sign * bot - u0; s = M^T r_top + r_bot; p = s
+    const float rb = ep.cg_sign * ep.cg_bot[i] - ep.cg_u[i];
+    const float sv = u + rb;
+    ep.cg_rb[i] = rb;
+    ep.cg_s[i] = sv;
+    ep.cg_p[i] = sv;
+    df_add_prod(res[0], sv, sv);
+    df_add_prod(res[1], rb, rb);
+  } else if constexpr (E == 7) {     // q = M p
+    ep.out1[i] = u;
+    df_add_prod(res[0], u, u);
+  } else {                           // s = M^T r_top + r_bot
+    const float sv = u + ep.cg_rb[i];
+    ep.cg_s[i] = sv;
+    df_add_prod(res[0], sv, sv);
+  }
+}
+
 template <int EPI>
 __device__ __forceinline__ void epi_t(const EpiArgs& ep, int j, float t1, float t2, float t3, Df* res) {
   if constexpr (EPI == EPT_RAW) {
@@ -131,6 +157,8 @@ __device__ __forceinline__ void epi_t(const EpiArgs& ep, int j, float t1, float 
     df_add_prod(res[0], ej, t1);   // sum_ij d_i A_ij^2 e_j = ||D A E||_F^2 (p = 2)
   } else if constexpr (EPI == EPT_REFINE) {
     ep.out1[j] = ep.in1[j] - ep.in2[j] - t1;
+  } else if constexpr (EPI >= EPT_CG_R) {
+    epi_cg<EPI>(ep, j, t1, res);
   }
 }
 
@@ -143,6 +171,7 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(const float* __restrict__ A
                                                      EpiArgs ep, const DevState* __restrict__ guard) {
   __shared__ double sh[2 * 8];
   if (guard && guard->done) return;
+  if (ep.cg_done && *ep.cg_done) return;
   const int tid = threadIdx.x;
   const int64_t c0 = (int64_t)blockIdx.x * 1024 + 4 * tid;
   const bool active = c0 < lda;
@@ -257,6 +286,8 @@ __device__ __forceinline__ void epi_n(const EpiArgs& ep, int i, float u1, float 
     ep.sk_vec[i] = ep.sk_num / (u1 + ep.sk_reg);
   } else if constexpr (EPI == EPN_REFINE) {
     ep.out1[i] = ep.in1[i] - ep.in2[i] - u1;
+  } else if constexpr (EPI >= EPN_CG_R) {
+    epi_cg<EPI>(ep, i, u1, res);
   }
 }
 
@@ -271,6 +302,7 @@ __global__ void __launch_bounds__(256) gemv_n_kernel(const float* __restrict__ A
   extern __shared__ float4 sx[];
   __shared__ double sh[2 * 8];
   if (guard && guard->done) return;
+  if (ep.cg_done && *ep.cg_done) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t cbeg = (int64_t)blockIdx.y * cols;
   const int64_t cend = min((int64_t)lda, cbeg + cols);
@@ -667,6 +699,10 @@ static void gemv_t_dispatch(int epi, const float* A, int64_t lda, int m, int n, 
     case EPT_FAT_X: POGS_T(EPT_FAT_X); break;
     case EPT_SK_COL: POGS_T(EPT_SK_COL); break;
     case EPT_REFINE: POGS_T(EPT_REFINE); break;
+    case EPT_CG_R: POGS_T(EPT_CG_R); break;
+    case EPT_CG_S0: POGS_T(EPT_CG_S0); break;
+    case EPT_CG_Q: POGS_T(EPT_CG_Q); break;
+    case EPT_CG_S: POGS_T(EPT_CG_S); break;
   }
 #undef POGS_T
 }
@@ -703,6 +739,10 @@ static void gemv_n_dispatch(int epi, const float* A, int64_t lda, int m, int n, 
     case EPN_FAT_R: POGS_N(EPN_FAT_R); break;
     case EPN_SK_ROW: POGS_N(EPN_SK_ROW); break;
     case EPN_REFINE: POGS_N(EPN_REFINE); break;
+    case EPN_CG_R: POGS_N(EPN_CG_R); break;
+    case EPN_CG_S0: POGS_N(EPN_CG_S0); break;
+    case EPN_CG_Q: POGS_N(EPN_CG_Q); break;
+    case EPN_CG_S: POGS_N(EPN_CG_S); break;
   }
 #undef POGS_N
 }

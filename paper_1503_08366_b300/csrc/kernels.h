@@ -11,6 +11,10 @@ enum EpiT : int {
   EPT_FAT_X = 2,    // fat x^{k+1} = c + A^T (d - y^{k+1}); x~ = -A^T y~; dual residual
   EPT_SK_COL = 3,   // Algorithm 2 e-update; Frobenius partial sum e_j * colsum_j
   EPT_REFINE = 4,   // refinement residual out1 = r - x0 - t1 (tall)
+  EPT_CG_R = 5,     // CGLS (indirect projection): r_top = top - M u0             (fat: M = A^T)
+  EPT_CG_S0 = 6,    //   r_bot = sign*bot - u0, s = M^T r_top + r_bot, p = s       (tall)
+  EPT_CG_Q = 7,     //   q = M p                                                  (fat)
+  EPT_CG_S = 8,     //   s = M^T r_top + r_bot                                    (tall)
 };
 // Epilogues of the row-dot GEMV  u = A [x1, x2]  (one row per output element).
 enum EpiN : int {
@@ -19,6 +23,10 @@ enum EpiN : int {
   EPN_FAT_R = 2,    // fat projection input r = A c - d; primal residual
   EPN_SK_ROW = 3,   // Algorithm 2 d-update
   EPN_REFINE = 4,   // refinement residual out1 = r - y0 - u1 (fat)
+  EPN_CG_R = 5,     // CGLS: r_top = top - M u0 (tall: M = A)
+  EPN_CG_S0 = 6,    //   init gradient (fat)
+  EPN_CG_Q = 7,     //   q = M p (tall)
+  EPN_CG_S = 8,     //   s = M^T r_top + r_bot (fat)
 };
 // Epilogues of the packed-triangle products z = M v (M = L^{-1}) and M^T v.
 enum EpiR : int {
@@ -38,6 +46,11 @@ struct EpiArgs {
   float* sk_vec;                      // SK output vector (d or e)
   float sk_num, sk_reg;               // n and gamma/m (rows) or m and gamma/n (cols)
   Df* res_part;                       // 2 per block: residual^2, unscaled residual^2 (double-float)
+  // CGLS (indirect projection): see cgls.cu
+  float *cg_rt, *cg_rb, *cg_s, *cg_p;  // r_top, r_bot, s, p
+  const float *cg_top, *cg_bot, *cg_u; // top, bot, u0
+  float cg_sign;                       // bot enters as cg_sign * cg_bot
+  const int* cg_done;                  // a set flag makes the GEMV return at once
 };
 
 // Loop parameters in device memory (so a captured graph survives parameter changes).
@@ -78,6 +91,32 @@ void launch_fold(FnDev raw, int64_t k, const float* scale, int is_f, uint8_t* h,
 void launch_fill(float* p, int64_t k, float v, cudaStream_t s);
 void launch_warm(const float* src, const float* scale, int64_t k, float factor, float* out_pos, float* out_neg,
                  cudaStream_t s);
+
+// ---- CGLS indirect projection (cgls.cu) ----------------------------------------------------
+struct CgState {
+  double gamma;     // ||s||^2 of the current step
+  double pnorm2;    // ||p||^2
+  double rnorm2;    // ||r_top||^2 + ||r_bot||^2
+  double gmin;      // smallest gamma of this projection (divergence test)
+  int done, steps, max_steps;
+  float tol;
+};
+// After the init passes: gamma and ||r||^2 from the init partials, steps = 0, done flag.
+void launch_cg_start(CgState* cg, const DevState* st, const Df* r0_part, int nr0, const Df* s0_part, int ns0,
+                     cudaStream_t s);
+// x += alpha p on u, r_top -= alpha q, r_bot -= alpha p; alpha = gamma / (||q||^2 + ||p||^2).
+void launch_cg_alpha(CgState* cg, const DevState* st, const Df* q_part, int nq, float* u, float* rt, float* rb,
+                     const float* p, const float* q, int ntop, int nu, Df* r_part, int nblk, cudaStream_t s);
+// p = s + beta p (beta = ||s_new||^2 / gamma); the last block updates gamma, ||p||^2, ||r||^2,
+// steps and the stop flag (||s|| <= tol ||r|| or the step cap).
+void launch_cg_beta(CgState* cg, const DevState* st, const Df* s_part, int ns, const Df* r_part, int nr,
+                    float* p, const float* sv, int nu, Df* p_part, unsigned* cnt, int nblk, cudaStream_t s);
+// Blocks of the elementwise CGLS kernels for k elements.
+int cg_blocks(int64_t k);
+// Tall: x~ += c - x.  Fat: y = d + z, w = d - y, y~ += d - y.
+void launch_cg_tall_finish(int n, float* xt, const float* cx, const float* x, const DevState* st, cudaStream_t s);
+void launch_cg_fat_finish(int m, const float* dy, const float* z, float* y, float* w, float* yt,
+                          const DevState* st, cudaStream_t s);
 void launch_unscale(int n, int m, const float* xh, const float* mu, const float* yh, const float* nu,
                     const float* D, const float* E, float* x, float* muo, float* y, float* nuo,
                     cudaStream_t s);

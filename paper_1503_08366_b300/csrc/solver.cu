@@ -43,6 +43,16 @@ struct pogs_handle {
   float *part_t = nullptr, *part_n = nullptr, *part_tr = nullptr;
   unsigned *cnt_t = nullptr, *cnt_n = nullptr, *cnt_tr = nullptr;
   Df *prox_part = nullptr, *pri_part = nullptr, *dual_part = nullptr;   // block partials (double-float)
+  // indirect projection (CGLS): vectors, state, partials
+  bool indirect = false;             // set up without a factor (proj_mode CGLS)
+  float *cg_rt = nullptr, *cg_rb = nullptr, *cg_s = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_z = nullptr;
+  CgState* cg = nullptr;
+  CgState* cg_host = nullptr;        // pinned staging
+  Df *cg_r0_part = nullptr, *cg_s0_part = nullptr, *cg_q_part = nullptr, *cg_s_part = nullptr;
+  Df *cg_r_part = nullptr, *cg_p_part = nullptr;
+  unsigned* cg_cnt = nullptr;
+  int cg_nblk = 1;
+  int graph_cg = -1;
   DevState* st = nullptr;
   DevCfg* cfg = nullptr;
   DevState* st_host = nullptr;     // pinned mirror
@@ -138,7 +148,7 @@ int dalloc(pogs_handle* h, T** p, size_t count) {
 // Pinned host slots for each handle's status / parameter mirror, allocated in chunks and
 // recycled (never released while the library is loaded: cudaFreeHost synchronises the device).
 constexpr size_t kPinSlot = 512;
-static_assert(sizeof(DevState) + sizeof(DevCfg) <= kPinSlot, "pinned slot too small");
+static_assert(sizeof(DevState) + sizeof(DevCfg) + sizeof(CgState) + 16 <= kPinSlot, "pinned slot too small");
 std::mutex g_pin_mu;
 std::vector<void*> g_pin_free;
 
@@ -202,8 +212,97 @@ EpiArgs epi0() {
   return e;
 }
 
+// CGLS steps per projection for a solve with parameters p: 0 selects the direct projection.
+// A handle set up without a factor always projects indirectly (at least one step).
+int cg_steps_for(const pogs_handle* h, const pogs_params* p) {
+  if (h->indirect || p->proj_mode == POGS_PROJ_CGLS) return std::max(1, p->cg_max_iter);
+  return 0;
+}
+
+// Indirect projection of one iteration (Section 3.5): `steps` unrolled CGLS steps, each of
+// which returns at once after the stopping test has fired.  Tall: u = x (the previous x is the
+// warm start), M = A^; fat: u = z (kept from the previous projection), M = A^T.  The passes
+// that give the residual norms, x~ and the final y (tall) or x (fat) are those of the direct
+// projection.
+void enqueue_projection_cgls(pogs_handle* h, int steps, cudaStream_t s) {
+  const int m = (int)h->m, n = (int)h->n;
+  const GemvGeom& g = h->geom;
+  const int* done = &h->cg->done;
+  if (h->tall) {
+    // dual residual ||A^T nu + mu||, x~ = -A^T y~ (r = c + A^T d is not needed here)
+    EpiArgs e1 = epi0();
+    e1.r = h->r; e1.cx = h->cx; e1.mu = h->mu; e1.E = h->E; e1.xt = h->xt; e1.res_part = h->dual_part;
+    launch_gemv_t(3, false, EPT_TALL_R, h->A, h->lda, m, n, h->dy, h->nu, h->yt, g, h->part_t, h->cnt_t, e1, h->st, s);
+    // r_top = d - A x0 ; r_bot = c - x0, s = A^T r_top + r_bot, p = s
+    EpiArgs a = epi0();
+    a.cg_top = h->dy; a.cg_rt = h->cg_rt; a.res_part = h->cg_r0_part;
+    launch_gemv_n(1, false, EPN_CG_R, h->A, h->lda, m, n, h->x, nullptr, g, h->part_n, h->cnt_n, a, h->st, s);
+    EpiArgs b = epi0();
+    b.cg_bot = h->cx; b.cg_sign = 1.0f; b.cg_u = h->x; b.cg_rb = h->cg_rb; b.cg_s = h->cg_s; b.cg_p = h->cg_p;
+    b.res_part = h->cg_s0_part;
+    launch_gemv_t(1, false, EPT_CG_S0, h->A, h->lda, m, n, h->cg_rt, nullptr, nullptr, g, h->part_t, h->cnt_t, b,
+                  h->st, s);
+    launch_cg_start(h->cg, h->st, h->cg_r0_part, g.n_nrowblk, h->cg_s0_part, g.t_ncolblk, s);
+    for (int k = 0; k < steps; ++k) {
+      EpiArgs q = epi0();
+      q.out1 = h->cg_q; q.res_part = h->cg_q_part; q.cg_done = done;
+      launch_gemv_n(1, false, EPN_CG_Q, h->A, h->lda, m, n, h->cg_p, nullptr, g, h->part_n, h->cnt_n, q, h->st, s);
+      launch_cg_alpha(h->cg, h->st, h->cg_q_part, g.n_nrowblk, h->x, h->cg_rt, h->cg_rb, h->cg_p, h->cg_q, m, n,
+                      h->cg_r_part, h->cg_nblk, s);
+      EpiArgs sv = epi0();
+      sv.cg_rb = h->cg_rb; sv.cg_s = h->cg_s; sv.res_part = h->cg_s_part; sv.cg_done = done;
+      launch_gemv_t(1, false, EPT_CG_S, h->A, h->lda, m, n, h->cg_rt, nullptr, nullptr, g, h->part_t, h->cnt_t, sv,
+                    h->st, s);
+      launch_cg_beta(h->cg, h->st, h->cg_s_part, g.t_ncolblk, h->cg_r_part, h->cg_nblk, h->cg_p, h->cg_s, n,
+                     h->cg_p_part, h->cg_cnt, cg_blocks(n), s);
+    }
+    launch_cg_tall_finish(n, h->xt, h->cx, h->x, h->st, s);
+    // [y, w] = A [x, x^{1/2}] ; y~ += d - y ; primal residual
+    EpiArgs e8 = epi0();
+    e8.y = h->y; e8.yt = h->yt; e8.dy = h->dy; e8.yh = h->yh; e8.D = h->D; e8.res_part = h->pri_part;
+    launch_gemv_n(2, false, EPN_TALL_Y, h->A, h->lda, m, n, h->x, h->xh, g, h->part_n, h->cnt_n, e8, h->st, s);
+  } else {
+    // primal residual ||A x^{1/2} - y^{1/2}|| (r = A c - d is not needed here)
+    EpiArgs e1 = epi0();
+    e1.r = h->r; e1.dy = h->dy; e1.yh = h->yh; e1.D = h->D; e1.res_part = h->pri_part;
+    launch_gemv_n(2, false, EPN_FAT_R, h->A, h->lda, m, n, h->cx, h->xh, g, h->part_n, h->cnt_n, e1, h->st, s);
+    // r_top = c - A^T z0 ; r_bot = -d - z0, s = A r_top + r_bot, p = s
+    EpiArgs a = epi0();
+    a.cg_top = h->cx; a.cg_rt = h->cg_rt; a.res_part = h->cg_r0_part;
+    launch_gemv_t(1, false, EPT_CG_R, h->A, h->lda, m, n, h->cg_z, nullptr, nullptr, g, h->part_t, h->cnt_t, a,
+                  h->st, s);
+    EpiArgs b = epi0();
+    b.cg_bot = h->dy; b.cg_sign = -1.0f; b.cg_u = h->cg_z; b.cg_rb = h->cg_rb; b.cg_s = h->cg_s; b.cg_p = h->cg_p;
+    b.res_part = h->cg_s0_part;
+    launch_gemv_n(1, false, EPN_CG_S0, h->A, h->lda, m, n, h->cg_rt, nullptr, g, h->part_n, h->cnt_n, b, h->st, s);
+    launch_cg_start(h->cg, h->st, h->cg_r0_part, g.t_ncolblk, h->cg_s0_part, g.n_nrowblk, s);
+    for (int k = 0; k < steps; ++k) {
+      EpiArgs q = epi0();
+      q.out1 = h->cg_q; q.res_part = h->cg_q_part; q.cg_done = done;
+      launch_gemv_t(1, false, EPT_CG_Q, h->A, h->lda, m, n, h->cg_p, nullptr, nullptr, g, h->part_t, h->cnt_t, q,
+                    h->st, s);
+      launch_cg_alpha(h->cg, h->st, h->cg_q_part, g.t_ncolblk, h->cg_z, h->cg_rt, h->cg_rb, h->cg_p, h->cg_q, n, m,
+                      h->cg_r_part, h->cg_nblk, s);
+      EpiArgs sv = epi0();
+      sv.cg_rb = h->cg_rb; sv.cg_s = h->cg_s; sv.res_part = h->cg_s_part; sv.cg_done = done;
+      launch_gemv_n(1, false, EPN_CG_S, h->A, h->lda, m, n, h->cg_rt, nullptr, g, h->part_n, h->cnt_n, sv, h->st, s);
+      launch_cg_beta(h->cg, h->st, h->cg_s_part, g.n_nrowblk, h->cg_r_part, h->cg_nblk, h->cg_p, h->cg_s, m,
+                     h->cg_p_part, h->cg_cnt, cg_blocks(m), s);
+    }
+    launch_cg_fat_finish(m, h->dy, h->cg_z, h->y, h->w, h->yt, h->st, s);
+    // x = c + A^T (d - y) ; x~ = -A^T y~ ; dual residual
+    EpiArgs e8 = epi0();
+    e8.x = h->x; e8.xt = h->xt; e8.cx = h->cx; e8.mu = h->mu; e8.E = h->E; e8.res_part = h->dual_part;
+    launch_gemv_t(3, false, EPT_FAT_X, h->A, h->lda, m, n, h->w, h->nu, h->yt, g, h->part_t, h->cnt_t, e8, h->st, s);
+  }
+}
+
 // The projection of one iteration (tall or fat), optionally with refinement.
-void enqueue_projection(pogs_handle* h, int refine, cudaStream_t s) {
+void enqueue_projection(pogs_handle* h, int refine, int cg_steps, cudaStream_t s) {
+  if (cg_steps > 0 || h->indirect) {
+    enqueue_projection_cgls(h, cg_steps, s);
+    return;
+  }
   const int m = (int)h->m, n = (int)h->n, q = (int)h->q;
   const GemvGeom& g = h->geom;
   if (h->tall) {
@@ -280,21 +379,23 @@ void enqueue_projection(pogs_handle* h, int refine, cudaStream_t s) {
   }
 }
 
-void enqueue_iteration(pogs_handle* h, int refine, cudaStream_t s, unsigned long long cond, int use_cond) {
+void enqueue_iteration(pogs_handle* h, int refine, int cg_steps, cudaStream_t s, unsigned long long cond,
+                       int use_cond) {
   launch_prox_step((int)h->n, (int)h->m, h->x, h->xt, h->xh, h->cx, h->mu, h->y, h->yt, h->yh, h->dy, h->nu,
                    fn_g(h), fn_f(h), h->st, h->cfg, h->prox_part, h->nprox, s);
-  enqueue_projection(h, refine, s);
+  enqueue_projection(h, refine, cg_steps, s);
   launch_check(h->st, h->cfg, h->prox_part, h->nprox, h->pri_part, h->geom.n_nrowblk, h->dual_part,
                h->geom.t_ncolblk, cond, use_cond, s);
 }
 
-int kernels_per_iteration(const pogs_handle* h, int refine) {
-  (void)h;
+int kernels_per_iteration(const pogs_handle* h, int refine, int cg_steps) {
+  if (cg_steps > 0 || h->indirect)   // prox, 2 passes, CGLS init (3), 4 per step, finish, check
+    return 8 + 4 * cg_steps;
   return 6 + (refine ? 4 : 0);   // prox, 2 A passes, 2 triangle products, check (+ refinement)
 }
 
-int build_graph(pogs_handle* h, int refine, int mode) {
-  if (h->gexec && h->graph_refine == refine && h->graph_mode == mode) return 0;
+int build_graph(pogs_handle* h, int refine, int mode, int cg_steps) {
+  if (h->gexec && h->graph_refine == refine && h->graph_mode == mode && h->graph_cg == cg_steps) return 0;
   if (h->gexec) {
     cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;
@@ -314,14 +415,14 @@ int build_graph(pogs_handle* h, int refine, int mode) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     ++g_capture_depth;
-    enqueue_iteration(h, refine, h->cap, (unsigned long long)ch, 1);
+    enqueue_iteration(h, refine, cg_steps, h->cap, (unsigned long long)ch, 1);
     --g_capture_depth;
     cudaGraph_t captured = nullptr;
     CK(cudaStreamEndCapture(h->cap, &captured));
   } else {
     CK(cudaStreamBeginCaptureToGraph(h->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     ++g_capture_depth;
-    enqueue_iteration(h, refine, h->cap, 0ull, 0);
+    enqueue_iteration(h, refine, cg_steps, h->cap, 0ull, 0);
     --g_capture_depth;
     cudaGraph_t captured = nullptr;
     CK(cudaStreamEndCapture(h->cap, &captured));
@@ -330,6 +431,7 @@ int build_graph(pogs_handle* h, int refine, int mode) {
   cudaGraphDestroy(g);
   h->graph_refine = refine;
   h->graph_mode = mode;
+  h->graph_cg = cg_steps;
   return 0;
 }
 
@@ -338,7 +440,9 @@ int validate_params(const pogs_params* p) {
   if (!(p->abs_tol >= 0) || !(p->rel_tol >= 0) || p->max_iter < 1 || !(p->rho0 > 0) || !(p->alpha > 0) ||
       !(p->alpha < 2) || !(p->delta >= 1) || !(p->tau > 0) || p->sk_sweeps < 0 || p->refine_steps < 0 ||
       p->refine_steps > 1 || p->gram_prec < POGS_GRAM_BF16 || p->gram_prec > POGS_GRAM_FP32 ||
-      p->loop_mode < 0 || p->loop_mode > 1 || p->chol_prec < POGS_CHOL_FP64 || p->chol_prec > POGS_CHOL_MIXED)
+      p->loop_mode < 0 || p->loop_mode > 1 || p->chol_prec < POGS_CHOL_FP64 || p->chol_prec > POGS_CHOL_MIXED ||
+      p->proj_mode < POGS_PROJ_DIRECT || p->proj_mode > POGS_PROJ_CGLS || p->cg_max_iter < 0 ||
+      p->cg_max_iter > 1000 || !(p->cg_tol >= 0))
     return POGS_ERR_ARG;
   return 0;
 }
@@ -415,6 +519,15 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order) {
   launch_scale(h->A, h->lda, m, n, h->D, h->E, s);
   CK(cudaGetLastError());
   phase("equil");
+  if (h->sp.proj_mode == POGS_PROJ_CGLS) {
+    // indirect projection: no Gram, no factorization (the phases are recorded empty)
+    h->indirect = true;
+    phase("gram");
+    phase("cholesky");
+    phase("inverse");
+    CK(cudaStreamSynchronize(s));
+    return 0;
+  }
   // ---- Gram -----------------------------------------------------------------------------
   // square work matrices share one 128-byte-aligned pitch (vector loads in the factorization)
   const int64_t ldq = round_up(q, 32);
@@ -503,12 +616,25 @@ int alloc_state(pogs_handle* h) {
   TRY(dalloc(h, &h->prox_part, (size_t)h->nprox * 6));
   TRY(dalloc(h, &h->pri_part, (size_t)g.n_nrowblk * 2));
   TRY(dalloc(h, &h->dual_part, (size_t)g.t_ncolblk * 2));
+  {
+    float** cgv[] = {&h->cg_rt, &h->cg_rb, &h->cg_s, &h->cg_p, &h->cg_q, &h->cg_z};
+    for (auto p : cgv) TRY(dalloc(h, p, qv));
+    const size_t np = (size_t)std::max(g.n_nrowblk, g.t_ncolblk) * 2;
+    Df** cgp[] = {&h->cg_r0_part, &h->cg_s0_part, &h->cg_q_part, &h->cg_s_part};
+    for (auto p : cgp) TRY(dalloc(h, p, np));
+    h->cg_nblk = cg_blocks(std::max(h->mv, h->nv));
+    TRY(dalloc(h, &h->cg_r_part, (size_t)h->cg_nblk * 2));
+    TRY(dalloc(h, &h->cg_p_part, (size_t)h->cg_nblk * 2));
+    TRY(dalloc(h, &h->cg_cnt, 1));
+    TRY(dalloc(h, &h->cg, 1));
+  }
   TRY(dalloc(h, &h->st, 1));
   TRY(dalloc(h, &h->cfg, 1));
   void* pin = pin_slot_get();
   if (!pin) return POGS_ERR_OOM;
   h->st_host = static_cast<DevState*>(pin);
   h->cfg_host = reinterpret_cast<DevCfg*>(static_cast<char*>(pin) + sizeof(DevState));
+  h->cg_host = reinterpret_cast<CgState*>(static_cast<char*>(pin) + ((sizeof(DevState) + sizeof(DevCfg) + 15) & ~size_t(15)));
   return 0;
 }
 
@@ -574,6 +700,15 @@ int reset_state(pogs_handle* h, const pogs_params* p) {
   *h->cfg_host = c;
   CK(cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(h->cfg, h->cfg_host, sizeof(DevCfg), cudaMemcpyHostToDevice, s));
+  {
+    CgState cg;
+    memset(&cg, 0, sizeof(cg));
+    cg.max_steps = cg_steps_for(h, p);
+    cg.tol = (float)p->cg_tol;
+    *h->cg_host = cg;
+    CK(cudaMemcpyAsync(h->cg, h->cg_host, sizeof(CgState), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(h->cg_z, 0, std::max(h->nv, h->mv) * sizeof(float), s));   // fat CGLS warm start
+  }
   CK(cudaMemsetAsync(h->x, 0, h->nv * sizeof(float), s));
   CK(cudaMemsetAsync(h->xt, 0, h->nv * sizeof(float), s));
   CK(cudaMemsetAsync(h->y, 0, h->mv * sizeof(float), s));
@@ -613,6 +748,9 @@ void pogs_default_params(pogs_params* p) {
   p->loop_mode = 0;
   p->check_every = 10;
   p->chol_prec = POGS_CHOL_MIXED;
+  p->proj_mode = POGS_PROJ_DIRECT;
+  p->cg_max_iter = 30;
+  p->cg_tol = 1e-4;
 }
 
 int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order, const pogs_params* p, void* stream,
@@ -639,6 +777,7 @@ int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order, co
   h->nv = round_up(std::max<int64_t>(h->lda, h->tall ? (int64_t)h->T * kTile : 0), kTile);
   h->mv = round_up(std::max<int64_t>(m, h->tall ? 0 : (int64_t)h->T * kTile), kTile);
   h->sp = *p;
+  h->indirect = p->proj_mode == POGS_PROJ_CGLS;
   h->stream = static_cast<cudaStream_t>(stream);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -725,7 +864,8 @@ int pogs_solve_warm(pogs_handle* h, const pogs_fn* f, const pogs_fn* g, const po
   TRY(upload_fn(h, g, h->n, 0));
   if (x0 || nu0) TRY(warm_start(h, x0, nu0, p->rho0));
   const int refine = p->refine_steps;
-  TRY(build_graph(h, refine, p->loop_mode));
+  const int cg_steps = cg_steps_for(h, p);
+  TRY(build_graph(h, refine, p->loop_mode, cg_steps));
   if (p->loop_mode == 0) {
     CK(cudaGraphLaunch(h->gexec, s));
   } else {
@@ -748,7 +888,7 @@ int pogs_solve_warm(pogs_handle* h, const pogs_fn* f, const pogs_fn* g, const po
   CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const DevState& st = *h->st_host;
-  count_launch(st.k * kernels_per_iteration(h, refine));
+  count_launch(st.k * kernels_per_iteration(h, refine, cg_steps));
   h->solved = true;
   int status = st.status;
   if (st.err != 0) status = st.err;
@@ -830,7 +970,7 @@ int pogs_project(pogs_handle* h, const float* c, const float* d, float* x, float
   CK(cudaMemsetAsync(h->mu, 0, h->nv * sizeof(float), s));
   CK(cudaMemsetAsync(h->yh, 0, h->mv * sizeof(float), s));
   CK(cudaMemsetAsync(h->nu, 0, h->mv * sizeof(float), s));
-  enqueue_projection(h, p->refine_steps, s);
+  enqueue_projection(h, p->refine_steps, cg_steps_for(h, p), s);
   CK(cudaGetLastError());
   TRY(copy_out(h->x, x, h->n, s));
   TRY(copy_out(h->y, y, h->m, s));
@@ -858,7 +998,7 @@ int pogs_get_setup_report(const pogs_handle* h, pogs_setup_report* r) {
 long long pogs_kernel_launches(void) { return g_launch_count.load(); }
 
 int pogs_time_kernels(pogs_handle* h, int reps, double* ms, double* bytes) {
-  if (!h || reps < 1 || !h->solved) return POGS_ERR_ARG;
+  if (!h || reps < 1 || !h->solved || h->indirect) return POGS_ERR_ARG;   // times the direct projection
   cudaStream_t s = h->stream;
   const double m = (double)h->m, n = (double)h->n, q = (double)h->q;
   const double A = 4.0 * m * n, tri = 2.0 * q * (q + 1.0);
