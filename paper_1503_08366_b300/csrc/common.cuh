@@ -82,11 +82,13 @@ POGS_DEV void df_add_prod(Df& a, float x, float y) {   // a += x y
 POGS_DEV double df_value(const Df& a) { return (double)a.hi + (double)a.lo; }
 
 // Block-wide sum of NV double-float values per thread: a fixed xor-shuffle tree on the FP32
-// pipes inside each warp, then the per-warp results in FP64 in warp order; `out` valid in
-// thread 0; `sh` holds NV * (blockDim/32) doubles.  Deterministic.
+// pipes inside each warp, then the same across the per-warp results in warp 0 (no serial FP64
+// chain); `out` valid in thread 0; `sh` holds NV * (blockDim/32) doubles (used as double-float
+// pairs).  Deterministic.
 template <int NV>
 POGS_DEV void block_sum_df(Df (&v)[NV], double (&out)[NV], double* sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  Df* sd = reinterpret_cast<Df*>(sh);
 #pragma unroll
   for (int t = 0; t < NV; ++t) {
 #pragma unroll
@@ -97,15 +99,18 @@ POGS_DEV void block_sum_df(Df (&v)[NV], double (&out)[NV], double* sh) {
   }
   if (lane == 0) {
 #pragma unroll
-    for (int t = 0; t < NV; ++t) sh[t * nw + wid] = df_value(v[t]);
+    for (int t = 0; t < NV; ++t) sd[t * nw + wid] = v[t];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (wid == 0) {
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += sh[t * nw + w];
-      out[t] = s;
+      Df a = lane < nw ? sd[t * nw + lane] : Df{0.0f, 0.0f};
+      for (int o = 1; o < nw; o <<= 1) {
+        const Df b{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+        df_add(a, b);
+      }
+      out[t] = df_value(a);
     }
   }
   __syncthreads();
