@@ -57,6 +57,8 @@ def equilibrate(A: np.ndarray, sweeps: int = 10, gamma: float | None = None) -> 
         D, E = np.ones(m), np.ones(n)
     Ahat = D[:, None] * A * E[None, :]
     s = np.linalg.norm(Ahat) / np.sqrt(min(m, n))
+    if s == 0.0:
+        s = 1.0      # A = 0: there is no norm to rescale to (the rescale is skipped)
     D = D / np.sqrt(s)
     E = E / np.sqrt(s)
     Ahat = D[:, None] * A * E[None, :]

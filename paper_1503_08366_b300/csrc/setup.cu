@@ -88,7 +88,8 @@ __global__ void sk_finish_kernel(const float* dvec, const float* evec, int64_t m
   double v[1] = {0.0};
   for (int i = threadIdx.x; i < nfrob; i += blockDim.x) v[0] += df_value(frob_part[2 * i]);
   block_sum<1>(v, sh);
-  if (threadIdx.x == 0) s_inv = 1.0 / sqrt(v[0] / (double)q);
+  // A = 0: there is no norm to rescale to (the rescale is skipped)
+  if (threadIdx.x == 0) s_inv = v[0] > 0.0 ? 1.0 / sqrt(v[0] / (double)q) : 1.0;
   __syncthreads();
   const double si = s_inv;
   for (int64_t i = threadIdx.x; i < m; i += blockDim.x) D[i] = (float)sqrt((double)dvec[i] * si);

@@ -62,6 +62,21 @@ def test_rescale_frobenius(shape):
     assert np.allclose(eq.Ahat, eq.D[:, None] * A * eq.E[None, :])
 
 
+def test_zero_matrix_skips_the_rescale():
+    """A = 0 has no Frobenius norm to rescale to: D and E stay the finite Algorithm 2 factors
+    (for A = 0 those are d = n m / gamma, e = m n / gamma in closed form) and A^ = 0; the
+    projection is then (c, 0) for the tall form, the closed form with G = 0."""
+    m, n = 9, 4
+    eq = OE.equilibrate(np.zeros((m, n)), 10)
+    gamma = OE.default_gamma(m, n)
+    assert np.all(np.isfinite(eq.D)) and np.all(np.isfinite(eq.E))
+    assert np.allclose(eq.D ** 2, n * m / gamma) and np.allclose(eq.E ** 2, m * n / gamma)
+    assert np.all(eq.Ahat == 0)
+    c, d = np.arange(n, dtype=float), np.arange(m, dtype=float)
+    x, y = OPJ.Projector(eq.Ahat)(c, d)
+    assert np.allclose(x, c) and np.allclose(y, 0)
+
+
 def test_folding_matches_composed_function():
     """Eq. 12: f_hat(yh) = f(yh / D) and g_hat(xh) = g(E xh), evaluated pointwise."""
     rng = np.random.default_rng(5)
