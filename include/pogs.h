@@ -154,6 +154,19 @@ void pogs_default_params(pogs_params* p);
 int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order,
                const pogs_params* p, void* stream, pogs_handle** out);
 
+/* Setup for a sparse A given in CSR form (Section 3.5: sparse A; Section 4.1 equilibration
+ * over the nonzeros).  rowptr has m + 1 entries with rowptr[0] = 0 and rowptr[m] = nnz;
+ * colind and val have nnz entries, the column indices of each row strictly increasing (sorted,
+ * no duplicates) and in [0, n); int32 indices, FP32 values; host or device arrays, which the
+ * caller keeps.  The handle stores the CSR of A^ and of A^T (a stable device transpose,
+ * entries of each column in row order) and runs every pass over A^ as a CSR kernel with the
+ * dense pass's epilogue.  p->proj_mode CGLS: no Gram, no factor.  DIRECT: the reduced update's
+ * I + A^T A (or I + A A^T) is factored as for dense A, its Gram formed from a temporary dense
+ * copy of A^ that setup frees (the factor of a matrix with scattered nonzeros is dense).
+ * Errors: ARG (sizes, NULL, a malformed CSR structure), OOM, NONFINITE, NUMERIC, CUDA. */
+int pogs_setup_csr(int64_t m, int64_t n, int64_t nnz, const int* rowptr, const int* colind, const float* val,
+                   const pogs_params* p, void* stream, pogs_handle** out);
+
 /* Solve with the cached factor: Algorithm 1 + over-relaxation + Algorithm 3 until the
  * Section 3.4 test holds (status 0) or p->max_iter iterations (status 1).  f has m
  * elements, g has n.  Outputs are the unscaled half-step tuple returned by POGS

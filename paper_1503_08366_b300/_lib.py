@@ -82,6 +82,8 @@ lib.pogs_default_params.argtypes = [C.POINTER(pogs_params)]
 lib.pogs_default_params.restype = None
 lib.pogs_setup.argtypes = [_P, C.c_int64, C.c_int64, C.c_int64, C.c_char, C.POINTER(pogs_params), _P, C.POINTER(_P)]
 lib.pogs_setup.restype = C.c_int
+lib.pogs_setup_csr.argtypes = [C.c_int64, C.c_int64, C.c_int64, _P, _P, _P, C.POINTER(pogs_params), _P, C.POINTER(_P)]
+lib.pogs_setup_csr.restype = C.c_int
 lib.pogs_solve.argtypes = [_P, C.POINTER(pogs_fn), C.POINTER(pogs_fn), C.POINTER(pogs_params), _P, _P, _P, _P,
                            C.POINTER(pogs_info)]
 lib.pogs_solve.restype = C.c_int
@@ -208,6 +210,37 @@ def pogs_setup(A, params: pogs_params | None = None, stream=None, order: str = "
     rc = lib.pogs_setup(ptr, m, n, lda, o.encode(), C.byref(params) if params is not None else None,
                         _stream_ptr(stream), C.byref(h))
     _check(rc, "pogs_setup")
+    return h.value
+
+
+def pogs_setup_csr(indptr, indices, data, shape, params: pogs_params | None = None, stream=None):
+    """Sparse A in CSR form: indptr (m + 1), indices (nnz, sorted and unique in each row), data
+    (nnz); numpy arrays or torch tensors (host or CUDA), converted to int32 / float32.  Also
+    accepts a scipy.sparse matrix as `indptr` (shape and the other arrays then come from it)."""
+    if hasattr(indptr, "tocsr"):
+        Asp = indptr.tocsr()
+        Asp.sort_indices()
+        Asp.sum_duplicates()
+        indptr, indices, data, shape = Asp.indptr, Asp.indices, Asp.data, Asp.shape
+    m, n = shape
+    keep: list = []
+
+    def arr(a, dt):
+        if hasattr(a, "data_ptr"):
+            import torch
+            t = a.to(torch.int32 if dt == np.int32 else torch.float32).contiguous()
+            keep.append(t)
+            return t.data_ptr()
+        v = np.ascontiguousarray(a, dt)
+        keep.append(v)
+        return v.ctypes.data
+
+    rp, ci, va = arr(indptr, np.int32), arr(indices, np.int32), arr(data, np.float32)
+    nnz = int(indices.numel() if hasattr(indices, "numel") else len(indices))
+    h = _P()
+    rc = lib.pogs_setup_csr(m, n, nnz, rp, ci, va, C.byref(params) if params is not None else None,
+                            _stream_ptr(stream), C.byref(h))
+    _check(rc, "pogs_setup_csr")
     return h.value
 
 

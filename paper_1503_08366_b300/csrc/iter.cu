@@ -20,6 +20,7 @@
 #include <cstdio>
 
 #include "kernels.h"
+#include "epi.cuh"
 #include "prox.cuh"
 
 namespace pogs {
@@ -98,70 +99,6 @@ void launch_prox_step(int n, int m, const float* x, float* xt, float* xh, float*
 // sums go to part[by][rhs][col]; the last block of each slab reduces the splits in a fixed
 // order and applies the epilogue.
 // ------------------------------------------------------------------------------------------
-// CGLS epilogues (indirect projection), shared by both GEMV orientations with one right-hand
-// side: i indexes the output vector, u = (M v)_i.  Codes 5..8 of EpiT / EpiN.
-template <int E>
-__device__ __forceinline__ void epi_cg(const EpiArgs& ep, int i, float u, Df* res) {
-  if constexpr (E == 5) {            // r_top = top - M u0
-    const float r = ep.cg_top[i] - u;
-    ep.cg_rt[i] = r;
-    df_add_prod(res[0], r, r);
-  } else if constexpr (E == 6) {     // r_bot = sign * bot - u0; s = M^T r_top + r_bot; p = s
-    const float rb = ep.cg_sign * ep.cg_bot[i] - ep.cg_u[i];
-    const float sv = u + rb;
-    ep.cg_rb[i] = rb;
-    ep.cg_s[i] = sv;
-    ep.cg_p[i] = sv;
-    df_add_prod(res[0], sv, sv);
-    df_add_prod(res[1], rb, rb);
-  } else if constexpr (E == 7) {     // q = M p
-    ep.out1[i] = u;
-    df_add_prod(res[0], u, u);
-  } else {                           // s = M^T r_top + r_bot
-    const float sv = u + ep.cg_rb[i];
-    ep.cg_s[i] = sv;
-    df_add_prod(res[0], sv, sv);
-  }
-}
-
-template <int EPI>
-__device__ __forceinline__ void epi_t(const EpiArgs& ep, int j, float t1, float t2, float t3, Df* res) {
-  if constexpr (EPI == EPT_RAW) {
-    ep.out1[j] = t1;
-    if (ep.out2) ep.out2[j] = t2;
-  } else if constexpr (EPI == EPT_TALL_R) {
-    ep.r[j] = ep.cx[j] + t1;
-    ep.xt[j] = -t3;                     // x~ re-derived as -A^T y~ (Section 3.3 invariant)
-    const float dr = t2 + ep.mu[j];
-    df_add_prod(res[0], dr, dr);
-    const float du = dr / ep.E[j];
-    df_add_prod(res[1], du, du);
-  } else if constexpr (EPI == EPT_FAT_X) {
-    const float c = ep.cx[j];
-    const float xp = c + t1;
-    ep.x[j] = xp;
-    ep.xt[j] = -t3;                     // x~^{k+1} = -A^T y~^{k+1} (Section 3.3 invariant)
-    const float dr = t2 + ep.mu[j];
-    df_add_prod(res[0], dr, dr);
-    const float du = dr / ep.E[j];
-    df_add_prod(res[1], du, du);
-  } else if constexpr (EPI == EPT_SK_COL) {
-    // sk_num < 0: keep e (Frobenius norm only, no Sinkhorn-Knopp update)
-    float ej;
-    if (ep.sk_num > 0.0f) {
-      ej = ep.sk_num / (t1 + ep.sk_reg);
-      ep.sk_vec[j] = ej;
-    } else {
-      ej = ep.sk_vec[j];
-    }
-    df_add_prod(res[0], ej, t1);   // sum_ij d_i A_ij^2 e_j = ||D A E||_F^2 (p = 2)
-  } else if constexpr (EPI == EPT_REFINE) {
-    ep.out1[j] = ep.in1[j] - ep.in2[j] - t1;
-  } else if constexpr (EPI >= EPT_CG_R) {
-    epi_cg<EPI>(ep, j, t1, res);
-  }
-}
-
 template <int NRHS, bool SQ, int EPI>
 __global__ void __launch_bounds__(256) gemv_t_kernel(const float* __restrict__ A, int64_t lda, int m, int n,
                                                      const float* __restrict__ v1,
@@ -264,33 +201,6 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(const float* __restrict__ A
 // shuffle reduction; partials part[by][rhs][row]; the last chunk-block of a row block
 // reduces in a fixed order and applies the epilogue.
 // ------------------------------------------------------------------------------------------
-template <int EPI>
-__device__ __forceinline__ void epi_n(const EpiArgs& ep, int i, float u1, float u2, Df* res) {
-  if constexpr (EPI == EPN_RAW) {
-    ep.out1[i] = u1;
-    if (ep.out2) ep.out2[i] = u2;
-  } else if constexpr (EPI == EPN_TALL_Y) {
-    ep.y[i] = u1;
-    ep.yt[i] += ep.dy[i] - u1;          // y~ <- y~ + y_r - y^{k+1}
-    const float pr = u2 - ep.yh[i];
-    df_add_prod(res[0], pr, pr);
-    const float pu = pr / ep.D[i];
-    df_add_prod(res[1], pu, pu);
-  } else if constexpr (EPI == EPN_FAT_R) {
-    ep.r[i] = u1 - ep.dy[i];
-    const float pr = u2 - ep.yh[i];
-    df_add_prod(res[0], pr, pr);
-    const float pu = pr / ep.D[i];
-    df_add_prod(res[1], pu, pu);
-  } else if constexpr (EPI == EPN_SK_ROW) {
-    ep.sk_vec[i] = ep.sk_num / (u1 + ep.sk_reg);
-  } else if constexpr (EPI == EPN_REFINE) {
-    ep.out1[i] = ep.in1[i] - ep.in2[i] - u1;
-  } else if constexpr (EPI >= EPN_CG_R) {
-    epi_cg<EPI>(ep, i, u1, res);
-  }
-}
-
 // U: float4 loads in flight per lane.  8 when a block holds at least 32 rows (long-running
 // blocks, where per-warp memory parallelism matters more than resident blocks), else 4.
 template <int NRHS, bool SQ, int EPI, int U>
@@ -710,6 +620,10 @@ static void gemv_t_dispatch(int epi, const float* A, int64_t lda, int m, int n, 
 void launch_gemv_t(int nrhs, bool sq, int epi, const float* A, int64_t lda, int m, int n, const float* v1,
                    const float* v2, const float* v3, const GemvGeom& g, float* part, unsigned* cnt,
                    const EpiArgs& ep, const DevState* guard, cudaStream_t s) {
+  if (g.sparse) {
+    launch_spmv(true, nrhs, sq, epi, g, m, n, v1, v2, v3, ep, guard, s);
+    return;
+  }
   if (nrhs == 3) gemv_t_dispatch<3, false>(epi, A, lda, m, n, v1, v2, v3, g, part, cnt, ep, guard, s);
   else if (nrhs == 2) gemv_t_dispatch<2, false>(epi, A, lda, m, n, v1, v2, v3, g, part, cnt, ep, guard, s);
   else if (sq) gemv_t_dispatch<1, true>(epi, A, lda, m, n, v1, v2, v3, g, part, cnt, ep, guard, s);
@@ -750,6 +664,10 @@ static void gemv_n_dispatch(int epi, const float* A, int64_t lda, int m, int n, 
 void launch_gemv_n(int nrhs, bool sq, int epi, const float* A, int64_t lda, int m, int n, const float* x1,
                    const float* x2, const GemvGeom& g, float* part, unsigned* cnt, const EpiArgs& ep,
                    const DevState* guard, cudaStream_t s) {
+  if (g.sparse) {
+    launch_spmv(false, nrhs, sq, epi, g, m, n, x1, x2, nullptr, ep, guard, s);
+    return;
+  }
   if (nrhs == 2) gemv_n_dispatch<2, false>(epi, A, lda, m, n, x1, x2, g, part, cnt, ep, guard, s);
   else if (sq) gemv_n_dispatch<1, true>(epi, A, lda, m, n, x1, x2, g, part, cnt, ep, guard, s);
   else gemv_n_dispatch<1, false>(epi, A, lda, m, n, x1, x2, g, part, cnt, ep, guard, s);

@@ -64,8 +64,36 @@ struct GemvGeom {
   int t_cols_per_blk;   // 1024 (fixed: 256 threads x float4)
   int t_ncolblk, t_nsplit, t_rows;
   int n_rows, n_cols, n_nrowblk, n_ncolsplit;
+  // Sparse A (csr.cu): the two passes run the CSR kernels over A^ (m rows) and A^T (n rows)
+  // instead; n_nrowblk and t_ncolblk are then their grid sizes (the number of residual
+  // partials each pass writes), sp_lanes_* their lanes per row.
+  int sparse, sp_lanes_n, sp_lanes_t;
+  const int *rp_n, *ci_n, *rp_t, *ci_t;
+  const float *va_n, *va_t;
 };
 GemvGeom choose_geometry(int64_t m, int64_t n, int64_t lda, int num_sms);
+
+// ---- sparse A (csr.cu) ---------------------------------------------------------------------
+void csr_geometry(GemvGeom& g, int64_t m, int64_t n, int64_t nnz, int num_sms);
+// One pass over sparse A^ (trans: column sums via the CSR of A^T), with the dense pass's epilogue.
+void launch_spmv(bool trans, int nrhs, bool sq, int epi, const GemvGeom& g, int m, int n, const float* v1,
+                 const float* v2, const float* v3, const EpiArgs& ep, const DevState* guard, cudaStream_t s);
+// Flags POGS_ERR_ARG (structure) or POGS_ERR_NONFINITE (values) in *err.
+void launch_csr_check(const int* rp, const int* ci, const float* va, int64_t m, int64_t n, int64_t nnz, int* err,
+                      cudaStream_t s);
+// Chunks of the stable multi-split (its table holds chunks x n ints).
+int csr_transpose_chunks(int64_t nnz, int64_t n);
+// CSR of A^T (t_rp: n + 1, t_ci / t_va / perm: nnz) from the CSR of A; scratch rowidx (nnz),
+// cnt (chunks x n, zeroed), tot (n).
+void launch_csr_transpose(const int* rp, const int* ci, const float* va, int64_t m, int64_t n, int64_t nnz,
+                          int nch, int* rowidx, int* cnt, int* tot, int* t_rp, int* t_ci, float* t_va, int* perm,
+                          cudaStream_t s);
+// va <- D va E on the CSR values; t_va[i] = va[perm[i]].
+void launch_csr_scale(const int* rp, const int* ci, float* va, int64_t m, const float* D, const float* E,
+                      const int* perm, int64_t nnz, float* t_va, cudaStream_t s);
+// Scatter the CSR matrix into a zeroed m x lda row-major buffer.
+void launch_csr_densify(const int* rp, const int* ci, const float* va, int64_t m, float* A, int64_t lda,
+                        cudaStream_t s);
 
 // ---- iteration kernels (iter.cu) --------------------------------------------------------
 void launch_prox_step(int n, int m, const float* x, float* xt, float* xh, float* cx, float* mu,

@@ -31,7 +31,12 @@ struct pogs_handle {
   GemvGeom geom{};
   int nprox = 0;
   int gram_used = -1;
-  float* A = nullptr;
+  float* A = nullptr;               // dense A^ (row-major, pitch lda); null for sparse A
+  // sparse A: CSR of A^ (m rows) and of A^T (n rows); perm maps the second's entries to the first's
+  bool sparse = false;
+  int64_t nnz = 0;
+  int *csr_rp = nullptr, *csr_ci = nullptr, *csc_rp = nullptr, *csc_ci = nullptr, *csc_perm = nullptr;
+  float *csr_va = nullptr, *csc_va = nullptr;
   float *D = nullptr, *E = nullptr;
   float* Mt = nullptr;
   float *x = nullptr, *y = nullptr, *xt = nullptr, *yt = nullptr, *xh = nullptr, *yh = nullptr;
@@ -447,7 +452,21 @@ int validate_params(const pogs_params* p) {
   return 0;
 }
 
-int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order) {
+// Sparse input of pogs_setup_csr (host or device arrays).
+struct CsrIn {
+  const int *rp, *ci;
+  const float* va;
+};
+
+template <class T>
+int copy_in_array(T* dst, const T* src, int64_t count, cudaStream_t s) {
+  if (count <= 0) return 0;
+  CK(cudaMemcpyAsync(dst, src, (size_t)count * sizeof(T),
+                     is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  return 0;
+}
+
+int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order, const CsrIn* csr) {
   const int64_t m = h->m, n = h->n, q = h->q;
   cudaStream_t s = h->stream;
   Scratch scr;
@@ -459,12 +478,22 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order) {
     if (nphase < 6) cudaEventRecord(h->ev[nphase++], s);
   };
   // ---- ingest -------------------------------------------------------------------------
-  TRY(dalloc(h, &h->A, (size_t)(m * h->lda)));
   int* err = &h->st->err;
   const bool colmajor = (order == 'C' || order == 'c');
-  if (is_device_ptr(A)) {
+  if (csr) {
+    const int64_t nnz = h->nnz;
+    TRY(dalloc(h, &h->csr_rp, (size_t)(m + 1)));
+    TRY(dalloc(h, &h->csr_ci, (size_t)nnz));
+    TRY(dalloc(h, &h->csr_va, (size_t)nnz));
+    TRY(copy_in_array(h->csr_rp, csr->rp, m + 1, s));
+    TRY(copy_in_array(h->csr_ci, csr->ci, nnz, s));
+    TRY(copy_in_array(h->csr_va, csr->va, nnz, s));
+    launch_csr_check(h->csr_rp, h->csr_ci, h->csr_va, m, n, nnz, err, s);
+  } else if (is_device_ptr(A)) {
+    TRY(dalloc(h, &h->A, (size_t)(m * h->lda)));
     launch_copy_in(A, m, n, lds, colmajor, h->A, h->lda, err, s);
   } else {
+    TRY(dalloc(h, &h->A, (size_t)(m * h->lda)));
     const int64_t rows = colmajor ? n : m, cols = colmajor ? m : n;
     if (!colmajor && lds == n) {
       // contiguous host rows straight into the padded layout
@@ -487,6 +516,25 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order) {
     CK(cudaMemcpyAsync(&err_host, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (err_host != 0) return err_host;
+  }
+  if (csr) {
+    // CSR of A^T by a stable multi-split (entries of each column in increasing row order)
+    const int64_t nnz = h->nnz;
+    TRY(dalloc(h, &h->csc_rp, (size_t)(n + 1)));
+    TRY(dalloc(h, &h->csc_ci, (size_t)nnz));
+    TRY(dalloc(h, &h->csc_va, (size_t)nnz));
+    TRY(dalloc(h, &h->csc_perm, (size_t)nnz));
+    const int nch = csr_transpose_chunks(nnz, n);
+    int *rowidx = nullptr, *cnt = nullptr, *tot = nullptr;
+    TRY(scr.get(&rowidx, (size_t)nnz, s));
+    TRY(scr.get(&cnt, (size_t)nch * (size_t)n, s));
+    TRY(scr.get(&tot, (size_t)n, s));
+    launch_csr_transpose(h->csr_rp, h->csr_ci, h->csr_va, m, n, nnz, nch, rowidx, cnt, tot, h->csc_rp, h->csc_ci,
+                         h->csc_va, h->csc_perm, s);
+    GemvGeom& g = h->geom;
+    g.rp_n = h->csr_rp; g.ci_n = h->csr_ci; g.va_n = h->csr_va;
+    g.rp_t = h->csc_rp; g.ci_t = h->csc_ci; g.va_t = h->csc_va;
+    CK(cudaGetLastError());
   }
   // ---- Algorithm 2 + rescale ----------------------------------------------------------
   float *dvec = nullptr, *evec = nullptr;
@@ -516,7 +564,8 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order) {
                   ec, nullptr, s);
   }
   launch_sk_finish(dvec, evec, m, n, h->dual_part, h->geom.t_ncolblk, q, h->D, h->E, s);
-  launch_scale(h->A, h->lda, m, n, h->D, h->E, s);
+  if (csr) launch_csr_scale(h->csr_rp, h->csr_ci, h->csr_va, m, h->D, h->E, h->csc_perm, h->nnz, h->csc_va, s);
+  else launch_scale(h->A, h->lda, m, n, h->D, h->E, s);
   CK(cudaGetLastError());
   phase("equil");
   if (h->sp.proj_mode == POGS_PROJ_CGLS) {
@@ -533,6 +582,31 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order) {
   const int64_t ldq = round_up(q, 32);
   float* G = nullptr;
   TRY(scr.get(&G, (size_t)(ldq * ldq), s));
+  // sparse A: the Gram of the reduced update is formed from a temporary dense copy of A^
+  // (for A with scattered nonzeros A^T A is dense anyway); the iterations use the CSR passes
+  float* dense = nullptr;
+  if (csr) {
+    void* q0 = nullptr;
+    TRY(pool_alloc(&q0, (size_t)(m * h->lda) * sizeof(float), s));
+    dense = static_cast<float*>(q0);
+    if (cudaMemsetAsync(dense, 0, (size_t)(m * h->lda) * sizeof(float), s) != cudaSuccess) {
+      cudaFreeAsync(dense, s);
+      return POGS_ERR_CUDA;
+    }
+    launch_csr_densify(h->csr_rp, h->csr_ci, h->csr_va, m, dense, h->lda, s);
+    h->A = dense;
+  }
+  struct DenseRelease {
+    pogs_handle* h;
+    float* p;
+    cudaStream_t s;
+    ~DenseRelease() {
+      if (p) {
+        cudaFreeAsync(p, s);
+        h->A = nullptr;
+      }
+    }
+  } dense_release{h, dense, s};
   int used = -1;
   if (h->sp.gram_prec != POGS_GRAM_FP32) {
     size_t need = 0;
@@ -553,6 +627,11 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order) {
   }
   h->gram_used = used;
   CK(cudaGetLastError());
+  if (dense) {
+    cudaFreeAsync(dense, s);
+    h->A = nullptr;
+    dense_release.p = nullptr;
+  }
   phase("gram");
   // ---- Cholesky of I + G -------------------------------------------------------------------
   float *Md = nullptr, *Lf = nullptr;
@@ -753,18 +832,12 @@ void pogs_default_params(pogs_params* p) {
   p->cg_tol = 1e-4;
 }
 
-int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order, const pogs_params* p, void* stream,
-               pogs_handle** out) {
-  if (!out) return POGS_ERR_ARG;
-  *out = nullptr;
-  if (!A || m < 1 || n < 1 || m > (1ll << 31) - 1 || n > (1ll << 31) - 1) return POGS_ERR_ARG;
-  const bool colmajor = (order == 'C' || order == 'c');
-  if (!(colmajor || order == 'R' || order == 'r')) return POGS_ERR_ARG;
-  if ((!colmajor && lda < n) || (colmajor && lda < m)) return POGS_ERR_ARG;
-  pogs_params def;
-  pogs_default_params(&def);
-  if (!p) p = &def;
-  if (validate_params(p) != 0) return POGS_ERR_ARG;
+}  // extern "C"
+
+// The part of pogs_setup and pogs_setup_csr after argument checks: handle, geometry, state,
+// ingest, equilibration and (direct projection) the cached factor.
+static int setup_common(const float* A, int64_t m, int64_t n, int64_t lda, char order, const CsrIn* csr,
+                        int64_t nnz, const pogs_params* p, void* stream, pogs_handle** out) {
   const double t0 = now_ms();
   pogs_handle* h = new (std::nothrow) pogs_handle();
   if (!h) return POGS_ERR_OOM;
@@ -797,10 +870,13 @@ int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order, co
       return POGS_ERR_CUDA;
     }
   }
-  h->geom = choose_geometry(m, n, h->lda, h->num_sms);
+  h->sparse = csr != nullptr;
+  h->nnz = nnz;
+  if (h->sparse) csr_geometry(h->geom, m, n, nnz, h->num_sms);
+  else h->geom = choose_geometry(m, n, h->lda, h->num_sms);
   h->nprox = (int)std::min<int64_t>(cdiv(m + n, 256), (int64_t)h->num_sms * 4);
   int rc = alloc_state(h);
-  if (rc == 0) rc = setup_impl(h, A, lda, order);
+  if (rc == 0) rc = setup_impl(h, A, lda, order, csr);
   if (rc == 0) {
     if (cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess)
@@ -822,6 +898,39 @@ int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order, co
   }
   *out = h;
   return 0;
+}
+
+
+extern "C" {
+
+int pogs_setup(const float* A, int64_t m, int64_t n, int64_t lda, char order, const pogs_params* p, void* stream,
+               pogs_handle** out) {
+  if (!out) return POGS_ERR_ARG;
+  *out = nullptr;
+  if (!A || m < 1 || n < 1 || m > (1ll << 31) - 1 || n > (1ll << 31) - 1) return POGS_ERR_ARG;
+  const bool colmajor = (order == 'C' || order == 'c');
+  if (!(colmajor || order == 'R' || order == 'r')) return POGS_ERR_ARG;
+  if ((!colmajor && lda < n) || (colmajor && lda < m)) return POGS_ERR_ARG;
+  pogs_params def;
+  pogs_default_params(&def);
+  if (!p) p = &def;
+  if (validate_params(p) != 0) return POGS_ERR_ARG;
+  return setup_common(A, m, n, lda, order, nullptr, 0, p, stream, out);
+}
+
+int pogs_setup_csr(int64_t m, int64_t n, int64_t nnz, const int* rowptr, const int* colind, const float* val,
+                   const pogs_params* p, void* stream, pogs_handle** out) {
+  if (!out) return POGS_ERR_ARG;
+  *out = nullptr;
+  if (!rowptr || m < 1 || n < 1 || m > (1ll << 31) - 2 || n > (1ll << 31) - 2 || nnz < 0 ||
+      nnz > (1ll << 31) - 1 || (nnz > 0 && (!colind || !val)))
+    return POGS_ERR_ARG;
+  pogs_params def;
+  pogs_default_params(&def);
+  if (!p) p = &def;
+  if (validate_params(p) != 0) return POGS_ERR_ARG;
+  const CsrIn in{rowptr, colind, val};
+  return setup_common(nullptr, m, n, n, 'R', &in, nnz, p, stream, out);
 }
 
 // Warm start (Section 5): the graph point (x^0 / E, A^ x^0 / E) and the scaled duals
@@ -952,6 +1061,24 @@ int pogs_get_equil(const pogs_handle* h, float* D, float* E) {
 
 int pogs_get_ahat(const pogs_handle* h, float* Ahat) {
   if (!h || !Ahat) return POGS_ERR_ARG;
+  if (h->sparse) {
+    // dense m x n copy of the CSR values
+    const size_t bytes = (size_t)(h->m * h->n) * sizeof(float);
+    void* q = nullptr;
+    TRY(pool_alloc(&q, bytes, h->stream));
+    float* tmp = static_cast<float*>(q);
+    int rc = 0;
+    if (cudaMemsetAsync(tmp, 0, bytes, h->stream) != cudaSuccess) rc = POGS_ERR_CUDA;
+    if (rc == 0) {
+      launch_csr_densify(h->csr_rp, h->csr_ci, h->csr_va, h->m, tmp, h->n, h->stream);
+      if (cudaMemcpyAsync(Ahat, tmp, bytes, is_device_ptr(Ahat) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          h->stream) != cudaSuccess)
+        rc = POGS_ERR_CUDA;
+    }
+    cudaFreeAsync(tmp, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return POGS_ERR_CUDA;
+    return rc;
+  }
   CK(cudaMemcpy2DAsync(Ahat, h->n * sizeof(float), h->A, h->lda * sizeof(float), h->n * sizeof(float), h->m,
                        is_device_ptr(Ahat) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -1001,19 +1128,24 @@ int pogs_time_kernels(pogs_handle* h, int reps, double* ms, double* bytes) {
   if (!h || reps < 1 || !h->solved || h->indirect) return POGS_ERR_ARG;   // times the direct projection
   cudaStream_t s = h->stream;
   const double m = (double)h->m, n = (double)h->n, q = (double)h->q;
-  const double A = 4.0 * m * n, tri = 2.0 * q * (q + 1.0);
+  // one pass over A^: dense m x n FP32; sparse: values + column indices + row pointers of the
+  // CSR of A^ (row dots) or of A^T (column sums)
+  const double nz = (double)h->nnz;
+  const double An = h->sparse ? 8.0 * nz + 4.0 * (m + 1) : 4.0 * m * n;
+  const double At = h->sparse ? 8.0 * nz + 4.0 * (n + 1) : 4.0 * m * n;
+  const double tri = 2.0 * q * (q + 1.0);
   double b[7];
   b[0] = 41.0 * (m + n);                                   // prox: x, x~, params in; x^, c, mu out
   if (h->tall) {
-    b[1] = A + 12 * m + 20 * n;                            // A^T [d, nu, y~] ; c, mu, E in ; r, x~ out
+    b[1] = At + 12 * m + 20 * n;                            // A^T [d, nu, y~] ; c, mu, E in ; r, x~ out
     b[2] = tri + 8 * q;
     b[3] = tri + 20 * q;                                   // z, c, x~ in ; x, x~ out
-    b[4] = A + 8 * n + 24 * m;                             // A [x, x^] ; d, y^, D, y~ in ; y, y~ out
+    b[4] = An + 8 * n + 24 * m;                            // A [x, x^] ; d, y^, D, y~ in ; y, y~ out
   } else {
-    b[1] = A + 8 * n + 16 * m;                             // A [c, x^] ; d, y^, D in ; r out
+    b[1] = An + 8 * n + 16 * m;                            // A [c, x^] ; d, y^, D in ; r out
     b[2] = tri + 8 * q;
     b[3] = tri + 24 * q;                                   // z, d, y~ in ; y, y~, w out
-    b[4] = A + 12 * m + 20 * n;                            // A^T [w, nu, y~] ; c, mu, E in ; x, x~ out
+    b[4] = At + 12 * m + 20 * n;                           // A^T [w, nu, y~] ; c, mu, E in ; x, x~ out
   }
   b[5] = 0.0;
   b[6] = b[0] + b[1] + b[2] + b[3] + b[4];

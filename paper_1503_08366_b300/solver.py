@@ -10,9 +10,13 @@ class Solver:
     """Owns one pogs_handle: factorization caching for a fixed matrix A (Section 3.5)."""
 
     def __init__(self, A, params: L.pogs_params | None = None, stream=None, order: str = "R"):
+        """A: dense (numpy / torch) or a scipy.sparse matrix (set up through the CSR entry point)."""
         self.m, self.n = A.shape
         self.params = params if params is not None else L.pogs_default_params()
-        self.handle = L.pogs_setup(A, self.params, stream=stream, order=order)
+        if hasattr(A, "tocsr"):
+            self.handle = L.pogs_setup_csr(A, None, None, A.shape, self.params, stream=stream)
+        else:
+            self.handle = L.pogs_setup(A, self.params, stream=stream, order=order)
 
     def solve(self, f, g, params: L.pogs_params | None = None, device_out: bool = False, x0=None, nu0=None):
         """Returns (info, x, y, mu, nu) -- the unscaled half-step tuple.  x0 / nu0: optional warm

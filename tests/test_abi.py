@@ -68,3 +68,23 @@ def test_setup_rejects_bad_arguments_without_device_work():
     assert P.lib.pogs_setup(buf, 0, 5, 5, b"R", None, None, ctypes.byref(h)) == -1    # empty
     p = P.pogs_default_params(alpha=2.5)
     assert P.lib.pogs_setup(buf, 10, 5, 5, b"R", ctypes.byref(p), None, ctypes.byref(h)) == -1
+
+
+def test_setup_csr_rejects_bad_arguments_without_device_work():
+    """Sizes, NULL arrays and out-of-range counts are refused before any CUDA call."""
+    import paper_1503_08366_b300 as P
+    h = ctypes.c_void_p()
+    rp = (ctypes.c_int * 3)(0, 1, 2)
+    ci = (ctypes.c_int * 2)(0, 1)
+    va = (ctypes.c_float * 2)(1.0, 2.0)
+    f = P.lib.pogs_setup_csr
+    assert f(2, 2, 2, None, ci, va, None, None, ctypes.byref(h)) == -1          # no row pointers
+    assert f(2, 2, 2, rp, None, va, None, None, ctypes.byref(h)) == -1          # nnz > 0, no indices
+    assert f(2, 2, 2, rp, ci, None, None, None, ctypes.byref(h)) == -1          # nnz > 0, no values
+    assert f(0, 2, 0, rp, ci, va, None, None, ctypes.byref(h)) == -1            # no rows
+    assert f(2, 0, 0, rp, ci, va, None, None, ctypes.byref(h)) == -1            # no columns
+    assert f(2, 2, -1, rp, ci, va, None, None, ctypes.byref(h)) == -1           # negative nnz
+    assert f(2, 2, 1 << 31, rp, ci, va, None, None, ctypes.byref(h)) == -1      # nnz beyond int32
+    p = P.pogs_default_params(alpha=2.5)
+    assert f(2, 2, 2, rp, ci, va, ctypes.byref(p), None, ctypes.byref(h)) == -1
+    assert f(2, 2, 2, rp, ci, va, None, None, None) == -1                       # no output
