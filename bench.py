@@ -689,8 +689,38 @@ def run_next(args):
         ind.append(row)
         del Ad
     out["indirect"] = ind
+    # (4) sparse A (CSR passes): 200000 x 20000 Lasso, 100 nonzeros per row (0.5%), direct and CGLS
+    prob = W.sparse_lasso(200000, 20000, seed=53_000, per_row=100)
+    M = prob.A
+    dev = tuple(torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (M.indptr.astype(np.int32), M.indices,
+                                                                             M.data))
+    sparse = dict(shape=list(M.shape), nnz=int(M.nnz), per_row=100)
+    peaks = _peaks()
+    for mode in ("DIRECT", "CGLS"):
+        prm = P.pogs_default_params(max_iter=20000, proj_mode=mode)
+        reps = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            h = P.pogs_setup_csr(*dev, M.shape, prm)
+            info = P.pogs_solve(h, prob.f, prob.g, prm)
+            torch.cuda.synchronize()
+            reps.append(time.perf_counter() - t1)
+            if mode == "DIRECT" and len(reps) == 2:
+                kt = P.pogs_time_kernels(h, reps=20)
+                passes = {}
+                for k in ("A_pass1", "A_pass2"):
+                    ms, by = kt[k]
+                    passes[k] = dict(us=ms * 1000.0, bytes=by, gbs=by / ms / 1e6, frac=by / ms / 1e6 / peaks["hbm"])
+                sparse["csr_passes"] = passes
+                sparse["iteration_us"] = kt["iteration"][0] * 1000.0
+            P.pogs_free(h)
+        sparse[mode.lower()] = dict(status=info.status, iters=info.iters, obj=info.obj, setup_ms=info.setup_ms,
+                                    solve_ms=info.solve_ms, wall_s_median=float(np.median(reps)))
+    out["sparse"] = sparse
+    del dev
     print(json.dumps(dict(workload="next", metric="warm-start path solves/s and iterations; class solves; "
-                          "indirect vs direct projection", **out)))
+                          "indirect vs direct projection; sparse A", **out)))
 
 
 def main():

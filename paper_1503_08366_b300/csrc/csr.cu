@@ -22,12 +22,40 @@ constexpr unsigned kFull = 0xffffffffu;
 // on the group's first lane (TR: the column-sum epilogue, row = column of A).  Every thread
 // makes the same number of row trips so that the shuffles always see whole warps.  Each block
 // writes its two residual partials to ep.res_part[2 * blockIdx.x + t].
-template <int NRHS, bool SQ, bool TR, int EPI, int G>
-__global__ void __launch_bounds__(256) spmv_kernel(const int* __restrict__ rp, const int* __restrict__ ci,
+// PK: the right-hand sides come interleaved in vp (float2 for two, float4 for three), one
+// gather per nonzero instead of one per right-hand side.
+template <int NRHS, int PK>
+struct Gather {
+  const float *v1, *v2, *v3;
+  const float* vp;
+  __device__ __forceinline__ void operator()(int c, float a, float& s1, float& s2, float& s3) const {
+    if constexpr (PK && NRHS == 3) {
+      const float4 x = __ldg(reinterpret_cast<const float4*>(vp) + c);
+      s1 = fmaf(a, x.x, s1);
+      s2 = fmaf(a, x.y, s2);
+      s3 = fmaf(a, x.z, s3);
+    } else if constexpr (PK && NRHS == 2) {
+      const float2 x = __ldg(reinterpret_cast<const float2*>(vp) + c);
+      s1 = fmaf(a, x.x, s1);
+      s2 = fmaf(a, x.y, s2);
+    } else {
+      s1 = fmaf(a, __ldg(v1 + c), s1);
+      if constexpr (NRHS >= 2) s2 = fmaf(a, __ldg(v2 + c), s2);
+      if constexpr (NRHS == 3) s3 = fmaf(a, __ldg(v3 + c), s3);
+    }
+  }
+};
+
+// Eight resident 256-thread blocks per SM (at most 32 registers); the grid is one such wave.
+constexpr int kSpmvBlocksPerSm = 8;
+
+template <int NRHS, bool SQ, bool TR, int EPI, int G, int PK>
+__global__ void __launch_bounds__(256, kSpmvBlocksPerSm) spmv_kernel(const int* __restrict__ rp, const int* __restrict__ ci,
                                                    const float* __restrict__ va, int nrows,
                                                    const float* __restrict__ v1, const float* __restrict__ v2,
-                                                   const float* __restrict__ v3, EpiArgs ep,
-                                                   const DevState* __restrict__ guard) {
+                                                   const float* __restrict__ v3, const float* __restrict__ vp,
+                                                   EpiArgs ep, const DevState* __restrict__ guard) {
+  const Gather<NRHS, PK> gather{v1, v2, v3, vp};
   __shared__ double sh[2 * 8];
   if (guard && guard->done) return;
   if (ep.cg_done && *ep.cg_done) return;
@@ -41,14 +69,22 @@ __global__ void __launch_bounds__(256) spmv_kernel(const int* __restrict__ rp, c
     float s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
     if (row < nrows) {
       const int k1 = __ldg(rp + row + 1);
-#pragma unroll 4
-      for (int k = __ldg(rp + row) + lg; k < k1; k += G) {
-        float a = __ldg(va + k);
-        if (SQ) a *= a;
-        const int c = __ldg(ci + k);
-        s1 = fmaf(a, __ldg(v1 + c), s1);
-        if constexpr (NRHS >= 2) s2 = fmaf(a, __ldg(v2 + c), s2);
-        if constexpr (NRHS == 3) s3 = fmaf(a, __ldg(v3 + c), s3);
+      int k = __ldg(rp + row) + lg;
+      // four entries per lane per step: their values and indices load together, then the gathers
+      for (; k + 3 * G < k1; k += 4 * G) {
+        float a[4];
+        int c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a[u] = __ldg(va + k + u * G);
+          c[u] = __ldg(ci + k + u * G);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) gather(c[u], SQ ? a[u] * a[u] : a[u], s1, s2, s3);
+      }
+      for (; k < k1; k += G) {
+        const float av = __ldg(va + k);
+        gather(__ldg(ci + k), SQ ? av * av : av, s1, s2, s3);
       }
     }
 #pragma unroll
@@ -213,6 +249,19 @@ __global__ void gather_kernel(const float* __restrict__ src, const int* __restri
     dst[i] = src[perm[i]];
 }
 
+// Interleave two or three right-hand sides for the packed gathers: vp[i] = (v1, v2[, v3, 0]).
+template <int NRHS>
+__global__ void pack_rhs_kernel(const float* __restrict__ v1, const float* __restrict__ v2,
+                                const float* __restrict__ v3, int k, float* __restrict__ vp,
+                                const DevState* __restrict__ guard, const int* __restrict__ cg_done) {
+  if (guard && guard->done) return;
+  if (cg_done && *cg_done) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+    if constexpr (NRHS == 3) reinterpret_cast<float4*>(vp)[i] = make_float4(v1[i], v2[i], v3[i], 0.0f);
+    else reinterpret_cast<float2*>(vp)[i] = make_float2(v1[i], v2[i]);
+  }
+}
+
 // Dense copy of the CSR matrix into a zeroed m x lda row-major buffer.
 __global__ void csr_densify_kernel(const int* __restrict__ rp, const int* __restrict__ ci,
                                    const float* __restrict__ va, int m, float* __restrict__ A, int64_t lda) {
@@ -223,17 +272,18 @@ __global__ void csr_densify_kernel(const int* __restrict__ rp, const int* __rest
     for (int k = rp[r] + lane; k < rp[r + 1]; k += 32) A[r * lda + ci[k]] = va[k];
 }
 
-int grid_rows(int64_t rows, int per_block, int num_sms) {
+int grid_rows(int64_t rows, int per_block, int num_sms, int per_sm = 8) {
   const int64_t g = (rows + per_block - 1) / per_block;
-  const int64_t cap = (int64_t)num_sms * 8;
+  const int64_t cap = (int64_t)num_sms * per_sm;
   return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
-template <int NRHS, bool SQ, bool TR, int G>
+template <int NRHS, bool SQ, bool TR, int G, int PK>
 void spmv_dispatch(int epi, const int* rp, const int* ci, const float* va, int nrows, const float* v1,
-                   const float* v2, const float* v3, int grid, const EpiArgs& ep, const DevState* guard,
-                   cudaStream_t s) {
-#define POGS_S(E) spmv_kernel<NRHS, SQ, TR, E, G><<<grid, 256, 0, s>>>(rp, ci, va, nrows, v1, v2, v3, ep, guard)
+                   const float* v2, const float* v3, const float* vp, int grid, const EpiArgs& ep,
+                   const DevState* guard, cudaStream_t s) {
+#define POGS_S(E) \
+  spmv_kernel<NRHS, SQ, TR, E, G, PK><<<grid, 256, 0, s>>>(rp, ci, va, nrows, v1, v2, v3, vp, ep, guard)
   if constexpr (TR) {
     switch (epi) {
       case EPT_RAW: POGS_S(EPT_RAW); break;
@@ -262,41 +312,45 @@ void spmv_dispatch(int epi, const int* rp, const int* ci, const float* va, int n
 #undef POGS_S
 }
 
-template <int NRHS, bool SQ, bool TR>
+template <int NRHS, bool SQ, bool TR, int PK>
 void spmv_lanes(int lanes, int epi, const int* rp, const int* ci, const float* va, int nrows, const float* v1,
-                const float* v2, const float* v3, int grid, const EpiArgs& ep, const DevState* guard,
-                cudaStream_t s) {
+                const float* v2, const float* v3, const float* vp, int grid, const EpiArgs& ep,
+                const DevState* guard, cudaStream_t s) {
   switch (lanes) {
-    case 4: spmv_dispatch<NRHS, SQ, TR, 4>(epi, rp, ci, va, nrows, v1, v2, v3, grid, ep, guard, s); break;
-    case 8: spmv_dispatch<NRHS, SQ, TR, 8>(epi, rp, ci, va, nrows, v1, v2, v3, grid, ep, guard, s); break;
-    case 16: spmv_dispatch<NRHS, SQ, TR, 16>(epi, rp, ci, va, nrows, v1, v2, v3, grid, ep, guard, s); break;
-    default: spmv_dispatch<NRHS, SQ, TR, 32>(epi, rp, ci, va, nrows, v1, v2, v3, grid, ep, guard, s); break;
+    case 4: spmv_dispatch<NRHS, SQ, TR, 4, PK>(epi, rp, ci, va, nrows, v1, v2, v3, vp, grid, ep, guard, s); break;
+    case 8: spmv_dispatch<NRHS, SQ, TR, 8, PK>(epi, rp, ci, va, nrows, v1, v2, v3, vp, grid, ep, guard, s); break;
+    case 16: spmv_dispatch<NRHS, SQ, TR, 16, PK>(epi, rp, ci, va, nrows, v1, v2, v3, vp, grid, ep, guard, s); break;
+    default: spmv_dispatch<NRHS, SQ, TR, 32, PK>(epi, rp, ci, va, nrows, v1, v2, v3, vp, grid, ep, guard, s); break;
   }
 }
 
 template <bool TR>
-void spmv_rhs(int nrhs, bool sq, int lanes, int epi, const int* rp, const int* ci, const float* va, int nrows,
-              const float* v1, const float* v2, const float* v3, int grid, const EpiArgs& ep,
-              const DevState* guard, cudaStream_t s) {
-  if (nrhs == 3) spmv_lanes<3, false, TR>(lanes, epi, rp, ci, va, nrows, v1, v2, v3, grid, ep, guard, s);
-  else if (nrhs == 2) spmv_lanes<2, false, TR>(lanes, epi, rp, ci, va, nrows, v1, v2, v3, grid, ep, guard, s);
-  else if (sq) spmv_lanes<1, true, TR>(lanes, epi, rp, ci, va, nrows, v1, v2, v3, grid, ep, guard, s);
-  else spmv_lanes<1, false, TR>(lanes, epi, rp, ci, va, nrows, v1, v2, v3, grid, ep, guard, s);
+void spmv_rhs(int nrhs, bool sq, bool pk, int lanes, int epi, const int* rp, const int* ci, const float* va,
+              int nrows, const float* v1, const float* v2, const float* v3, const float* vp, int grid,
+              const EpiArgs& ep, const DevState* guard, cudaStream_t s) {
+  if (nrhs == 3 && pk) spmv_lanes<3, false, TR, 1>(lanes, epi, rp, ci, va, nrows, v1, v2, v3, vp, grid, ep, guard, s);
+  else if (nrhs == 3) spmv_lanes<3, false, TR, 0>(lanes, epi, rp, ci, va, nrows, v1, v2, v3, vp, grid, ep, guard, s);
+  else if (nrhs == 2 && pk) spmv_lanes<2, false, TR, 1>(lanes, epi, rp, ci, va, nrows, v1, v2, v3, vp, grid, ep, guard, s);
+  else if (nrhs == 2) spmv_lanes<2, false, TR, 0>(lanes, epi, rp, ci, va, nrows, v1, v2, v3, vp, grid, ep, guard, s);
+  else if (sq) spmv_lanes<1, true, TR, 0>(lanes, epi, rp, ci, va, nrows, v1, v2, v3, vp, grid, ep, guard, s);
+  else spmv_lanes<1, false, TR, 0>(lanes, epi, rp, ci, va, nrows, v1, v2, v3, vp, grid, ep, guard, s);
 }
 
 }  // namespace
 
+// Lanes per row: 8 lanes already read whole 32-byte sectors of the values and indices, and
+// fewer lanes per row give each lane more entries to keep in flight; long rows get more lanes.
 int csr_lanes(int64_t rows, int64_t nnz) {
   const double avg = rows > 0 ? (double)nnz / (double)rows : 0.0;
-  return avg >= 64 ? 32 : (avg >= 24 ? 16 : (avg >= 10 ? 8 : 4));
+  return avg >= 512 ? 32 : (avg >= 160 ? 16 : (avg >= 6 ? 8 : 4));
 }
 
 void csr_geometry(GemvGeom& g, int64_t m, int64_t n, int64_t nnz, int num_sms) {
   g.sparse = 1;
   g.sp_lanes_n = csr_lanes(m, nnz);
   g.sp_lanes_t = csr_lanes(n, nnz);
-  g.n_nrowblk = grid_rows(m, 256 / g.sp_lanes_n, num_sms);
-  g.t_ncolblk = grid_rows(n, 256 / g.sp_lanes_t, num_sms);
+  g.n_nrowblk = grid_rows(m, 256 / g.sp_lanes_n, num_sms, kSpmvBlocksPerSm);
+  g.t_ncolblk = grid_rows(n, 256 / g.sp_lanes_t, num_sms, kSpmvBlocksPerSm);
   // the dense kernels' partial buffers are not used
   g.t_cols_per_blk = 1024;
   g.t_nsplit = 1;
@@ -306,13 +360,34 @@ void csr_geometry(GemvGeom& g, int64_t m, int64_t n, int64_t nnz, int num_sms) {
   g.n_ncolsplit = 1;
 }
 
+// The gathered vectors have m entries (column sums) or n (row dots); from kPackMin entries on
+// they no longer stay in L1 and two or three right-hand sides are interleaved first.
+constexpr int kPackMin = 8192;
+
+bool csr_packs(const GemvGeom& g, bool trans, int nrhs, int m, int n) {
+  return g.sparse && g.pack && nrhs >= 2 && (trans ? m : n) >= kPackMin;
+}
+
+int csr_pack_launches(const GemvGeom& g, int m, int n) {
+  return (csr_packs(g, true, 3, m, n) ? 1 : 0) + (csr_packs(g, false, 2, m, n) ? 1 : 0);
+}
+
 void launch_spmv(bool trans, int nrhs, bool sq, int epi, const GemvGeom& g, int m, int n, const float* v1,
                  const float* v2, const float* v3, const EpiArgs& ep, const DevState* guard, cudaStream_t s) {
+  const bool pk = csr_packs(g, trans, nrhs, m, n);
+  if (pk) {
+    const int k = trans ? m : n;
+    count_launch();
+    if (nrhs == 3) pack_rhs_kernel<3><<<grid_rows(k, 256, 148), 256, 0, s>>>(v1, v2, v3, k, g.pack, guard, ep.cg_done);
+    else pack_rhs_kernel<2><<<grid_rows(k, 256, 148), 256, 0, s>>>(v1, v2, v3, k, g.pack, guard, ep.cg_done);
+  }
   count_launch();
   if (trans)
-    spmv_rhs<true>(nrhs, sq, g.sp_lanes_t, epi, g.rp_t, g.ci_t, g.va_t, n, v1, v2, v3, g.t_ncolblk, ep, guard, s);
+    spmv_rhs<true>(nrhs, sq, pk, g.sp_lanes_t, epi, g.rp_t, g.ci_t, g.va_t, n, v1, v2, v3, g.pack, g.t_ncolblk, ep,
+                   guard, s);
   else
-    spmv_rhs<false>(nrhs, sq, g.sp_lanes_n, epi, g.rp_n, g.ci_n, g.va_n, m, v1, v2, v3, g.n_nrowblk, ep, guard, s);
+    spmv_rhs<false>(nrhs, sq, pk, g.sp_lanes_n, epi, g.rp_n, g.ci_n, g.va_n, m, v1, v2, v3, g.pack, g.n_nrowblk, ep,
+                    guard, s);
 }
 
 void launch_csr_check(const int* rp, const int* ci, const float* va, int64_t m, int64_t n, int64_t nnz, int* err,

@@ -70,6 +70,7 @@ struct GemvGeom {
   int sparse, sp_lanes_n, sp_lanes_t;
   const int *rp_n, *ci_n, *rp_t, *ci_t;
   const float *va_n, *va_t;
+  float* pack;   // max(m, n) x 4 floats: interleaved right-hand sides of the long gathers
 };
 GemvGeom choose_geometry(int64_t m, int64_t n, int64_t lda, int num_sms);
 
@@ -78,6 +79,8 @@ void csr_geometry(GemvGeom& g, int64_t m, int64_t n, int64_t nnz, int num_sms);
 // One pass over sparse A^ (trans: column sums via the CSR of A^T), with the dense pass's epilogue.
 void launch_spmv(bool trans, int nrhs, bool sq, int epi, const GemvGeom& g, int m, int n, const float* v1,
                  const float* v2, const float* v3, const EpiArgs& ep, const DevState* guard, cudaStream_t s);
+// Extra launches (right-hand-side interleaving) of one iteration's two main passes.
+int csr_pack_launches(const GemvGeom& g, int m, int n);
 // Flags POGS_ERR_ARG (structure) or POGS_ERR_NONFINITE (values) in *err.
 void launch_csr_check(const int* rp, const int* ci, const float* va, int64_t m, int64_t n, int64_t nnz, int* err,
                       cudaStream_t s);

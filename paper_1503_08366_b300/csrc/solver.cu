@@ -394,9 +394,11 @@ void enqueue_iteration(pogs_handle* h, int refine, int cg_steps, cudaStream_t s,
 }
 
 int kernels_per_iteration(const pogs_handle* h, int refine, int cg_steps) {
+  // sparse A: the two main passes may interleave their right-hand sides first
+  const int pk = csr_pack_launches(h->geom, (int)h->m, (int)h->n);
   if (cg_steps > 0 || h->indirect)   // prox, 2 passes, CGLS init (3), 4 per step, finish, check
-    return 8 + 4 * cg_steps;
-  return 6 + (refine ? 4 : 0);   // prox, 2 A passes, 2 triangle products, check (+ refinement)
+    return 8 + 4 * cg_steps + pk;
+  return 6 + (refine ? 4 : 0) + pk;   // prox, 2 A passes, 2 triangle products, check (+ refinement)
 }
 
 int build_graph(pogs_handle* h, int refine, int mode, int cg_steps) {
@@ -532,6 +534,7 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order, const Cs
     launch_csr_transpose(h->csr_rp, h->csr_ci, h->csr_va, m, n, nnz, nch, rowidx, cnt, tot, h->csc_rp, h->csc_ci,
                          h->csc_va, h->csc_perm, s);
     GemvGeom& g = h->geom;
+    TRY(dalloc(h, &g.pack, (size_t)std::max(h->mv, h->nv) * 4));
     g.rp_n = h->csr_rp; g.ci_n = h->csr_ci; g.va_n = h->csr_va;
     g.rp_t = h->csc_rp; g.ci_t = h->csc_ci; g.va_t = h->csc_va;
     CK(cudaGetLastError());

@@ -39,15 +39,11 @@ def _csr(A):
 
 
 def _sparse(cls, shape, seed, frac):
-    """The class's generator, with its A masked to about `frac` nonzeros (seeded) when the
-    generator has no sparsity parameter of its own."""
-    gen = W.CLASSES[cls]
-    try:
-        return gen(*shape, seed=seed, nnz_frac=frac)
-    except TypeError:
-        prob = gen(*shape, seed=seed)
-        keep = np.random.default_rng(seed + 1).random(prob.A.shape) < frac
-        return W.Problem(prob.name, (prob.A * keep).astype(np.float32), prob.f, prob.g, {})
+    """The class's generator with its A masked to about `frac` nonzeros (seeded); f and g as
+    generated (any f, g pose a valid problem on the masked A)."""
+    prob = W.CLASSES[cls](*shape, seed=seed)
+    keep = np.random.default_rng(seed + 1).random(prob.A.shape) < frac
+    return W.Problem(prob.name, (prob.A * keep).astype(np.float32), prob.f, prob.g, {})
 
 
 def _rel(a, b):
@@ -62,8 +58,9 @@ def _tight(prob):
 
 @pytest.mark.parametrize("shape,frac", [((700, 300), 0.05), ((300, 900), 0.02), ((1200, 1100), 0.01)])
 def test_sparse_equilibration_matches_oracle_and_dense(P, shape, frac):
-    prob = W.lasso(*shape, seed=71, nnz_frac=frac)
+    prob = _sparse("lasso", shape, 71, frac)
     A = prob.A.astype(np.float32)
+    assert (A != 0).mean() < 2 * frac
     prm = P.pogs_default_params()
     with P.Solver(_csr(A), prm) as s:
         Ahat_s = s.ahat()
@@ -104,6 +101,20 @@ def test_sparse_solve_matches_oracle(P, mode, cls, shape, frac):
     assert abs(info.obj - ref.obj) <= 1e-3 * max(1.0, abs(ref.obj)), (info.obj, ref.obj)
     Ad = prob.A.astype(np.float64)
     assert np.linalg.norm(Ad @ x - y) <= 1e-2 * max(1.0, np.linalg.norm(y))
+
+
+@pytest.mark.parametrize("mode", ["DIRECT", "CGLS"])
+@pytest.mark.parametrize("shape,per_row", [((3000, 800), 20), ((600, 2500), 40)])
+def test_sparse_lasso_generator_solve(P, mode, shape, per_row):
+    """The CSR workload generator (row-wise random pattern) end to end, tall and fat."""
+    prob = W.sparse_lasso(*shape, seed=77, per_row=per_row)
+    prm = P.pogs_default_params(max_iter=5000, proj_mode=mode)
+    with P.Solver(prob.A, prm) as s:
+        info, x, y, mu, nu = s.solve(prob.f, prob.g)
+    assert info.status == 0, info.as_dict()
+    dense = W.Problem(prob.name, prob.A.toarray(), prob.f, prob.g, {})
+    ref = _tight(dense)
+    assert abs(info.obj - ref.obj) <= 1e-3 * max(1.0, abs(ref.obj)), (info.obj, ref.obj)
 
 
 def test_empty_rows_columns_and_a_full_row(P):
@@ -155,7 +166,7 @@ def test_malformed_csr_is_rejected(P):
 
 def test_host_and_device_arrays_agree_and_runs_repeat(P):
     import torch
-    prob = W.logistic(500, 400, seed=75, nnz_frac=0.05)
+    prob = _sparse("logistic", (500, 400), 75, 0.05)
     M = _csr(prob.A)
     prm = P.pogs_default_params(max_iter=5000)
     outs = []

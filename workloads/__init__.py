@@ -252,6 +252,32 @@ def portfolio(n: int, k: int, seed: int, gamma: float = 1.0) -> Problem:
     return Problem("portfolio", A, f, g, dict(seed=seed, gamma=gamma))
 
 
+def sparse_lasso(m: int, n: int, seed: int, per_row: int = 100, nnz_frac=0.1, noise_std=0.01,
+                 lam_frac=0.1) -> Problem:
+    """Lasso (Appendix A.4) on a sparse A, returned in CSR form (scipy.sparse, float32, sorted
+    unique column indices): each row has `per_row` column positions drawn uniformly (repeats
+    dropped), values N(0, 1/per_row) so that rows have the dense generator's expected norm;
+    x_true has nnz_frac nonzeros ~ N(0, 1); b = A x_true + N(0, noise_std^2);
+    lambda = lam_frac * ||A^T b||_inf.  Built row-block by row-block without a dense copy."""
+    import scipy.sparse as sp
+    rng = _rng(seed)
+    cols = np.sort(rng.integers(0, n, size=(m, per_row), dtype=np.int64), axis=1)
+    keep = np.ones_like(cols, dtype=bool)
+    keep[:, 1:] = cols[:, 1:] != cols[:, :-1]
+    vals = _normal32(rng, (m, per_row), std=1.0 / math.sqrt(per_row))
+    counts = keep.sum(axis=1)
+    indptr = np.zeros(m + 1, np.int64)
+    np.cumsum(counts, out=indptr[1:])
+    A = sp.csr_matrix((vals[keep], cols[keep].astype(np.int32), indptr), shape=(m, n), dtype=np.float32)
+    x_true = _sparse_vector(rng, n, nnz_frac)
+    A64 = A.astype(np.float64)
+    b = (A64 @ x_true + rng.standard_normal(m) * noise_std).astype(np.float32)
+    lam = float(lam_frac * np.max(np.abs(A64.T @ b.astype(np.float64))))
+    f = FnParams.make(m, H["SQUARE"], b=b)
+    g = FnParams.make(n, H["ABS"], c=lam)
+    return Problem("sparse_lasso", A, f, g, dict(lam=lam, seed=seed, nnz=int(A.nnz)))
+
+
 CLASSES = dict(lasso=lasso, logistic=logistic, huber=huber, svm=svm, nnls=nnls, lp=lp,
                basis_pursuit=basis_pursuit, entropy=entropy, portfolio=portfolio)
 
