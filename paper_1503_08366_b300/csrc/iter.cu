@@ -100,7 +100,7 @@ void launch_prox_step(int n, int m, const float* x, float* xt, float* xh, float*
 // order and applies the epilogue.
 // ------------------------------------------------------------------------------------------
 template <int NRHS, bool SQ, int EPI>
-__global__ void __launch_bounds__(256) gemv_t_kernel(const float* __restrict__ A, int64_t lda, int m, int n,
+__global__ void __launch_bounds__(256, 5) gemv_t_kernel(const float* __restrict__ A, int64_t lda, int m, int n,
                                                      const float* __restrict__ v1,
                                                      const float* __restrict__ v2,
                                                      const float* __restrict__ v3, int rows,
@@ -171,11 +171,31 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(const float* __restrict__ A
     float s[NRHS][4];
 #pragma unroll
     for (int r = 0; r < NRHS; ++r) s[r][0] = s[r][1] = s[r][2] = s[r][3] = 0.0f;
-    for (int sp = 0; sp < (int)gridDim.y; ++sp) {
+    // SPU splits' partials are loaded before they are added (in split order), so that the slab's
+    // final reduction waits for one L2 round trip per SPU splits, not per split
+    constexpr int SPU = NRHS == 3 ? 2 : 3;
+    const int nsp = (int)gridDim.y;
+    const float4* pp = reinterpret_cast<const float4*>(part + c0);
+    const int64_t rs = lda >> 2, ss = NRHS * rs;   // float4 strides: right-hand side, split
+    int sp = 0;
+    for (; sp + SPU <= nsp; sp += SPU) {
+      float4 p[SPU][NRHS];
+#pragma unroll
+      for (int u = 0; u < SPU; ++u)
+#pragma unroll
+        for (int r = 0; r < NRHS; ++r) p[u][r] = __ldcg(pp + (sp + u) * ss + r * rs);
+#pragma unroll
+      for (int u = 0; u < SPU; ++u)
+#pragma unroll
+        for (int r = 0; r < NRHS; ++r) {
+          s[r][0] += p[u][r].x; s[r][1] += p[u][r].y; s[r][2] += p[u][r].z; s[r][3] += p[u][r].w;
+        }
+    }
+    for (; sp < nsp; ++sp) {
 #pragma unroll
       for (int r = 0; r < NRHS; ++r) {
-        const float4 p = __ldcg(reinterpret_cast<const float4*>(part + ((int64_t)sp * NRHS + r) * lda + c0));
-        s[r][0] += p.x; s[r][1] += p.y; s[r][2] += p.z; s[r][3] += p.w;
+        const float4 q = __ldcg(pp + sp * ss + r * rs);
+        s[r][0] += q.x; s[r][1] += q.y; s[r][2] += q.z; s[r][3] += q.w;
       }
     }
 #pragma unroll
@@ -266,9 +286,23 @@ __global__ void __launch_bounds__(256) gemv_n_kernel(const float* __restrict__ A
   Df res[2] = {};
   for (int row = r0 + tid; row < r1; row += blockDim.x) {
     float u1 = 0.0f, u2 = 0.0f;
-    for (int sp = 0; sp < (int)gridDim.y; ++sp) {
-      u1 += __ldcg(part + ((int64_t)sp * NRHS) * m + row);
-      if constexpr (NRHS == 2) u2 += __ldcg(part + ((int64_t)sp * NRHS + 1) * m + row);
+    // four chunks' partials per round trip, added in chunk order
+    const int nsp = (int)gridDim.y;
+    for (int sp0 = 0; sp0 < nsp; sp0 += 4) {
+      float p1[4], p2[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool ok = sp0 + u < nsp;
+        p1[u] = ok ? __ldcg(part + ((int64_t)(sp0 + u) * NRHS) * m + row) : 0.0f;
+        if constexpr (NRHS == 2) p2[u] = ok ? __ldcg(part + ((int64_t)(sp0 + u) * NRHS + 1) * m + row) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (sp0 + u < nsp) {
+          u1 += p1[u];
+          if constexpr (NRHS == 2) u2 += p2[u];
+        }
+      }
     }
     epi_n<EPI>(ep, row, u1, u2, res);
   }
