@@ -431,18 +431,34 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(const float* __restrict_
 constexpr size_t kDiagSmem = (size_t)(2 * kDB * kDS + kDB) * sizeof(float);
 
 // Recursive 2 x 2 block inverse on the FP32 factor (leaves already in M).
+// Tensor-core scratch of the inverse (nullptr: SIMT GEMMs only).
+struct TcScratch {
+  void* p;
+  size_t bytes;
+  int* err;
+};
+constexpr int64_t kTcInvMin = 512;   // blocks from this size on use the tensor cores
+
 void inv_rec(const float* L, int64_t ldl, float* M, int64_t ldm, int64_t r0, int64_t nsz, float* work,
-             cudaStream_t s) {
+             const TcScratch& tc, cudaStream_t s) {
   if (nsz <= kTile) return;
   const int64_t nblk = cdiv(nsz, kTile);
   const int64_t n1 = (nblk / 2) * kTile, n2 = nsz - n1;
-  inv_rec(L, ldl, M, ldm, r0, n1, work, s);
-  inv_rec(L, ldl, M, ldm, r0 + n1, n2, work, s);
-  // T = L21 M11 (M11 lower triangular), then M21 = -M22 T (M22 lower triangular)
-  sgemm_launch<false, OUT_F32, 1>(n2, n1, n1, L + (r0 + n1) * ldl + r0, ldl, M + r0 * ldm + r0, ldm, 1.0f, work,
-                                  nullptr, n1, false, 1, s);
-  sgemm_launch<false, OUT_F32, 1>(n2, n1, n2, M + (r0 + n1) * ldm + r0 + n1, ldm, work, n1, -1.0f,
-                                  M + (r0 + n1) * ldm + r0, nullptr, ldm, false, 2, s);
+  inv_rec(L, ldl, M, ldm, r0, n1, work, tc, s);
+  inv_rec(L, ldl, M, ldm, r0 + n1, n2, work, tc, s);
+  // T = L21 M11 (M11 lower triangular), then M21 = -M22 T (M22 lower triangular).  The blocks
+  // above the diagonal of M11 and M22 hold zeros, so the tensor-core products over the full K
+  // equal the SIMT kernel's triangular ones.
+  const float* L21 = L + (r0 + n1) * ldl + r0;
+  const float* M11 = M + r0 * ldm + r0;
+  const float* M22 = M + (r0 + n1) * ldm + r0 + n1;
+  float* M21 = M + (r0 + n1) * ldm + r0;
+  if (tc.p && std::min(n1, n2) >= kTcInvMin &&
+      tc_gemm_nn_tf32x3(n2, n1, n1, L21, ldl, M11, ldm, 1.0f, work, n1, tc.p, tc.bytes, nullptr, tc.err, s) == 0 &&
+      tc_gemm_nn_tf32x3(n2, n1, n2, M22, ldm, work, n1, -1.0f, M21, ldm, tc.p, tc.bytes, nullptr, tc.err, s) == 0)
+    return;
+  sgemm_launch<false, OUT_F32, 1>(n2, n1, n1, L21, ldl, M11, ldm, 1.0f, work, nullptr, n1, false, 1, s);
+  sgemm_launch<false, OUT_F32, 1>(n2, n1, n2, M22, ldm, work, n1, -1.0f, M21, nullptr, ldm, false, 2, s);
 }
 
 // I + G as the double-float pair (G in place becomes hi; lo receives the rounding error of the
@@ -546,8 +562,23 @@ int chol_mixed(float* G, float* Hlo, int64_t ldh, int64_t q, float* Lf, int64_t 
   return rc;
 }
 
-void tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ldm, float* work, cudaStream_t s) {
-  inv_rec(L, ldl, M, ldm, 0, q, work, s);
+int tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ldm, float* work, bool tensor,
+                    int* err, cudaStream_t s) {
+  TcScratch tc{nullptr, 0, err};
+  if (tensor && q > kTile) {
+    // the top level's two products are the largest; every lower level fits in their scratch
+    const int64_t n1 = (cdiv(q, kTile) / 2) * kTile, n2 = q - n1;
+    size_t need1 = 0, need2 = 0;
+    if (std::min(n1, n2) >= kTcInvMin &&
+        tc_gemm_nn_tf32x3(n2, n1, n1, L, ldl, M, ldm, 1.0f, work, n1, nullptr, 0, &need1, err, s) == 0 &&
+        tc_gemm_nn_tf32x3(n2, n1, n2, M, ldm, work, n1, -1.0f, M, ldm, nullptr, 0, &need2, err, s) == 0) {
+      tc.bytes = std::max(need1, need2);
+      if (pool_alloc(&tc.p, tc.bytes, s) != 0) tc.p = nullptr;
+    }
+  }
+  inv_rec(L, ldl, M, ldm, 0, q, work, tc, s);
+  if (tc.p) cudaFreeAsync(tc.p, s);
+  return cudaGetLastError() == cudaSuccess ? 0 : POGS_ERR_CUDA;
 }
 
 }  // namespace pogs

@@ -7,6 +7,8 @@
 //   BF16:    X_hi = bf16(X)                                  one MMA per K step
 //   BF16x3:  X_hi = bf16(X), X_lo = bf16(X - X_hi)           hi.hi + hi.lo + lo.hi per K step
 //   TF32:    X rounded to TF32 (kept in 32-bit words)        one kind::tf32 MMA per K step
+//   TF32x3:  X_hi = tf32(X), X_lo = tf32(X - X_hi)           hi.hi + hi.lo + lo.hi per K step
+//            (about 21 significant bits per product; the triangular inverse's GEMMs)
 // FP32 accumulation in tensor memory, drained in K chunks.  One CTA computes one 128 x 128
 // output tile: one thread streams X tiles with TMA through a multi-stage shared-memory ring
 // (128-byte swizzle), one thread issues tcgen05.mma, four warps read the accumulator back with
@@ -27,27 +29,30 @@ namespace {
 constexpr int kTileRows = 128;   // M = N = 128 per CTA
 constexpr int kTileBytes = kTileRows * 128;   // one operand tile: 128 rows x 128 bytes
 
-enum TcMode : int { TC_BF16 = 0, TC_BF16X3 = 1, TC_TF32 = 2 };
+enum TcMode : int { TC_BF16 = 0, TC_BF16X3 = 1, TC_TF32 = 2, TC_TF32X3 = 3 };
 
 template <int MODE>
 struct TcCfg {
-  static constexpr int kOps = MODE == TC_BF16X3 ? 4 : 2;            // operand tiles per stage
-  static constexpr int kStages = MODE == TC_BF16X3 ? 3 : 6;
+  static constexpr bool kSplit = MODE == TC_BF16X3 || MODE == TC_TF32X3;   // hi/lo operand pairs
+  static constexpr bool kTf32 = MODE == TC_TF32 || MODE == TC_TF32X3;
+  static constexpr int kOps = kSplit ? 4 : 2;                        // operand tiles per stage
+  static constexpr int kStages = kSplit ? 3 : 6;
   static constexpr int kStageBytes = kOps * kTileBytes;
-  static constexpr int kElemsPerBox = MODE == TC_TF32 ? 32 : 64;     // K elements per 128-byte row
+  static constexpr int kElemsPerBox = kTf32 ? 32 : 64;               // K elements per 128-byte row
   static constexpr int kMmaPerBox = 4;                              // 32 bytes of K per MMA
   static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024 + 256;
 };
 
 struct TcArgs {
   int nkb;                 // K boxes
-  int tiles;               // tiles along M (and N)
+  int tiles;               // tiles along M (and N, lower_only)
+  int tiles_n;             // tiles along N (full grid)
   int lower_only;          // enumerate the lower triangle of tiles
   int64_t M, N;            // valid output extent
   float* C;                // FP32 output (epi 0)
   double* C64;             // FP64 output (epi 1: C64 += alpha * acc, lower triangle)
   int64_t ldc;
-  double alpha;
+  double alpha;            // epi 0: C = alpha * acc; epi 1: C64 += alpha * acc
   int epi;
   int* err;
 };
@@ -85,8 +90,8 @@ __global__ void __launch_bounds__(192, 1)
     ti = i;
     tj = b - i * (i + 1) / 2;
   } else {
-    ti = blockIdx.x / a.tiles;
-    tj = blockIdx.x % a.tiles;
+    ti = blockIdx.x / a.tiles_n;
+    tj = blockIdx.x % a.tiles_n;
   }
   const int nchunks = (a.nkb + kChunkBoxes - 1) / kChunkBoxes;
 
@@ -116,7 +121,7 @@ __global__ void __launch_bounds__(192, 1)
       // ---- TMA producer ---------------------------------------------------------------------
       tc::prefetch_tmap(&mxh);
       tc::prefetch_tmap(&myh);
-      if (MODE == TC_BF16X3) {
+      if (Cfg::kSplit) {
         tc::prefetch_tmap(&mxl);
         tc::prefetch_tmap(&myl);
       }
@@ -132,7 +137,7 @@ __global__ void __launch_bounds__(192, 1)
         const int x = kb * Cfg::kElemsPerBox;
         tc::tma_load_2d(st, &mxh, x, ti * kTileRows, full + s);
         tc::tma_load_2d(st + kTileBytes, &myh, x, tj * kTileRows, full + s);
-        if (MODE == TC_BF16X3) {
+        if (Cfg::kSplit) {
           tc::tma_load_2d(st + 2 * kTileBytes, &mxl, x, ti * kTileRows, full + s);
           tc::tma_load_2d(st + 3 * kTileBytes, &myl, x, tj * kTileRows, full + s);
         }
@@ -167,6 +172,11 @@ __global__ void __launch_bounds__(192, 1)
             const uint64_t adv = 2ull * k;   // +32 bytes along K
             if (MODE == TC_TF32) {
               tc::mma_tf32(d, ah + adv, bh + adv, tc::kIdescTF32, acc);
+            } else if (MODE == TC_TF32X3) {
+              const uint64_t al = tc::desc_sw128(st + 2 * kTileBytes), bl = tc::desc_sw128(st + 3 * kTileBytes);
+              tc::mma_tf32(d, ah + adv, bh + adv, tc::kIdescTF32, acc);
+              tc::mma_tf32(d, ah + adv, bl + adv, tc::kIdescTF32, 1u);
+              tc::mma_tf32(d, al + adv, bh + adv, tc::kIdescTF32, 1u);
             } else {
               tc::mma_bf16(d, ah + adv, bh + adv, tc::kIdescBF16, acc);
               if (MODE == TC_BF16X3) {
@@ -217,6 +227,11 @@ __global__ void __launch_bounds__(192, 1)
     } else if (row < a.M) {
       const int64_t col0 = (int64_t)tj * kTileRows;
       if (a.epi == 0) {
+        const float al = (float)a.alpha;
+        if (al != 1.0f) {
+#pragma unroll
+          for (int i = 0; i < 128; ++i) acc[i] *= al;
+        }
         float* out = a.C + row * a.ldc + col0;
         if (col0 + 128 <= a.N && ((reinterpret_cast<uintptr_t>(out) & 15) == 0)) {
 #pragma unroll
@@ -265,10 +280,16 @@ __global__ void pack_kernel(const float* __restrict__ src, int64_t ld, int64_t r
     const int64_t r = r0 + i, k = k0 + threadIdx.x;
     const float v = t[threadIdx.x][i];
     const int64_t o = r * Kp + k;
-    if (MODE == TC_TF32) {
+    if (MODE == TC_TF32 || MODE == TC_TF32X3) {
       uint32_t u;
       asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
-      static_cast<float*>(hi)[o] = __uint_as_float(u);
+      const float h = __uint_as_float(u);
+      static_cast<float*>(hi)[o] = h;
+      if (MODE == TC_TF32X3) {
+        uint32_t w;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w) : "f"(__fsub_rn(v, h)));
+        static_cast<float*>(lo)[o] = __uint_as_float(w);
+      }
     } else {
       const __nv_bfloat16 h = __float2bfloat16_rn(v);
       static_cast<__nv_bfloat16*>(hi)[o] = h;
@@ -368,6 +389,7 @@ int gram_tensor(int prec, const float* A, int64_t lda, int64_t m, int64_t n, boo
   memset(&a, 0, sizeof(a));
   a.nkb = (int)(Kp / kbox);
   a.tiles = (int)(rp / kTileRows);
+  a.tiles_n = a.tiles;
   a.lower_only = 1;
   a.M = q;
   a.N = q;
@@ -380,6 +402,51 @@ int gram_tensor(int prec, const float* A, int64_t lda, int64_t m, int64_t n, boo
   if (mode == TC_BF16) return launch_tc<TC_BF16>(mh, ml, mh, ml, a, ntiles, s);
   if (mode == TC_BF16X3) return launch_tc<TC_BF16X3>(mh, ml, mh, ml, a, ntiles, s);
   return launch_tc<TC_TF32>(mh, ml, mh, ml, a, ntiles, s);
+}
+
+// C (M x N, row-major, ld ldc) = alpha A B with A (M x K, ld lda) and B (K x N, ld ldb) row-major,
+// on the tensor cores in TF32x3: X = A and Y = B^T are packed K-major as TF32 hi/lo pairs (zero
+// padded to 128 rows and 32 columns of K), every 128 x 128 tile of C is one CTA.  scratch ==
+// nullptr: *need_bytes receives the scratch size only.
+int tc_gemm_nn_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
+                      float alpha, float* C, int64_t ldc, void* scratch, size_t scratch_bytes, size_t* need_bytes,
+                      int* err, cudaStream_t s) {
+  if (!encode_fn()) return -1;
+  const int64_t mp = round_up(M, kTileRows), np = round_up(N, kTileRows), Kp = round_up(K, 32);
+  const size_t xs = (size_t)mp * Kp * 4, ys = (size_t)np * Kp * 4;
+  const size_t need = 2 * xs + 2 * ys + 4 * 256;
+  if (need_bytes) *need_bytes = need;
+  if (!scratch) return 0;
+  if (scratch_bytes < need) return -1;
+  char* base = static_cast<char*>(scratch);
+  void* xh = base;
+  void* xl = base + round_up((int64_t)xs, 256);
+  void* yh = static_cast<char*>(xl) + round_up((int64_t)xs, 256);
+  void* yl = static_cast<char*>(yh) + round_up((int64_t)ys, 256);
+  count_launch(2);
+  pack_kernel<false, TC_TF32X3><<<dim3((unsigned)(Kp / 32), (unsigned)(mp / 32)), dim3(32, 8), 0, s>>>(
+      A, lda, M, K, Kp, xh, xl);
+  pack_kernel<true, TC_TF32X3><<<dim3((unsigned)(Kp / 32), (unsigned)(np / 32)), dim3(32, 8), 0, s>>>(
+      B, ldb, N, K, Kp, yh, yl);
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  CUtensorMap mxh, mxl, myh, myl;
+  if (make_map(&mxh, xh, true, (uint64_t)Kp, (uint64_t)mp) != 0 || make_map(&mxl, xl, true, (uint64_t)Kp, (uint64_t)mp) != 0 ||
+      make_map(&myh, yh, true, (uint64_t)Kp, (uint64_t)np) != 0 || make_map(&myl, yl, true, (uint64_t)Kp, (uint64_t)np) != 0)
+    return -1;
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nkb = (int)(Kp / 32);
+  a.tiles = (int)(mp / kTileRows);
+  a.tiles_n = (int)(np / kTileRows);
+  a.lower_only = 0;
+  a.M = M;
+  a.N = N;
+  a.C = C;
+  a.ldc = ldc;
+  a.alpha = alpha;
+  a.epi = 0;
+  a.err = err;
+  return launch_tc<TC_TF32X3>(mxh, mxl, myh, myl, a, a.tiles * a.tiles_n, s);
 }
 
 }  // namespace pogs

@@ -185,8 +185,15 @@ int chol_mixed(float* G, float* Hlo, int64_t ldh, int64_t q, float* Lf, int64_t 
                int* err, cudaStream_t s);
 void launch_leaf_inverse(const double* L, int64_t ldl, int64_t q, float* Minv, int64_t ldm, cudaStream_t s);
 void launch_l_to_f32(const double* L, int64_t ldl, int64_t q, float* Lf, int64_t ldf, cudaStream_t s);
-void tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ldm, float* work,
-                     cudaStream_t s);
+// M = L^{-1} (lower, FP32) by recursive 2 x 2 block inversion; tensor: its products of blocks of
+// 512 and more in TF32x3 on the tensor cores (else FP32 SIMT).
+int tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ldm, float* work, bool tensor,
+                    int* err, cudaStream_t s);
+// C = alpha A B (row-major FP32) on the tensor cores in TF32x3 (gram.cu); scratch == nullptr
+// returns the scratch size in *need_bytes.
+int tc_gemm_nn_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
+                      float alpha, float* C, int64_t ldc, void* scratch, size_t scratch_bytes, size_t* need_bytes,
+                      int* err, cudaStream_t s);
 void launch_pack_tiles(const float* M, int64_t ldm, int64_t q, int T, float* Mt, cudaStream_t s);
 // Tensor-core Gram (gram.cu): G = X X^T over the K-major packed operand(s).
 int gram_tensor(int prec, const float* A, int64_t lda, int64_t m, int64_t n, bool tall, float* G,

@@ -660,7 +660,7 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order, const Cs
   // ---- M = L^{-1} (FP32), packed tiles --------------------------------------------------
   float* wk = nullptr;
   TRY(scr.get(&wk, (size_t)(q * (q / 2 + kTile)), s));
-  tri_inverse_f32(Lf, ldq, q, Md, ldq, wk, s);
+  TRY(tri_inverse_f32(Lf, ldq, q, Md, ldq, wk, h->sp.chol_prec == POGS_CHOL_MIXED, err, s));
   TRY(dalloc(h, &h->Mt, (size_t)h->T * (h->T + 1) / 2 * kTile * kTile));
   launch_pack_tiles(Md, ldq, q, h->T, h->Mt, s);
   CK(cudaGetLastError());
