@@ -31,17 +31,6 @@ constexpr int kLDS = kBM + 4;   // shared k-row pitch (floats): 16-byte aligned 
 
 enum { OUT_F32 = 0, OUT_SUB_DF = 1 };
 
-// (hi, lo) <- (hi, lo) - x exactly up to the final rounding of the pair: TwoSum of hi and -x
-// (the rounding error e of s = hi - x is recovered exactly), then Fast2Sum of s and lo + e.
-__device__ __forceinline__ void df_sub(float& hi, float& lo, float x) {
-  const float s = __fsub_rn(hi, x);
-  const float bb = __fsub_rn(s, hi);
-  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(-x, bb));
-  const float t = __fadd_rn(lo, e);
-  hi = __fadd_rn(s, t);
-  lo = __fsub_rn(t, __fsub_rn(hi, s));
-}
-
 // Four consecutive elements r[0 .. 3] of a row whose remaining length is `left` (zero past
 // it).  The caller guarantees 16-byte alignment of r (ld % 4 == 0, k % 4 == 0).
 __device__ __forceinline__ float4 ld4(const float* __restrict__ r, int64_t left) {
@@ -560,6 +549,88 @@ int chol_mixed(float* G, float* Hlo, int64_t ldh, int64_t q, float* Lf, int64_t 
   if (ca) cudaStreamDestroy(ca);
   if (cb) cudaStreamDestroy(cb);
   return rc;
+}
+
+namespace {
+
+// Recursive factorization and inversion of the Schur block [r0, r0 + n) (see chol_inv_mixed).
+struct RecCtx {
+  float *Hhi, *Hlo;
+  int64_t ldh;
+  float* Lf;
+  int64_t ldf;
+  float* Md;
+  int64_t ldm;
+  float* T;
+  TcScratch tc;
+  cudaStream_t s;
+};
+
+void chol_inv_rec(const RecCtx& c, int64_t r0, int64_t n) {
+  if (n <= kDB) {
+    count_launch();
+    chol_diag_kernel<<<1, 256, kDiagSmem, c.s>>>(c.Hhi + r0 * c.ldh + r0, c.ldh, (int)n, c.Md + r0 * c.ldm + r0,
+                                                 c.ldm, c.tc.err);
+    return;
+  }
+  const int64_t n1 = (cdiv(n, kDB) / 2) * kDB, n2 = n - n1, r1 = r0 + n1;
+  chol_inv_rec(c, r0, n1);
+  const bool tc = c.tc.p && std::min(n1, n2) >= kTcInvMin;
+  const float* H21 = c.Hhi + r1 * c.ldh + r0;
+  const float* M11 = c.Md + r0 * c.ldm + r0;
+  float* L21 = c.Lf + r1 * c.ldf + r0;
+  // L21 = H21 M11^T (from the hi part: the pair rounds to hi)
+  if (!(tc && tc_gemm_tf32x3(n2, n1, n1, H21, c.ldh, false, M11, c.ldm, false, 1.0f, L21, nullptr, c.ldf,
+                             TC_EPI_STORE, false, c.tc.p, c.tc.bytes, nullptr, c.tc.err, c.s) == 0))
+    sgemm_launch<true, OUT_F32, 2>(n2, n1, n1, H21, c.ldh, M11, c.ldm, 1.0f, L21, nullptr, c.ldf, false, 0, c.s);
+  // H22 -= L21 L21^T on the double-float pair (lower triangle)
+  float* H22 = c.Hhi + r1 * c.ldh + r1;
+  float* H22lo = c.Hlo + r1 * c.ldh + r1;
+  if (!(tc && tc_gemm_tf32x3(n2, n2, n1, L21, c.ldf, false, L21, c.ldf, false, 1.0f, H22, H22lo, c.ldh,
+                             TC_EPI_DF_SUB, true, c.tc.p, c.tc.bytes, nullptr, c.tc.err, c.s) == 0))
+    sgemm_launch<true, OUT_SUB_DF, 2>(n2, n2, n1, L21, c.ldf, L21, c.ldf, 1.0f, H22, H22lo, c.ldh, true, 0, c.s);
+  chol_inv_rec(c, r1, n2);
+  // M21 = -M22 (L21 M11): the off-diagonal block of the inverse
+  const float* M22 = c.Md + r1 * c.ldm + r1;
+  float* M21 = c.Md + r1 * c.ldm + r0;
+  if (tc && tc_gemm_nn_tf32x3(n2, n1, n1, L21, c.ldf, M11, c.ldm, 1.0f, c.T, n1, c.tc.p, c.tc.bytes, nullptr,
+                              c.tc.err, c.s) == 0 &&
+      tc_gemm_nn_tf32x3(n2, n1, n2, M22, c.ldm, c.T, n1, -1.0f, M21, c.ldm, c.tc.p, c.tc.bytes, nullptr, c.tc.err,
+                        c.s) == 0)
+    return;
+  sgemm_launch<false, OUT_F32, 1>(n2, n1, n1, L21, c.ldf, M11, c.ldm, 1.0f, c.T, nullptr, n1, false, 1, c.s);
+  sgemm_launch<false, OUT_F32, 1>(n2, n1, n2, M22, c.ldm, c.T, n1, -1.0f, M21, nullptr, c.ldm, false, 2, c.s);
+}
+
+}  // namespace
+
+int chol_inv_mixed(float* G, float* Hlo, int64_t ldh, int64_t q, float* Lf, int64_t ldf, float* Md, int64_t ldm,
+                   float* work, int* err, cudaStream_t s) {
+  if ((ldh | ldf | ldm) & 3) return POGS_ERR_ARG;   // 16-byte rows for the vector loads
+  if (cudaFuncSetAttribute(chol_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiagSmem) !=
+      cudaSuccess)
+    return POGS_ERR_CUDA;
+  count_launch();
+  gram_to_df_kernel<<<(int)std::min<int64_t>(cdiv(q * q, 256), 148 * 16), 256, 0, s>>>(G, ldh, q, Hlo);
+  RecCtx c{G, Hlo, ldh, Lf, ldf, Md, ldm, work, TcScratch{nullptr, 0, err}, s};
+  const int64_t n1 = (cdiv(q, kDB) / 2) * kDB, n2 = q - n1;
+  if (std::min(n1, n2) >= kTcInvMin) {
+    // the top level's products are the largest; every lower level fits in their scratch
+    size_t need[4] = {0, 0, 0, 0};
+    int rc = tc_gemm_tf32x3(n2, n1, n1, G, ldh, false, Md, ldm, false, 1.0f, Lf, nullptr, ldf, TC_EPI_STORE, false,
+                            nullptr, 0, &need[0], err, s);
+    rc |= tc_gemm_tf32x3(n2, n2, n1, Lf, ldf, false, Lf, ldf, false, 1.0f, G, Hlo, ldh, TC_EPI_DF_SUB, true,
+                         nullptr, 0, &need[1], err, s);
+    rc |= tc_gemm_nn_tf32x3(n2, n1, n1, Lf, ldf, Md, ldm, 1.0f, work, n1, nullptr, 0, &need[2], err, s);
+    rc |= tc_gemm_nn_tf32x3(n2, n1, n2, Md, ldm, work, n1, -1.0f, Md, ldm, nullptr, 0, &need[3], err, s);
+    if (rc == 0) {
+      c.tc.bytes = std::max(std::max(need[0], need[1]), std::max(need[2], need[3]));
+      if (pool_alloc(&c.tc.p, c.tc.bytes, s) != 0) c.tc.p = nullptr;
+    }
+  }
+  chol_inv_rec(c, 0, q);
+  if (c.tc.p) cudaFreeAsync(c.tc.p, s);
+  return cudaGetLastError() == cudaSuccess ? 0 : POGS_ERR_CUDA;
 }
 
 int tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ldm, float* work, bool tensor,

@@ -80,6 +80,16 @@ POGS_DEV void df_add_prod(Df& a, float x, float y) {   // a += x y
   a.lo = __fadd_rn(a.lo, pe);
 }
 POGS_DEV double df_value(const Df& a) { return (double)a.hi + (double)a.lo; }
+// (hi, lo) <- (hi, lo) - x exactly up to the final rounding of the pair: TwoSum of hi and -x
+// (the rounding error e of s = hi - x is recovered exactly), then Fast2Sum of s and lo + e.
+POGS_DEV void df_sub(float& hi, float& lo, float x) {
+  const float s = __fsub_rn(hi, x);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(-x, bb));
+  const float t = __fadd_rn(lo, e);
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
 
 // Block-wide sum of NV double-float values per thread: a fixed xor-shuffle tree on the FP32
 // pipes inside each warp, then the same across the per-warp results in warp 0 (no serial FP64

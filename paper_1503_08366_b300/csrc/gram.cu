@@ -49,10 +49,11 @@ struct TcArgs {
   int tiles_n;             // tiles along N (full grid)
   int lower_only;          // enumerate the lower triangle of tiles
   int64_t M, N;            // valid output extent
-  float* C;                // FP32 output (epi 0)
+  float* C;                // FP32 output (epi 0), hi part of the pair (epi 2)
+  float* Clo;              // lo part of the double-float pair (epi 2)
   double* C64;             // FP64 output (epi 1: C64 += alpha * acc, lower triangle)
   int64_t ldc;
-  double alpha;            // epi 0: C = alpha * acc; epi 1: C64 += alpha * acc
+  double alpha;            // epi 0: C = alpha * acc; epi 1: C64 += alpha * acc; epi 2: (C, Clo) -= acc
   int epi;
   int* err;
 };
@@ -242,11 +243,36 @@ __global__ void __launch_bounds__(192, 1)
           for (int i = 0; i < 128; ++i)
             if (col0 + i < a.N) out[i] = acc[i];
         }
-      } else {
+      } else if (a.epi == 1) {
         double* out = a.C64 + row * a.ldc + col0;
 #pragma unroll
         for (int i = 0; i < 128; ++i)
           if (col0 + i < a.N && col0 + i <= row) out[i] += a.alpha * (double)acc[i];
+      } else {
+        // double-float Schur complement update, lower triangle
+        float* oh = a.C + row * a.ldc + col0;
+        float* ol = a.Clo + row * a.ldc + col0;
+        if (tj < ti && col0 + 128 <= a.N && ((reinterpret_cast<uintptr_t>(oh) | reinterpret_cast<uintptr_t>(ol)) & 15) == 0) {
+#pragma unroll
+          for (int i = 0; i < 128; i += 4) {
+            float4 h = *reinterpret_cast<float4*>(oh + i), l = *reinterpret_cast<float4*>(ol + i);
+            df_sub(h.x, l.x, acc[i]);
+            df_sub(h.y, l.y, acc[i + 1]);
+            df_sub(h.z, l.z, acc[i + 2]);
+            df_sub(h.w, l.w, acc[i + 3]);
+            *reinterpret_cast<float4*>(oh + i) = h;
+            *reinterpret_cast<float4*>(ol + i) = l;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 128; ++i)
+            if (col0 + i < a.N && col0 + i <= row) {
+              float h = oh[i], l = ol[i];
+              df_sub(h, l, acc[i]);
+              oh[i] = h;
+              ol[i] = l;
+            }
+        }
       }
     }
   }
@@ -404,30 +430,37 @@ int gram_tensor(int prec, const float* A, int64_t lda, int64_t m, int64_t n, boo
   return launch_tc<TC_TF32>(mh, ml, mh, ml, a, ntiles, s);
 }
 
-// C (M x N, row-major, ld ldc) = alpha A B with A (M x K, ld lda) and B (K x N, ld ldb) row-major,
-// on the tensor cores in TF32x3: X = A and Y = B^T are packed K-major as TF32 hi/lo pairs (zero
-// padded to 128 rows and 32 columns of K), every 128 x 128 tile of C is one CTA.  scratch ==
-// nullptr: *need_bytes receives the scratch size only.
-int tc_gemm_nn_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
-                      float alpha, float* C, int64_t ldc, void* scratch, size_t scratch_bytes, size_t* need_bytes,
-                      int* err, cudaStream_t s) {
+// C (M x N, row-major, ld ldc) op= X Y^T on the tensor cores in TF32x3, with X (M x K) and Y (N x K)
+// read from row-major A and B: X[i][k] = transA ? A[k*lda + i] : A[i*lda + k], likewise Y from B.
+// X and Y are packed K-major as TF32 hi/lo pairs (zero padded to 128 rows and 32 columns of K);
+// every 128 x 128 tile of C (the lower ones when `lower`) is one CTA.  epi TC_EPI_STORE:
+// C = alpha X Y^T; TC_EPI_DF_SUB: the double-float pair (C, Clo) -= X Y^T on and below the
+// diagonal.  When A == B with equal layout and M == N (a rank-K update), one packing serves both.
+// scratch == nullptr: *need_bytes receives the scratch size only.
+int tc_gemm_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, bool transA, const float* B,
+                   int64_t ldb, bool transB, float alpha, float* C, float* Clo, int64_t ldc, int epi, bool lower,
+                   void* scratch, size_t scratch_bytes, size_t* need_bytes, int* err, cudaStream_t s) {
   if (!encode_fn()) return -1;
+  const bool same = A == B && lda == ldb && transA == transB && M == N;
   const int64_t mp = round_up(M, kTileRows), np = round_up(N, kTileRows), Kp = round_up(K, 32);
-  const size_t xs = (size_t)mp * Kp * 4, ys = (size_t)np * Kp * 4;
-  const size_t need = 2 * xs + 2 * ys + 4 * 256;
+  const int64_t xs = round_up(mp * Kp * 4, 256), ys = same ? 0 : round_up(np * Kp * 4, 256);
+  const size_t need = (size_t)(2 * xs + 2 * ys);
   if (need_bytes) *need_bytes = need;
   if (!scratch) return 0;
   if (scratch_bytes < need) return -1;
   char* base = static_cast<char*>(scratch);
   void* xh = base;
-  void* xl = base + round_up((int64_t)xs, 256);
-  void* yh = static_cast<char*>(xl) + round_up((int64_t)xs, 256);
-  void* yl = static_cast<char*>(yh) + round_up((int64_t)ys, 256);
-  count_launch(2);
-  pack_kernel<false, TC_TF32X3><<<dim3((unsigned)(Kp / 32), (unsigned)(mp / 32)), dim3(32, 8), 0, s>>>(
-      A, lda, M, K, Kp, xh, xl);
-  pack_kernel<true, TC_TF32X3><<<dim3((unsigned)(Kp / 32), (unsigned)(np / 32)), dim3(32, 8), 0, s>>>(
-      B, ldb, N, K, Kp, yh, yl);
+  void* xl = base + xs;
+  void* yh = same ? xh : base + 2 * xs;
+  void* yl = same ? xl : base + 2 * xs + ys;
+  auto pack = [&](const float* src, int64_t ld, bool trans, int64_t rows, int64_t rp, void* hi, void* lo) {
+    const dim3 grid((unsigned)(Kp / 32), (unsigned)(rp / 32)), blk(32, 8);
+    count_launch();
+    if (trans) pack_kernel<true, TC_TF32X3><<<grid, blk, 0, s>>>(src, ld, rows, K, Kp, hi, lo);
+    else pack_kernel<false, TC_TF32X3><<<grid, blk, 0, s>>>(src, ld, rows, K, Kp, hi, lo);
+  };
+  pack(A, lda, transA, M, mp, xh, xl);
+  if (!same) pack(B, ldb, transB, N, np, yh, yl);
   if (cudaGetLastError() != cudaSuccess) return -1;
   CUtensorMap mxh, mxl, myh, myl;
   if (make_map(&mxh, xh, true, (uint64_t)Kp, (uint64_t)mp) != 0 || make_map(&mxl, xl, true, (uint64_t)Kp, (uint64_t)mp) != 0 ||
@@ -438,15 +471,25 @@ int tc_gemm_nn_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t l
   a.nkb = (int)(Kp / 32);
   a.tiles = (int)(mp / kTileRows);
   a.tiles_n = (int)(np / kTileRows);
-  a.lower_only = 0;
+  a.lower_only = lower ? 1 : 0;
+  if (lower && a.tiles != a.tiles_n) return -1;
   a.M = M;
   a.N = N;
   a.C = C;
+  a.Clo = Clo;
   a.ldc = ldc;
   a.alpha = alpha;
-  a.epi = 0;
+  a.epi = epi;
   a.err = err;
-  return launch_tc<TC_TF32X3>(mxh, mxl, myh, myl, a, a.tiles * a.tiles_n, s);
+  const int ntiles = lower ? a.tiles * (a.tiles + 1) / 2 : a.tiles * a.tiles_n;
+  return launch_tc<TC_TF32X3>(mxh, mxl, myh, myl, a, ntiles, s);
+}
+
+int tc_gemm_nn_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
+                      float alpha, float* C, int64_t ldc, void* scratch, size_t scratch_bytes, size_t* need_bytes,
+                      int* err, cudaStream_t s) {
+  return tc_gemm_tf32x3(M, N, K, A, lda, false, B, ldb, true, alpha, C, nullptr, ldc, TC_EPI_STORE, false, scratch,
+                        scratch_bytes, need_bytes, err, s);
 }
 
 }  // namespace pogs

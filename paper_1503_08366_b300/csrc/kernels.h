@@ -183,14 +183,27 @@ int pool_alloc(void** q, size_t bytes, cudaStream_t s);
 // Md.  ldh, ldf, ldm must be multiples of 4.
 int chol_mixed(float* G, float* Hlo, int64_t ldh, int64_t q, float* Lf, int64_t ldf, float* Md, int64_t ldm,
                int* err, cudaStream_t s);
+// Recursive factorization of I + G with its inverse (chol.cu): at each level of a 2 x 2 block
+// split, L21 = H21 M11^T, H22 -= L21 L21^T on the double-float pair, M21 = -M22 L21 M11; the
+// products of blocks of 512 and more on the tensor cores (TF32x3), leaves are the one-CTA 128-block
+// kernel.  Writes the whole lower triangle of M = L^{-1} to Md (and the off-diagonal blocks of L
+// to Lf); work holds (q/2 + 128) x (q/2) floats.
+int chol_inv_mixed(float* G, float* Hlo, int64_t ldh, int64_t q, float* Lf, int64_t ldf, float* Md, int64_t ldm,
+                   float* work, int* err, cudaStream_t s);
 void launch_leaf_inverse(const double* L, int64_t ldl, int64_t q, float* Minv, int64_t ldm, cudaStream_t s);
 void launch_l_to_f32(const double* L, int64_t ldl, int64_t q, float* Lf, int64_t ldf, cudaStream_t s);
 // M = L^{-1} (lower, FP32) by recursive 2 x 2 block inversion; tensor: its products of blocks of
 // 512 and more in TF32x3 on the tensor cores (else FP32 SIMT).
 int tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ldm, float* work, bool tensor,
                     int* err, cudaStream_t s);
-// C = alpha A B (row-major FP32) on the tensor cores in TF32x3 (gram.cu); scratch == nullptr
-// returns the scratch size in *need_bytes.
+// Tensor-core GEMM in TF32x3 (gram.cu): C op= X Y^T with X, Y read from row-major A, B (or their
+// transposes); TC_EPI_STORE: C = alpha X Y^T; TC_EPI_DF_SUB: (C, Clo) -= X Y^T on and below the
+// diagonal (lower: lower tiles only).  scratch == nullptr returns the scratch size in *need_bytes.
+enum : int { TC_EPI_STORE = 0, TC_EPI_DF_SUB = 2 };
+int tc_gemm_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, bool transA, const float* B,
+                   int64_t ldb, bool transB, float alpha, float* C, float* Clo, int64_t ldc, int epi, bool lower,
+                   void* scratch, size_t scratch_bytes, size_t* need_bytes, int* err, cudaStream_t s);
+// C = alpha A B (row-major FP32), the special case above.
 int tc_gemm_nn_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
                       float alpha, float* C, int64_t ldc, void* scratch, size_t scratch_bytes, size_t* need_bytes,
                       int* err, cudaStream_t s);

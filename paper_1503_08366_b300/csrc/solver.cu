@@ -640,7 +640,17 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order, const Cs
   float *Md = nullptr, *Lf = nullptr;
   TRY(scr.get(&Md, (size_t)(ldq * ldq), s));
   TRY(scr.get(&Lf, (size_t)(ldq * ldq), s));
-  if (h->sp.chol_prec == POGS_CHOL_MIXED) {
+  float* wk = nullptr;
+  TRY(scr.get(&wk, (size_t)(q * (q / 2 + kTile)), s));
+  // from q = 4096 on the mixed factorization runs recursively with the inverse formed alongside,
+  // its large products on the tensor cores; below that the blocked factorization, whose
+  // 128-block leaves overlap its trailing updates, is faster (q = 2000: 2.6 against 2.9 ms)
+  const bool recursive = h->sp.chol_prec == POGS_CHOL_MIXED && q >= 4096;
+  if (recursive) {
+    float* Hlo = nullptr;
+    TRY(scr.get(&Hlo, (size_t)(ldq * ldq), s));
+    TRY(chol_inv_mixed(G, Hlo, ldq, q, Lf, ldq, Md, ldq, wk, err, s));
+  } else if (h->sp.chol_prec == POGS_CHOL_MIXED) {
     // double-float Schur complement (G becomes its hi part); also writes the diagonal blocks of M
     float* Hlo = nullptr;
     TRY(scr.get(&Hlo, (size_t)(ldq * ldq), s));
@@ -657,10 +667,8 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order, const Cs
   }
   CK(cudaGetLastError());
   phase("cholesky");
-  // ---- M = L^{-1} (FP32), packed tiles --------------------------------------------------
-  float* wk = nullptr;
-  TRY(scr.get(&wk, (size_t)(q * (q / 2 + kTile)), s));
-  TRY(tri_inverse_f32(Lf, ldq, q, Md, ldq, wk, h->sp.chol_prec == POGS_CHOL_MIXED, err, s));
+  // ---- M = L^{-1} (FP32; already complete after the recursive factorization), packed tiles --
+  if (!recursive) TRY(tri_inverse_f32(Lf, ldq, q, Md, ldq, wk, h->sp.chol_prec == POGS_CHOL_MIXED, err, s));
   TRY(dalloc(h, &h->Mt, (size_t)h->T * (h->T + 1) / 2 * kTile * kTile));
   launch_pack_tiles(Md, ldq, q, h->T, h->Mt, s);
   CK(cudaGetLastError());
