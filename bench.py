@@ -325,8 +325,11 @@ def run_ours(args):
         P.pogs_free(h)
         it = info.iters
         tall = p.m >= p.n
-        names = dict(prox="prox", A_pass1="gemv_t" if tall else "gemv_n", Linv="trmv", LinvT="trmv_t",
+        sym = kt["LinvT"][1] == 0.0   # the inverse applied as one symmetric product
+        names = dict(prox="prox", A_pass1="gemv_t" if tall else "gemv_n", Linv="symv" if sym else "trmv",
                      A_pass2="gemv_n" if tall else "gemv_t", check="check")
+        if not sym:
+            names["LinvT"] = "trmv_t"
         for name, t in (("equil", rep.equil_ms), ("gram", rep.gram_ms), ("factor", rep.factor_ms),
                         ("inverse", rep.inverse_ms), ("ingest", rep.ingest_ms)):
             comp[(name, i)] = dict(total=t, ms=t, bytes=None, launches=1)

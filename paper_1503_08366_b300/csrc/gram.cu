@@ -48,6 +48,8 @@ struct TcArgs {
   int tiles;               // tiles along M (and N, lower_only)
   int tiles_n;             // tiles along N (full grid)
   int lower_only;          // enumerate the lower triangle of tiles
+  int kskip;               // X, Y are lower triangular in K (X[i][k] = 0 for k < i): tile (ti, tj) starts
+                           // its K loop at 128 max(ti, tj)
   int64_t M, N;            // valid output extent
   float* C;                // FP32 output (epi 0), hi part of the pair (epi 2)
   float* Clo;              // lo part of the double-float pair (epi 2)
@@ -94,7 +96,10 @@ __global__ void __launch_bounds__(192, 1)
     ti = blockIdx.x / a.tiles_n;
     tj = blockIdx.x % a.tiles_n;
   }
-  const int nchunks = (a.nkb + kChunkBoxes - 1) / kChunkBoxes;
+  // K boxes of this tile: [kb0, kb0 + nkb)
+  const int kb0 = a.kskip ? (max(ti, tj) * kTileRows) / Cfg::kElemsPerBox : 0;
+  const int nkb = a.nkb - kb0;
+  const int nchunks = (nkb + kChunkBoxes - 1) / kChunkBoxes;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::kStages; ++s) {
@@ -126,7 +131,7 @@ __global__ void __launch_bounds__(192, 1)
         tc::prefetch_tmap(&mxl);
         tc::prefetch_tmap(&myl);
       }
-      for (int kb = 0; kb < a.nkb; ++kb) {
+      for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % Cfg::kStages;
         const uint32_t ph = (uint32_t)(kb / Cfg::kStages) & 1u;
         if (kb >= Cfg::kStages && !tc::mbar_wait(empty + s, ph ^ 1u)) {
@@ -135,7 +140,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         uint8_t* st = smem + s * Cfg::kStageBytes;
         tc::mbar_arrive_expect_tx(full + s, Cfg::kStageBytes);
-        const int x = kb * Cfg::kElemsPerBox;
+        const int x = (kb0 + kb) * Cfg::kElemsPerBox;
         tc::tma_load_2d(st, &mxh, x, ti * kTileRows, full + s);
         tc::tma_load_2d(st + kTileBytes, &myh, x, tj * kTileRows, full + s);
         if (Cfg::kSplit) {
@@ -156,7 +161,7 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         tc::fence_after_sync();
-        const int kb1 = min(a.nkb, (c + 1) * kChunkBoxes);
+        const int kb1 = min(nkb, (c + 1) * kChunkBoxes);
         for (int kb = c * kChunkBoxes; kb < kb1; ++kb) {
           const int s = kb % Cfg::kStages;
           const uint32_t ph = (uint32_t)(kb / Cfg::kStages) & 1u;
@@ -439,7 +444,7 @@ int gram_tensor(int prec, const float* A, int64_t lda, int64_t m, int64_t n, boo
 // scratch == nullptr: *need_bytes receives the scratch size only.
 int tc_gemm_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, bool transA, const float* B,
                    int64_t ldb, bool transB, float alpha, float* C, float* Clo, int64_t ldc, int epi, bool lower,
-                   void* scratch, size_t scratch_bytes, size_t* need_bytes, int* err, cudaStream_t s) {
+                   void* scratch, size_t scratch_bytes, size_t* need_bytes, int* err, cudaStream_t s, bool kskip) {
   if (!encode_fn()) return -1;
   const bool same = A == B && lda == ldb && transA == transB && M == N;
   const int64_t mp = round_up(M, kTileRows), np = round_up(N, kTileRows), Kp = round_up(K, 32);
@@ -472,6 +477,7 @@ int tc_gemm_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
   a.tiles = (int)(mp / kTileRows);
   a.tiles_n = (int)(np / kTileRows);
   a.lower_only = lower ? 1 : 0;
+  a.kskip = kskip ? 1 : 0;
   if (lower && a.tiles != a.tiles_n) return -1;
   a.M = M;
   a.N = N;

@@ -347,6 +347,21 @@ __device__ __forceinline__ void epi_r(const EpiArgs& ep, int idx, int q, float v
   }
 }
 
+// Sum of k partials p[0], p[stride], ... in index order, eight loads in flight per round trip.
+__device__ __forceinline__ float sum_slots(const float* __restrict__ p, int k, int64_t stride) {
+  float s = 0.0f;
+  int i = 0;
+  for (; i + 8 <= k; i += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(p + (int64_t)(i + u) * stride);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
+  for (; i < k; ++i) s += __ldcg(p + (int64_t)i * stride);
+  return s;
+}
+
 __device__ __forceinline__ void tile_coords(int b, int& I, int& J) {
   int i = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
   while ((i + 1) * (i + 2) / 2 <= b) ++i;
@@ -381,9 +396,7 @@ __global__ void __launch_bounds__(256) trmv_kernel(const float* __restrict__ Mt,
     if (!arrive_last(cnt + I, I + 1)) return;
     if (tid < kTile) {
       const int64_t base = (int64_t)I * (I + 1) / 2;
-      float s = 0.0f;
-      for (int jj = 0; jj <= I; ++jj) s += __ldcg(part + (base + jj) * kTile + tid);
-      epi_r<EPI>(ep, I * kTile + tid, q, s);
+      epi_r<EPI>(ep, I * kTile + tid, q, sum_slots(part + base * kTile + tid, I + 1, kTile));
     }
   } else {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -409,11 +422,68 @@ __global__ void __launch_bounds__(256) trmv_kernel(const float* __restrict__ Mt,
     if (!arrive_last(cnt + J, T - J)) return;
     if (tid < kTile) {
       const int64_t base = (int64_t)J * T - (int64_t)J * (J - 1) / 2;
-      float s = 0.0f;
-      for (int ii = 0; ii < T - J; ++ii) s += __ldcg(part + (base + ii) * kTile + tid);
-      epi_r<EPI>(ep, J * kTile + tid, q, s);
+      epi_r<EPI>(ep, J * kTile + tid, q, sum_slots(part + base * kTile + tid, T - J, kTile));
     }
   }
+}
+
+// Symmetric product y = S v with S = M^T M = (I + G)^{-1} stored as its lower 128 x 128 tiles
+// (diagonal tiles full).  One block per tile (I, J): its rows give block I the contribution
+// S_IJ v_J (slot J of block I), and for I > J its columns give block J the contribution
+// S_IJ^T v_I (slot I of block J), both from one read of the tile.  Every output block receives
+// T contributions; the last block to deliver one sums the T slots in slot order and applies the
+// epilogue.  One pass over the packed triangle instead of the two of M v and M^T z.
+template <int EPI>
+__global__ void __launch_bounds__(256) symv_kernel(const float* __restrict__ St, int T, int q,
+                                                   const float* __restrict__ vin, float* __restrict__ part,
+                                                   unsigned* __restrict__ cnt, EpiArgs ep,
+                                                   const DevState* __restrict__ guard) {
+  __shared__ float4 shc[8][32];
+  if (guard && guard->done) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = blockIdx.x;
+  int I, J;
+  tile_coords(b, I, J);
+  const float4* tile = reinterpret_cast<const float4*>(St + (int64_t)b * kTile * kTile);
+  const float4 vj = __ldg(reinterpret_cast<const float4*>(vin + (int64_t)J * kTile) + lane);
+  const bool off = I != J;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  // each warp's 16 rows in two batches of 8 (eight loads in flight, few registers):
+  // rows -> block I, slot J; columns (off-diagonal tiles) -> block J, slot I
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float4 a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = ldg_stream(tile + (warp * 16 + h * 8 + u) * 32 + lane);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int r = warp * 16 + h * 8 + u;
+      float s = a[u].x * vj.x + a[u].y * vj.y + a[u].z * vj.z + a[u].w * vj.w;
+      s = warp_sum(s);
+      if (lane == 0) part[((int64_t)I * T + J) * kTile + r] = s;
+      if (off) {
+        const float zr = __ldg(vin + (int64_t)I * kTile + r);
+        acc.x = fmaf(a[u].x, zr, acc.x); acc.y = fmaf(a[u].y, zr, acc.y);
+        acc.z = fmaf(a[u].z, zr, acc.z); acc.w = fmaf(a[u].w, zr, acc.w);
+      }
+    }
+  }
+  if (off) {
+    shc[warp][lane] = acc;
+    __syncthreads();
+    if (tid < kTile) {
+      const float* shf = reinterpret_cast<const float*>(&shc[0][0]);
+      float s = 0.0f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) s += shf[w * kTile + tid];
+      part[((int64_t)J * T + I) * kTile + tid] = s;
+    }
+  }
+  auto finish = [&](int blk) {
+    if (tid < kTile) epi_r<EPI>(ep, blk * kTile + tid, q, sum_slots(part + (int64_t)blk * T * kTile + tid, T, kTile));
+  };
+  if (arrive_last(cnt + I, T)) finish(I);
+  if (I != J && arrive_last(cnt + J, T)) finish(J);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -705,6 +775,18 @@ void launch_gemv_n(int nrhs, bool sq, int epi, const float* A, int64_t lda, int 
   if (nrhs == 2) gemv_n_dispatch<2, false>(epi, A, lda, m, n, x1, x2, g, part, cnt, ep, guard, s);
   else if (sq) gemv_n_dispatch<1, true>(epi, A, lda, m, n, x1, x2, g, part, cnt, ep, guard, s);
   else gemv_n_dispatch<1, false>(epi, A, lda, m, n, x1, x2, g, part, cnt, ep, guard, s);
+}
+
+void launch_symv(int epi, const float* St, int T, int q, const float* vin, float* part, unsigned* cnt,
+                 const EpiArgs& ep, const DevState* guard, cudaStream_t s) {
+  const int nt = T * (T + 1) / 2;
+  count_launch();
+  switch (epi) {
+    case EPR_RAW: symv_kernel<EPR_RAW><<<nt, 256, 0, s>>>(St, T, q, vin, part, cnt, ep, guard); break;
+    case EPR_TALL_X: symv_kernel<EPR_TALL_X><<<nt, 256, 0, s>>>(St, T, q, vin, part, cnt, ep, guard); break;
+    case EPR_FAT_Y: symv_kernel<EPR_FAT_Y><<<nt, 256, 0, s>>>(St, T, q, vin, part, cnt, ep, guard); break;
+    case EPR_ADD: symv_kernel<EPR_ADD><<<nt, 256, 0, s>>>(St, T, q, vin, part, cnt, ep, guard); break;
+  }
 }
 
 void launch_trmv(bool trans, int epi, const float* Mt, int T, int q, const float* vin, float* part, unsigned* cnt,

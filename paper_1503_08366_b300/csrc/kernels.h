@@ -112,6 +112,10 @@ void launch_gemv_n(int nrhs, bool sq, int epi, const float* A, int64_t lda, int 
                    const EpiArgs& ep, const DevState* guard, cudaStream_t s);
 void launch_trmv(bool trans, int epi, const float* Mt, int T, int q, const float* vin, float* part,
                  unsigned* cnt, const EpiArgs& ep, const DevState* guard, cudaStream_t s);
+// y = S v with S = M^T M = (I + G)^{-1} as packed lower tiles (diagonal tiles full); part holds
+// T x T x 128 floats, cnt T counters.
+void launch_symv(int epi, const float* St, int T, int q, const float* vin, float* part, unsigned* cnt,
+                 const EpiArgs& ep, const DevState* guard, cudaStream_t s);
 void launch_check(DevState* st, const DevCfg* cfg, const Df* prox_part, int nprox,
                   const Df* pri_part, int npri, const Df* dual_part, int ndual,
                   unsigned long long cond_handle, int use_cond, cudaStream_t s);
@@ -202,12 +206,14 @@ int tri_inverse_f32(const float* L, int64_t ldl, int64_t q, float* M, int64_t ld
 enum : int { TC_EPI_STORE = 0, TC_EPI_DF_SUB = 2 };
 int tc_gemm_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, bool transA, const float* B,
                    int64_t ldb, bool transB, float alpha, float* C, float* Clo, int64_t ldc, int epi, bool lower,
-                   void* scratch, size_t scratch_bytes, size_t* need_bytes, int* err, cudaStream_t s);
+                   void* scratch, size_t scratch_bytes, size_t* need_bytes, int* err, cudaStream_t s,
+                   bool kskip = false);   // kskip: X[i][k] = Y[i][k] = 0 for k < i (skip those K boxes)
 // C = alpha A B (row-major FP32), the special case above.
 int tc_gemm_nn_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
                       float alpha, float* C, int64_t ldc, void* scratch, size_t scratch_bytes, size_t* need_bytes,
                       int* err, cudaStream_t s);
-void launch_pack_tiles(const float* M, int64_t ldm, int64_t q, int T, float* Mt, cudaStream_t s);
+// Lower 128-tiles of M (sym: diagonal tiles copied whole, else their upper part zeroed).
+void launch_pack_tiles(const float* M, int64_t ldm, int64_t q, int T, float* Mt, cudaStream_t s, bool sym = false);
 // Tensor-core Gram (gram.cu): G = X X^T over the K-major packed operand(s).
 int gram_tensor(int prec, const float* A, int64_t lda, int64_t m, int64_t n, bool tall, float* G,
                 int64_t ldg, void* scratch, size_t scratch_bytes, size_t* need_bytes, int* err,

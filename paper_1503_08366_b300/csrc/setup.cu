@@ -346,7 +346,8 @@ void launch_l_to_f32(const double* L, int64_t ldl, int64_t q, float* Lf, int64_t
 }
 
 // Pack the lower triangle of M (dense, ld ldm) into 128 x 128 tiles, zero outside.
-__global__ void __launch_bounds__(256) pack_tiles_kernel(const float* M, int64_t ldm, int64_t q, float* Mt) {
+__global__ void __launch_bounds__(256) pack_tiles_kernel(const float* M, int64_t ldm, int64_t q, float* Mt,
+                                                         bool sym) {
   const int b = blockIdx.x;
   int I = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
   while ((I + 1) * (I + 2) / 2 <= b) ++I;
@@ -356,12 +357,12 @@ __global__ void __launch_bounds__(256) pack_tiles_kernel(const float* M, int64_t
   for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
     const int rr = e / kTile, cc = e % kTile;
     const int64_t gi = (int64_t)I * kTile + rr, gj = (int64_t)J * kTile + cc;
-    out[e] = (gi < q && gj < q && gj <= gi) ? M[gi * ldm + gj] : 0.0f;
+    out[e] = (gi < q && gj < q && (gj <= gi || sym)) ? M[gi * ldm + gj] : 0.0f;
   }
 }
-void launch_pack_tiles(const float* M, int64_t ldm, int64_t q, int T, float* Mt, cudaStream_t s) {
+void launch_pack_tiles(const float* M, int64_t ldm, int64_t q, int T, float* Mt, cudaStream_t s, bool sym) {
   count_launch();
-  pack_tiles_kernel<<<T * (T + 1) / 2, 256, 0, s>>>(M, ldm, q, Mt);
+  pack_tiles_kernel<<<T * (T + 1) / 2, 256, 0, s>>>(M, ldm, q, Mt, sym);
 }
 
 }  // namespace pogs

@@ -38,7 +38,9 @@ struct pogs_handle {
   int *csr_rp = nullptr, *csr_ci = nullptr, *csc_rp = nullptr, *csc_ci = nullptr, *csc_perm = nullptr;
   float *csr_va = nullptr, *csc_va = nullptr;
   float *D = nullptr, *E = nullptr;
-  float* Mt = nullptr;
+  float* Mt = nullptr;              // packed lower tiles of M = L^{-1} (two triangular products)
+  float* St = nullptr;              // packed lower tiles of S = M^T M = (I + G)^{-1} (one pass), or null
+  float* part_sy = nullptr;         // T x T x 128 partials of the symmetric product
   float *x = nullptr, *y = nullptr, *xt = nullptr, *yt = nullptr, *xh = nullptr, *yh = nullptr;
   float *cx = nullptr, *dy = nullptr, *mu = nullptr, *nu = nullptr, *r = nullptr, *z = nullptr, *w = nullptr;
   float *x0 = nullptr, *v0 = nullptr, *r2 = nullptr, *tn = nullptr;
@@ -302,6 +304,19 @@ void enqueue_projection_cgls(pogs_handle* h, int steps, cudaStream_t s) {
   }
 }
 
+// (I + G)^{-1} v with the given final epilogue: one symmetric pass over S, or z = M v then M^T z.
+void apply_inverse(pogs_handle* h, const float* v, int epi, const EpiArgs& ep, cudaStream_t s) {
+  const int q = (int)h->q;
+  if (h->St) {
+    launch_symv(epi, h->St, h->T, q, v, h->part_sy, h->cnt_tr, ep, h->st, s);
+    return;
+  }
+  EpiArgs e = epi0();
+  e.out1 = h->z;
+  launch_trmv(false, EPR_RAW, h->Mt, h->T, q, v, h->part_tr, h->cnt_tr, e, h->st, s);
+  launch_trmv(true, epi, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, ep, h->st, s);
+}
+
 // The projection of one iteration (tall or fat), optionally with refinement.
 void enqueue_projection(pogs_handle* h, int refine, int cg_steps, cudaStream_t s) {
   if (cg_steps > 0 || h->indirect) {
@@ -315,16 +330,13 @@ void enqueue_projection(pogs_handle* h, int refine, int cg_steps, cudaStream_t s
     EpiArgs e1 = epi0();
     e1.r = h->r; e1.cx = h->cx; e1.mu = h->mu; e1.E = h->E; e1.xt = h->xt; e1.res_part = h->dual_part;
     launch_gemv_t(3, false, EPT_TALL_R, h->A, h->lda, m, n, h->dy, h->nu, h->yt, g, h->part_t, h->cnt_t, e1, h->st, s);
-    EpiArgs e2 = epi0();
-    e2.out1 = h->z;
-    launch_trmv(false, EPR_RAW, h->Mt, h->T, q, h->r, h->part_tr, h->cnt_tr, e2, h->st, s);
     EpiArgs e3 = epi0();
     if (!refine) {
       e3.x = h->x; e3.xt = h->xt; e3.cx = h->cx;
-      launch_trmv(true, EPR_TALL_X, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, e3, h->st, s);
+      apply_inverse(h, h->r, EPR_TALL_X, e3, s);
     } else {
       e3.out1 = h->x;   // x0 only; the dual update waits for the refined x
-      launch_trmv(true, EPR_RAW, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, e3, h->st, s);
+      apply_inverse(h, h->r, EPR_RAW, e3, s);
     }
     if (refine) {
       // r2 = r - x0 - A^T (A x0);  x = x0 + L^{-T} L^{-1} r2
@@ -335,12 +347,9 @@ void enqueue_projection(pogs_handle* h, int refine, int cg_steps, cudaStream_t s
       e5.out1 = h->r2; e5.in1 = h->r; e5.in2 = h->x;
       launch_gemv_t(1, false, EPT_REFINE, h->A, h->lda, m, n, h->v0, nullptr, nullptr, g, h->part_t, h->cnt_t, e5,
                     h->st, s);
-      EpiArgs e6 = epi0();
-      e6.out1 = h->z;
-      launch_trmv(false, EPR_RAW, h->Mt, h->T, q, h->r2, h->part_tr, h->cnt_tr, e6, h->st, s);
       EpiArgs e7 = epi0();
       e7.x = h->x; e7.xt = h->xt; e7.cx = h->cx; e7.in1 = h->x;
-      launch_trmv(true, EPR_TALL_X, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, e7, h->st, s);
+      apply_inverse(h, h->r2, EPR_TALL_X, e7, s);
     }
     // [y, w] = A [x, x^{1/2}] ; y~ = d - y ; primal residual ||A x^{1/2} - y^{1/2}||
     EpiArgs e8 = epi0();
@@ -351,17 +360,14 @@ void enqueue_projection(pogs_handle* h, int refine, int cg_steps, cudaStream_t s
     EpiArgs e1 = epi0();
     e1.r = h->r; e1.dy = h->dy; e1.yh = h->yh; e1.D = h->D; e1.res_part = h->pri_part;
     launch_gemv_n(2, false, EPN_FAT_R, h->A, h->lda, m, n, h->cx, h->xh, g, h->part_n, h->cnt_n, e1, h->st, s);
-    EpiArgs e2 = epi0();
-    e2.out1 = h->z;
-    launch_trmv(false, EPR_RAW, h->Mt, h->T, q, h->r, h->part_tr, h->cnt_tr, e2, h->st, s);
     if (!refine) {
       EpiArgs e3 = epi0();
       e3.y = h->y; e3.yt = h->yt; e3.dy = h->dy; e3.w = h->w;
-      launch_trmv(true, EPR_FAT_Y, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, e3, h->st, s);
+      apply_inverse(h, h->r, EPR_FAT_Y, e3, s);
     } else {
       EpiArgs e3 = epi0();
       e3.out1 = h->v0;
-      launch_trmv(true, EPR_RAW, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, e3, h->st, s);
+      apply_inverse(h, h->r, EPR_RAW, e3, s);
       // r2 = r - v0 - A (A^T v0)
       EpiArgs e4 = epi0();
       e4.out1 = h->tn;
@@ -370,12 +376,9 @@ void enqueue_projection(pogs_handle* h, int refine, int cg_steps, cudaStream_t s
       EpiArgs e5 = epi0();
       e5.out1 = h->r2; e5.in1 = h->r; e5.in2 = h->v0;
       launch_gemv_n(1, false, EPN_REFINE, h->A, h->lda, m, n, h->tn, nullptr, g, h->part_n, h->cnt_n, e5, h->st, s);
-      EpiArgs e6 = epi0();
-      e6.out1 = h->z;
-      launch_trmv(false, EPR_RAW, h->Mt, h->T, q, h->r2, h->part_tr, h->cnt_tr, e6, h->st, s);
       EpiArgs e7 = epi0();
       e7.y = h->y; e7.yt = h->yt; e7.dy = h->dy; e7.w = h->w; e7.in1 = h->v0;
-      launch_trmv(true, EPR_FAT_Y, h->Mt, h->T, q, h->z, h->part_tr, h->cnt_tr, e7, h->st, s);
+      apply_inverse(h, h->r2, EPR_FAT_Y, e7, s);
     }
     // x = c + A^T (d - y) ; x~ = c - x ; dual residual
     EpiArgs e8 = epi0();
@@ -398,7 +401,10 @@ int kernels_per_iteration(const pogs_handle* h, int refine, int cg_steps) {
   const int pk = csr_pack_launches(h->geom, (int)h->m, (int)h->n);
   if (cg_steps > 0 || h->indirect)   // prox, 2 passes, CGLS init (3), 4 per step, finish, check
     return 8 + 4 * cg_steps + pk;
-  return 6 + (refine ? 4 : 0) + pk;   // prox, 2 A passes, 2 triangle products, check (+ refinement)
+  // prox, 2 A passes, check, the inverse (one symmetric or two triangular products) (+ refinement:
+  // 2 passes and the inverse again)
+  const int inv = h->St ? 1 : 2;
+  return 4 + inv + (refine ? 2 + inv : 0) + pk;
 }
 
 int build_graph(pogs_handle* h, int refine, int mode, int cg_steps) {
@@ -669,8 +675,31 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order, const Cs
   phase("cholesky");
   // ---- M = L^{-1} (FP32; already complete after the recursive factorization), packed tiles --
   if (!recursive) TRY(tri_inverse_f32(Lf, ldq, q, Md, ldq, wk, h->sp.chol_prec == POGS_CHOL_MIXED, err, s));
-  TRY(dalloc(h, &h->Mt, (size_t)h->T * (h->T + 1) / 2 * kTile * kTile));
-  launch_pack_tiles(Md, ldq, q, h->T, h->Mt, s);
+  if (h->sp.chol_prec == POGS_CHOL_MIXED && q >= 1024) {
+    // S = M^T M = (I + G)^{-1}, lower tiles on the tensor cores (TF32x3); each iteration then
+    // applies it in one pass over its packed triangle instead of M and M^T in two.  From q = 1024
+    // on, where the inverse's own products are TF32x3 already; below, M v and M^T z in FP32 keep
+    // the iterates closest to the FP64 trajectory and cost little.
+    float* S = nullptr;
+    TRY(scr.get(&S, (size_t)(ldq * ldq), s));
+    size_t need = 0;
+    // X = Y = M^T, zero for k < i (M lower triangular): each tile skips the K boxes before its rows
+    if (tc_gemm_tf32x3(q, q, q, Md, ldq, true, Md, ldq, true, 1.0f, S, nullptr, ldq, TC_EPI_STORE, true, nullptr, 0,
+                       &need, err, s, true) == 0) {
+      char* ws = nullptr;
+      TRY(scr.get(&ws, need, s));
+      if (tc_gemm_tf32x3(q, q, q, Md, ldq, true, Md, ldq, true, 1.0f, S, nullptr, ldq, TC_EPI_STORE, true, ws, need,
+                         nullptr, err, s, true) == 0) {
+        TRY(dalloc(h, &h->St, (size_t)h->T * (h->T + 1) / 2 * kTile * kTile));
+        TRY(dalloc(h, &h->part_sy, (size_t)h->T * h->T * kTile));
+        launch_pack_tiles(S, ldq, q, h->T, h->St, s, true);
+      }
+    }
+  }
+  if (!h->St) {
+    TRY(dalloc(h, &h->Mt, (size_t)h->T * (h->T + 1) / 2 * kTile * kTile));
+    launch_pack_tiles(Md, ldq, q, h->T, h->Mt, s);
+  }
   CK(cudaGetLastError());
   phase("inverse");
   CK(cudaStreamSynchronize(s));
@@ -1151,11 +1180,19 @@ int pogs_time_kernels(pogs_handle* h, int reps, double* ms, double* bytes) {
     b[1] = At + 12 * m + 20 * n;                            // A^T [d, nu, y~] ; c, mu, E in ; r, x~ out
     b[2] = tri + 8 * q;
     b[3] = tri + 20 * q;                                   // z, c, x~ in ; x, x~ out
+    if (h->St) {
+      b[2] = tri + 24 * q;                                 // S tiles; r, c, x~ in ; x, x~ out
+      b[3] = 0.0;
+    }
     b[4] = An + 8 * n + 24 * m;                            // A [x, x^] ; d, y^, D, y~ in ; y, y~ out
   } else {
     b[1] = An + 8 * n + 16 * m;                            // A [c, x^] ; d, y^, D in ; r out
     b[2] = tri + 8 * q;
     b[3] = tri + 24 * q;                                   // z, d, y~ in ; y, y~, w out
+    if (h->St) {
+      b[2] = tri + 28 * q;                                 // S tiles; r, d, y~ in ; y, y~, w out
+      b[3] = 0.0;
+    }
     b[4] = At + 12 * m + 20 * n;                           // A^T [w, nu, y~] ; c, mu, E in ; x, x~ out
   }
   b[5] = 0.0;
@@ -1196,11 +1233,22 @@ int pogs_time_kernels(pogs_handle* h, int reps, double* ms, double* bytes) {
       }
       case 2: {
         EpiArgs e = epi0();
+        if (h->St) {   // the whole inverse in one symmetric pass
+          if (h->tall) {
+            e.x = h->x; e.xt = h->xt; e.cx = h->cx;
+            launch_symv(EPR_TALL_X, h->St, h->T, Q, h->r, h->part_sy, h->cnt_tr, e, h->st, s);
+          } else {
+            e.y = h->y; e.yt = h->yt; e.dy = h->dy; e.w = h->w;
+            launch_symv(EPR_FAT_Y, h->St, h->T, Q, h->r, h->part_sy, h->cnt_tr, e, h->st, s);
+          }
+          break;
+        }
         e.out1 = h->z;
         launch_trmv(false, EPR_RAW, h->Mt, h->T, Q, h->r, h->part_tr, h->cnt_tr, e, h->st, s);
         break;
       }
       case 3: {
+        if (h->St) break;
         EpiArgs e = epi0();
         if (h->tall) {
           e.x = h->x; e.xt = h->xt; e.cx = h->cx;
