@@ -117,11 +117,17 @@ enum { POGS_PROJ_DIRECT = 0, POGS_PROJ_CGLS = 1 };
 /* Arithmetic of the Cholesky factorization of I + G (Section 3.5). */
 enum {
   POGS_CHOL_FP64 = 0,  /* every operation in FP64                                          */
-  POGS_CHOL_MIXED = 1  /* FP64 diagonal blocks, panel solves and Schur complement; trailing
-                          products of the FP32-rounded panel formed in FP32                 */
+  POGS_CHOL_MIXED = 1  /* Schur complement carried as a double-float pair (error-free
+                          transformations), 128-blocks factored in FP32, products in FP32
+                          (SIMT) or, for blocks of 512 and more, TF32x3 on the tensor cores
+                          (about 21 significant bits); from q = 4096 on recursive, with the
+                          inverse formed alongside; from q = 1024 on the iteration applies
+                          S = (I + G)^{-1} in one symmetric pass                             */
 };
 
-/* Timing/precision report of pogs_setup. */
+/* Timing/precision report of pogs_setup.  factor_ms covers the factorization (and, when it is
+ * recursive, the inverse formed alongside); inverse_ms the remaining inverse work, the
+ * symmetric operator S and the tile packing. */
 typedef struct {
   double ingest_ms, equil_ms, gram_ms, factor_ms, inverse_ms;
   int gram_prec_used, chol_prec_used;
@@ -325,7 +331,8 @@ int pogs_get_setup_report(const pogs_handle* hdl, pogs_setup_report* r);
  * events, averaged over `reps` launches (reps >= 1) after one warm-up launch of each.
  * ms[0..5]: prox step, first A pass (column sums if m >= n, row dots if m < n), L^{-1}
  * product, L^{-T} product, second A pass, stopping/adaptive-rho check; ms[6]: one whole
- * iteration.  bytes[0..6]: the algorithmic HBM bytes each launch must move (A once per pass,
+ * iteration.  When the iteration applies S = (I + G)^{-1} in one symmetric pass, ms[2] is that
+ * pass and ms[3] (and bytes[3]) are 0.  bytes[0..6]: the algorithmic HBM bytes each launch must move (A once per pass,
  * the triangle q(q+1)/2 once per product, the vectors it reads and writes).  Either array
  * may be NULL.  Overwrites the iterate state of the last solve (solve again before reading
  * results).  Errors: ARG (no prior solve, reps < 1), CUDA. */
