@@ -342,6 +342,13 @@ int pogs_time_kernels(pogs_handle* hdl, int reps, double* ms, double* bytes);
  * included). */
 long long pogs_kernel_launches(void);
 
+/* Failure detection: every device-side wait of the tensor-core kernels (mbarrier phases of the
+ * TMA / MMA pipeline) is bounded (about 2 s of SM clock) and reports POGS_ERR_TIMEOUT instead of
+ * spinning forever.  This runs that wait once on a barrier no thread completes, on `stream`,
+ * and returns its status: POGS_ERR_TIMEOUT when the bound works (the context stays usable),
+ * POGS_ERR_CUDA / POGS_ERR_OOM on a runtime failure. */
+int pogs_check_bounded_wait(void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,8 @@ lib.pogs_setup.argtypes = [_P, C.c_int64, C.c_int64, C.c_int64, C.c_char, C.POIN
 lib.pogs_setup.restype = C.c_int
 lib.pogs_setup_csr.argtypes = [C.c_int64, C.c_int64, C.c_int64, _P, _P, _P, C.POINTER(pogs_params), _P, C.POINTER(_P)]
 lib.pogs_setup_csr.restype = C.c_int
+lib.pogs_check_bounded_wait.argtypes = [_P]
+lib.pogs_check_bounded_wait.restype = C.c_int
 lib.pogs_solve.argtypes = [_P, C.POINTER(pogs_fn), C.POINTER(pogs_fn), C.POINTER(pogs_params), _P, _P, _P, _P,
                            C.POINTER(pogs_info)]
 lib.pogs_solve.restype = C.c_int

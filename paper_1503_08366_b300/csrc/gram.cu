@@ -498,4 +498,33 @@ int tc_gemm_nn_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t l
                         scratch_bytes, need_bytes, err, s);
 }
 
+namespace {
+// One thread waits, with the bounded wait every tcgen05 kernel uses, on a barrier whose phase
+// no thread completes; the wait gives up after its budget and the status says so.
+__global__ void bounded_wait_probe_kernel(int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    *status = tc::mbar_wait(&bar, 0) ? 0 : POGS_ERR_TIMEOUT;
+  }
+}
+}  // namespace
+
+int bounded_wait_probe(cudaStream_t s) {
+  void* q = nullptr;
+  if (pool_alloc(&q, sizeof(int), s) != 0) return POGS_ERR_OOM;
+  int* d = static_cast<int*>(q);
+  int h = POGS_ERR_CUDA;
+  count_launch();
+  bounded_wait_probe_kernel<<<1, 32, 0, s>>>(d);
+  if (cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    h = POGS_ERR_CUDA;
+  }
+  cudaFreeAsync(d, s);
+  return h;
+}
+
 }  // namespace pogs

@@ -208,6 +208,8 @@ int tc_gemm_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
                    int64_t ldb, bool transB, float alpha, float* C, float* Clo, int64_t ldc, int epi, bool lower,
                    void* scratch, size_t scratch_bytes, size_t* need_bytes, int* err, cudaStream_t s,
                    bool kskip = false);   // kskip: X[i][k] = Y[i][k] = 0 for k < i (skip those K boxes)
+// Status of one bounded barrier wait that no thread completes (POGS_ERR_TIMEOUT expected).
+int bounded_wait_probe(cudaStream_t s);
 // C = alpha A B (row-major FP32), the special case above.
 int tc_gemm_nn_tf32x3(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
                       float alpha, float* C, int64_t ldc, void* scratch, size_t scratch_bytes, size_t* need_bytes,

@@ -1305,6 +1305,10 @@ int pogs_time_kernels(pogs_handle* h, int reps, double* ms, double* bytes) {
 
 }  // extern "C"
 
+extern "C" int pogs_check_bounded_wait(void* stream) {
+  return pogs::bounded_wait_probe(static_cast<cudaStream_t>(stream));
+}
+
 extern "C" int pogs_gram(const float* A, int64_t m, int64_t n, int64_t lda, int gram_prec, float* G, void* stream) {
   if (!A || !G || m < 1 || n < 1 || lda < n || gram_prec < POGS_GRAM_BF16 || gram_prec > POGS_GRAM_FP32)
     return POGS_ERR_ARG;
