@@ -226,6 +226,7 @@ void sgemm_launch(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, 
 // ---- diagonal block ------------------------------------------------------------------------
 constexpr int kDB = 128;        // block edge
 constexpr int kDS = kDB + 1;    // shared row pitch (conflict-free column walks)
+constexpr int kDiagThreads = 512;   // 16 warps: one 128-block per CTA, latency-bound phases
 
 // One CTA factors the nb x nb diagonal block Hkk (hi part, lower triangle read) in FP32 and
 // writes W = L_kk^{-1} (lower triangular, zero above the diagonal) to W (ld ldw).  Rows and
@@ -234,14 +235,14 @@ constexpr int kDS = kDB + 1;    // shared row pitch (conflict-free column walks)
 // shuffles) and inverts it (lane = column, forward substitution on e_c); all warps then form
 // the panel below it, P = S_panel V^T, and update the trailing rows.  The off-diagonal blocks
 // of W follow by block forward substitution, W_ij = -W_ii sum_{k=j}^{i-1} L_ik W_kj.
-__global__ void __launch_bounds__(256) chol_diag_kernel(const float* __restrict__ Hkk, int64_t ldh, int nb,
+__global__ void __launch_bounds__(kDiagThreads) chol_diag_kernel(const float* __restrict__ Hkk, int64_t ldh, int nb,
                                                         float* __restrict__ W, int64_t ldw, int* err) {
   extern __shared__ float sm[];
   float* S = sm;               // [128][129]: Schur block, then L
   float* V = S + kDB * kDS;    // [128][129]: W in the lower triangle; panel and T scratch
   float* Dv = V + kDB * kDS;   // [128]: 1 / L_jj
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < kDB * kDB; e += 256) {
+  for (int e = tid; e < kDB * kDB; e += kDiagThreads) {
     const int i = e >> 7, k = e & 127;
     float v = 0.0f;
     if (i < nb && k <= i) v = Hkk[(int64_t)i * ldh + k];
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(const float* __restrict_
     __syncthreads();
     const int rows = kDB - o - 32;   // 96, 64, 32, 0: whole warps
     // panel P = S_panel V_jj^T into the (still unused) lower part of V; task = one element
-    for (int t = tid; t < rows * 32; t += 256) {
+    for (int t = tid; t < rows * 32; t += kDiagThreads) {
       const int rr = o + 32 + (t % rows), cc = t / rows;
       const float* Sr = S + rr * kDS + o;
       const float* Vc = V + (o + cc) * kDS + o;
@@ -321,12 +322,12 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(const float* __restrict_
     if (rows > 0) {
       // P back into S (the factor's panel), and S[i][k] -= sum_c P[i][c] P[k][c] for
       // o+32 <= k <= i < 128 in 4 x 4 register blocks
-      for (int e = tid; e < rows * 32; e += 256) {
+      for (int e = tid; e < rows * 32; e += kDiagThreads) {
         const int rr = o + 32 + (e >> 5), cc = o + (e & 31);
         S[rr * kDS + cc] = V[rr * kDS + cc];
       }
       const int nbk = rows / 4;
-      for (int b = tid; b < nbk * nbk; b += 256) {
+      for (int b = tid; b < nbk * nbk; b += kDiagThreads) {
         const int bi = b / nbk, bk = b - bi * nbk;
         if (bk > bi) continue;
         const int i0 = o + 32 + bi * 4, k0 = o + 32 + bk * 4;
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(const float* __restrict_
   // the (j, bi) block of V (strictly above the block diagonal, never part of W), then
   // W_{bi,j} = -V_{bi} T_j.  Task = 4 x 4 outputs.
   for (int bi = 1; bi < 4; ++bi) {
-    for (int t = tid; t < bi * 64; t += 256) {
+    for (int t = tid; t < bi * 64; t += kDiagThreads) {
       const int j = t >> 6, r0 = ((t >> 3) & 7) * 4, c0 = (t & 7) * 4;
       float a[4][4];
 #pragma unroll
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(const float* __restrict_
         for (int y = 0; y < 4; ++y) V[(j * 32 + r0 + x) * kDS + bi * 32 + c0 + y] = a[x][y];
     }
     __syncthreads();
-    for (int t = tid; t < bi * 64; t += 256) {
+    for (int t = tid; t < bi * 64; t += kDiagThreads) {
       const int j = t >> 6, r0 = ((t >> 3) & 7) * 4, c0 = (t & 7) * 4;
       float a[4][4];
 #pragma unroll
@@ -410,7 +411,7 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(const float* __restrict_
     }
     __syncthreads();
   }
-  for (int e = tid; e < nb * nb; e += 256) {
+  for (int e = tid; e < nb * nb; e += kDiagThreads) {
     const int i = e / nb, k = e - (e / nb) * nb;
     W[(int64_t)i * ldw + k] = k <= i ? V[i * kDS + k] : 0.0f;
   }
@@ -510,7 +511,7 @@ int chol_mixed(float* G, float* Hlo, int64_t ldh, int64_t q, float* Lf, int64_t 
     for (int64_t k0 = 0; k0 < q; k0 += kDB) {
       const int nb = (int)std::min<int64_t>(kDB, q - k0);
       count_launch();
-      chol_diag_kernel<<<1, 256, kDiagSmem, ca>>>(Hhi + k0 * ldh + k0, ldh, nb, Md + k0 * ldm + k0, ldm, err);
+      chol_diag_kernel<<<1, kDiagThreads, kDiagSmem, ca>>>(Hhi + k0 * ldh + k0, ldh, nb, Md + k0 * ldm + k0, ldm, err);
       const int64_t rest = q - k0 - nb;
       if (rest <= 0) break;
       // L21 = H21 W_kk^T (from the hi part: the pair rounds to hi)
@@ -569,7 +570,7 @@ struct RecCtx {
 void chol_inv_rec(const RecCtx& c, int64_t r0, int64_t n) {
   if (n <= kDB) {
     count_launch();
-    chol_diag_kernel<<<1, 256, kDiagSmem, c.s>>>(c.Hhi + r0 * c.ldh + r0, c.ldh, (int)n, c.Md + r0 * c.ldm + r0,
+    chol_diag_kernel<<<1, kDiagThreads, kDiagSmem, c.s>>>(c.Hhi + r0 * c.ldh + r0, c.ldh, (int)n, c.Md + r0 * c.ldm + r0,
                                                  c.ldm, c.tc.err);
     return;
   }
