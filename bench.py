@@ -484,9 +484,12 @@ def run_serve(args):
     prm = P.pogs_default_params()
     n_req = len(trace)
 
+    big = [min(pool[i % len(pool)].A.shape) > 512 for i in range(n_req)]
+    fin, steps = [], []
+
     def served():
         lat, iters, st = [], [], []
-        with P.Server(int(120e9), large_workers=args.workers, max_resident=8192, params=prm) as srv:
+        with P.Server(int(120e9), large_workers=args.workers, max_resident=args.max_resident, params=prm) as srv:
             t0 = time.monotonic()
             i = 0
             while len(lat) < n_req:
@@ -495,11 +498,14 @@ def run_serve(args):
                     srv.submit(pool[i % len(pool)], i)
                     i += 1
                 if srv.pending() > 0:
+                    ts = time.monotonic()
                     srv.step(args.step_iters)
+                    steps.append(time.monotonic() - ts)
                 else:
                     time.sleep(min(1e-4, max(0.0, trace[i].arrival_s - now)) if i < n_req else 0)
                 for tag, info, _s, _a, done_s, *_ in srv.poll():
                     lat.append(done_s - (t0 + trace[tag].arrival_s))
+                    fin.append((tag, done_s - t0))
                     iters.append(info.iters)
                     st.append(info.status)
             wall = time.monotonic() - t0
@@ -524,13 +530,25 @@ def run_serve(args):
     wall, lat, iters, st = served()
     pwall, plat, pst = plain(args.plain_limit)
     pct = lambda v, q: float(np.percentile(np.asarray(v) * 1e3, q)) if v else None
+
+    def by_class(large):
+        """Completions of one class (large: min(m, n) > 512, served by the worker threads):
+        count, when the last one finished, and how many finished in each 10 s of the run."""
+        t = sorted(d for tag, d in fin if big[tag] == large)
+        if not t:
+            return dict(count=0)
+        return dict(count=len(t), last_s=t[-1], per_10s=np.bincount((np.asarray(t) // 10).astype(int)).tolist())
     print(json.dumps(dict(
         workload="serve", metric="solves/s & p50/p99 latency at eps_rel=1e-3, served vs plain",
         value=len(lat) / wall, unit="solves/s", latency_ms=dict(p50=pct(lat, 50), p99=pct(lat, 99)),
         statuses={str(s_): st.count(s_) for s_ in set(st)}, iters_mean=float(np.mean(iters)),
+        small=by_class(False), large=by_class(True),
+        step_calls=dict(count=len(steps), total_s=float(np.sum(steps)), p50_ms=pct(steps, 50),
+                        max_ms=pct(steps, 100)),
         plain=dict(value=len(plat) / pwall, unit="solves/s", served=len(plat), of=n_req,
                    latency_ms=dict(p50=pct(plat, 50), p99=pct(plat, 99)), limit_s=args.plain_limit),
         config=dict(requests=n_req, rate_hz=2000, budget_gb=120, payload_pool=len(pool), step_iters=args.step_iters,
+                    max_resident=args.max_resident,
                     large_workers=args.workers, m="log-U[100,8000]", n="log-U[50,4000]",
                     classes="lasso,logistic,huber,svm,nnls"))))
 
@@ -736,10 +754,11 @@ def main():
     ap.add_argument("--workload", default="large", choices=["large", "batch", "serve", "precision", "next"])
     ap.add_argument("--count", type=int, default=2048, help="batch workload: instances")
     ap.add_argument("--plain-sample", type=int, default=128, help="batch workload: plain-path sample")
-    ap.add_argument("--requests", type=int, default=4000, help="serve workload: requests in the trace")
+    ap.add_argument("--requests", type=int, default=20000, help="serve workload: requests in the trace")
     ap.add_argument("--pool", type=int, default=256, help="serve workload: distinct payloads")
     ap.add_argument("--workers", type=int, default=8, help="serve workload: threads for large requests")
     ap.add_argument("--step-iters", type=int, default=25, help="serve workload: iterations per step")
+    ap.add_argument("--max-resident", type=int, default=8192, help="serve workload: resident small requests")
     ap.add_argument("--plain-limit", type=float, default=60.0, help="serve workload: seconds for the plain run")
     ap.add_argument("--loop-mode", type=int, default=0,
                     help="0: one graph per solve (conditional WHILE node); 1: host-checked loop over a "

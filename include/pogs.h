@@ -244,23 +244,30 @@ typedef struct {
 /* Create a server that keeps admitted requests resident on the device within `hbm_budget`
  * bytes (matrix, factor, scalings and ADMM state; an estimate of each request's footprint is
  * charged at admission and released at completion).  Requests with min(m, n) <= 512 are
- * stepped together by the batched engine, at most `max_resident` of them at a time; larger
- * ones run on `large_workers` host threads with their own streams through the single-problem
- * path.  `stream` carries the batched work.  Errors: ARG, OOM. */
+ * stepped together by the batched engine, at most `max_resident` of them at a time, admitted
+ * first come first served by pogs_server_step; larger ones run on `large_workers` host threads
+ * with their own streams through the single-problem path, each admitted (and charged) when a
+ * worker starts it, in arrival order.  The two queues are independent: a large request waiting
+ * for a worker does not hold back small ones.  The two take turns on the device: a step runs alone, large solves run together, and
+ * every large solve that waited through a step starts before the next step.  `stream` carries
+ * the batched work.  Errors: ARG, OOM. */
 int pogs_server_create(size_t hbm_budget, int large_workers, int max_resident, const pogs_params* p,
                        void* stream, pogs_server** out);
 
-/* Queue a request.  The problem's arrays and the output arrays (host or device, may be NULL)
- * must stay valid until the request is returned by pogs_server_poll.  Errors: ARG, CAPACITY
+/* Queue a request (host work only: no CUDA call).  The problem's arrays and the output arrays
+ * (host or device, may be NULL) must stay valid until the request is returned by
+ * pogs_server_poll.  Device inputs are read after work queued before this call on the server's
+ * stream (on the legacy default stream when the server was created without one).  Errors: ARG, CAPACITY
  * (a footprint above the whole budget). */
 int pogs_server_submit(pogs_server* s, const pogs_problem* prob, float* x, float* y, float* mu, float* nu,
                        int64_t tag);
 
-/* One step of continuous batching: admit waiting requests (first come, first served) while
- * the budget allows, set up the new ones, advance every resident batched request by up to
+/* One step of continuous batching: admit waiting small requests (first come, first served)
+ * while the budget and the slots allow, set up the new ones, advance every resident batched request by up to
  * `iters` iterations (Algorithm 1 with its adaptive rho, continued exactly from the previous
  * step), and retire the finished ones (outputs copied).  Large requests progress on their own
- * threads.  Returns when the step's device work is done.  Errors: ARG, OOM, CUDA. */
+ * threads between steps; a step waits for the large solves under way to finish.  Returns when
+ * the step's device work is done.  Errors: ARG, OOM, CUDA. */
 int pogs_server_step(pogs_server* s, int iters);
 
 /* Move up to `max` finished requests into `out`; returns how many. */

@@ -5,9 +5,10 @@
 // iteration kernel once over every resident request, advancing each by up to `iters`
 // iterations from its saved loop state; requests admitted between steps join at the next one
 // and finished ones retire (outputs copied, memory released) after it.  Larger requests run
-// through the single-problem path on worker threads with their own streams, concurrently with
-// the batched steps.  A request's result does not depend on what else is resident: the batched
-// engine's arithmetic is fixed per instance and exact across step boundaries.
+// through the single-problem path on worker threads with their own streams.  The two kinds take
+// turns on the device (GpuGate below).  A request's result does not depend on what else is
+// resident: the batched engine's arithmetic is fixed per instance and exact across step
+// boundaries.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -19,6 +20,7 @@
 #include <vector>
 
 #include "batch.h"
+#include "gate.h"
 #include "kernels.h"
 
 using namespace pogs;
@@ -40,6 +42,20 @@ bool is_dev(const void* p) {
 }
 
 constexpr int kSmallMaxQ = 512;
+
+// A step's hold on the gate, released on every return path.
+struct StepHold {
+  GpuGate* g = nullptr;
+  void take(GpuGate& gate) {
+    gate.write_lock();
+    g = &gate;
+  }
+  void release() {
+    if (g) g->write_unlock();
+    g = nullptr;
+  }
+  ~StepHold() { release(); }
+};
 
 struct SReq {
   int64_t tag = 0;
@@ -87,16 +103,17 @@ struct pogs_server {
   BInst* d_new = nullptr;
   int* d_queue = nullptr;
   std::vector<int> free_slots;
-  std::deque<SReq*> waiting;
+  std::deque<SReq*> waiting;         // small requests not yet admitted
   std::vector<SReq*> active;
   std::vector<pogs_server_done> done;
   std::vector<BOut> h_outs;
   std::vector<BLoop> h_loops;
   // large requests
   std::vector<std::thread> workers;
-  std::deque<SReq*> large_q;
+  std::deque<SReq*> large_q;         // large requests not yet started by a worker
   std::mutex mu;
   std::condition_variable cv;
+  GpuGate gate;
   bool stop = false;
   int large_inflight = 0;
   int64_t submitted = 0, completed = 0;
@@ -105,23 +122,35 @@ struct pogs_server {
 namespace {
 
 void worker_main(pogs_server* S) {
-  // large requests run at the lowest stream priority, so that the block scheduler places the
-  // batched engine's CTAs first when both are pending
+  // large requests run on low-priority streams; they take turns with the batched steps (the
+  // gate), so the priority only orders what is left pending at a turn's boundary
   cudaStream_t st;
+  cudaEvent_t ev = nullptr;
   int lo = 0, hi = 0;
   cudaDeviceGetStreamPriorityRange(&lo, &hi);
   if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, lo) != cudaSuccess) {
     cudaGetLastError();
     st = nullptr;
   }
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    ev = nullptr;
+  }
   while (true) {
     SReq* r = nullptr;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv.wait(lk, [&] { return S->stop || !S->large_q.empty(); });
-      if (S->large_q.empty()) break;
+      // a large request is charged to the budget when a worker starts it: queued, it holds
+      // no device memory
+      S->cv.wait(lk, [&] {
+        return S->stop || (!S->large_q.empty() && S->used + S->large_q.front()->bytes <= S->budget);
+      });
+      if (S->stop) break;
       r = S->large_q.front();
       S->large_q.pop_front();
+      S->used += r->bytes;
+      ++S->large_inflight;
+      r->t_admit = now_s();
     }
     pogs_server_done d;
     memset(&d, 0, sizeof(d));
@@ -129,11 +158,19 @@ void worker_main(pogs_server* S) {
     d.submit_s = r->t_submit;
     d.admit_s = r->t_admit;
     pogs_handle* h = nullptr;
+    // device inputs written before the submission, on the server's stream (or the legacy
+    // default stream when the server owns its stream), are ordered before their use here
+    if (st && ev) {
+      cudaEventRecord(ev, S->own_stream ? (cudaStream_t)0 : S->stream);
+      cudaStreamWaitEvent(st, ev, 0);
+    }
+    S->gate.read_lock();
     int rc = pogs_setup(r->prob.A, r->prob.m, r->prob.n, r->prob.lda, 'R', &S->p, st, &h);
     if (rc == 0) {
       rc = pogs_solve(h, &r->prob.f, &r->prob.g, &S->p, r->x, r->y, r->mu, r->nu, &d.info);
       pogs_free(h);
     }
+    S->gate.read_unlock();
     d.info.status = rc;
     d.done_s = now_s();
     {
@@ -143,8 +180,10 @@ void worker_main(pogs_server* S) {
       --S->large_inflight;
       ++S->completed;
     }
+    S->cv.notify_all();
     delete r;
   }
+  if (ev) cudaEventDestroy(ev);
   if (st) cudaStreamDestroy(st);
 }
 
@@ -278,12 +317,9 @@ int pogs_server_submit(pogs_server* S, const pogs_problem* prob, float* x, float
                        int64_t tag) {
   if (!S || !prob || !prob->A || prob->m < 1 || prob->n < 1 || prob->lda < prob->n || !prob->f.h || !prob->g.h)
     return POGS_ERR_ARG;
-  if (S->own_stream) {
-    // device inputs written on the legacy default stream are ordered before their use on the
-    // server's internal (non-blocking) stream
-    cudaEventRecord(S->ev_in, 0);
-    cudaStreamWaitEvent(S->stream, S->ev_in, 0);
-  }
+  // no CUDA call here: with the workers busy in the driver, each one could wait milliseconds,
+  // and submission is on the caller's critical path.  The stream ordering of device inputs is
+  // set up when a request is admitted (pogs_server_step, worker_main).
   SReq* r = new SReq();
   r->tag = tag;
   r->prob = *prob;
@@ -295,37 +331,45 @@ int pogs_server_submit(pogs_server* S, const pogs_problem* prob, float* x, float
     return POGS_ERR_CAPACITY;
   }
   r->t_submit = now_s();
-  std::lock_guard<std::mutex> lk(S->mu);
-  S->waiting.push_back(r);
-  ++S->submitted;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    (r->small ? S->waiting : S->large_q).push_back(r);
+    ++S->submitted;
+  }
+  if (!r->small) S->cv.notify_all();
   return 0;
 }
 
 int pogs_server_step(pogs_server* S, int iters) {
   if (!S || iters < 1) return POGS_ERR_ARG;
   cudaStream_t s = S->stream;
-  // ---- admission: first come first served, within the memory budget and the slot count -----
+  // ---- admission of small requests: first come first served, within the memory budget and
+  // the slot count (large requests are admitted by the workers, in their own order) ----------
   std::vector<SReq*> fresh;
   {
     std::unique_lock<std::mutex> lk(S->mu);
     while (!S->waiting.empty()) {
       SReq* r = S->waiting.front();
-      if (S->used + r->bytes > S->budget) break;
-      if (r->small && S->free_slots.empty()) break;
+      if (S->used + r->bytes > S->budget || S->free_slots.empty()) break;
       S->waiting.pop_front();
       S->used += r->bytes;
       r->t_admit = now_s();
-      if (r->small) {
-        r->slot = S->free_slots.back();
-        S->free_slots.pop_back();
-        fresh.push_back(r);
-      } else {
-        ++S->large_inflight;
-        S->large_q.push_back(r);
-        S->cv.notify_one();
-      }
+      r->slot = S->free_slots.back();
+      S->free_slots.pop_back();
+      fresh.push_back(r);
     }
   }
+  if (fresh.empty() && S->active.empty()) return 0;
+  if (!fresh.empty() && S->own_stream) {
+    // device inputs written on the legacy default stream before their submission are ordered
+    // before their use on the server's internal (non-blocking) stream
+    if (cudaEventRecord(S->ev_in, 0) != cudaSuccess || cudaStreamWaitEvent(s, S->ev_in, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return POGS_ERR_CUDA;
+    }
+  }
+  StepHold hold;
+  hold.take(S->gate);
   for (SReq* r : fresh) {
     if (cudaMallocAsync((void**)&r->arena, r->bytes, s) != cudaSuccess) {
       cudaGetLastError();
@@ -364,6 +408,7 @@ int pogs_server_step(pogs_server* S, int iters) {
     cudaGetLastError();
     return POGS_ERR_CUDA;
   }
+  hold.release();
   // ---- retire finished requests ------------------------------------------------------------------
   std::vector<SReq*> keep;
   const double t = now_s();
@@ -410,6 +455,7 @@ int pogs_server_step(pogs_server* S, int iters) {
     delete r;
   }
   S->active.swap(keep);
+  S->cv.notify_all();   // budget returned: a worker may start a large request
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return POGS_ERR_CUDA;
@@ -446,6 +492,7 @@ void pogs_server_destroy(pogs_server* S) {
     delete r;
   }
   for (SReq* r : S->waiting) delete r;
+  for (SReq* r : S->large_q) delete r;
   cudaFree(S->d_outs);
   cudaFree(S->d_loops);
   cudaFree(S->d_active);
