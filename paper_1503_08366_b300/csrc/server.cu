@@ -115,7 +115,6 @@ struct pogs_server {
   std::condition_variable cv;
   GpuGate gate;
   bool stop = false;
-  int large_inflight = 0;
   int64_t submitted = 0, completed = 0;
 };
 
@@ -149,7 +148,6 @@ void worker_main(pogs_server* S) {
       r = S->large_q.front();
       S->large_q.pop_front();
       S->used += r->bytes;
-      ++S->large_inflight;
       r->t_admit = now_s();
     }
     pogs_server_done d;
@@ -177,7 +175,6 @@ void worker_main(pogs_server* S) {
       std::lock_guard<std::mutex> lk(S->mu);
       S->done.push_back(d);
       S->used -= r->bytes;
-      --S->large_inflight;
       ++S->completed;
     }
     S->cv.notify_all();
@@ -390,10 +387,8 @@ int pogs_server_step(pogs_server* S, int iters) {
     int rc = batch_setup(S->d_new, (int)hn.size(), S->cfg, s);
     if (rc != 0) return rc;
   }
-  if (S->active.empty()) return 0;
   // ---- one launch advances every resident request ------------------------------------------
   std::vector<BInst> ha;
-  std::vector<int> order;
   for (SReq* r : S->active) ha.push_back(r->inst);
   const int na = (int)ha.size();
   if (cudaMemcpyAsync(S->d_active, ha.data(), sizeof(BInst) * na, cudaMemcpyHostToDevice, s) != cudaSuccess ||
