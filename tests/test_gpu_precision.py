@@ -130,3 +130,23 @@ def test_full_size_nnls_against_stored_oracle(P):
         kkt = np.linalg.norm(rhs - (x64 + Ah.T @ (Ah @ x64))) / np.linalg.norm(rhs)
         assert kkt < PROJ_TOL.get((gram, refine), 1e-5), (gram, refine, kkt)
         del Ah
+
+
+def test_full_size_lp_against_stored_oracle(P):
+    """30000 x 15000 inequality-form LP (10% nonzeros stored dense), every converging mode,
+    against the stored oracle results: within 1e-3 of the oracle stopped by the same test, and
+    within the LP bound 1e-2 of p* (the oracle itself stops 1.1e-3 from p* at eps_rel = 1e-3)."""
+    import torch
+    path = os.path.join(GOLDEN, "precision_lp_30000x15000.json")
+    ref = json.load(open(path))
+    prob = W.lp_precision_large()
+    assert (prob.m, prob.n, int(prob.meta["seed"])) == (ref["m"], ref["n"], ref["seed"])
+    same, pstar = ref["same_tol"]["obj"], ref["tight"]["obj"]
+    Adev = torch.from_numpy(prob.A).cuda()
+    for gram, refine in sorted(CONVERGE):
+        prm = P.pogs_default_params(gram_prec=gram, refine_steps=refine, max_iter=20000)
+        with P.Solver(Adev, prm) as s:
+            info, *_ = s.solve(prob.f, prob.g)
+        assert info.status == 0, (gram, refine, info.as_dict())
+        assert abs(info.obj - same) <= 1e-3 * max(1.0, abs(same)), (gram, refine, info.obj, same)
+        assert abs(info.obj - pstar) <= 1e-2 * max(1.0, abs(pstar)), (gram, refine, info.obj, pstar)
