@@ -83,3 +83,18 @@ def test_batch_logistic_instances_converge_and_match_oracle(P):
         if k % 3 == 0:
             ref = _tight(prob)
             assert abs(info.obj - ref.obj) <= 1e-3 * max(1.0, abs(ref.obj)), (k, info.obj, ref.obj)
+
+
+def test_the_mix_iteration_tail_is_the_methods(P):
+    """The batch mix's slowest instances are slow under the method itself: a near-square Huber
+    instance (183 x 199) takes 5377 iterations in the FP64 oracle and, within 2%, as many in
+    the batched engine; another (175 x 184) reaches the 10000-iteration cap in both."""
+    slow, stuck = W.batch_mix_instance(880), W.batch_mix_instance(742)
+    assert (slow.name, slow.A.shape, stuck.name, stuck.A.shape) == ("huber", (183, 199), "huber", (175, 184))
+    res = P.pogs_solve_batch([slow, stuck], P.pogs_default_params(max_iter=10000))
+    ref = OA.solve(slow.A, slow.f, slow.g, OA.Params(max_iter=10000))
+    assert ref.status == 0 and res[0][0].status == 0, (ref.status, res[0][0].as_dict())
+    assert abs(res[0][0].iters - ref.iters) <= 0.02 * ref.iters, (res[0][0].iters, ref.iters)
+    assert abs(res[0][0].obj - ref.obj) <= 1e-3 * max(1.0, abs(ref.obj)), (res[0][0].obj, ref.obj)
+    ref2 = OA.solve(stuck.A, stuck.f, stuck.g, OA.Params(max_iter=10000))
+    assert ref2.status == 1 and res[1][0].status == 1 and res[1][0].iters == 10000

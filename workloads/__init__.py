@@ -311,17 +311,20 @@ def logistic_fat_large(seed: int = 10_001) -> Problem:
     return logistic(2000, 40000, seed, nnz_frac=0.05, lam_frac=0.05)
 
 
+def batch_mix_instance(i: int, base_seed: int = 20_000, m_range=(64, 2048), n_range=(32, 512),
+                       classes=("lasso", "huber", "svm", "nnls")) -> Problem:
+    """Instance i of `batch_mix`, built on its own from its seed."""
+    rng = _rng(base_seed + i)
+    cls = classes[int(rng.integers(len(classes)))]
+    m = _log_uniform_int(rng, *m_range)
+    n = _log_uniform_int(rng, *n_range)
+    return CLASSES[cls](m, n, base_seed + 100_000 + i)
+
+
 def batch_mix(count: int = 2048, base_seed: int = 20_000, m_range=(64, 2048), n_range=(32, 512),
               classes=("lasso", "huber", "svm", "nnls")) -> list:
     """Many small independent instances: class uniform over `classes`, m and n log-uniform."""
-    out = []
-    for i in range(count):
-        rng = _rng(base_seed + i)
-        cls = classes[int(rng.integers(len(classes)))]
-        m = _log_uniform_int(rng, *m_range)
-        n = _log_uniform_int(rng, *n_range)
-        out.append(CLASSES[cls](m, n, base_seed + 100_000 + i))
-    return out
+    return [batch_mix_instance(i, base_seed, m_range, n_range, classes) for i in range(count)]
 
 
 @dataclasses.dataclass
