@@ -88,3 +88,38 @@ def test_setup_csr_rejects_bad_arguments_without_device_work():
     p = P.pogs_default_params(alpha=2.5)
     assert f(2, 2, 2, rp, ci, va, ctypes.byref(p), None, ctypes.byref(h)) == -1
     assert f(2, 2, 2, rp, ci, va, None, None, None) == -1                       # no output
+
+
+def test_server_and_batch_reject_bad_arguments_without_device_work():
+    """The server and batch entry points check their arguments before any CUDA call (ARG = -1);
+    destroying a NULL server is a no-op."""
+    import paper_1503_08366_b300 as P
+    lib = P.lib
+    s = ctypes.c_void_p()
+    assert lib.pogs_server_create(0, 1, 4, None, None, ctypes.byref(s)) == -1          # no budget
+    assert lib.pogs_server_create(1 << 20, -1, 4, None, None, ctypes.byref(s)) == -1   # workers < 0
+    assert lib.pogs_server_create(1 << 20, 1, 0, None, None, ctypes.byref(s)) == -1    # no slots
+    assert lib.pogs_server_create(1 << 20, 1, 4, None, None, None) == -1               # no out
+    pr = P.pogs_problem()
+    assert lib.pogs_server_submit(None, ctypes.byref(pr), None, None, None, None, 0) == -1
+    assert lib.pogs_server_step(None, 25) == -1
+    assert lib.pogs_server_poll(None, None, 0) == -1
+    assert lib.pogs_server_pending(None) == -1
+    lib.pogs_server_destroy(None)
+    out = (P.pogs_result * 2)()
+    probs = (P.pogs_problem * 2)()
+    assert lib.pogs_solve_batch(-1, probs, None, out, None) == -1                      # count < 0
+    assert lib.pogs_solve_batch(2, None, None, out, None) == -1                        # no problems
+    assert lib.pogs_solve_batch(2, probs, None, None, None) == -1                      # no results
+    buf = (ctypes.c_float * 12)()
+    h = (ctypes.c_uint8 * 4)()
+    for k in range(2):
+        probs[k].A = ctypes.cast(buf, ctypes.c_void_p)
+        probs[k].m, probs[k].n, probs[k].lda = 4, 3, 3
+        probs[k].f.h = ctypes.cast(h, ctypes.c_void_p)
+        probs[k].g.h = ctypes.cast(h, ctypes.c_void_p)
+    probs[1].lda = 2                                                                  # lda < n
+    assert lib.pogs_solve_batch(2, probs, None, out, None) == -1
+    probs[1].lda, probs[1].m = 3, 0                                                   # empty
+    assert lib.pogs_solve_batch(2, probs, None, out, None) == -1
+    assert lib.pogs_solve_batch(0, probs, None, out, None) == 0                        # nothing to do
