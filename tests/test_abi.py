@@ -123,3 +123,29 @@ def test_server_and_batch_reject_bad_arguments_without_device_work():
     probs[1].lda, probs[1].m = 3, 0                                                   # empty
     assert lib.pogs_solve_batch(2, probs, None, out, None) == -1
     assert lib.pogs_solve_batch(0, probs, None, out, None) == 0                        # nothing to do
+
+
+def test_handle_entry_points_reject_null_before_device_work():
+    """Every entry point that takes a handle returns ARG (-1) for a NULL handle or a missing
+    required array without touching the device; prox evaluation of zero elements is a no-op."""
+    import paper_1503_08366_b300 as P
+    lib = P.lib
+    fn = P.pogs_fn()
+    info = P.pogs_info()
+    buf = (ctypes.c_float * 8)()
+    assert lib.pogs_solve(None, ctypes.byref(fn), ctypes.byref(fn), None, None, None, None, None,
+                          ctypes.byref(info)) == -1
+    assert lib.pogs_solve_warm(None, ctypes.byref(fn), ctypes.byref(fn), None, None, None, None, None, None,
+                               None, ctypes.byref(info)) == -1
+    assert lib.pogs_get_equil(None, buf, buf) == -1
+    assert lib.pogs_get_ahat(None, buf) == -1
+    assert lib.pogs_project(None, buf, buf, buf, buf, None) == -1
+    rep = P.pogs_setup_report()
+    assert lib.pogs_get_setup_report(None, ctypes.byref(rep)) == -1
+    ms = (ctypes.c_double * 8)()
+    assert lib.pogs_time_kernels(None, 3, ms, ms) == -1
+    h = (ctypes.c_uint8 * 4)()
+    fn.h = ctypes.cast(h, ctypes.c_void_p)
+    assert lib.pogs_prox_eval(None, 4, buf, None, ctypes.c_float(1.0), buf, None) == -1   # no function
+    assert lib.pogs_prox_eval(ctypes.byref(fn), -1, buf, None, ctypes.c_float(1.0), buf, None) == -1
+    assert lib.pogs_prox_eval(ctypes.byref(fn), 0, buf, None, ctypes.c_float(1.0), buf, None) == 0
