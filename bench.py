@@ -192,6 +192,38 @@ def cpu_oracle_estimate(probs, gpu_iters, frac=4, iters_sample=10):
     return len(probs) / total, parts
 
 
+def serve_oracle_check(pool, served_obj, seconds=20.0):
+    """The oracle as it stands, solving the serving pool's distinct payloads one after another
+    until `seconds` have passed (a bounded sample; its sequential throughput is the serving
+    workload's CPU baseline), and each served request that carries a sampled payload checked
+    against the oracle's objective at the same stopping test.
+
+    served_obj: {payload index: [objective of every served request carrying it]}.
+    Returns (cpu_baseline, check)."""
+    from oracle import admm as OA
+    t0 = time.perf_counter()
+    ref = {}
+    for k, pb in enumerate(pool):
+        if ref and time.perf_counter() - t0 >= seconds:
+            break
+        r = OA.solve(pb.A, pb.f, pb.g, OA.Params())
+        ref[k] = (float(r.obj), int(r.status))
+    elapsed = time.perf_counter() - t0
+    errs, checked = [], 0
+    for k, (obj, status) in ref.items():
+        if status != 0:
+            continue
+        for v in served_obj.get(k, []):
+            errs.append(abs(v - obj) / max(1.0, abs(obj)))
+            checked += 1
+    cpu = dict(value=len(ref) / elapsed, unit="solves/s", cores=_threads(), kind="oracle",
+               sample=f"first {len(ref)} of {len(pool)} distinct payloads, solved in sequence ({elapsed:.1f} s)")
+    check = dict(payloads=len(ref), oracle_converged=sum(1 for o in ref.values() if o[1] == 0),
+                 requests_checked=checked, max_rel_obj_err=max(errs) if errs else None,
+                 within_1e_3=sum(e <= 1e-3 for e in errs), within_1e_2=sum(e <= 1e-2 for e in errs))
+    return cpu, check
+
+
 def _threads():
     try:
         from threadpoolctl import threadpool_info
@@ -531,6 +563,7 @@ def run_serve(args):
 
     big = [min(pool[i % len(pool)].A.shape) > 512 for i in range(n_req)]
     fin, steps = [], []
+    served_obj = {}
 
     def served():
         lat, iters, st = [], [], []
@@ -551,6 +584,7 @@ def run_serve(args):
                 for tag, info, _s, _a, done_s, *_ in srv.poll():
                     lat.append(done_s - (t0 + trace[tag].arrival_s))
                     fin.append((tag, done_s - t0))
+                    served_obj.setdefault(tag % len(pool), []).append(info.obj)
                     iters.append(info.iters)
                     st.append(info.status)
             wall = time.monotonic() - t0
@@ -574,6 +608,7 @@ def run_serve(args):
 
     wall, lat, iters, st = served()
     pwall, plat, pst = plain(args.plain_limit)
+    cpu, check = (None, None) if args.no_cpu_baseline else serve_oracle_check(pool, served_obj)
     pct = lambda v, q: float(np.percentile(np.asarray(v) * 1e3, q)) if v else None
 
     def by_class(large):
@@ -587,7 +622,7 @@ def run_serve(args):
         workload="serve", metric="solves/s & p50/p99 latency at eps_rel=1e-3, served vs plain",
         value=len(lat) / wall, unit="solves/s", latency_ms=dict(p50=pct(lat, 50), p99=pct(lat, 99)),
         statuses={str(s_): st.count(s_) for s_ in set(st)}, iters_mean=float(np.mean(iters)),
-        small=by_class(False), large=by_class(True),
+        small=by_class(False), large=by_class(True), cpu_baseline=cpu, oracle_check=check,
         step_calls=dict(count=len(steps), total_s=float(np.sum(steps)), p50_ms=pct(steps, 50),
                         max_ms=pct(steps, 100)),
         plain=dict(value=len(plat) / pwall, unit="solves/s", served=len(plat), of=n_req,
