@@ -192,13 +192,13 @@ def cpu_oracle_estimate(probs, gpu_iters, frac=4, iters_sample=10):
     return len(probs) / total, parts
 
 
-def serve_oracle_check(pool, served_obj, seconds=20.0):
-    """The oracle as it stands, solving the serving pool's distinct payloads one after another
-    until `seconds` have passed (a bounded sample; its sequential throughput is the serving
-    workload's CPU baseline), and each served request that carries a sampled payload checked
-    against the oracle's objective at the same stopping test.
+def oracle_sample_check(pool, served_obj, seconds=20.0):
+    """The oracle as it stands, solving the distinct problems of `pool` one after another until
+    `seconds` have passed (a bounded sample; its sequential throughput is the workload's CPU
+    baseline), and every GPU result for a sampled problem checked against the oracle's
+    objective at the same stopping test.
 
-    served_obj: {payload index: [objective of every served request carrying it]}.
+    served_obj: {index into pool: [objective of every GPU result for that problem]}.
     Returns (cpu_baseline, check)."""
     from oracle import admm as OA
     t0 = time.perf_counter()
@@ -217,7 +217,7 @@ def serve_oracle_check(pool, served_obj, seconds=20.0):
             errs.append(abs(v - obj) / max(1.0, abs(obj)))
             checked += 1
     cpu = dict(value=len(ref) / elapsed, unit="solves/s", cores=_threads(), kind="oracle",
-               sample=f"first {len(ref)} of {len(pool)} distinct payloads, solved in sequence ({elapsed:.1f} s)")
+               sample=f"first {len(ref)} of {len(pool)} distinct problems, solved in sequence ({elapsed:.1f} s)")
     check = dict(payloads=len(ref), oracle_converged=sum(1 for o in ref.values() if o[1] == 0),
                  requests_checked=checked, max_rel_obj_err=max(errs) if errs else None,
                  within_1e_3=sum(e <= 1e-3 for e in errs), within_1e_2=sum(e <= 1e-2 for e in errs))
@@ -517,6 +517,8 @@ def run_batch(args):
             b_sub += res[i][0].iters * (8.0 * m * n + 4.0 * q * (q + 1) + 56.0 * (m + n))
         bulk = dict(count=len(conv), value=len(conv) / t_sub, unit="solves/s", achieved=b_sub / t_sub / 1e9,
                     frac=b_sub / t_sub / 1e9 / peaks["hbm"], iters_max=max(res[i][0].iters for i in conv))
+    cpu, check = (None, None) if args.no_cpu_baseline else \
+        oracle_sample_check(probs, {i: [r[0].obj] for i, r in enumerate(res)})
     # plain: the single-problem path, one instance at a time (a bounded sample, extrapolated)
     k = min(args.plain_sample, len(probs))
     t0 = time.perf_counter()
@@ -530,7 +532,7 @@ def run_batch(args):
                           plain=dict(value=len(probs) / t_plain, unit="solves/s", sample=k),
                           statuses={str(s_): st.count(s_) for s_ in set(st)},
                           iters_mean=float(np.mean([r[0].iters for r in res])),
-                          iters_max=int(max(r[0].iters for r in res)),
+                          iters_max=int(max(r[0].iters for r in res)), cpu_baseline=cpu, oracle_check=check,
                           converged_only=bulk,
                           roofline=dict(bound="hbm", achieved=achieved, peak=peaks["hbm"], unit="GB/s",
                                         frac=achieved / peaks["hbm"], bytes=algo,
@@ -608,7 +610,7 @@ def run_serve(args):
 
     wall, lat, iters, st = served()
     pwall, plat, pst = plain(args.plain_limit)
-    cpu, check = (None, None) if args.no_cpu_baseline else serve_oracle_check(pool, served_obj)
+    cpu, check = (None, None) if args.no_cpu_baseline else oracle_sample_check(pool, served_obj)
     pct = lambda v, q: float(np.percentile(np.asarray(v) * 1e3, q)) if v else None
 
     def by_class(large):
