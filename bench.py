@@ -192,13 +192,15 @@ def cpu_oracle_estimate(probs, gpu_iters, frac=4, iters_sample=10):
     return len(probs) / total, parts
 
 
-def oracle_sample_check(pool, served_obj, seconds=20.0):
+def oracle_sample_check(pool, served_obj, seconds=20.0, one_thread_seconds=0.0):
     """The oracle as it stands, solving the distinct problems of `pool` one after another until
     `seconds` have passed (a bounded sample; its sequential throughput is the workload's CPU
     baseline), and every GPU result for a sampled problem checked against the oracle's
     objective at the same stopping test.
 
     served_obj: {index into pool: [objective of every GPU result for that problem]}.
+    one_thread_seconds > 0 also times the same problems in order with BLAS limited to one
+    thread, for about that long (`value_1thread`).
     Returns (cpu_baseline, check)."""
     from oracle import admm as OA
     t0 = time.perf_counter()
@@ -216,8 +218,21 @@ def oracle_sample_check(pool, served_obj, seconds=20.0):
         for v in served_obj.get(k, []):
             errs.append(abs(v - obj) / max(1.0, abs(obj)))
             checked += 1
-    cpu = dict(value=len(ref) / elapsed, unit="solves/s", cores=_threads(), kind="oracle",
+    cpu = dict(value=len(ref) / elapsed, unit="solves/s", cores=_threads(), cpu_count=os.cpu_count(),
+               kind="oracle",
                sample=f"first {len(ref)} of {len(pool)} distinct problems, solved in sequence ({elapsed:.1f} s)")
+    if one_thread_seconds > 0:
+        from threadpoolctl import threadpool_limits
+        done = 0
+        with threadpool_limits(limits=1):
+            t1 = time.perf_counter()
+            for pb in pool[:len(ref)]:
+                if done and time.perf_counter() - t1 >= one_thread_seconds:
+                    break
+                OA.solve(pb.A, pb.f, pb.g, OA.Params())
+                done += 1
+            cpu["value_1thread"] = done / (time.perf_counter() - t1)
+            cpu["sample_1thread"] = f"first {done} of the same problems, BLAS limited to one thread"
     check = dict(payloads=len(ref), oracle_converged=sum(1 for o in ref.values() if o[1] == 0),
                  requests_checked=checked, max_rel_obj_err=max(errs) if errs else None,
                  within_1e_3=sum(e <= 1e-3 for e in errs), within_1e_2=sum(e <= 1e-2 for e in errs))
@@ -518,7 +533,7 @@ def run_batch(args):
         bulk = dict(count=len(conv), value=len(conv) / t_sub, unit="solves/s", achieved=b_sub / t_sub / 1e9,
                     frac=b_sub / t_sub / 1e9 / peaks["hbm"], iters_max=max(res[i][0].iters for i in conv))
     cpu, check = (None, None) if args.no_cpu_baseline else \
-        oracle_sample_check(probs, {i: [r[0].obj] for i, r in enumerate(res)})
+        oracle_sample_check(probs, {i: [r[0].obj] for i, r in enumerate(res)}, one_thread_seconds=10.0)
     # plain: the single-problem path, one instance at a time (a bounded sample, extrapolated)
     k = min(args.plain_sample, len(probs))
     t0 = time.perf_counter()
