@@ -20,8 +20,9 @@ Modules
   project  graph projection: the KKT form of Eq. 9 and the reduced (block
            elimination) updates of Section 3.5, with an FP64 Cholesky factor.
   admm     Algorithm 1 with over-relaxation (Section 3.2), the feasible iterates of
-           Section 3.3, residual stopping Eq. 11, the half-tuple gap, and
-           Algorithm 3 (adaptive rho); unscaling of the returned tuple.
+           Section 3.3, residual stopping Eq. 11 with the Section 3.4 tolerances, the
+           half-tuple gap, the adaptive penalty of Section 4.3 with the Section 3.2
+           rescale of the scaled duals; unscaling of the returned tuple.
 
 Pins (tests/test_oracle_*.py, run with -m "not gpu"): each part is checked against
 something other than itself -- brute-force 1-D minimisation and subgradient
@@ -29,7 +30,9 @@ membership for every prox, Sinkhorn-Knopp optimality conditions and limits, the
 diagonal-Sigma projection formulas of Section 4.1.1, the KKT solve, normal equations,
 soft thresholding, critical-lambda zeros, vertex enumeration on tiny LPs, support
 enumeration on tiny NNLS, KKT conditions of the converged solution, the dual
-feasibility invariant of Section 3.3 and the D/E scaling invariance of Section 4.1.
+feasibility invariant of Section 3.3, the D/E scaling invariance of Section 4.1, a
+hand-worked rho sequence for the adaptive penalty, ADMM replayed in unscaled duals for
+the rescale, and the Section 3.4 test evaluated outside the oracle on its returned tuples.
 No part of the oracle is left unpinned.
 """
 from . import prox, equil, project, admm  # noqa: F401

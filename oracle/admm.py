@@ -1,5 +1,5 @@
-"""Graph-form ADMM, FP64 (Algorithm 1 + over-relaxation + Algorithm 3), on the
-pre-conditioned problem of Eq. 12, returning the unscaled half-step tuple.
+"""Graph-form ADMM, FP64 (Algorithm 1 + over-relaxation + the adaptive penalty of
+Section 4.3), on the pre-conditioned problem of Eq. 12, returning the unscaled half-step tuple.
 
 Readings of places where the paper is silent or ambiguous (each one is also listed in
 the design notes):
@@ -12,12 +12,12 @@ the design notes):
     eps_dual = eps_abs + eps_rel ||mu^{k+1/2}|| (Section 3.4), literal norms.
   * Gap test: the half-step tuple is Fenchel feasible (Section 3.3), so its gap is
     eta = y^T nu + x^T mu (Eq. 7); with gap_stop it must also satisfy
-    |eta| <= eps_abs + eps_rel |f(y) + g(x)| (Section 3.4's eps_gap).  gap_stop = False is
-    Algorithm 3 verbatim.
-  * Algorithm 3: the convergence test is taken first; when it fails, rho is updated
-    (dual test before primal test, both strict), with l = u = 0 and the iteration
-    counter k = 0, 1, ...; on a change x~, y~ are rescaled by rho^k / rho^{k+1}
-    (Section 3.2, 'Varying penalty').
+    |eta| <= eps_abs + eps_rel |f(y) + g(x)| (Section 3.4's eps_gap).  gap_stop = False
+    stops on the two residual tests alone, as Section 4.3 does.
+  * Adaptive penalty (Section 4.3): the convergence test comes first; when it fails, the
+    penalty controller below may change rho, with both bookkeeping steps starting at 0 and
+    the iteration counter k = 0, 1, ...; on a change x~, y~ are rescaled by
+    rho^k / rho^{k+1} (Section 3.2, 'Varying penalty').
   * Returned tuple (Section 5): x = E x^, y = D^{-1} y^, mu = E^{-1} mu^, nu = D nu^
     (the dual scalings follow from nu^T y = nu^^T y^ and mu^T x = mu^^T x^).
 """
@@ -80,6 +80,70 @@ def _identity_equil(A):
     return Equilibration(np.ones(m), np.ones(n), A.copy())
 
 
+@dataclasses.dataclass
+class PenaltyController:
+    """Adaptive penalty of Section 4.3.
+
+    The controller waits until one residual has (approximately) converged and then nudges rho
+    by the factor delta so that the other one follows: a small dual residual calls for a
+    larger rho (a larger penalty favours primal feasibility, Section 3.2), a small primal
+    residual for a smaller one.  To keep rho from flip-flopping, a change of direction is
+    allowed only once tau * k has passed the iteration of the last change in the other
+    direction.  When both residuals are small, the dual case is served first.  The state is
+    just those two iteration numbers, both 0 at the start (k itself starts at 0, so nothing
+    changes before k = 1).
+    """
+    delta: float
+    tau: float
+    k_last_increase: int = 0
+    k_last_decrease: int = 0
+
+    def next_rho(self, k: int, rho: float, dual_small: bool, primal_small: bool) -> float:
+        """rho^{k+1} after the (not converged) iteration k run with rho^k = rho."""
+        if dual_small and self.tau * k > self.k_last_decrease:
+            self.k_last_increase = k
+            return self.delta * rho
+        if primal_small and self.tau * k > self.k_last_increase:
+            self.k_last_decrease = k
+            return rho / self.delta
+        return rho
+
+
+def rescale_scaled_duals(xt, yt, rho_old: float, rho_new: float):
+    """Section 3.2, 'Varying penalty': x~ and y~ are duals scaled by 1/rho (Section 3.3 has
+    mu^k = -rho x~^k, nu^k = -rho y~^k), so a change of rho multiplies them by
+    rho^k / rho^{k+1}, which leaves the unscaled duals mu^k and nu^k as they were."""
+    s = rho_old / rho_new
+    return xt * s, yt * s
+
+
+@dataclasses.dataclass
+class StopTest:
+    """The Section 3.4 quantities of one half-step tuple (pre-conditioned variables)."""
+    r_pri: float       # ||A x^{k+1/2} - y^{k+1/2}||         (Eq. 11)
+    r_dual: float      # ||A^T nu^{k+1/2} + mu^{k+1/2}||     (Eq. 11)
+    eps_pri: float     # eps_abs + eps_rel ||y^{k+1/2}||
+    eps_dual: float    # eps_abs + eps_rel ||mu^{k+1/2}||
+    gap: float         # y^T nu + x^T mu of the Fenchel-feasible half tuple (Eq. 7)
+    obj: float         # f(y^{k+1/2}) + g(x^{k+1/2})
+    eps_gap: float     # eps_abs + eps_rel |obj|
+
+    def converged(self, gap_stop: bool) -> bool:
+        residuals_ok = self.r_pri < self.eps_pri and self.r_dual < self.eps_dual
+        return residuals_ok and (not gap_stop or abs(self.gap) < self.eps_gap)
+
+
+def section34_test(p: "Params", Ah, fh, gh, xh, yh, mu, nu) -> StopTest:
+    """Residuals of Eq. 11 and the tolerances of Section 3.4 at the half-step tuple."""
+    obj = float(np.sum(f_value(fh, yh, 1e-9)) + np.sum(f_value(gh, xh, 1e-9)))
+    return StopTest(r_pri=float(np.linalg.norm(Ah @ xh - yh)),
+                    r_dual=float(np.linalg.norm(Ah.T @ nu + mu)),
+                    eps_pri=p.abs_tol + p.rel_tol * float(np.linalg.norm(yh)),
+                    eps_dual=p.abs_tol + p.rel_tol * float(np.linalg.norm(mu)),
+                    gap=float(yh @ nu + xh @ mu), obj=obj,
+                    eps_gap=p.abs_tol + p.rel_tol * abs(obj))
+
+
 def solve(A, f, g, params: Params | None = None, eq: Equilibration | None = None,
           record: bool = False, x0=None, nu0=None) -> Result:
     p = params or Params()
@@ -110,11 +174,11 @@ def solve(A, f, g, params: Params | None = None, eq: Equilibration | None = None
     if nu0 is not None:
         yt = -(np.asarray(nu0, np.float64) / D) / rho
         xt = -(Ah.T @ yt)
-    l = u = 0
+    ctrl = PenaltyController(delta=p.delta, tau=p.tau)
     hist = []
     status, iters = 1, p.max_iter
     xh = yh = mu = nu = None
-    r_pri = r_dual = eps_pri = eps_dual = gap = obj = np.nan
+    st = None
     for k in range(p.max_iter):
         # Algorithm 1, prox step
         vx, vy = x - xt, y - yt
@@ -134,36 +198,27 @@ def solve(A, f, g, params: Params | None = None, eq: Equilibration | None = None
         xt = xt + xr - xn
         yt = yt + yr - yn
         x, y = xn, yn
-        # Eq. 11 residuals and Section 3.4 tolerances
-        r_pri = float(np.linalg.norm(Ah @ xh - yh))
-        r_dual = float(np.linalg.norm(Ah.T @ nu + mu))
-        eps_pri = p.abs_tol + p.rel_tol * float(np.linalg.norm(yh))
-        eps_dual = p.abs_tol + p.rel_tol * float(np.linalg.norm(mu))
-        gap = float(yh @ nu + xh @ mu)
-        obj = float(np.sum(f_value(fh, yh, 1e-9)) + np.sum(f_value(gh, xh, 1e-9)))
-        eps_gap = p.abs_tol + p.rel_tol * abs(obj)
+        # Section 3.4
+        st = section34_test(p, Ah, fh, gh, xh, yh, mu, nu)
         if record:
-            hist.append(dict(k=k, rho=rho, r_pri=r_pri, r_dual=r_dual, eps_pri=eps_pri,
-                             eps_dual=eps_dual, gap=gap, obj=obj,
+            hist.append(dict(k=k, rho=rho, r_pri=st.r_pri, r_dual=st.r_dual, eps_pri=st.eps_pri,
+                             eps_dual=st.eps_dual, gap=st.gap, obj=st.obj,
                              dual_inv=float(np.linalg.norm(xt + Ah.T @ yt))))
-        converged = r_pri < eps_pri and r_dual < eps_dual and (not p.gap_stop or abs(gap) < eps_gap)
-        if converged:
+        if st.converged(p.gap_stop):
             status, iters = 0, k + 1
             break
-        # Algorithm 3
+        # Section 4.3 adaptive penalty, then the Section 3.2 rescale of the scaled duals
         if p.adaptive_rho:
-            rho_new = rho
-            if r_dual < eps_dual and p.tau * k > l:
-                rho_new = p.delta * rho
-                u = k
-            elif r_pri < eps_pri and p.tau * k > u:
-                rho_new = rho / p.delta
-                l = k
+            rho_new = ctrl.next_rho(k, rho, st.r_dual < st.eps_dual, st.r_pri < st.eps_pri)
             if rho_new != rho:
-                xt = xt * (rho / rho_new)
-                yt = yt * (rho / rho_new)
+                xt, yt = rescale_scaled_duals(xt, yt, rho, rho_new)
                 rho = rho_new
 
+    if st is None:
+        r_pri = r_dual = eps_pri = eps_dual = gap = obj = np.nan
+    else:
+        r_pri, r_dual, eps_pri, eps_dual, gap, obj = (st.r_pri, st.r_dual, st.eps_pri, st.eps_dual,
+                                                      st.gap, st.obj)
     return Result(status=status, iters=iters, rho=rho,
                   x=E * xh, y=yh / D, mu=mu / E, nu=D * nu,
                   xh=xh, yh=yh, muh=mu, nuh=nu,

@@ -105,3 +105,105 @@ def test_relaxed_half_step_in_duals_breaks_fenchel_pin(monkeypatch):
         return 1.7 * orig(params, v, rho) - 0.7 * np.asarray(v, float)
     monkeypatch.setattr(OP, "prox_f", bad)
     _fails(TP.test_prox_output_is_fenchel_feasible, OP.ABS)
+
+
+# ---- adaptive penalty (Section 4.3), rescale (Section 3.2) and stopping test (Section 3.4) ----
+
+from oracle import admm as OA  # noqa: E402
+from tests import test_oracle_penalty as TR  # noqa: E402
+
+
+def test_dropped_rescale_on_rho_change(monkeypatch):
+    monkeypatch.setattr(OA, "rescale_scaled_duals", lambda xt, yt, r0, r1: (xt, yt))
+    _fails(TR.test_rescale_on_rho_change_matches_unscaled_duals, "lasso", (80, 30), 4)
+
+
+def test_inverted_rescale_on_rho_change(monkeypatch):
+    monkeypatch.setattr(OA, "rescale_scaled_duals", lambda xt, yt, r0, r1: (xt * (r1 / r0), yt * (r1 / r0)))
+    _fails(TR.test_rescale_on_rho_change_matches_unscaled_duals, "lasso", (80, 30), 4)
+
+
+def _planted_controller(monkeypatch, rule):
+    def next_rho(self, k, rho, dual_small, primal_small):
+        return rule(self, k, rho, dual_small, primal_small)
+    monkeypatch.setattr(OA.PenaltyController, "next_rho", next_rho)
+
+
+def test_delta_applied_in_the_wrong_direction(monkeypatch):
+    def rule(self, k, rho, dual_small, primal_small):   # small dual residual lowers rho
+        if dual_small and self.tau * k > self.k_last_decrease:
+            self.k_last_increase = k
+            return rho / self.delta
+        if primal_small and self.tau * k > self.k_last_increase:
+            self.k_last_decrease = k
+            return rho * self.delta
+        return rho
+    _planted_controller(monkeypatch, rule)
+    _fails(TR.test_penalty_controller_hand_worked_sequence)
+
+
+def test_primal_case_tested_first(monkeypatch):
+    def rule(self, k, rho, dual_small, primal_small):
+        if primal_small and self.tau * k > self.k_last_increase:
+            self.k_last_decrease = k
+            return rho / self.delta
+        if dual_small and self.tau * k > self.k_last_decrease:
+            self.k_last_increase = k
+            return rho * self.delta
+        return rho
+    _planted_controller(monkeypatch, rule)
+    _fails(TR.test_penalty_controller_hand_worked_sequence)
+
+
+def test_non_strict_hysteresis(monkeypatch):
+    def rule(self, k, rho, dual_small, primal_small):
+        if dual_small and self.tau * k >= self.k_last_decrease:
+            self.k_last_increase = k
+            return rho * self.delta
+        if primal_small and self.tau * k >= self.k_last_increase:
+            self.k_last_decrease = k
+            return rho / self.delta
+        return rho
+    _planted_controller(monkeypatch, rule)
+    _fails(TR.test_penalty_controller_hand_worked_sequence)
+
+
+def test_hysteresis_against_the_same_direction(monkeypatch):
+    def rule(self, k, rho, dual_small, primal_small):   # waits on its own last change instead
+        if dual_small and self.tau * k > self.k_last_increase:
+            self.k_last_increase = k
+            return rho * self.delta
+        if primal_small and self.tau * k > self.k_last_decrease:
+            self.k_last_decrease = k
+            return rho / self.delta
+        return rho
+    _planted_controller(monkeypatch, rule)
+    _fails(TR.test_penalty_controller_hand_worked_sequence)
+
+
+def _planted_tolerances(monkeypatch, eps_pri_of, eps_dual_of):
+    orig = OA.section34_test
+
+    def bad(p, Ah, fh, gh, xh, yh, mu, nu):
+        st = orig(p, Ah, fh, gh, xh, yh, mu, nu)
+        v = dict(x=xh, y=yh, mu=mu, nu=nu)
+        st.eps_pri = p.abs_tol + p.rel_tol * float(np.linalg.norm(v[eps_pri_of]))
+        st.eps_dual = p.abs_tol + p.rel_tol * float(np.linalg.norm(v[eps_dual_of]))
+        return st
+    monkeypatch.setattr(OA, "section34_test", bad)
+
+
+def test_dual_tolerance_on_nu(monkeypatch):
+    _planted_tolerances(monkeypatch, "y", "nu")
+    _fails(TR.test_stop_iteration_is_the_first_meeting_section34, "huber", (60, 25), 2, False)
+
+
+def test_primal_tolerance_on_x(monkeypatch):
+    _planted_tolerances(monkeypatch, "x", "mu")
+    _fails(TR.test_stop_iteration_is_the_first_meeting_section34, "nnls", (25, 60), 0, False)
+
+
+def test_gap_test_dropped(monkeypatch):
+    monkeypatch.setattr(OA.StopTest, "converged",
+                        lambda self, gap_stop: self.r_pri < self.eps_pri and self.r_dual < self.eps_dual)
+    _fails(TR.test_stop_iteration_is_the_first_meeting_section34, "lasso", (200, 100), 0, True)
