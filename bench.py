@@ -150,45 +150,52 @@ def job_rate(units_per_rank: int, world_size: int, t_ms_max: float) -> float:
 # ----------------------------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle as it stands, on a bounded sample of the same workload.
 # ----------------------------------------------------------------------------------------------
-def cpu_oracle_estimate(probs, gpu_iters, frac=4, iters_sample=10):
-    """Time the oracle on leading (m/frac) x (n/frac) blocks of each matrix -- equilibration,
-    factorization (Gram + Cholesky) and `iters_sample` ADMM iterations -- and scale each part
-    to the full size with the paper's cost model (Section 3.5): Sinkhorn-Knopp sweeps and one
-    iteration ~ m n, factorization ~ p q^2 + q^3/3.  Returns (solves/s, details)."""
+def _oracle_iters(prob):
+    """The oracle's own iteration count on a large benchmark problem at the benchmark's stopping
+    test, from the stored full oracle run (tests/golden/make_bench_refs.py), or None."""
+    try:
+        m, n = prob.A.shape
+        with open(os.path.join(ROOT, "tests", "golden", f"bench_{prob.name}_{m}x{n}.json")) as f:
+            rec = json.load(f)
+        return dict(iters=int(rec["iters"]), obj=float(rec["obj"]), seconds=rec.get("seconds"))
+    except Exception:
+        return None
+
+
+def oracle_full_size_timing(probs, iters, sample_iters):
+    """The oracle as it stands, timed on the full-size problems on the host cores: its setup
+    (Sinkhorn-Knopp equilibration and the FP64 Gram + Cholesky factorization) once, then
+    `sample_iters[i]` ADMM iterations of problem i with that cached factor.  Every iteration does
+    the same work (two passes of A, the triangular solves, the proxes), so a solve to the
+    iteration count `iters[i]` takes t_setup + iters[i] * t_iter; nothing is scaled by size.
+    Returns (solves/s, per-problem details)."""
     from oracle import admm as OA
     from oracle import equil as OE
     from oracle import project as OPJ
     total = 0.0
     parts = []
-    for prob, it in zip(probs, gpu_iters):
+    for prob, it, k in zip(probs, iters, sample_iters):
         m, n = prob.A.shape
-        mb, nb = max(1, m // frac), max(1, n // frac)
-        A = prob.A[:mb, :nb].astype(np.float64)
+        A = prob.A.astype(np.float64)
         t0 = time.perf_counter()
         eq = OE.equilibrate(A, 10)
         t_eq = time.perf_counter() - t0
         t0 = time.perf_counter()
-        OPJ.Projector(eq.Ahat)
+        factor = OPJ.Projector(eq.Ahat)
         t_fac = time.perf_counter() - t0
-        sub = type(prob.f)(*(getattr(prob.f, k)[:mb] for k in "habcde"))
-        gsub = type(prob.g)(*(getattr(prob.g, k)[:nb] for k in "habcde"))
-        # solve() builds its own factor once: the difference of two runs isolates the iterations
-        runs = []
-        for its in (1, 1 + iters_sample):
-            prm = OA.Params(max_iter=its, abs_tol=0.0, rel_tol=0.0, gap_stop=False)
-            t0 = time.perf_counter()
-            OA.solve(A, sub, gsub, prm, eq=eq)
-            runs.append(time.perf_counter() - t0)
-        t_iter = max(runs[1] - runs[0], 0.0) / iters_sample
-        p, q = max(m, n), min(m, n)
-        pb, qb = max(mb, nb), min(mb, nb)
-        s_mn = (m * n) / (mb * nb)
-        s_fac = (p * q * q + q ** 3 / 3) / (pb * qb * qb + qb ** 3 / 3)
-        s_it = (4.0 * m * n + q * q) / (4.0 * mb * nb + qb * qb)
-        t_solve = t_eq * s_mn + t_fac * s_fac + it * t_iter * s_it
+        prm = OA.Params(max_iter=k, abs_tol=0.0, rel_tol=0.0, gap_stop=False)
+        t0 = time.perf_counter()
+        OA.solve(A, prob.f, prob.g, prm, eq=eq, factor=factor)
+        t_iter = (time.perf_counter() - t0) / k
+        t_solve = t_eq + t_fac + it * t_iter
         total += t_solve
-        parts.append(dict(shape=[m, n], block=[mb, nb], t_equil_s=t_eq, t_factor_s=t_fac, t_iter_s=t_iter,
-                          iters=it, est_solve_s=t_solve))
+        rec = dict(shape=[m, n], t_equil_s=t_eq, t_factor_s=t_fac, t_iter_s=t_iter, iters_timed=k, iters=it,
+                   solve_s=t_solve)
+        ref = _oracle_iters(prob)
+        if ref:
+            rec["oracle_own_iters"] = ref["iters"]
+        parts.append(rec)
+        del A, eq, factor
     return len(probs) / total, parts
 
 
@@ -248,31 +255,65 @@ def _threads():
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on the host cores, on the benchmark's own
+    full-size problems.  Each problem's setup (equilibration, Gram + Cholesky) is timed once at
+    full size; each step is then one full-size ADMM iteration of each problem with its cached
+    factor (W untimed, K timed).  value = solves/s of a solve to the iteration counts the GPU
+    path and the oracle both take on these problems (90 and 449): 2 / sum(setup + iters * t_iter)."""
     dist, rank, ws, _ = _dist()
     if rank != 0:
         return
+    from oracle import admm as OA
+    from oracle import equil as OE
+    from oracle import project as OPJ
     probs = problems(0)
-    # iteration counts of the two solves at eps_rel = 1e-3 on these data: the GPU path takes 90
-    # and 449; the oracle's own full run of the logistic problem also takes 449
     iters = [90, 449]
+    t_run = time.perf_counter()
+    state = []
+    for prob in probs:
+        A = prob.A.astype(np.float64)
+        t0 = time.perf_counter()
+        eq = OE.equilibrate(A, 10)
+        t_eq = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        factor = OPJ.Projector(eq.Ahat)
+        t_fac = time.perf_counter() - t0
+        state.append((A, prob, eq, factor, t_eq, t_fac))
+    one = OA.Params(max_iter=1, abs_tol=0.0, rel_tol=0.0, gap_stop=False)
+
+    def step():
+        out = []
+        for A, prob, eq, factor, *_ in state:
+            t0 = time.perf_counter()
+            OA.solve(A, prob.f, prob.g, one, eq=eq, factor=factor)
+            out.append(time.perf_counter() - t0)
+        return out
+
     for _ in range(args.warmup):
-        cpu_oracle_estimate(probs, iters, frac=8, iters_sample=3)
+        step()
     t0 = time.perf_counter()
-    vals = []
-    details = None
-    for _ in range(args.steps):
-        v, details = cpu_oracle_estimate(probs, iters, frac=8, iters_sample=3)
-        vals.append(v)
-    wall = time.perf_counter() - t0
-    value = float(np.mean(vals))
-    sample = ("oracle (FP64 NumPy) on leading m/8 x n/8 blocks of both matrices: equilibration, "
-              "factorization and 3 iterations, scaled to full size by the Section 3.5 cost model and to "
-              f"{iters} iterations")
+    per = [step() for _ in range(args.steps)]
+    t_steps = time.perf_counter() - t0
+    wall = time.perf_counter() - t_run
+    t_iter = [float(np.mean([p[i] for p in per])) for i in range(len(probs))]
+    details = []
+    total = 0.0
+    for (A, prob, eq, factor, t_eq, t_fac), ti, it in zip(state, t_iter, iters):
+        solve_s = t_eq + t_fac + it * ti
+        total += solve_s
+        details.append(dict(shape=list(prob.A.shape), t_equil_s=t_eq, t_factor_s=t_fac, t_iter_s=ti, iters=it,
+                            solve_s=solve_s))
+    value = len(probs) / total
+    sample = ("FP64 oracle on the full-size problems: setup (equilibration + Gram + Cholesky) timed once per "
+              f"problem, then {args.steps} timed full-size iterations of each (after {args.warmup} untimed); "
+              f"solve time = setup + {iters} iterations x the measured time per iteration")
     line = dict(impl="reference", metric=METRIC, value=value, unit="solves/s", n_gpus=ws, steps=args.steps,
-                warmup=args.warmup, ms_per_step=1000 * 2 / value, higher_is_better=True, scaling="weak",
-                vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=WORKLOAD, l2="inputs larger than L2"),
-                cpu_baseline=dict(value=value, unit="solves/s", cores=_threads(), kind="oracle", sample=sample),
+                warmup=args.warmup, ms_per_step=1000.0 * t_steps / max(1, args.steps), higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD, l2="inputs larger than L2",
+                            step="one full-size ADMM iteration of each of the two problems"),
+                cpu_baseline=dict(value=value, unit="solves/s", cores=_threads(), cpu_count=os.cpu_count(),
+                                  kind="oracle", sample=sample),
                 e2e=dict(value=value, unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
                 wall_s=wall, details=details)
     print(json.dumps(line))
@@ -438,11 +479,19 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, parts = cpu_oracle_estimate(probs, [pp["iters"] for pp in per_problem])
-        cpu = dict(value=v, unit="solves/s", cores=_threads(), kind="oracle",
-                   sample=("oracle (FP64 NumPy) on leading m/4 x n/4 blocks of both matrices: equilibration, "
-                           "factorization and 10 iterations timed, scaled to full size by the Section 3.5 cost "
-                           "model and to the GPU solves' iteration counts"), parts=parts)
+        its = [pp["iters"] for pp in per_problem]
+        v, parts = oracle_full_size_timing(probs, its, sample_iters=[5, 20])
+        cpu = dict(value=v, unit="solves/s", cores=_threads(), cpu_count=os.cpu_count(), kind="oracle",
+                   sample=("FP64 oracle on the full-size problems: setup (equilibration + Gram + Cholesky) "
+                           "timed once each, then 5 (tall) and 20 (fat) full-size iterations with the cached "
+                           f"factor; solve time = setup + the GPU solves' iteration counts {its} x the measured "
+                           "time per iteration"), parts=parts)
+
+    extras = {}
+    if rank == 0 and ws == 1 and not args.no_extras:
+        extras["small_lasso"] = _extra("small_lasso", small_lasso_measure)
+        extras["serve"] = _extra("serve", lambda: serve_measure(args))
+        extras["batch"] = _extra("batch", lambda: batch_measure(args))
 
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit="solves/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
@@ -454,10 +503,69 @@ def run_ours(args):
                     latency_ms=dict(p50=p50, p99=p99, n=len(lats)),
                     e2e=dict(value=e2e_value, unit="solves/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                     gpu_launches=launches, roofline=roof, proj_hbm=proj, time_shares=shares,
-                    per_problem=per_problem, clocks=clk, cpu_baseline=cpu)
+                    per_problem=per_problem, clocks=clk, cpu_baseline=cpu, **extras)
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def small_lasso_measure(reps=50):
+    """The 200 x 100 Lasso (A ~ N(0, 1/100), 10 nonzeros in x_true, lambda = 0.1 ||A^T b||_inf):
+    one plain solve through the C ABI from host arrays (setup + iterations + copies), timed over
+    `reps` solves after warm-up; the oracle as it stands on the same problem with all host cores
+    and with BLAS limited to one thread; and the GPU objective against the oracle's at the same
+    stopping test."""
+    import torch
+    import paper_1503_08366_b300 as P
+    import workloads as W
+    from oracle import admm as OA
+    from threadpoolctl import threadpool_limits
+    prob = W.lasso_small(0)
+    prm = P.pogs_default_params(max_iter=2000)
+
+    def gpu_once():
+        with P.Solver(prob.A, prm) as s_:
+            return s_.solve(prob.f, prob.g)[0]
+    for _ in range(5):
+        gpu_once()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        info = gpu_once()
+        ts.append(time.perf_counter() - t0)
+    oprm = OA.Params(max_iter=2000)
+
+    def oracle_times(k):
+        out, r = [], None
+        for _ in range(k):
+            t0 = time.perf_counter()
+            r = OA.solve(prob.A, prob.f, prob.g, oprm)
+            out.append(time.perf_counter() - t0)
+        return out, r
+    o_all, ref = oracle_times(5)
+    with threadpool_limits(limits=1):
+        o_one, _ = oracle_times(5)
+    med = lambda v: float(np.median(v))
+    return dict(workload="plain single Lasso solve 200x100, eps_abs=1e-4, eps_rel=1e-3, max_iter 2000",
+                gpu=dict(ms_per_solve=1e3 * med(ts), solves_per_s=1.0 / med(ts), iters=info.iters,
+                         status=info.status, obj=info.obj, reps=reps,
+                         timing="wall clock per pogs_setup + pogs_solve + pogs_free call from host arrays"),
+                oracle=dict(ms_per_solve=1e3 * med(o_all), solves_per_s=1.0 / med(o_all), iters=ref.iters,
+                            obj=ref.obj, cores=_threads(), cpu_count=os.cpu_count()),
+                oracle_1thread=dict(ms_per_solve=1e3 * med(o_one), solves_per_s=1.0 / med(o_one), cores=1),
+                obj_rel_err=abs(info.obj - ref.obj) / max(1.0, abs(ref.obj)))
+
+
+def _extra(name, fn):
+    """Run one extra comparison of the default line; a failure is recorded, not raised."""
+    try:
+        t0 = time.perf_counter()
+        out = fn()
+        out["wall_s"] = time.perf_counter() - t0
+        return out
+    except Exception as e:  # noqa: BLE001
+        return dict(error=f"{type(e).__name__}: {e}")
 
 
 def _traffic(kernel, shape):
@@ -481,6 +589,10 @@ def _traffic(kernel, shape):
 # Extra workloads (not the default bench line): many small instances, and serving.
 # ----------------------------------------------------------------------------------------------
 def run_batch(args):
+    print(json.dumps(batch_measure(args)))
+
+
+def batch_measure(args):
     """2048 independent instances (Lasso / Huber / SVM / NNLS, m log-U[64, 2048], n log-U[32, 512])
     in one pogs_solve_batch call, vs the plain single-problem path one instance at a time."""
     import torch
@@ -542,7 +654,7 @@ def run_batch(args):
             sv.solve(pb.f, pb.g, device_out=True)
     torch.cuda.synchronize()
     t_plain = (time.perf_counter() - t0) / k * len(probs)
-    print(json.dumps(dict(workload="batch", metric="solves/s", value=len(probs) / t_dev, unit="solves/s",
+    return (dict(workload="batch", metric="solves/s", value=len(probs) / t_dev, unit="solves/s",
                           e2e=dict(value=len(probs) / t_host, unit="solves/s"),
                           plain=dict(value=len(probs) / t_plain, unit="solves/s", sample=k),
                           statuses={str(s_): st.count(s_) for s_ in set(st)},
@@ -557,7 +669,7 @@ def run_batch(args):
                                              "instances staged in shared memory or resident in L2 "
                                              "read fewer bytes from DRAM"),
                           config=dict(count=len(probs), classes="lasso,huber,svm,nnls", m="log-U[64,2048]",
-                                      n="log-U[32,512]"))))
+                                      n="log-U[32,512]")))
 
 
 def _pool(trace, size):
@@ -567,9 +679,23 @@ def _pool(trace, size):
 
 
 def run_serve(args):
+    print(json.dumps(serve_measure(args)))
+
+
+def censored_percentile(done_ms, unfinished_lower_ms, q):
+    """Percentile q of a latency sample in which some requests had not finished when the run
+    stopped: each of those counts at its lower bound (stop time - arrival), so the result is a
+    lower bound on the true percentile (exact when nothing is unfinished)."""
+    v = list(done_ms) + list(unfinished_lower_ms)
+    return float(np.percentile(np.asarray(v), q)) if v else None
+
+
+def serve_measure(args):
     """Poisson arrivals at 2000 req/s, mixed Lasso / logistic / Huber / SVM / NNLS with
     m log-U[100, 8000], n log-U[50, 4000], served with continuous batching under a 120 GB budget,
-    vs the same trace served one request at a time by the single-problem path."""
+    vs the same trace served one request at a time by the single-problem path (run to the end
+    of the trace unless --plain-limit is given; latencies of requests a limited run did not
+    reach count at their lower bound)."""
     import torch
     import paper_1503_08366_b300 as P
     import workloads as W
@@ -612,7 +738,7 @@ def run_serve(args):
         t0 = time.monotonic()
         for i, req in enumerate(trace):
             now = time.monotonic() - t0
-            if now > limit_s:
+            if limit_s is not None and now > limit_s:
                 break
             if req.arrival_s > now:
                 time.sleep(req.arrival_s - now)
@@ -625,6 +751,8 @@ def run_serve(args):
 
     wall, lat, iters, st = served()
     pwall, plat, pst = plain(args.plain_limit)
+    # requests the plain run did not reach: latency at least (end of the run - arrival)
+    punf = [(pwall - trace[i].arrival_s) * 1e3 for i in range(len(plat), n_req)]
     cpu, check = (None, None) if args.no_cpu_baseline else oracle_sample_check(pool, served_obj)
     pct = lambda v, q: float(np.percentile(np.asarray(v) * 1e3, q)) if v else None
 
@@ -635,7 +763,7 @@ def run_serve(args):
         if not t:
             return dict(count=0)
         return dict(count=len(t), last_s=t[-1], per_10s=np.bincount((np.asarray(t) // 10).astype(int)).tolist())
-    print(json.dumps(dict(
+    return (dict(
         workload="serve", metric="solves/s & p50/p99 latency at eps_rel=1e-3, served vs plain",
         value=len(lat) / wall, unit="solves/s", latency_ms=dict(p50=pct(lat, 50), p99=pct(lat, 99)),
         statuses={str(s_): st.count(s_) for s_ in set(st)}, iters_mean=float(np.mean(iters)),
@@ -643,11 +771,17 @@ def run_serve(args):
         step_calls=dict(count=len(steps), total_s=float(np.sum(steps)), p50_ms=pct(steps, 50),
                         max_ms=pct(steps, 100)),
         plain=dict(value=len(plat) / pwall, unit="solves/s", served=len(plat), of=n_req,
-                   latency_ms=dict(p50=pct(plat, 50), p99=pct(plat, 99)), limit_s=args.plain_limit),
+                   statuses={str(s_): pst.count(s_) for s_ in set(pst)},
+                   latency_ms=dict(p50=censored_percentile([x * 1e3 for x in plat], punf, 50),
+                                   p99=censored_percentile([x * 1e3 for x in plat], punf, 99),
+                                   censored=len(punf)),
+                   limit_s=args.plain_limit),
+        served_p99_below_plain_p99=(pct(lat, 99) is not None and
+                                    pct(lat, 99) < censored_percentile([x * 1e3 for x in plat], punf, 99)),
         config=dict(requests=n_req, rate_hz=2000, budget_gb=120, payload_pool=len(pool), step_iters=args.step_iters,
                     max_resident=args.max_resident,
                     large_workers=args.workers, m="log-U[100,8000]", n="log-U[50,4000]",
-                    classes="lasso,logistic,huber,svm,nnls"))))
+                    classes="lasso,logistic,huber,svm,nnls")))
 
 
 def _precision_refs(name, m, n):
@@ -856,7 +990,10 @@ def main():
     ap.add_argument("--workers", type=int, default=8, help="serve workload: threads for large requests")
     ap.add_argument("--step-iters", type=int, default=25, help="serve workload: iterations per step")
     ap.add_argument("--max-resident", type=int, default=8192, help="serve workload: resident small requests")
-    ap.add_argument("--plain-limit", type=float, default=60.0, help="serve workload: seconds for the plain run")
+    ap.add_argument("--plain-limit", type=float, default=None,
+                    help="serve workload: stop the plain run after this many seconds (default: run the whole trace)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the small-Lasso, batch and serving comparisons")
     ap.add_argument("--loop-mode", type=int, default=0,
                     help="0: one graph per solve (conditional WHILE node); 1: host-checked loop over a "
                          "captured iteration (for profilers that skip conditional graphs)")

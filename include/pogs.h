@@ -152,8 +152,13 @@ void pogs_default_params(pogs_params* p);
 /* One-time setup for matrix A (Section 3.5 'factorization caching', Section 4.2, 5):
  * copies A to the device (host or device source), runs Algorithm 2 for p->sk_sweeps
  * sweeps, applies the Frobenius rescale, forms G = A^T A (m >= n) or A A^T (m < n) in
- * p->gram_prec, factors I + G = L L^T in FP64 and caches the factor (as FP32 L^{-1} in
- * 128 x 128 packed tiles).  The caller keeps ownership of A.  `stream` is a cudaStream_t
+ * p->gram_prec, factors I + G = L L^T in p->chol_prec and caches the result in FP32 packed
+ * 128 x 128 lower tiles.  With the default POGS_CHOL_MIXED the Schur complement is carried
+ * as a double-float pair (FP64-like) while the block products run in FP32 or, for blocks of
+ * 512 and more, in TF32x3 on the tensor cores; POGS_CHOL_FP64 factors entirely in FP64.
+ * What is cached: S = (I + G)^{-1} = L^{-T} L^{-1} from q = min(m, n) = 1024 on (mixed
+ * precision; one symmetric pass per projection), else M = L^{-1} (two triangular products
+ * per projection).  The caller keeps ownership of A.  `stream` is a cudaStream_t
  * (NULL = default).  On success *out owns all device memory until pogs_free.
  * Errors: ARG (m or n < 1, lda too small, order not 'R'/'C', NULL), OOM, NONFINITE,
  * NUMERIC, CUDA. */
@@ -320,12 +325,15 @@ int pogs_gram(const float* A, int64_t m, int64_t n, int64_t lda, int gram_prec, 
  * loads it and held until the process exits.  Its first 256 bytes hold a status word; the
  * rest holds the packed operands, rp * Kp * b bytes with rp = q rounded up to 128, Kp = the
  * contraction length (m if m >= n, else n) rounded up to 64 (32 for TF32), and b = 2 for
- * BF16, 4 for TF32 and BF16x3; POGS_GRAM_FP32 needs none.  Larger problems are rejected
- * with POGS_ERR_CAPACITY before any device work.
+ * BF16, 4 for TF32 and BF16x3; POGS_GRAM_FP32 needs none.  A problem is accepted when
+ * rp * Kp * b <= 32 MiB - 512 bytes (the status word's 256 bytes and 256 bytes of slack the
+ * packing keeps); larger ones are rejected with POGS_ERR_CAPACITY before any device work.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  Every call
- * shares the one array and leaves its last contents there: calls that overlap on the GPU
- * (different streams or threads) race and must be serialised by the caller. */
+ * with that device current; make that first call before any stream capture.  Each call
+ * waits for its own work on `stream` to finish (it reads the status word back) before it
+ * returns.  Every call shares the one array and leaves its last contents there: calls that
+ * overlap on the GPU (different streams or threads) race and must be serialised by the
+ * caller. */
 int pogs_gram_noalloc(const float* A, int64_t m, int64_t n, int64_t lda, int gram_prec, float* G, void* stream);
 
 /* ---- instrumentation ------------------------------------------------------------------ */
@@ -348,6 +356,10 @@ int pogs_time_kernels(pogs_handle* hdl, int reps, double* ms, double* bytes);
 /* Number of kernel launches this library has issued in the process so far (graph replays
  * included). */
 long long pogs_kernel_launches(void);
+
+/* Number of device memory allocations this library has requested in the process so far
+ * (stream-ordered pool allocations and cudaMalloc / cudaMallocAsync calls alike). */
+long long pogs_device_allocations(void);
 
 /* Failure detection: every device-side wait of the tensor-core kernels (mbarrier phases of the
  * TMA / MMA pipeline) is bounded (about 2 s of SM clock) and reports POGS_ERR_TIMEOUT instead of

@@ -145,7 +145,10 @@ def section34_test(p: "Params", Ah, fh, gh, xh, yh, mu, nu) -> StopTest:
 
 
 def solve(A, f, g, params: Params | None = None, eq: Equilibration | None = None,
-          record: bool = False, x0=None, nu0=None) -> Result:
+          record: bool = False, x0=None, nu0=None, factor: Projector | None = None) -> Result:
+    """Solve Eq. 1 for the given f, g.  eq: a precomputed equilibration of A (else Algorithm 2
+    runs here); factor: a Projector of eq.Ahat built earlier, reused instead of factoring again
+    (Section 3.5, factorization caching)."""
     p = params or Params()
     A = np.asarray(A, np.float64)
     m, n = A.shape
@@ -156,7 +159,7 @@ def solve(A, f, g, params: Params | None = None, eq: Equilibration | None = None
             eq = _identity_equil(A)
     Ah, D, E = eq.Ahat, eq.D, eq.E
     fh, gh = fold_f(f, D), fold_g(g, E)
-    proj = Projector(Ah) if p.proj == "direct" else None
+    proj = (factor if factor is not None else Projector(Ah)) if p.proj == "direct" else None
     u_cg = None   # CGLS warm start: the previous projection's least-squares variable
 
     x, xt = np.zeros(n), np.zeros(n)

@@ -126,6 +126,8 @@ lib.pogs_server_destroy.argtypes = [_P]
 lib.pogs_server_destroy.restype = None
 lib.pogs_kernel_launches.argtypes = []
 lib.pogs_kernel_launches.restype = C.c_longlong
+lib.pogs_device_allocations.argtypes = []
+lib.pogs_device_allocations.restype = C.c_longlong
 
 
 class PogsError(RuntimeError):
@@ -341,6 +343,10 @@ def pogs_time_kernels(handle, reps: int = 20):
 
 def pogs_kernel_launches() -> int:
     return int(lib.pogs_kernel_launches())
+
+
+def pogs_device_allocations() -> int:
+    return int(lib.pogs_device_allocations())
 
 
 def pogs_gram(A, gram_prec="BF16X3", stream=None):

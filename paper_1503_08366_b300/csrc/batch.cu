@@ -600,12 +600,17 @@ int batch_setup(BInst* d_inst, int count, const BCfg& cfg, cudaStream_t s) {
   bsetup_equil_kernel<<<count, NT, 0, s>>>(d_inst, cfg);
   bsetup_gram_kernel<<<count, NT, 0, s>>>(d_inst);
   const int chol_smem = 512 * 33 * sizeof(float);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(bsetup_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, chol_smem);
-    cudaFuncSetAttribute(batch_admm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_max_smem());
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  if (attr.run([&] {
+        if (cudaFuncSetAttribute(bsetup_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, chol_smem) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(batch_admm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 batch_max_smem()) == cudaSuccess)
+          return 0;
+        cudaGetLastError();
+        return -1;
+      }) != 0)
+    return POGS_ERR_CUDA;
   bsetup_chol_kernel<<<count, NT, chol_smem, s>>>(d_inst, cfg.mixed_chol);
   bsetup_inverse_kernel<<<count, NT, 0, s>>>(d_inst);
   return cudaGetLastError() == cudaSuccess ? 0 : POGS_ERR_CUDA;

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
 
 #include "../../include/pogs.h"
 
@@ -182,6 +183,33 @@ extern thread_local int g_capture_depth;
 inline void count_launch(int k = 1) {
   if (g_capture_depth == 0) g_launch_count.fetch_add(k, std::memory_order_relaxed);
 }
+
+// Process-wide count of device memory allocations requested by this library (pool
+// allocations and cudaMalloc / cudaMallocAsync calls).
+extern std::atomic<long long> g_alloc_count;
+inline void count_alloc(int k = 1) { g_alloc_count.fetch_add(k, std::memory_order_relaxed); }
+
+// Runs a set-up step (a cudaFuncSetAttribute call, say) once per device: function attributes
+// belong to a device's context, so a process that uses several devices needs the call on each.
+// Thread-safe; a step that fails is retried on the next call.
+struct PerDeviceOnce {
+  static constexpr int kMaxDevices = 64;
+  std::mutex mu;
+  bool done[kMaxDevices] = {};
+  template <class Fn>
+  int run(Fn fn) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+      cudaGetLastError();
+      return -1;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return 0;
+    const int rc = fn();
+    if (rc == 0) done[dev] = true;
+    return rc;
+  }
+};
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }

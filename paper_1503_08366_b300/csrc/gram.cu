@@ -363,13 +363,15 @@ template <int MODE>
 int launch_tc(const CUtensorMap& xh, const CUtensorMap& xl, const CUtensorMap& yh, const CUtensorMap& yl,
               const TcArgs& a, int ntiles, cudaStream_t s) {
   using Cfg = TcCfg<MODE>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem) !=
-        cudaSuccess)
-      return -1;
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  if (attr.run([] {
+        if (cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg::kSmem) == cudaSuccess)
+          return 0;
+        cudaGetLastError();
+        return -1;
+      }) != 0)
+    return -1;
   count_launch();
   tc_gemm_kernel<MODE><<<ntiles, 192, Cfg::kSmem, s>>>(xh, xl, yh, yl, a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

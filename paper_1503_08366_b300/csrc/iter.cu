@@ -100,7 +100,7 @@ void launch_prox_step(int n, int m, const float* x, float* xt, float* xh, float*
 // order and applies the epilogue.
 // ------------------------------------------------------------------------------------------
 template <int NRHS, bool SQ, int EPI>
-__global__ void __launch_bounds__(256, 5) gemv_t_kernel(const float* __restrict__ A, int64_t lda, int m, int n,
+__global__ void __launch_bounds__(256, 5) pogs_colsum_kernel(const float* __restrict__ A, int64_t lda, int m, int n,
                                                      const float* __restrict__ v1,
                                                      const float* __restrict__ v2,
                                                      const float* __restrict__ v3, int rows,
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256, 5) gemv_t_kernel(const float* __restrict_
 // U: float4 loads in flight per lane.  8 when a block holds at least 32 rows (long-running
 // blocks, where per-warp memory parallelism matters more than resident blocks), else 4.
 template <int NRHS, bool SQ, int EPI, int U>
-__global__ void __launch_bounds__(256) gemv_n_kernel(const float* __restrict__ A, int64_t lda, int m, int n,
+__global__ void __launch_bounds__(256) pogs_rowdot_kernel(const float* __restrict__ A, int64_t lda, int m, int n,
                                                      const float* __restrict__ x1,
                                                      const float* __restrict__ x2, int rows, int cols,
                                                      float* __restrict__ part, unsigned* __restrict__ cnt,
@@ -706,7 +706,7 @@ static void gemv_t_dispatch(int epi, const float* A, int64_t lda, int m, int n, 
                             const DevState* guard, cudaStream_t s) {
   dim3 grid(g.t_ncolblk, g.t_nsplit);
   count_launch();
-#define POGS_T(E) gemv_t_kernel<NRHS, SQ, E><<<grid, 256, 0, s>>>(A, lda, m, n, v1, v2, v3, g.t_rows, part, cnt, ep, guard)
+#define POGS_T(E) pogs_colsum_kernel<NRHS, SQ, E><<<grid, 256, 0, s>>>(A, lda, m, n, v1, v2, v3, g.t_rows, part, cnt, ep, guard)
   switch (epi) {
     case EPT_RAW: POGS_T(EPT_RAW); break;
     case EPT_TALL_R: POGS_T(EPT_TALL_R); break;
@@ -745,10 +745,10 @@ static void gemv_n_dispatch(int epi, const float* A, int64_t lda, int m, int n, 
 #define POGS_N(E)                                                                                         \
   do {                                                                                                    \
     if (g.n_rows >= 32)                                                                                   \
-      gemv_n_kernel<NRHS, SQ, E, 8><<<grid, 256, smem, s>>>(A, lda, m, n, x1, x2, g.n_rows, g.n_cols, part, \
+      pogs_rowdot_kernel<NRHS, SQ, E, 8><<<grid, 256, smem, s>>>(A, lda, m, n, x1, x2, g.n_rows, g.n_cols, part, \
                                                             cnt, ep, guard);                               \
     else                                                                                                  \
-      gemv_n_kernel<NRHS, SQ, E, 4><<<grid, 256, smem, s>>>(A, lda, m, n, x1, x2, g.n_rows, g.n_cols, part, \
+      pogs_rowdot_kernel<NRHS, SQ, E, 4><<<grid, 256, smem, s>>>(A, lda, m, n, x1, x2, g.n_rows, g.n_cols, part, \
                                                             cnt, ep, guard);                               \
   } while (0)
   switch (epi) {

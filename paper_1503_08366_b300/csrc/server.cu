@@ -281,6 +281,7 @@ int pogs_server_create(size_t hbm_budget, int large_workers, int max_resident, c
   c.adaptive = S->p.adaptive_rho; c.sk_sweeps = S->p.sk_sweeps; c.equil = S->p.equil;
   c.mixed_chol = S->p.chol_prec == POGS_CHOL_MIXED;
   int dev = 0;
+  count_alloc(5);
   bool ok = cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&S->num_sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
             cudaMalloc(&S->d_outs, sizeof(BOut) * S->cap) == cudaSuccess &&
@@ -368,6 +369,7 @@ int pogs_server_step(pogs_server* S, int iters) {
   StepHold hold;
   hold.take(S->gate);
   for (SReq* r : fresh) {
+    count_alloc();
     if (cudaMallocAsync((void**)&r->arena, r->bytes, s) != cudaSuccess) {
       cudaGetLastError();
       return POGS_ERR_OOM;

@@ -75,6 +75,7 @@ struct pogs_handle {
 };
 
 std::atomic<long long> pogs::g_launch_count{0};
+std::atomic<long long> pogs::g_alloc_count{0};
 thread_local int pogs::g_capture_depth = 0;
 
 // Stream-ordered device memory: one pool per device that keeps freed memory cached up to a
@@ -108,6 +109,7 @@ int pogs::pool_alloc(void** q, size_t bytes, cudaStream_t s) {
     }
     pool = pools[dev];
   }
+  count_alloc();
   if (cudaMallocFromPoolAsync(q, bytes, pool, s) != cudaSuccess) {
     cudaGetLastError();
     *q = nullptr;
@@ -1163,6 +1165,8 @@ int pogs_get_setup_report(const pogs_handle* h, pogs_setup_report* r) {
 }
 
 long long pogs_kernel_launches(void) { return g_launch_count.load(); }
+
+long long pogs_device_allocations(void) { return g_alloc_count.load(); }
 
 int pogs_time_kernels(pogs_handle* h, int reps, double* ms, double* bytes) {
   if (!h || reps < 1 || !h->solved || h->indirect) return POGS_ERR_ARG;   // times the direct projection

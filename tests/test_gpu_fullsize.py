@@ -6,8 +6,10 @@ inputs resident on the device, the device-side graph loop):
     by tests/golden/make_bench_refs.py, which runs only the oracle);
   * primal and dual feasibility of the returned unscaled tuple, ||A x - y|| and ||A^T nu + mu||,
     recomputed in FP64 on the host;
-  * one full-size projection of random (c, d): its optimality conditions x - c + A^T(y - d) = 0
-    and y = A x, checked in FP64 on the handle's A^ (a property that holds at any size).
+  * one full-size projection of random (c, d) in the benchmark's configuration: within 1e-5
+    relative, in x and in y, of the FP64 projection of the same input on the handle's A^
+    (factored on the host in FP64), and its optimality conditions x - c + A^T(y - d) = 0 and
+    y = A x.
 """
 import json
 import os
@@ -16,6 +18,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from oracle import project as OPJ
 
 pytestmark = pytest.mark.gpu
 
@@ -64,6 +67,10 @@ def test_benchmark_solves_at_full_size(P, gen):
     Ah = Ah.astype(np.float64)
     xp64, yp64 = xp.astype(np.float64), yp.astype(np.float64)
     c64, d64 = c.astype(np.float64), d.astype(np.float64)
+    xr, yr = OPJ.Projector(Ah)(c64, d64)
+    ex = np.linalg.norm(xp64 - xr) / np.linalg.norm(xr)
+    ey = np.linalg.norm(yp64 - yr) / np.linalg.norm(yr)
+    assert ex < 1e-5 and ey < 1e-5, (ex, ey)
     stat = xp64 - c64 + Ah.T @ (yp64 - d64)
     assert np.linalg.norm(stat) <= 1e-4 * np.linalg.norm(c64 + Ah.T @ d64), np.linalg.norm(stat)
     assert np.linalg.norm(yp64 - Ah @ xp64) <= 1e-5 * np.linalg.norm(yp64)

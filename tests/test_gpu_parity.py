@@ -135,9 +135,10 @@ CASES = [("lasso", (200, 100)), ("huber", (600, 200)), ("svm", (500, 150)), ("nn
 
 # Classes whose f carries a dense equality or many inequality indicators (the LP's A x <= b,
 # the portfolio's budget 1^T x = 1): at eps_rel = 1e-3 the residual test bounds their objective
-# only loosely -- the FP64 oracle stopped by the same test lands ~1e-3 from p* on them -- so the
-# objective bound is 1e-2 there; both residuals must still meet their tolerances.
-OBJ_TOL = {"portfolio": 1e-2}
+# only loosely -- the FP64 oracle stopped by the same test lands 1e-3 to 2e-3 from p* on them.
+# There the 1e-3 objective bound is taken against that same-test oracle run, and p* is only
+# checked to 1e-2; both residuals must still meet their tolerances.
+SAME_TEST = {"portfolio"}
 
 
 @pytest.mark.parametrize("cls,shape", CASES)
@@ -149,8 +150,12 @@ def test_solve_matches_oracle_objective(P, cls, shape):
     assert info.status == 0, info.as_dict()
     assert info.r_pri < info.eps_pri and info.r_dual < info.eps_dual
     ref = _tight(prob)
-    tol = OBJ_TOL.get(cls, 1e-3)
+    tol = 1e-2 if cls in SAME_TEST else 1e-3
     assert abs(info.obj - ref.obj) <= tol * max(1.0, abs(ref.obj)), (info.obj, ref.obj)
+    if cls in SAME_TEST:
+        same = OA.solve(prob.A, prob.f, prob.g, OA.Params(max_iter=5000))
+        assert same.status == 0
+        assert abs(info.obj - same.obj) <= 1e-3 * max(1.0, abs(same.obj)), (info.obj, same.obj)
     # the objective recomputed in FP64 from the returned (unscaled) tuple agrees too
     obj64 = OA.objective(prob.A, prob.f, prob.g, x.astype(float), y.astype(float), tol=1e-4)
     assert abs(obj64 - ref.obj) <= 2 * tol * max(1.0, abs(ref.obj))
@@ -165,7 +170,11 @@ def test_lp_solution_matches_linprog(P):
     assert info.status == 0
     res = linprog(prob.g.d.astype(float), A_ub=prob.A.astype(float), b_ub=prob.f.b.astype(float),
                   bounds=[(0, None)] * prob.n, method="highs")
+    # p* only to 1e-2: the FP64 oracle stopped by the same test is itself 2e-3 from it here
     assert abs(info.obj - res.fun) <= 1e-2 * max(1.0, abs(res.fun)), (info.obj, res.fun)
+    same = OA.solve(prob.A, prob.f, prob.g, OA.Params(max_iter=10000))
+    assert same.status == 0
+    assert abs(info.obj - same.obj) <= 1e-3 * max(1.0, abs(same.obj)), (info.obj, same.obj)
 
 
 @pytest.mark.parametrize("shape", [(400, 150), (150, 400)])
@@ -248,15 +257,24 @@ def test_degenerate_sizes(P):
         assert info.status in (0, 1) and np.all(np.isfinite(x))
 
 
-@pytest.mark.parametrize("shape", [(1100, 1030), (300, 700), (7000, 3333), (2100, 4100)])
+PROJ_SHAPES = [(1100, 1030), (300, 700), (7000, 3333),
+               (9000, 4100),    # q = 4100: just past the recursive factorization's threshold, ragged
+               (4100, 9000),    # the fat form of the same
+               (12000, 6000)]   # q = 6000: two recursion levels
+
+
+@pytest.mark.parametrize("shape", PROJ_SHAPES)
 @pytest.mark.parametrize("chol", ["FP64", "MIXED"])
-def test_projection_both_cholesky_precisions(P, shape, chol):
-    """Pure FP64 and mixed (FP32 diagonal blocks and products, FP64 Schur complement)
-    factorizations both reproduce the FP64 projection of the same input within 1e-5, up to
-    q = 4100 (33 block columns, ragged last block)."""
+@pytest.mark.parametrize("gram", ["FP32", "BF16X3"])
+def test_projection_both_cholesky_precisions(P, shape, chol, gram):
+    """Pure FP64 and mixed (double-float Schur complement; FP32 or TF32x3 tensor-core products)
+    factorizations, each under the FP32 and the default BF16x3 Gram, reproduce the FP64
+    projection of the same input (the handle's A^, upcast) within 1e-5 relative in x and in y,
+    for q = min(m, n) from 300 to 6000: the blocked factorization below q = 4096 and the
+    recursive one from there on."""
     m, n = shape
     prob = W.huber(m, n, seed=17)
-    prm = P.pogs_default_params(gram_prec="FP32", chol_prec=chol)
+    prm = P.pogs_default_params(gram_prec=gram, chol_prec=chol)
     with P.Solver(prob.A, prm) as s:
         proj = OPJ.Projector(s.ahat().astype(np.float64))
         rng = np.random.default_rng(3)
@@ -265,7 +283,7 @@ def test_projection_both_cholesky_precisions(P, shape, chol):
         x, y = s.project(c, d, prm)
         assert P.pogs_get_setup_report(s.handle).chol_prec_used == P.CHOL[chol]
     xr, yr = proj(c.astype(np.float64), d.astype(np.float64))
-    assert _rel(x, xr) < 1e-5 and _rel(y, yr) < 1e-5
+    assert _rel(x, xr) < 1e-5 and _rel(y, yr) < 1e-5, (_rel(x, xr), _rel(y, yr))
 
 
 def test_instrumentation_entry_points(P):
