@@ -199,7 +199,7 @@ def oracle_full_size_timing(probs, iters, sample_iters):
     return len(probs) / total, parts
 
 
-def oracle_sample_check(pool, served_obj, seconds=20.0, one_thread_seconds=0.0):
+def oracle_sample_check(pool, served_obj, seconds=20.0, one_thread_seconds=0.0, one_thread_pool=None):
     """The oracle as it stands, solving the distinct problems of `pool` one after another until
     `seconds` have passed (a bounded sample; its sequential throughput is the workload's CPU
     baseline), and every GPU result for a sampled problem checked against the oracle's
@@ -207,7 +207,8 @@ def oracle_sample_check(pool, served_obj, seconds=20.0, one_thread_seconds=0.0):
 
     served_obj: {index into pool: [objective of every GPU result for that problem]}.
     one_thread_seconds > 0 also times the same problems in order with BLAS limited to one
-    thread, for about that long (`value_1thread`).
+    thread, for about that long (`value_1thread`); one_thread_pool is the Python expression that
+    rebuilds `pool` in the child process that does it.
     Returns (cpu_baseline, check)."""
     from oracle import admm as OA
     t0 = time.perf_counter()
@@ -228,22 +229,39 @@ def oracle_sample_check(pool, served_obj, seconds=20.0, one_thread_seconds=0.0):
     cpu = dict(value=len(ref) / elapsed, unit="solves/s", cores=_threads(), cpu_count=os.cpu_count(),
                kind="oracle",
                sample=f"first {len(ref)} of {len(pool)} distinct problems, solved in sequence ({elapsed:.1f} s)")
-    if one_thread_seconds > 0:
-        from threadpoolctl import threadpool_limits
-        done = 0
-        with threadpool_limits(limits=1):
-            t1 = time.perf_counter()
-            for pb in pool[:len(ref)]:
-                if done and time.perf_counter() - t1 >= one_thread_seconds:
-                    break
-                OA.solve(pb.A, pb.f, pb.g, OA.Params())
-                done += 1
-            cpu["value_1thread"] = done / (time.perf_counter() - t1)
-            cpu["sample_1thread"] = f"first {done} of the same problems, BLAS limited to one thread"
+    if one_thread_seconds > 0 and one_thread_pool:
+        # the same problems in order, in a child process with one BLAS thread
+        out = oracle_one_thread(
+            "import json, time, workloads as W\n"
+            "from oracle import admm as OA\n"
+            f"probs = {one_thread_pool}\n"
+            "t1 = time.perf_counter(); done = 0\n"
+            "for pb in probs:\n"
+            f"    if done and time.perf_counter() - t1 >= {one_thread_seconds}: break\n"
+            "    OA.solve(pb.A, pb.f, pb.g, OA.Params()); done += 1\n"
+            "print(json.dumps(dict(done=done, seconds=time.perf_counter() - t1)))\n")
+        if out:
+            cpu["value_1thread"] = out["done"] / out["seconds"]
+            cpu["sample_1thread"] = (f"first {out['done']} of the same problems in a child process with one BLAS "
+                                     "thread")
     check = dict(payloads=len(ref), oracle_converged=sum(1 for o in ref.values() if o[1] == 0),
                  requests_checked=checked, max_rel_obj_err=max(errs) if errs else None,
                  within_1e_3=sum(e <= 1e-3 for e in errs), within_1e_2=sum(e <= 1e-2 for e in errs))
     return cpu, check
+
+
+def oracle_one_thread(script: str, timeout: float = 300.0):
+    """Run `script` (Python source that prints one JSON line last) in a child process whose BLAS
+    uses one thread: the thread counts are set in its environment before NumPy loads.  The child
+    runs only the oracle (no CUDA).  Returns the parsed line, or None if the child failed."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", script], env=env, cwd=ROOT, capture_output=True, text=True,
+                           timeout=timeout)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception:  # noqa: BLE001
+        return None
 
 
 def _threads():
@@ -519,7 +537,6 @@ def small_lasso_measure(reps=50):
     import paper_1503_08366_b300 as P
     import workloads as W
     from oracle import admm as OA
-    from threadpoolctl import threadpool_limits
     prob = W.lasso_small(0)
     prm = P.pogs_default_params(max_iter=2000)
 
@@ -544,8 +561,15 @@ def small_lasso_measure(reps=50):
             out.append(time.perf_counter() - t0)
         return out, r
     o_all, ref = oracle_times(5)
-    with threadpool_limits(limits=1):
-        o_one, _ = oracle_times(5)
+    one = oracle_one_thread(
+        "import json, time, numpy as np, workloads as W\n"
+        "from oracle import admm as OA\n"
+        "prob = W.lasso_small(0); ts = []\n"
+        "for _ in range(5):\n"
+        "    t0 = time.perf_counter(); OA.solve(prob.A, prob.f, prob.g, OA.Params(max_iter=2000))\n"
+        "    ts.append(time.perf_counter() - t0)\n"
+        "print(json.dumps(dict(ts=ts)))\n")
+    o_one = one["ts"] if one else [float("nan")]
     med = lambda v: float(np.median(v))
     return dict(workload="plain single Lasso solve 200x100, eps_abs=1e-4, eps_rel=1e-3, max_iter 2000",
                 gpu=dict(ms_per_solve=1e3 * med(ts), solves_per_s=1.0 / med(ts), iters=info.iters,
@@ -553,7 +577,8 @@ def small_lasso_measure(reps=50):
                          timing="wall clock per pogs_setup + pogs_solve + pogs_free call from host arrays"),
                 oracle=dict(ms_per_solve=1e3 * med(o_all), solves_per_s=1.0 / med(o_all), iters=ref.iters,
                             obj=ref.obj, cores=_threads(), cpu_count=os.cpu_count()),
-                oracle_1thread=dict(ms_per_solve=1e3 * med(o_one), solves_per_s=1.0 / med(o_one), cores=1),
+                oracle_1thread=dict(ms_per_solve=1e3 * med(o_one), solves_per_s=1.0 / med(o_one), cores=1,
+                                    how="child process with one BLAS thread"),
                 obj_rel_err=abs(info.obj - ref.obj) / max(1.0, abs(ref.obj)))
 
 
@@ -645,7 +670,8 @@ def batch_measure(args):
         bulk = dict(count=len(conv), value=len(conv) / t_sub, unit="solves/s", achieved=b_sub / t_sub / 1e9,
                     frac=b_sub / t_sub / 1e9 / peaks["hbm"], iters_max=max(res[i][0].iters for i in conv))
     cpu, check = (None, None) if args.no_cpu_baseline else \
-        oracle_sample_check(probs, {i: [r[0].obj] for i, r in enumerate(res)}, one_thread_seconds=10.0)
+        oracle_sample_check(probs, {i: [r[0].obj] for i, r in enumerate(res)}, one_thread_seconds=10.0,
+                            one_thread_pool=f"W.batch_mix(count={args.count})")
     # plain: the single-problem path, one instance at a time (a bounded sample, extrapolated)
     k = min(args.plain_sample, len(probs))
     t0 = time.perf_counter()

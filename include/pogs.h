@@ -106,13 +106,17 @@ typedef struct {
   int proj_mode;     /* POGS_PROJ_DIRECT (default): cached factor of I + A^T A (or I + A A^T);
                         POGS_PROJ_CGLS: indirect projection (Section 3.5), no Gram and no
                         factorization -- CGLS on the reduced least-squares problem, started
-                        from the previous projection; fixed at setup                     */
+                        from the previous projection;
+                        POGS_PROJ_LDL (sparse A, pogs_setup_csr only): sparse LDL^T of the
+                        quasi-definite K = [I A^T; A -I] (Section 3.5), fill-reducing
+                        ordering on the host, factored once on the device and cached;
+                        fixed at setup                                                   */
   int cg_max_iter;   /* CGLS steps per projection, at most (default 30)                 */
   double cg_tol;     /* CGLS stop: ||B^T r|| <= cg_tol ||r||, B = [A; I] or [A^T; I]
                         (LSQR's first test with ||B|| = 1; default 1e-4)                */
 } pogs_params;
 
-enum { POGS_PROJ_DIRECT = 0, POGS_PROJ_CGLS = 1 };
+enum { POGS_PROJ_DIRECT = 0, POGS_PROJ_CGLS = 1, POGS_PROJ_LDL = 2 };
 
 /* Arithmetic of the Cholesky factorization of I + G (Section 3.5). */
 enum {
@@ -367,6 +371,19 @@ long long pogs_device_allocations(void);
  * and returns its status: POGS_ERR_TIMEOUT when the bound works (the context stays usable),
  * POGS_ERR_CUDA / POGS_ERR_OOM on a runtime failure. */
 int pogs_check_bounded_wait(void* stream);
+
+/* Symbolic analysis of the sparse LDL^T factorization of the quasi-definite matrix
+ * K = [I A^T; A -I] (Section 3.5: for sparse A, factor K once and cache the factor), for the
+ * m x n pattern of A given in CSR (rowptr: m + 1 entries, rowptr[0] = 0; colind: sorted and
+ * unique within each row, in [0, n); host arrays the caller keeps).  Host work only, no device
+ * call.  The unknowns of K are numbered x_0..x_{n-1}, then y_0..y_{m-1} (index n + i).
+ * Outputs (each may be NULL): stats[0..7] = N = n + m, structural nonzeros of L below the
+ * diagonal, supernodes, levels of the supernodal tree, largest frontal matrix, factor entries
+ * stored, update-matrix entries, frontal scratch entries; perm[N]: the fill-reducing ordering
+ * (new position -> unknown); colcount[N]: nonzeros of each column of L below the diagonal, in
+ * the new order.  Errors: ARG (sizes, NULL, malformed pattern). */
+int pogs_ldl_analyze(int64_t m, int64_t n, const int* rowptr, const int* colind, int64_t* stats, int* perm,
+                     int* colcount);
 
 #ifdef __cplusplus
 }

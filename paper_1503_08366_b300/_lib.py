@@ -24,7 +24,7 @@ OK, MAX_ITER = 0, 1
 ERR = {-1: "ARG", -2: "OOM", -3: "NONFINITE", -4: "NUMERIC", -5: "TIMEOUT", -6: "CUDA", -7: "CAPACITY"}
 GRAM = dict(BF16=0, TF32=1, BF16X3=2, FP32=3)
 CHOL = dict(FP64=0, MIXED=1)
-PROJ = dict(DIRECT=0, CGLS=1)
+PROJ = dict(DIRECT=0, CGLS=1, LDL=2)
 
 
 class pogs_fn(C.Structure):
@@ -128,6 +128,8 @@ lib.pogs_kernel_launches.argtypes = []
 lib.pogs_kernel_launches.restype = C.c_longlong
 lib.pogs_device_allocations.argtypes = []
 lib.pogs_device_allocations.restype = C.c_longlong
+lib.pogs_ldl_analyze.argtypes = [C.c_int64, C.c_int64, _P, _P, _P, _P, _P]
+lib.pogs_ldl_analyze.restype = C.c_int
 
 
 class PogsError(RuntimeError):
@@ -347,6 +349,23 @@ def pogs_kernel_launches() -> int:
 
 def pogs_device_allocations() -> int:
     return int(lib.pogs_device_allocations())
+
+
+LDL_STATS = ("N", "nnz_l", "supernodes", "levels", "max_front", "panel_entries", "update_entries", "front_entries")
+
+
+def pogs_ldl_analyze(indptr, indices, shape):
+    """Symbolic analysis of the sparse LDL^T of K = [I A^T; A -I] for a CSR pattern (host arrays):
+    returns (stats dict, perm, colcount)."""
+    m, n = shape
+    rp = np.ascontiguousarray(indptr, dtype=np.int32)
+    ci = np.ascontiguousarray(indices, dtype=np.int32)
+    stats = (C.c_int64 * 8)()
+    perm = np.empty(m + n, np.int32)
+    cc = np.empty(m + n, np.int32)
+    _check(lib.pogs_ldl_analyze(m, n, rp.ctypes.data, ci.ctypes.data, stats, perm.ctypes.data, cc.ctypes.data),
+           "pogs_ldl_analyze")
+    return {k: int(stats[i]) for i, k in enumerate(LDL_STATS)}, perm, cc
 
 
 def pogs_gram(A, gram_prec="BF16X3", stream=None):

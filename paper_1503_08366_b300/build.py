@@ -15,8 +15,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libpogs_b300.so")
-SOURCES = ["iter.cu", "setup.cu", "chol.cu", "cgls.cu", "csr.cu", "solver.cu", "gram.cu", "noalloc.cu", "batch.cu", "batch_api.cu", "server.cu"]
-HEADERS = ["common.cuh", "prox.cuh", "kernels.h", "tc.cuh", "batch.h", "gate.h", os.path.join("..", "..", "include", "pogs.h")]
+SOURCES = ["iter.cu", "setup.cu", "chol.cu", "cgls.cu", "csr.cu", "solver.cu", "gram.cu", "noalloc.cu", "ldl_sym.cu", "ldl.cu", "batch.cu", "batch_api.cu", "server.cu"]
+HEADERS = ["common.cuh", "prox.cuh", "kernels.h", "tc.cuh", "batch.h", "gate.h", "ldl.h", os.path.join("..", "..", "include", "pogs.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

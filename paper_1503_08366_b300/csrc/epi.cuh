@@ -97,4 +97,30 @@ __device__ __forceinline__ void epi_n(const EpiArgs& ep, int i, float u1, float 
   }
 }
 
+// Epilogue of the products with the cached inverse (packed-triangle or sparse LDL^T solves): one
+// element idx of the result v.
+template <int EPI>
+__device__ __forceinline__ void epi_r(const EpiArgs& ep, int idx, int q, float v) {
+  if constexpr (EPI == EPR_RAW) {
+    ep.out1[idx] = v;
+  } else if constexpr (EPI == EPR_ADD) {
+    if (idx < q) ep.out1[idx] = ep.in1[idx] + v;
+  } else if constexpr (EPI == EPR_TALL_X) {
+    if (idx < q) {
+      const float c = ep.cx[idx];
+      const float xv = ep.in1 ? ep.in1[idx] + v : v;   // in1: refinement base x0
+      ep.x[idx] = xv;
+      ep.xt[idx] += c - xv;             // x~ <- x~ + x_r - x^{k+1}
+    }
+  } else if constexpr (EPI == EPR_FAT_Y) {
+    if (idx < q) {
+      const float d = ep.dy[idx];
+      const float yp = d + (ep.in1 ? ep.in1[idx] + v : v);
+      ep.y[idx] = yp;
+      ep.yt[idx] += d - yp;             // y~ <- y~ + y_r - y^{k+1}
+      ep.w[idx] = d - yp;
+    }
+  }
+}
+
 }  // namespace pogs

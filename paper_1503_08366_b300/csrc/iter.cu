@@ -323,30 +323,6 @@ __global__ void __launch_bounds__(256) pogs_rowdot_kernel(const float* __restric
 // padding rows/cols are zero).  One block per tile; partial tile products are reduced by
 // the last block of each tile row (z = M v) or tile column (x = M^T v).
 // ------------------------------------------------------------------------------------------
-template <int EPI>
-__device__ __forceinline__ void epi_r(const EpiArgs& ep, int idx, int q, float v) {
-  if constexpr (EPI == EPR_RAW) {
-    ep.out1[idx] = v;
-  } else if constexpr (EPI == EPR_ADD) {
-    if (idx < q) ep.out1[idx] = ep.in1[idx] + v;
-  } else if constexpr (EPI == EPR_TALL_X) {
-    if (idx < q) {
-      const float c = ep.cx[idx];
-      const float xv = ep.in1 ? ep.in1[idx] + v : v;   // in1: refinement base x0
-      ep.x[idx] = xv;
-      ep.xt[idx] += c - xv;             // x~ <- x~ + x_r - x^{k+1}
-    }
-  } else if constexpr (EPI == EPR_FAT_Y) {
-    if (idx < q) {
-      const float d = ep.dy[idx];
-      const float yp = d + (ep.in1 ? ep.in1[idx] + v : v);
-      ep.y[idx] = yp;
-      ep.yt[idx] += d - yp;             // y~ <- y~ + y_r - y^{k+1}
-      ep.w[idx] = d - yp;
-    }
-  }
-}
-
 // Sum of k partials p[0], p[stride], ... in index order, eight loads in flight per round trip.
 __device__ __forceinline__ float sum_slots(const float* __restrict__ p, int k, int64_t stride) {
   float s = 0.0f;

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "ldl.h"
 
 using namespace pogs;
 
@@ -52,6 +53,7 @@ struct pogs_handle {
   Df *prox_part = nullptr, *pri_part = nullptr, *dual_part = nullptr;   // block partials (double-float)
   // indirect projection (CGLS): vectors, state, partials
   bool indirect = false;             // set up without a factor (proj_mode CGLS)
+  LdlFactor* ldl = nullptr;          // sparse LDL^T of K (proj_mode LDL, CSR input)
   float *cg_rt = nullptr, *cg_rb = nullptr, *cg_s = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_z = nullptr;
   CgState* cg = nullptr;
   CgState* cg_host = nullptr;        // pinned staging
@@ -309,6 +311,10 @@ void enqueue_projection_cgls(pogs_handle* h, int steps, cudaStream_t s) {
 // (I + G)^{-1} v with the given final epilogue: one symmetric pass over S, or z = M v then M^T z.
 void apply_inverse(pogs_handle* h, const float* v, int epi, const EpiArgs& ep, cudaStream_t s) {
   const int q = (int)h->q;
+  if (h->ldl) {   // sparse LDL^T of K: (I + A^T A)^{-1} v or (I + A A^T)^{-1} v
+    ldl_apply(*h->ldl, h->tall, v, epi, ep, s);
+    return;
+  }
   if (h->St) {
     launch_symv(epi, h->St, h->T, q, v, h->part_sy, h->cnt_tr, ep, h->st, s);
     return;
@@ -405,7 +411,7 @@ int kernels_per_iteration(const pogs_handle* h, int refine, int cg_steps) {
     return 8 + 4 * cg_steps + pk;
   // prox, 2 A passes, check, the inverse (one symmetric or two triangular products) (+ refinement:
   // 2 passes and the inverse again)
-  const int inv = h->St ? 1 : 2;
+  const int inv = h->ldl ? ldl_launches(*h->ldl) : h->St ? 1 : 2;
   return 4 + inv + (refine ? 2 + inv : 0) + pk;
 }
 
@@ -456,7 +462,7 @@ int validate_params(const pogs_params* p) {
       !(p->alpha < 2) || !(p->delta >= 1) || !(p->tau > 0) || p->sk_sweeps < 0 || p->refine_steps < 0 ||
       p->refine_steps > 1 || p->gram_prec < POGS_GRAM_BF16 || p->gram_prec > POGS_GRAM_FP32 ||
       p->loop_mode < 0 || p->loop_mode > 1 || p->chol_prec < POGS_CHOL_FP64 || p->chol_prec > POGS_CHOL_MIXED ||
-      p->proj_mode < POGS_PROJ_DIRECT || p->proj_mode > POGS_PROJ_CGLS || p->cg_max_iter < 0 ||
+      p->proj_mode < POGS_PROJ_DIRECT || p->proj_mode > POGS_PROJ_LDL || p->cg_max_iter < 0 ||
       p->cg_max_iter > 1000 || !(p->cg_tol >= 0))
     return POGS_ERR_ARG;
   return 0;
@@ -579,6 +585,26 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order, const Cs
   else launch_scale(h->A, h->lda, m, n, h->D, h->E, s);
   CK(cudaGetLastError());
   phase("equil");
+  if (h->sp.proj_mode == POGS_PROJ_LDL) {
+    // sparse direct projection: symbolic analysis of K on the host, numeric LDL^T on the device
+    if (!csr) return POGS_ERR_ARG;
+    std::vector<int> hrp(m + 1), hci(std::max<int64_t>(1, h->nnz));
+    CK(cudaMemcpyAsync(hrp.data(), h->csr_rp, sizeof(int) * (m + 1), cudaMemcpyDeviceToHost, s));
+    if (h->nnz > 0) CK(cudaMemcpyAsync(hci.data(), h->csr_ci, sizeof(int) * h->nnz, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    LdlSymbolic S;
+    TRY(ldl_analyze((int)m, (int)n, hrp.data(), hci.data(), S));
+    phase("gram");
+    h->ldl = new (std::nothrow) LdlFactor();
+    if (!h->ldl) return POGS_ERR_OOM;
+    TRY(ldl_factor(S, h->csr_va, *h->ldl, err, s));
+    h->device_bytes += h->ldl->device_bytes;
+    CK(cudaGetLastError());
+    phase("cholesky");
+    phase("inverse");
+    CK(cudaStreamSynchronize(s));
+    return 0;
+  }
   if (h->sp.proj_mode == POGS_PROJ_CGLS) {
     // indirect projection: no Gram, no factorization (the phases are recorded empty)
     h->indirect = true;
@@ -764,6 +790,10 @@ void release(pogs_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
+  if (h->ldl) {
+    h->ldl->release(h->stream);
+    delete h->ldl;
+  }
   pin_slot_put(h->st_host);
   if (h->cap) cudaStreamDestroy(h->cap);
   for (cudaEvent_t e : h->ev)
@@ -1199,6 +1229,11 @@ int pogs_time_kernels(pogs_handle* h, int reps, double* ms, double* bytes) {
     }
     b[4] = At + 12 * m + 20 * n;                           // A^T [w, nu, y~] ; c, mu, E in ; x, x~ out
   }
+  if (h->ldl) {   // the factor read twice (forward, backward), the work vector, the in/out vectors
+    const LdlFactor& F = *h->ldl;
+    b[2] = 2.0 * (double)F.panel_entries * 8.0 + 4.0 * 8.0 * F.N + 24.0 * q;
+    b[3] = 0.0;
+  }
   b[5] = 0.0;
   b[6] = b[0] + b[1] + b[2] + b[3] + b[4];
   // keep the stopping test from ever firing: zero tolerances, no iteration cap
@@ -1237,6 +1272,16 @@ int pogs_time_kernels(pogs_handle* h, int reps, double* ms, double* bytes) {
       }
       case 2: {
         EpiArgs e = epi0();
+        if (h->ldl) {   // the sparse LDL^T solve (all its launches)
+          if (h->tall) {
+            e.x = h->x; e.xt = h->xt; e.cx = h->cx;
+            ldl_apply(*h->ldl, true, h->r, EPR_TALL_X, e, s);
+          } else {
+            e.y = h->y; e.yt = h->yt; e.dy = h->dy; e.w = h->w;
+            ldl_apply(*h->ldl, false, h->r, EPR_FAT_Y, e, s);
+          }
+          break;
+        }
         if (h->St) {   // the whole inverse in one symmetric pass
           if (h->tall) {
             e.x = h->x; e.xt = h->xt; e.cx = h->cx;
@@ -1252,7 +1297,7 @@ int pogs_time_kernels(pogs_handle* h, int reps, double* ms, double* bytes) {
         break;
       }
       case 3: {
-        if (h->St) break;
+        if (h->St || h->ldl) break;
         EpiArgs e = epi0();
         if (h->tall) {
           e.x = h->x; e.xt = h->xt; e.cx = h->cx;

@@ -17,7 +17,10 @@ def test_oracle_sample_check_bookkeeping():
     assert abs(check["max_rel_obj_err"] - 5e-3 * abs(ref[1]) / max(1.0, abs(ref[1]))) < 1e-12
     assert cpu["kind"] == "oracle" and cpu["value"] > 0 and cpu["cores"] >= 1
     assert cpu["cpu_count"] >= 1 and "value_1thread" not in cpu
-    cpu1, _ = bench.oracle_sample_check(pool, served, seconds=60.0, one_thread_seconds=60.0)
+    # one BLAS thread: a child process rebuilds the pool from the expression it is given
+    cpu1, _ = bench.oracle_sample_check(
+        pool, served, seconds=60.0, one_thread_seconds=60.0,
+        one_thread_pool="[W.lasso(60, 30, seed=1), W.nnls(50, 20, seed=2), W.huber(40, 25, seed=3)]")
     assert cpu1["value_1thread"] > 0 and "first 3 " in cpu1["sample_1thread"]
     # the sample is bounded: with no time allowed, only the first payload is solved
     cpu0, check0 = bench.oracle_sample_check(pool, served, seconds=0.0)

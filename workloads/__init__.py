@@ -278,6 +278,62 @@ def sparse_lasso(m: int, n: int, seed: int, per_row: int = 100, nnz_frac=0.1, no
     return Problem("sparse_lasso", A, f, g, dict(lam=lam, seed=seed, nnz=int(A.nnz)))
 
 
+def _csr_lasso(name, rows, cols, vals, m, n, rng, nnz_frac, noise_std, lam_frac, meta) -> Problem:
+    """Lasso data (the Appendix A.4 recipe) on a sparse A given as COO triples."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix((np.asarray(vals, np.float32), (rows, cols)), shape=(m, n), dtype=np.float32)
+    A.sum_duplicates()
+    A.sort_indices()
+    x_true = _sparse_vector(rng, n, nnz_frac)
+    A64 = A.astype(np.float64)
+    b = (A64 @ x_true + rng.standard_normal(m) * noise_std).astype(np.float32)
+    lam = float(lam_frac * np.max(np.abs(A64.T @ b.astype(np.float64))))
+    return Problem(name, A, FnParams.make(m, H["SQUARE"], b=b), FnParams.make(n, H["ABS"], c=lam),
+                   dict(meta, lam=lam, nnz=int(A.nnz)))
+
+
+def banded_lasso(m: int, n: int, seed: int, half_band: int = 8, nnz_frac=0.1, noise_std=0.01,
+                 lam_frac=0.1) -> Problem:
+    """Lasso on a banded sparse A (CSR, float32): row i has nonzeros in the 2 * half_band + 1
+    columns around c_i = round(i (n - 1) / (m - 1)) (clipped to [0, n)), values
+    N(0, 1 / (2 half_band + 1)), so that rows have the dense generator's expected norm."""
+    rng = _rng(seed)
+    w = 2 * half_band + 1
+    centre = np.rint(np.arange(m) * (n - 1) / max(1, m - 1)).astype(np.int64)
+    cols = centre[:, None] + np.arange(-half_band, half_band + 1)[None, :]
+    keep = (cols >= 0) & (cols < n)
+    rows = np.repeat(np.arange(m), w).reshape(m, w)
+    vals = _normal32(rng, (m, w), std=1.0 / math.sqrt(w))
+    return _csr_lasso("banded_lasso", rows[keep], cols[keep], vals[keep], m, n, rng, nnz_frac, noise_std,
+                      lam_frac, dict(seed=seed, half_band=half_band))
+
+
+def block_angular_lasso(blocks: int, mb: int, nb: int, coupling: int, seed: int, density=0.2,
+                        coupling_density=0.05, nnz_frac=0.1, noise_std=0.01, lam_frac=0.1) -> Problem:
+    """Lasso on a block-angular sparse A (CSR, float32): `blocks` diagonal blocks of mb x nb with
+    `density` nonzeros each, then `coupling` linking rows over all blocks * nb columns with
+    `coupling_density` nonzeros; values N(0, 1 / (nonzeros per row))."""
+    rng = _rng(seed)
+    m, n = blocks * mb + coupling, blocks * nb
+    R, Cc, V = [], [], []
+    per = max(1, int(round(density * nb)))
+    for k in range(blocks):
+        for i in range(mb):
+            c = np.sort(rng.choice(nb, size=per, replace=False)) + k * nb
+            R.append(np.full(per, k * mb + i))
+            Cc.append(c)
+            V.append(_normal32(rng, (per,), std=1.0 / math.sqrt(per)))
+    perc = max(1, int(round(coupling_density * n)))
+    for i in range(coupling):
+        c = np.sort(rng.choice(n, size=perc, replace=False))
+        R.append(np.full(perc, blocks * mb + i))
+        Cc.append(c)
+        V.append(_normal32(rng, (perc,), std=1.0 / math.sqrt(perc)))
+    return _csr_lasso("block_angular_lasso", np.concatenate(R), np.concatenate(Cc), np.concatenate(V), m, n, rng,
+                      nnz_frac, noise_std, lam_frac,
+                      dict(seed=seed, blocks=blocks, mb=mb, nb=nb, coupling=coupling))
+
+
 CLASSES = dict(lasso=lasso, logistic=logistic, huber=huber, svm=svm, nnls=nnls, lp=lp,
                basis_pursuit=basis_pursuit, entropy=entropy, portfolio=portfolio)
 
