@@ -436,8 +436,8 @@ def run_ours(args):
         it = info.iters
         tall = p.m >= p.n
         sym = kt["LinvT"][1] == 0.0   # the inverse applied as one symmetric product
-        names = dict(prox="prox", A_pass1="gemv_t" if tall else "gemv_n", Linv="symv" if sym else "trmv",
-                     A_pass2="gemv_n" if tall else "gemv_t", check="check")
+        names = dict(prox="prox", A_pass1="colsum" if tall else "rowdot", Linv="symv" if sym else "trmv",
+                     A_pass2="rowdot" if tall else "colsum", check="check")
         if not sym:
             names["LinvT"] = "trmv_t"
         for name, t in (("equil", rep.equil_ms), ("gram", rep.gram_ms), ("factor", rep.factor_ms),

@@ -290,7 +290,8 @@ __global__ void __launch_bounds__(NT) bsetup_chol_kernel(BInst* insts, int mixed
 
 // ---------------------------------------------------------------------------------------------
 // Setup 4: M = L^{-1} (FP32, dense lower, ld q), one column per thread by forward substitution
-// with FP64 accumulation.
+// with FP64 accumulation.  The loads of each dot product are issued eight at a time before they
+// are accumulated (in the same order), so a column waits for one L2 round trip per eight terms.
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) bsetup_inverse_kernel(BInst* insts) {
   BInst I = insts[blockIdx.x];
@@ -304,7 +305,19 @@ __global__ void __launch_bounds__(NT) bsetup_inverse_kernel(BInst* insts) {
     for (int i = c + 1; i < q; ++i) {
       const double* li = L + (int64_t)i * q;
       double acc = 0.0;
-      for (int k = c; k < i; ++k) acc -= li[k] * (double)M[(int64_t)k * q + c];
+      int k = c;
+      for (; k + 8 <= i; k += 8) {
+        double lv[8];
+        float mv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          lv[u] = li[k + u];
+          mv[u] = M[(int64_t)(k + u) * q + c];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc -= lv[u] * (double)mv[u];
+      }
+      for (; k < i; ++k) acc -= li[k] * (double)M[(int64_t)k * q + c];
       M[(int64_t)i * q + c] = (float)(acc / li[i]);
     }
   }
@@ -320,13 +333,29 @@ __device__ __forceinline__ void zero_state(const BInst& I) {
   for (int i = threadIdx.x; i < I.m; i += NT) { I.y[i] = 0.0f; I.yt[i] = 0.0f; }
 }
 
-// Row dots u = A [x1, x2] for the rows of the instance (warp per row).
+// Row dots u = A [x1, x2] for the rows of the instance (warp per row); four column steps' loads
+// are issued before they are accumulated (in column order).
 __device__ __forceinline__ void rowdots(const float* A, int lda, int m, int n, const float* x1, const float* x2,
                                         int i, float& u1, float& u2) {
   const int lane = threadIdx.x & 31;
   const float* a = A + (int64_t)i * lda;
   float s1 = 0.f, s2 = 0.f;
-  for (int j = lane; j < n; j += 32) {
+  int j = lane;
+  for (; j + 96 < n; j += 128) {
+    float av[4], v1[4], v2[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      av[u] = a[j + 32 * u];
+      v1[u] = x1[j + 32 * u];
+      v2[u] = x2[j + 32 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      s1 = fmaf(av[u], v1[u], s1);
+      s2 = fmaf(av[u], v2[u], s2);
+    }
+  }
+  for (; j < n; j += 32) {
     const float av = a[j];
     s1 = fmaf(av, x1[j], s1);
     s2 = fmaf(av, x2[j], s2);
@@ -335,24 +364,95 @@ __device__ __forceinline__ void rowdots(const float* A, int lda, int m, int n, c
   u2 = warp_sum(s2);
 }
 
-// Column sums t_j = sum_i A_ij v_i for three vectors (thread per column).
-__device__ __forceinline__ void colsum3(const float* A, int lda, int m, int j, const float* v1, const float* v2,
-                                        const float* v3, float& t1, float& t2, float& t3) {
-  float s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  for (int i = 0; i < m; ++i) {
-    const float av = A[(int64_t)i * lda + j];
-    s1 = fmaf(av, v1[i], s1);
-    s2 = fmaf(av, v2[i], s2);
-    s3 = fmaf(av, v3[i], s3);
+// z_i = sum_{k <= i} M_ik r_k for the rows of M (warp per row), loads hoisted as in rowdots.
+__device__ __forceinline__ float lower_rowdot(const float* mi, const float* r, int i) {
+  const int lane = threadIdx.x & 31;
+  float s = 0.f;
+  int k = lane;
+  for (; k + 96 <= i; k += 128) {
+    float mv[4], rv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      mv[u] = mi[k + 32 * u];
+      rv[u] = r[k + 32 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s = fmaf(mv[u], rv[u], s);
   }
-  t1 = s1;
-  t2 = s2;
-  t3 = s3;
+  for (; k <= i; k += 32) s = fmaf(mi[k], r[k], s);
+  return warp_sum(s);
 }
 
-__device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, double* red, Loop* L, int max_steps) {
+// Copies len floats from src to the shared-memory area dst with every thread (loads in flight
+// together) when `use`; returns the pointer the phase reads.  The caller synchronises.
+__device__ __forceinline__ const float* stage_vec(float* dst, const float* src, int len, bool use) {
+  if (!use) return src;
+  for (int i = threadIdx.x; i < len; i += NT) dst[i] = src[i];
+  return dst;
+}
+
+// Column sums t_r[j] = sum_i X[i][j] v_r[i] (r < NR) over `rows` rows of a row-major matrix, by
+// the whole CTA: warp w takes rows w, w + NW, ...; lane l the columns c0 + l + 32 t (t < 4) of
+// each 128-column chunk, so every warp reads whole rows; the warps' partial sums meet in `red`
+// (NW x NR x 128 floats) and are added in warp order.  fn(j, t) finishes column j (one thread).
+template <int NR, class Fn>
+__device__ __forceinline__ void cta_colsum(const float* X, int ldx, int rows, int cols, const float* v1,
+                                           const float* v2, const float* v3, float* red, Fn fn) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* v[3] = {v1, v2, v3};
+  for (int c0 = 0; c0 < cols; c0 += 128) {
+    float acc[NR][4];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.0f;
+    // four rows' loads in flight per step; each column still sums its rows in increasing order
+    for (int i0 = warp; i0 < rows; i0 += 4 * NW) {
+      float a[4][4], w[4][NR];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int i = i0 + h * NW;
+        const bool ok = i < rows;
+        const float* row = X + (int64_t)(ok ? i : 0) * ldx + c0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) w[h][r] = ok ? v[r][i] : 0.0f;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int j = lane + 32 * t;
+          a[h][t] = (ok && c0 + j < cols) ? row[j] : 0.0f;
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 4; ++h)
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int r = 0; r < NR; ++r) acc[r][t] = fmaf(a[h][t], w[h][r], acc[r][t]);
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) red[(warp * NR + r) * 128 + lane + 32 * t] = acc[r][t];
+    __syncthreads();
+    if (tid < 128 && c0 + tid < cols) {
+      float t[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) sum += red[(w * NR + r) * 128 + tid];
+        t[r] = sum;
+      }
+      fn(c0 + tid, t);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, float* sv, double* red, float* red3,
+                             Loop* L, int max_steps) {
   BOut* out = I.out;
   const int m = I.m, n = I.n, q = I.q, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // the vectors each phase reads are staged in shared memory when three of the longest fit
+  const bool vs = 3 * (m > n ? m : n) <= kBatchVecFloats;
   const float* A = I.A;
   int lda = I.lda;
   if (I.stage_smem) {   // same values, same loop order: only where they are read from changes
@@ -381,7 +481,7 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, doub
     const float rho = (float)L->rho, pend = (float)L->pend;
     const bool rescale = pend != 1.0f;
     // ---- prox step (Algorithm 1, Section 3.2, 3.3) ----
-    double pv[6] = {0, 0, 0, 0, 0, 0};
+    Df pv[6] = {};   // double-float partial sums on the FP32 pipes (B300's FP64 rate is a small fraction)
     for (int k = tid; k < n + m; k += NT) {
       if (k < n) {
         const int j = k;
@@ -394,9 +494,9 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, doub
         I.xh[j] = xhj;
         I.cx[j] = alpha * xhj + (1.0f - alpha) * xj;
         I.mu[j] = muj;
-        pv[0] += (double)muj * muj;
-        pv[1] += (double)xhj * muj;
-        pv[2] += (double)f_param(h, a, b, c, d, e, xhj);
+        df_add_prod(pv[0], muj, muj);
+        df_add_prod(pv[1], xhj, muj);
+        df_add(pv[2], f_param(h, a, b, c, d, e, xhj));
       } else {
         const int i = k - n;
         const float yti = pend * I.yt[i], yi = I.y[i], v = yi - yti;
@@ -408,102 +508,109 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, doub
         I.yh[i] = yhi;
         I.dy[i] = alpha * yhi + (1.0f - alpha) * yi;
         I.nu[i] = nui;
-        pv[3] += (double)yhi * yhi;
-        pv[4] += (double)yhi * nui;
-        pv[5] += (double)f_param(h, a, b, c, d, e, yhi);
+        df_add_prod(pv[3], yhi, yhi);
+        df_add_prod(pv[4], yhi, nui);
+        df_add(pv[5], f_param(h, a, b, c, d, e, yhi));
       }
     }
-    bsum<6>(pv, red);   // includes the barrier that publishes the prox outputs
-    double rs[4] = {0, 0, 0, 0};   // primal^2, primal_u^2, dual^2, dual_u^2
+    double pvs[6];
+    block_sum_df<6>(pv, pvs, red);   // totals in thread 0; its barriers publish the prox outputs
+    Df rs[4] = {};   // primal^2, primal_u^2, dual^2, dual_u^2
     if (I.tall) {
       // r = c + A^T d ; x~ = -A^T y~ ; dual residual (A^T nu + mu)
-      for (int j = tid; j < n; j += NT) {
-        float t1, t2, t3;
-        colsum3(A, lda, m, j, I.dy, I.nu, I.yt, t1, t2, t3);
-        I.r[j] = I.cx[j] + t1;
-        I.xt[j] = -t3;
-        const float dr = t2 + I.mu[j];
-        rs[2] += (double)dr * dr;
+      const float* v1 = stage_vec(sv, I.dy, m, vs);
+      const float* v2 = stage_vec(sv + m, I.nu, m, vs);
+      const float* v3 = stage_vec(sv + 2 * m, I.yt, m, vs);
+      __syncthreads();
+      cta_colsum<3>(A, lda, m, n, v1, v2, v3, red3, [&](int j, const float* t) {
+        I.r[j] = I.cx[j] + t[0];
+        I.xt[j] = -t[2];
+        const float dr = t[1] + I.mu[j];
+        df_add_prod(rs[2], dr, dr);
         const float du = dr / I.E[j];
-        rs[3] += (double)du * du;
-      }
+        df_add_prod(rs[3], du, du);
+      });
+      const float* rr = stage_vec(sv, I.r, q, vs);
       __syncthreads();
+      float* zz = vs ? sv + q : I.z;
       for (int i = warp; i < q; i += NW) {   // z = M r
-        const float* mi = I.M + (int64_t)i * q;
-        float s = 0.f;
-        for (int k = lane; k <= i; k += 32) s = fmaf(mi[k], I.r[k], s);
-        s = warp_sum(s);
-        if (lane == 0) I.z[i] = s;
+        const float s = lower_rowdot(I.M + (int64_t)i * q, rr, i);
+        if (lane == 0) zz[i] = s;
       }
       __syncthreads();
-      for (int j = tid; j < q; j += NT) {     // x = M^T z ; x~ += c - x
-        float s = 0.f;
-        for (int i = j; i < q; ++i) s = fmaf(I.M[(int64_t)i * q + j], I.z[i], s);
-        I.x[j] = s;
-        I.xt[j] += I.cx[j] - s;
-      }
+      cta_colsum<1>(I.M, q, q, q, zz, nullptr, nullptr, red3, [&](int j, const float* t) {   // x = M^T z
+        I.x[j] = t[0];
+        I.xt[j] += I.cx[j] - t[0];                                                         // x~ += c - x
+      });
+      const float* xx = stage_vec(sv, I.x, n, vs);
+      const float* xs = stage_vec(sv + n, I.xh, n, vs);
       __syncthreads();
       for (int i = warp; i < m; i += NW) {    // y = A x, w = A x^ ; y~ += d - y ; primal residual
         float u1, u2;
-        rowdots(A, lda, m, n, I.x, I.xh, i, u1, u2);
+        rowdots(A, lda, m, n, xx, xs, i, u1, u2);
         if (lane == 0) {
           I.y[i] = u1;
           I.yt[i] += I.dy[i] - u1;
           const float pr = u2 - I.yh[i];
-          rs[0] += (double)pr * pr;
+          df_add_prod(rs[0], pr, pr);
           const float pu = pr / I.D[i];
-          rs[1] += (double)pu * pu;
+          df_add_prod(rs[1], pu, pu);
         }
       }
     } else {
+      const float* cc = stage_vec(sv, I.cx, n, vs);
+      const float* xs = stage_vec(sv + n, I.xh, n, vs);
+      __syncthreads();
+      float* rw = vs ? sv + 2 * n : I.r;      // r, read by the next phase only
       for (int i = warp; i < m; i += NW) {    // r = A c - d ; primal residual
         float u1, u2;
-        rowdots(A, lda, m, n, I.cx, I.xh, i, u1, u2);
+        rowdots(A, lda, m, n, cc, xs, i, u1, u2);
         if (lane == 0) {
-          I.r[i] = u1 - I.dy[i];
+          rw[i] = u1 - I.dy[i];
           const float pr = u2 - I.yh[i];
-          rs[0] += (double)pr * pr;
+          df_add_prod(rs[0], pr, pr);
           const float pu = pr / I.D[i];
-          rs[1] += (double)pu * pu;
+          df_add_prod(rs[1], pu, pu);
         }
       }
       __syncthreads();
+      float* zz = vs ? sv : I.z;               // (r sits after the 2n staged floats: no overlap)
       for (int i = warp; i < q; i += NW) {    // z = M r
-        const float* mi = I.M + (int64_t)i * q;
-        float s = 0.f;
-        for (int k = lane; k <= i; k += 32) s = fmaf(mi[k], I.r[k], s);
-        s = warp_sum(s);
-        if (lane == 0) I.z[i] = s;
+        const float s = lower_rowdot(I.M + (int64_t)i * q, rw, i);
+        if (lane == 0) zz[i] = s;
       }
       __syncthreads();
-      for (int i = tid; i < q; i += NT) {     // v = M^T z ; y = d + v ; y~ += d - y ; w = d - y
-        float s = 0.f;
-        for (int k = i; k < q; ++k) s = fmaf(I.M[(int64_t)k * q + i], I.z[k], s);
-        const float d = I.dy[i], yp = d + s;
+      cta_colsum<1>(I.M, q, q, q, zz, nullptr, nullptr, red3, [&](int i, const float* t) {
+        const float d = I.dy[i], yp = d + t[0];   // v = M^T z ; y = d + v ; y~ += d - y ; w = d - y
         I.y[i] = yp;
         I.yt[i] += d - yp;
         I.w[i] = d - yp;
-      }
+      });
+      const float* v1 = stage_vec(sv, I.w, m, vs);
+      const float* v2 = stage_vec(sv + m, I.nu, m, vs);
+      const float* v3 = stage_vec(sv + 2 * m, I.yt, m, vs);
       __syncthreads();
-      for (int j = tid; j < n; j += NT) {     // x = c + A^T w ; x~ = -A^T y~ ; dual residual
-        float t1, t2, t3;
-        colsum3(A, lda, m, j, I.w, I.nu, I.yt, t1, t2, t3);
-        const float c = I.cx[j], xp = c + t1;
+      cta_colsum<3>(A, lda, m, n, v1, v2, v3, red3, [&](int j, const float* t) {
+        const float c = I.cx[j], xp = c + t[0];   // x = c + A^T w ; x~ = -A^T y~ ; dual residual
         I.x[j] = xp;
-        I.xt[j] = -t3;
-        const float dr = t2 + I.mu[j];
-        rs[2] += (double)dr * dr;
+        I.xt[j] = -t[2];
+        const float dr = t[1] + I.mu[j];
+        df_add_prod(rs[2], dr, dr);
         const float du = dr / I.E[j];
-        rs[3] += (double)du * du;
-      }
+        df_add_prod(rs[3], du, du);
+      });
     }
-    bsum<4>(rs, red);
+    double rss[4];
+    block_sum_df<4>(rs, rss, red);
     // ---- stopping test (Section 3.4 + gap) and Algorithm 3 ----
     if (tid == 0) {
-      const double r_pri = sqrt(rs[0]), r_dual = sqrt(rs[2]);
-      const double eps_pri = cfg.abs_tol + cfg.rel_tol * sqrt(pv[3]);
-      const double eps_dual = cfg.abs_tol + cfg.rel_tol * sqrt(pv[0]);
-      const double gap = pv[4] + pv[1], obj = pv[5] + pv[2];
+      // square roots in FP32 of the FP64 totals (seven significant digits are far more than the
+      // tolerance test needs; the FP64 square root is a long sequence on the FP64 pipe)
+      auto rt = [](double a) { return (double)sqrtf((float)a); };
+      const double r_pri = rt(rss[0]), r_dual = rt(rss[2]);
+      const double eps_pri = cfg.abs_tol + cfg.rel_tol * rt(pvs[3]);
+      const double eps_dual = cfg.abs_tol + cfg.rel_tol * rt(pvs[0]);
+      const double gap = pvs[4] + pvs[1], obj = pvs[5] + pvs[2];
       const double eps_gap = cfg.abs_tol + cfg.rel_tol * fabs(obj);
       const int k = L->k;
       L->k = k + 1;
@@ -545,8 +652,8 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, doub
         o.eps_dual = eps_dual;
         o.gap = gap;
         o.obj = obj;
-        o.r_pri_u = sqrt(rs[1]);
-        o.r_dual_u = sqrt(rs[3]);
+        o.r_pri_u = rt(rss[1]);
+        o.r_dual_u = rt(rss[3]);
         *out = o;
       }
     }
@@ -571,9 +678,11 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, doub
 }
 
 __global__ void __launch_bounds__(NT) batch_admm_kernel(BInst* insts, int count, BCfg cfg, int* queue,
-                                                       const int* order, int max_steps) {
+                                                       const int* order, int max_steps, int a_floats) {
   extern __shared__ float smemA[];
+  float* sv = smemA + a_floats;   // kBatchVecFloats of vector staging after the matrix budget
   __shared__ double red[6 * NW];
+  __shared__ float red3[NW * 3 * 128];
   __shared__ Loop L;
   __shared__ int s_idx;
   while (true) {
@@ -586,13 +695,13 @@ __global__ void __launch_bounds__(NT) batch_admm_kernel(BInst* insts, int count,
     const BInst& I = insts[idx];
     if (I.out->status != 0 && I.out->iters == 0) continue;   // setup failed: reported as is
     if (I.loop && I.loop->done) continue;                      // already finished
-    run_instance(I, cfg, smemA, red, &L, max_steps);
+    run_instance(I, cfg, smemA, sv, red, red3, &L, max_steps);
   }
 }
 
 }  // namespace
 
-int batch_max_smem() { return 200 * 1024; }
+int batch_max_smem() { return 184 * 1024; }
 
 int batch_setup(BInst* d_inst, int count, const BCfg& cfg, cudaStream_t s) {
   if (count <= 0) return 0;
@@ -605,7 +714,7 @@ int batch_setup(BInst* d_inst, int count, const BCfg& cfg, cudaStream_t s) {
         if (cudaFuncSetAttribute(bsetup_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, chol_smem) ==
                 cudaSuccess &&
             cudaFuncSetAttribute(batch_admm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 batch_max_smem()) == cudaSuccess)
+                                 batch_max_smem() + kBatchVecFloats * (int)sizeof(float)) == cudaSuccess)
           return 0;
         cudaGetLastError();
         return -1;
@@ -620,7 +729,8 @@ int batch_iterate(BInst* d_inst, int count, const BCfg& cfg, int* d_queue, const
                   int smem_bytes, int max_steps, cudaStream_t s) {
   if (count <= 0) return 0;
   count_launch();
-  batch_admm_kernel<<<grid, NT, smem_bytes, s>>>(d_inst, count, cfg, d_queue, d_order, max_steps);
+  batch_admm_kernel<<<grid, NT, smem_bytes + kBatchVecFloats * sizeof(float), s>>>(d_inst, count, cfg, d_queue,
+                                                                                  d_order, max_steps, smem_bytes / 4);
   return cudaGetLastError() == cudaSuccess ? 0 : POGS_ERR_CUDA;
 }
 

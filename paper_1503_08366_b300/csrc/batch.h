@@ -44,6 +44,8 @@ struct BCfg {
 };
 
 constexpr int kBatchThreads = 256;   // fixed: per-instance arithmetic never depends on the batch
+// Shared-memory floats for the vectors an iteration phase reads (after the matrix budget).
+constexpr int kBatchVecFloats = 6144;
 
 // setup (one CTA per instance) and the persistent iteration kernel
 int batch_setup(BInst* d_inst, int count, const BCfg& cfg, cudaStream_t s);

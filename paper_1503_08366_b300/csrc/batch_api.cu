@@ -38,8 +38,10 @@ struct LaunchCfg {
   int smem;          // shared-memory budget for staging an instance's matrix (0: stream from L2)
   int largest_first; // schedule order
 };
-const LaunchCfg kCandidates[] = {{1, 200 * 1024, 1}, {2, 100 * 1024, 1}, {2, 0, 1},
-                                 {4, 0, 1},          {3, 64 * 1024, 1},  {2, 100 * 1024, 0}};
+// (CTAs per SM, shared-memory budget for the matrix, largest first).  Each CTA also holds 24 KB of
+// staged vectors and 13 KB of reduction buffers, so the candidates fill the SM's 228 KB.
+const LaunchCfg kCandidates[] = {{1, 184 * 1024, 1}, {2, 76 * 1024, 1}, {2, 0, 1},
+                                 {4, 0, 1},          {3, 36 * 1024, 1}, {2, 76 * 1024, 0}};
 std::map<std::tuple<int, int, int>, LaunchCfg> g_tuned;
 std::mutex g_tuned_mu;
 

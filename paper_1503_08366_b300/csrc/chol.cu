@@ -21,6 +21,8 @@
 // recursively, splitting at multiples of 128 so that the leaves are the W_kk above.
 #include <algorithm>
 
+#include <vector>
+
 #include "kernels.h"
 
 namespace pogs {
@@ -242,13 +244,21 @@ __global__ void __launch_bounds__(kDiagThreads) chol_diag_kernel(const float* __
   float* V = S + kDB * kDS;    // [128][129]: W in the lower triangle; panel and T scratch
   float* Dv = V + kDB * kDS;   // [128]: 1 / L_jj
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < kDB * kDB; e += kDiagThreads) {
-    const int i = e >> 7, k = e & 127;
-    float v = 0.0f;
-    if (i < nb && k <= i) v = Hkk[(int64_t)i * ldh + k];
-    else if (i == k) v = 1.0f;
-    S[i * kDS + k] = v;
-    V[i * kDS + k] = 0.0f;
+  {
+    // every load of the block issued before the first store (one round trip to L2 / DRAM)
+    constexpr int kPer = kDB * kDB / kDiagThreads;
+    float ld[kPer];
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+      const int e = tid + t * kDiagThreads, i = e >> 7, k = e & 127;
+      ld[t] = (i < nb && k <= i) ? Hkk[(int64_t)i * ldh + k] : (i == k ? 1.0f : 0.0f);
+    }
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+      const int e = tid + t * kDiagThreads, i = e >> 7, k = e & 127;
+      S[i * kDS + k] = ld[t];
+      V[i * kDS + k] = 0.0f;
+    }
   }
   __syncthreads();
   bool bad = false;
@@ -555,6 +565,11 @@ int chol_mixed(float* G, float* Hlo, int64_t ldh, int64_t q, float* Lf, int64_t 
 namespace {
 
 // Recursive factorization and inversion of the Schur block [r0, r0 + n) (see chol_inv_mixed).
+// The critical chain (leaves, L21, the Schur update, the right half, M21) runs on `s`; the
+// product T = L21 M11 of each level needs only the left half and L21, so it runs on the side
+// stream `s2` (its own tensor-core scratch) while the right half is factored, and M21 = -M22 T
+// waits for it.  Each active level keeps its T in the work area, stacked: a level's T at `T`,
+// its right half's levels above it.
 struct RecCtx {
   float *Hhi, *Hlo;
   int64_t ldh;
@@ -562,12 +577,22 @@ struct RecCtx {
   int64_t ldf;
   float* Md;
   int64_t ldm;
-  float* T;
-  TcScratch tc;
-  cudaStream_t s;
+  TcScratch tc, tc2;
+  cudaStream_t s, s2;
+  std::vector<cudaEvent_t>* events;
 };
 
-void chol_inv_rec(const RecCtx& c, int64_t r0, int64_t n) {
+cudaEvent_t rec_event(const RecCtx& c) {
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  c.events->push_back(e);
+  return e;
+}
+
+void chol_inv_rec(const RecCtx& c, int64_t r0, int64_t n, float* T) {
   if (n <= kDB) {
     count_launch();
     chol_diag_kernel<<<1, kDiagThreads, kDiagSmem, c.s>>>(c.Hhi + r0 * c.ldh + r0, c.ldh, (int)n, c.Md + r0 * c.ldm + r0,
@@ -575,7 +600,7 @@ void chol_inv_rec(const RecCtx& c, int64_t r0, int64_t n) {
     return;
   }
   const int64_t n1 = (cdiv(n, kDB) / 2) * kDB, n2 = n - n1, r1 = r0 + n1;
-  chol_inv_rec(c, r0, n1);
+  chol_inv_rec(c, r0, n1, T);
   const bool tc = c.tc.p && std::min(n1, n2) >= kTcInvMin;
   const float* H21 = c.Hhi + r1 * c.ldh + r0;
   const float* M11 = c.Md + r0 * c.ldm + r0;
@@ -584,23 +609,35 @@ void chol_inv_rec(const RecCtx& c, int64_t r0, int64_t n) {
   if (!(tc && tc_gemm_tf32x3(n2, n1, n1, H21, c.ldh, false, M11, c.ldm, false, 1.0f, L21, nullptr, c.ldf,
                              TC_EPI_STORE, false, c.tc.p, c.tc.bytes, nullptr, c.tc.err, c.s) == 0))
     sgemm_launch<true, OUT_F32, 2>(n2, n1, n1, H21, c.ldh, M11, c.ldm, 1.0f, L21, nullptr, c.ldf, false, 0, c.s);
+  // T = L21 M11 on the side stream, overlapping everything below until M21
+  cudaEvent_t e_l21 = rec_event(c), e_t = rec_event(c);
+  const bool side = c.s2 && e_l21 && e_t;
+  cudaStream_t st = side ? c.s2 : c.s;
+  if (side) {
+    cudaEventRecord(e_l21, c.s);
+    cudaStreamWaitEvent(c.s2, e_l21, 0);
+  }
+  const bool tc_side = tc && (side ? c.tc2.p != nullptr : true);
+  const TcScratch& ts = side ? c.tc2 : c.tc;
+  if (!(tc_side && tc_gemm_nn_tf32x3(n2, n1, n1, L21, c.ldf, M11, c.ldm, 1.0f, T, n1, ts.p, ts.bytes, nullptr,
+                                     ts.err, st) == 0))
+    sgemm_launch<false, OUT_F32, 1>(n2, n1, n1, L21, c.ldf, M11, c.ldm, 1.0f, T, nullptr, n1, false, 1, st);
+  if (side) cudaEventRecord(e_t, c.s2);
   // H22 -= L21 L21^T on the double-float pair (lower triangle)
   float* H22 = c.Hhi + r1 * c.ldh + r1;
   float* H22lo = c.Hlo + r1 * c.ldh + r1;
   if (!(tc && tc_gemm_tf32x3(n2, n2, n1, L21, c.ldf, false, L21, c.ldf, false, 1.0f, H22, H22lo, c.ldh,
                              TC_EPI_DF_SUB, true, c.tc.p, c.tc.bytes, nullptr, c.tc.err, c.s) == 0))
     sgemm_launch<true, OUT_SUB_DF, 2>(n2, n2, n1, L21, c.ldf, L21, c.ldf, 1.0f, H22, H22lo, c.ldh, true, 0, c.s);
-  chol_inv_rec(c, r1, n2);
-  // M21 = -M22 (L21 M11): the off-diagonal block of the inverse
+  chol_inv_rec(c, r1, n2, T + n2 * n1);
+  // M21 = -M22 T: the off-diagonal block of the inverse
+  if (side) cudaStreamWaitEvent(c.s, e_t, 0);
   const float* M22 = c.Md + r1 * c.ldm + r1;
   float* M21 = c.Md + r1 * c.ldm + r0;
-  if (tc && tc_gemm_nn_tf32x3(n2, n1, n1, L21, c.ldf, M11, c.ldm, 1.0f, c.T, n1, c.tc.p, c.tc.bytes, nullptr,
-                              c.tc.err, c.s) == 0 &&
-      tc_gemm_nn_tf32x3(n2, n1, n2, M22, c.ldm, c.T, n1, -1.0f, M21, c.ldm, c.tc.p, c.tc.bytes, nullptr, c.tc.err,
-                        c.s) == 0)
+  if (tc && tc_gemm_nn_tf32x3(n2, n1, n2, M22, c.ldm, T, n1, -1.0f, M21, c.ldm, c.tc.p, c.tc.bytes, nullptr,
+                              c.tc.err, c.s) == 0)
     return;
-  sgemm_launch<false, OUT_F32, 1>(n2, n1, n1, L21, c.ldf, M11, c.ldm, 1.0f, c.T, nullptr, n1, false, 1, c.s);
-  sgemm_launch<false, OUT_F32, 1>(n2, n1, n2, M22, c.ldm, c.T, n1, -1.0f, M21, nullptr, c.ldm, false, 2, c.s);
+  sgemm_launch<false, OUT_F32, 1>(n2, n1, n2, M22, c.ldm, T, n1, -1.0f, M21, nullptr, c.ldm, false, 2, c.s);
 }
 
 }  // namespace
@@ -613,7 +650,8 @@ int chol_inv_mixed(float* G, float* Hlo, int64_t ldh, int64_t q, float* Lf, int6
     return POGS_ERR_CUDA;
   count_launch();
   gram_to_df_kernel<<<(int)std::min<int64_t>(cdiv(q * q, 256), 148 * 16), 256, 0, s>>>(G, ldh, q, Hlo);
-  RecCtx c{G, Hlo, ldh, Lf, ldf, Md, ldm, work, TcScratch{nullptr, 0, err}, s};
+  std::vector<cudaEvent_t> events;
+  RecCtx c{G, Hlo, ldh, Lf, ldf, Md, ldm, TcScratch{nullptr, 0, err}, TcScratch{nullptr, 0, err}, s, nullptr, &events};
   const int64_t n1 = (cdiv(q, kDB) / 2) * kDB, n2 = q - n1;
   if (std::min(n1, n2) >= kTcInvMin) {
     // the top level's products are the largest; every lower level fits in their scratch
@@ -627,10 +665,36 @@ int chol_inv_mixed(float* G, float* Hlo, int64_t ldh, int64_t q, float* Lf, int6
     if (rc == 0) {
       c.tc.bytes = std::max(std::max(need[0], need[1]), std::max(need[2], need[3]));
       if (pool_alloc(&c.tc.p, c.tc.bytes, s) != 0) c.tc.p = nullptr;
+      c.tc2.bytes = need[2];
+      if (pool_alloc(&c.tc2.p, c.tc2.bytes, s) != 0) c.tc2.p = nullptr;
     }
   }
-  chol_inv_rec(c, 0, q);
+  // side stream for the T products (lowest priority: the critical chain goes first)
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t e_fork = nullptr, e_join = nullptr;
+  if (cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, lo) == cudaSuccess &&
+      cudaEventCreateWithFlags(&e_fork, cudaEventDisableTiming) == cudaSuccess &&
+      cudaEventCreateWithFlags(&e_join, cudaEventDisableTiming) == cudaSuccess) {
+    cudaEventRecord(e_fork, s);   // the side stream starts after everything before this call
+    cudaStreamWaitEvent(s2, e_fork, 0);
+    c.s2 = s2;
+  } else {
+    cudaGetLastError();
+  }
+  chol_inv_rec(c, 0, q, work);
+  if (c.s2) {   // join: the caller's stream continues after the side stream's last product
+    cudaEventRecord(e_join, s2);
+    cudaStreamWaitEvent(s, e_join, 0);
+  }
   if (c.tc.p) cudaFreeAsync(c.tc.p, s);
+  if (c.tc2.p) cudaFreeAsync(c.tc2.p, s);
+  for (cudaEvent_t e : events)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : {e_fork, e_join})
+    if (e) cudaEventDestroy(e);
+  if (s2) cudaStreamDestroy(s2);
   return cudaGetLastError() == cudaSuccess ? 0 : POGS_ERR_CUDA;
 }
 
