@@ -116,6 +116,14 @@ struct pogs_server {
   GpuGate gate;
   bool stop = false;
   int64_t submitted = 0, completed = 0;
+  // staging of admitted requests' host inputs: packed into one pinned buffer, copied to the
+  // device in one transfer, and scattered to their arenas by one kernel (grow-only buffers)
+  char* h_stage = nullptr;
+  size_t h_stage_bytes = 0;
+  char* d_stage = nullptr;
+  size_t d_stage_bytes = 0;
+  struct Piece* d_pieces = nullptr;
+  size_t d_pieces_cap = 0;
 };
 
 namespace {
@@ -227,6 +235,152 @@ void layout_small(SReq* r, BOut* out, BLoop* loop) {
   for (int t = 0; t < 17; ++t) *vecs[t] = vec + (size_t)t * v;
   I.out = out;
   I.loop = loop;
+}
+
+}  // namespace
+
+// One staged input: `rows` rows of `row_bytes` bytes, contiguous at `src` in the device staging
+// buffer, written `pitch` bytes apart at `dst` (an arena).
+struct Piece {
+  size_t src;
+  char* dst;
+  int64_t rows, row_bytes, pitch;
+};
+
+namespace {
+
+// One block per piece; 16-byte words where the row is 16-byte sized and both ends aligned
+// (the matrix rows when n is a multiple of 4), bytes otherwise.
+__global__ void scatter_pieces_kernel(const char* __restrict__ stage, const Piece* __restrict__ pieces) {
+  const Piece pc = pieces[blockIdx.x];
+  const char* src = stage + pc.src;
+  const bool wide = ((pc.row_bytes | pc.pitch | (int64_t)(uintptr_t)pc.dst | (int64_t)pc.src) & 15) == 0;
+  for (int64_t r = 0; r < pc.rows; ++r) {
+    const char* sr = src + r * pc.row_bytes;
+    char* dr = pc.dst + r * pc.pitch;
+    if (wide) {
+      for (int64_t k = threadIdx.x; k < pc.row_bytes / 16; k += blockDim.x)
+        reinterpret_cast<float4*>(dr)[k] = reinterpret_cast<const float4*>(sr)[k];
+    } else {
+      for (int64_t k = threadIdx.x; k < pc.row_bytes; k += blockDim.x) dr[k] = sr[k];
+    }
+  }
+}
+
+// The host inputs of the requests in `list` (all host-resident), in chunks of about kStageChunk
+// bytes: each chunk is packed into the pinned staging buffer (several threads for large chunks),
+// copied to the device in one transfer and scattered to the arenas by one launch; the stream is
+// synchronised before the buffers are reused.
+constexpr size_t kStageChunk = (size_t)1 << 30;
+
+int stage_chunk(pogs_server* S, const std::vector<Piece>& pieces, const std::vector<const char*>& hsrc,
+                size_t total, cudaStream_t s) {
+  if (total > S->h_stage_bytes) {
+    if (S->h_stage) cudaFreeHost(S->h_stage);
+    S->h_stage = nullptr;
+    S->h_stage_bytes = 0;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&S->h_stage), total, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return POGS_ERR_OOM;
+    }
+    S->h_stage_bytes = total;
+  }
+  if (total > S->d_stage_bytes) {
+    if (S->d_stage) cudaFreeAsync(S->d_stage, s);
+    S->d_stage = nullptr;
+    S->d_stage_bytes = 0;
+    count_alloc();
+    if (cudaMallocAsync(reinterpret_cast<void**>(&S->d_stage), total, s) != cudaSuccess) {
+      cudaGetLastError();
+      return POGS_ERR_OOM;
+    }
+    S->d_stage_bytes = total;
+  }
+  if (pieces.size() > S->d_pieces_cap) {
+    if (S->d_pieces) cudaFreeAsync(S->d_pieces, s);
+    S->d_pieces = nullptr;
+    S->d_pieces_cap = 0;
+    count_alloc();
+    if (cudaMallocAsync(reinterpret_cast<void**>(&S->d_pieces), pieces.size() * sizeof(Piece), s) != cudaSuccess) {
+      cudaGetLastError();
+      return POGS_ERR_OOM;
+    }
+    S->d_pieces_cap = pieces.size();
+  }
+  const int nth = total > ((size_t)64 << 20) ? 8 : 1;
+  auto pack = [&](size_t lo, size_t hi) {
+    for (size_t i = lo; i < hi; ++i)
+      std::memcpy(S->h_stage + pieces[i].src, hsrc[i], (size_t)(pieces[i].rows * pieces[i].row_bytes));
+  };
+  if (nth == 1) {
+    pack(0, pieces.size());
+  } else {   // pieces split evenly by bytes
+    std::vector<size_t> cut(nth + 1, pieces.size());
+    cut[0] = 0;
+    size_t i = 0;
+    for (int t = 1; t < nth; ++t) {
+      const size_t goal = total * t / nth;
+      while (i < pieces.size() && pieces[i].src < goal) ++i;
+      cut[t] = i;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nth; ++t) th.emplace_back(pack, cut[t], cut[t + 1]);
+    for (auto& x : th) x.join();
+  }
+  if (cudaMemcpyAsync(S->d_stage, S->h_stage, total, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(S->d_pieces, pieces.data(), pieces.size() * sizeof(Piece), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return POGS_ERR_CUDA;
+  }
+  count_launch();
+  scatter_pieces_kernel<<<(unsigned)pieces.size(), 256, 0, s>>>(S->d_stage, S->d_pieces);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return POGS_ERR_CUDA;
+  }
+  return 0;
+}
+
+int stage_host_inputs(pogs_server* S, const std::vector<SReq*>& list, cudaStream_t s) {
+  std::vector<Piece> pieces;
+  std::vector<const char*> hsrc;
+  size_t total = 0;
+  auto add = [&](const void* src, void* dst, int64_t rows, int64_t row_bytes, int64_t pitch, int64_t src_pitch) {
+    // rows of a strided host source are packed contiguously, one piece per row
+    const bool contiguous = src_pitch == row_bytes;
+    for (int64_t r = 0; r < (contiguous ? 1 : rows); ++r) {
+      Piece pc;
+      pc.src = total;
+      pc.dst = static_cast<char*>(dst) + r * pitch;
+      pc.rows = contiguous ? rows : 1;
+      pc.row_bytes = row_bytes;
+      pc.pitch = pitch;
+      pieces.push_back(pc);
+      hsrc.push_back(static_cast<const char*>(src) + r * src_pitch);
+      total += (size_t)((pc.rows * row_bytes + 15) & ~int64_t(15));
+    }
+  };
+  for (SReq* r : list) {
+    const pogs_problem& pr = r->prob;
+    const BInst& I = r->inst;
+    add(pr.A, I.A, pr.m, pr.n * 4, (int64_t)I.lda * 4, pr.lda * 4);
+    const void* src[12] = {pr.f.h, pr.f.a, pr.f.b, pr.f.c, pr.f.d, pr.f.e, pr.g.h, pr.g.a, pr.g.b, pr.g.c, pr.g.d, pr.g.e};
+    const void* dst[12] = {I.fh0, I.fa0, I.fb0, I.fc0, I.fd0, I.fe0, I.gh0, I.ga0, I.gb0, I.gc0, I.gd0, I.ge0};
+    for (int t = 0; t < 12; ++t) {
+      if (!src[t]) continue;
+      const int64_t bytes = (t < 6 ? pr.m : pr.n) * ((t % 6) == 0 ? 1 : 4);
+      add(src[t], const_cast<void*>(dst[t]), 1, bytes, bytes, bytes);
+    }
+    if (total >= kStageChunk) {
+      const int rc = stage_chunk(S, pieces, hsrc, total, s);
+      if (rc != 0) return rc;
+      pieces.clear();
+      hsrc.clear();
+      total = 0;
+    }
+  }
+  return pieces.empty() ? 0 : stage_chunk(S, pieces, hsrc, total, s);
 }
 
 int copy_inputs(SReq* r, cudaStream_t s) {
@@ -368,6 +522,7 @@ int pogs_server_step(pogs_server* S, int iters) {
   }
   StepHold hold;
   hold.take(S->gate);
+  std::vector<SReq*> host_in;
   for (SReq* r : fresh) {
     count_alloc();
     if (cudaMallocAsync((void**)&r->arena, r->bytes, s) != cudaSuccess) {
@@ -375,11 +530,25 @@ int pogs_server_step(pogs_server* S, int iters) {
       return POGS_ERR_OOM;
     }
     layout_small(r, S->d_outs + r->slot, S->d_loops + r->slot);
-    if (copy_inputs(r, s) != 0) return POGS_ERR_CUDA;
+    // requests whose inputs all live in host memory are staged together below
+    const pogs_problem& pr = r->prob;
+    const void* ins[13] = {pr.A, pr.f.h, pr.f.a, pr.f.b, pr.f.c, pr.f.d, pr.f.e,
+                           pr.g.h, pr.g.a, pr.g.b, pr.g.c, pr.g.d, pr.g.e};
+    bool any_dev = false;
+    for (const void* p : ins) any_dev = any_dev || is_dev(p);
+    if (any_dev) {
+      if (copy_inputs(r, s) != 0) return POGS_ERR_CUDA;
+    } else {
+      host_in.push_back(r);
+    }
     if (cudaMemsetAsync(S->d_outs + r->slot, 0, sizeof(BOut), s) != cudaSuccess ||
         cudaMemsetAsync(S->d_loops + r->slot, 0, sizeof(BLoop), s) != cudaSuccess)
       return POGS_ERR_CUDA;
     S->active.push_back(r);
+  }
+  if (!host_in.empty()) {
+    const int rc = stage_host_inputs(S, host_in, s);
+    if (rc != 0) return rc;
   }
   if (!fresh.empty()) {
     std::vector<BInst> hn;
@@ -495,6 +664,9 @@ void pogs_server_destroy(pogs_server* S) {
   cudaFree(S->d_active);
   cudaFree(S->d_new);
   cudaFree(S->d_queue);
+  if (S->d_stage) cudaFree(S->d_stage);
+  if (S->d_pieces) cudaFree(S->d_pieces);
+  if (S->h_stage) cudaFreeHost(S->h_stage);
   if (S->ev_in) cudaEventDestroy(S->ev_in);
   if (S->own_stream) cudaStreamDestroy(S->stream);
   delete S;
