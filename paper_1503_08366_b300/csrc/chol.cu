@@ -209,13 +209,179 @@ __global__ void __launch_bounds__(256, MINB)
   }
 }
 
+// ---- small tiles ---------------------------------------------------------------------------
+// The same products on 32 x 32 tiles, 64 threads, 4 x 4 outputs per thread, for shapes whose
+// 128 x 128 grid would leave most SMs idle (the lookahead panels and the small levels of the
+// recursion): 16 times the CTAs for the same work.  Every output accumulates the same terms
+// in the same k order as the 128-tile kernel (the skipped leading and trailing k of triangular
+// operands are exact zeros in both), so both kernels give the same bits.
+constexpr int kSB = 32, kSK = 32;   // tile edge, K step
+constexpr int kSLD = kSB + 4;       // shared k-row pitch (floats): 16-byte aligned rows
+constexpr int64_t kSmallTileGrid = 64;   // 128-tile grids below this size take the 32-tile kernel
+template <bool BT, int OUT>
+__global__ void __launch_bounds__(64)
+    sgemm32_kernel(int M, int N, int K, const float* __restrict__ A, int64_t lda, const float* __restrict__ B,
+                   int64_t ldb, float alpha, float* __restrict__ Cf, float* __restrict__ Clo, int64_t ldc,
+                   int lower, int tri) {
+  __shared__ __align__(16) float As[2][kSK][kSLD];
+  __shared__ __align__(16) float Bs[2][kSK][kSLD];
+  int bi, bj;
+  if (lower) {
+    const int b = blockIdx.x;
+    int I = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
+    while ((I + 1) * (I + 2) / 2 <= b) ++I;
+    while (I * (I + 1) / 2 > b) --I;
+    bi = I;
+    bj = b - I * (I + 1) / 2;
+  } else {
+    bi = blockIdx.y;
+    bj = blockIdx.x;
+  }
+  const int row0 = bi * kSB, col0 = bj * kSB;
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  int kbeg = 0, kend = K;
+  if (tri & 1) kbeg = col0 < K ? col0 : K;
+  if (tri & 2) kend = row0 + kSB < K ? row0 + kSB : K;
+  // per-thread global sources: A rows tid/8 (+8, +16, +24), K offset 4*(tid%8); B likewise
+  // when BT, else K rows tid/8 (+8, ...) and columns 4*(tid%8)
+  const int r_ld = tid >> 3, kq = (tid & 7) * 4;
+  const float* ap[4];
+  const float* bp[4];
+  bool aok[4], bok[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const int ar = row0 + r_ld + 8 * l;
+    aok[l] = ar < M;
+    ap[l] = A + (int64_t)(aok[l] ? ar : 0) * lda + kq;
+    if (BT) {
+      const int br = col0 + r_ld + 8 * l;
+      bok[l] = br < N;
+      bp[l] = B + (int64_t)(bok[l] ? br : 0) * ldb + kq;
+    } else {
+      const int bc = col0 + kq;
+      bok[l] = bc < N;
+      bp[l] = B + (int64_t)(r_ld + 8 * l) * ldb + (bok[l] ? bc : 0);
+    }
+  }
+  const int bc_left = N - (col0 + kq);
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  float4 ra[4], rb[4];
+  auto gload = [&](int k0) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      ra[l] = aok[l] ? ld4(ap[l] + k0, K - (k0 + kq)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (BT) {
+        rb[l] = bok[l] ? ld4(bp[l] + k0, K - (k0 + kq)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        const int kr = k0 + r_ld + 8 * l;
+        rb[l] = (bok[l] && kr < K) ? ld4(bp[l] + (int64_t)k0 * ldb, bc_left) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int r = r_ld + 8 * l;
+      As[buf][kq + 0][r] = ra[l].x;
+      As[buf][kq + 1][r] = ra[l].y;
+      As[buf][kq + 2][r] = ra[l].z;
+      As[buf][kq + 3][r] = ra[l].w;
+      if (BT) {
+        Bs[buf][kq + 0][r] = rb[l].x;
+        Bs[buf][kq + 1][r] = rb[l].y;
+        Bs[buf][kq + 2][r] = rb[l].z;
+        Bs[buf][kq + 3][r] = rb[l].w;
+      } else {
+        *reinterpret_cast<float4*>(&Bs[buf][r][kq]) = rb[l];
+      }
+    }
+  };
+  if (kbeg < kend) {
+    gload(kbeg);
+    sstore(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = kbeg; k0 < kend; k0 += kSK) {
+      const bool more = k0 + kSK < kend;
+      if (more) gload(k0 + kSK);
+#pragma unroll
+      for (int k = 0; k < kSK; ++k) {
+        const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4]);
+        const float4 b4 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 4]);
+        const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+        const float b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+      if (more) sstore(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+  const int gj0 = col0 + tx * 4;
+  if (gj0 >= N) return;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = row0 + ty * 4 + i;
+    if (gi >= M) continue;
+    const float v0 = acc[i][0], v1 = acc[i][1], v2 = acc[i][2], v3 = acc[i][3];
+    if (OUT == OUT_F32) {
+      float* c = Cf + (int64_t)gi * ldc + gj0;
+      if (gj0 + 3 < N) {
+        *reinterpret_cast<float4*>(c) = make_float4(alpha * v0, alpha * v1, alpha * v2, alpha * v3);
+      } else {
+        c[0] = alpha * v0;
+        if (gj0 + 1 < N) c[1] = alpha * v1;
+        if (gj0 + 2 < N) c[2] = alpha * v2;
+      }
+    } else {
+      float* ch = Cf + (int64_t)gi * ldc + gj0;
+      float* cl = Clo + (int64_t)gi * ldc + gj0;
+      const int lim = min(N, lower ? gi + 1 : N) - gj0;
+      if (lim >= 4) {
+        float4 h = *reinterpret_cast<float4*>(ch);
+        float4 l = *reinterpret_cast<float4*>(cl);
+        df_sub(h.x, l.x, v0);
+        df_sub(h.y, l.y, v1);
+        df_sub(h.z, l.z, v2);
+        df_sub(h.w, l.w, v3);
+        *reinterpret_cast<float4*>(ch) = h;
+        *reinterpret_cast<float4*>(cl) = l;
+      } else if (lim > 0) {
+        df_sub(ch[0], cl[0], v0);
+        if (lim > 1) df_sub(ch[1], cl[1], v1);
+        if (lim > 2) df_sub(ch[2], cl[2], v2);
+      }
+    }
+  }
+}
+
 template <bool BT, int OUT, int MINB>
 void sgemm_launch(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
                   float alpha, float* Cf, float* Clo, int64_t ldc, bool lower, int tri, cudaStream_t s) {
   if (M <= 0 || N <= 0) return;
   count_launch();   // sizes fit int: q <= 2^31 / 128 rows of 128-tiles
+  const int64_t T = cdiv(M, kBM);
+  const int64_t tiles = lower ? T * (T + 1) / 2 : cdiv(N, kBN) * T;
+  if (tiles < kSmallTileGrid) {
+    if (lower) {
+      const int64_t Ts = cdiv(M, kSB);
+      sgemm32_kernel<BT, OUT><<<(unsigned)(Ts * (Ts + 1) / 2), 64, 0, s>>>((int)M, (int)N, (int)K, A, lda, B, ldb,
+                                                                         alpha, Cf, Clo, ldc, 1, tri);
+    } else {
+      dim3 grid((unsigned)cdiv(N, kSB), (unsigned)cdiv(M, kSB));
+      sgemm32_kernel<BT, OUT><<<grid, 64, 0, s>>>((int)M, (int)N, (int)K, A, lda, B, ldb, alpha, Cf, Clo, ldc, 0,
+                                                  tri);
+    }
+    return;
+  }
   if (lower) {
-    const int64_t T = cdiv(M, kBM);
     sgemm128_kernel<BT, OUT, MINB><<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(
         (int)M, (int)N, (int)K, A, lda, B, ldb, alpha, Cf, Clo, ldc, 1, tri);
   } else {
@@ -230,22 +396,47 @@ constexpr int kDB = 128;        // block edge
 constexpr int kDS = kDB + 1;    // shared row pitch (conflict-free column walks)
 constexpr int kDiagThreads = 512;   // 16 warps: one 128-block per CTA, latency-bound phases
 
+constexpr int kPT = 100;   // pitch of the transposed panel (at most 96 rows), 16-byte rows
+constexpr int kLB = 36;    // pitch of the aligned copy of the 32 x 32 diagonal factor
+
 // One CTA factors the nb x nb diagonal block Hkk (hi part, lower triangle read) in FP32 and
 // writes W = L_kk^{-1} (lower triangular, zero above the diagonal) to W (ld ldw).  Rows and
 // columns nb..127 are padded with the identity.  Four 32-wide sub-block steps: warp 0 factors
-// the 32 x 32 diagonal sub-block in registers (lane = row, pivot columns broadcast by
-// shuffles) and inverts it (lane = column, forward substitution on e_c); all warps then form
-// the panel below it, P = S_panel V^T, and update the trailing rows.  The off-diagonal blocks
-// of W follow by block forward substitution, W_ij = -W_ii sum_{k=j}^{i-1} L_ik W_kj.
+// the 32 x 32 diagonal sub-block in registers (lane = row; each pivot column is published in
+// shared memory and read back as float4 broadcasts) and inverts it (lane = column, forward
+// substitution on e_c over an aligned copy of the factor); all warps then form the panel below
+// it, P = S_panel V^T (kept transposed), and update the trailing rows from it.  The
+// off-diagonal blocks of W follow by block forward substitution,
+// W_ij = -W_ii sum_{k=j}^{i-1} L_ik W_kj.
 __global__ void __launch_bounds__(kDiagThreads) chol_diag_kernel(const float* __restrict__ Hkk, int64_t ldh, int nb,
                                                         float* __restrict__ W, int64_t ldw, int* err) {
-  extern __shared__ float sm[];
-  float* S = sm;               // [128][129]: Schur block, then L
-  float* V = S + kDB * kDS;    // [128][129]: W in the lower triangle; panel and T scratch
-  float* Dv = V + kDB * kDS;   // [128]: 1 / L_jj
+  extern __shared__ __align__(16) float sm[];
+  float* S = sm;                 // [128][129]: Schur block, then L
+  float* V = S + kDB * kDS;      // [128][129]: W in the lower triangle; T scratch
+  float* Dv = V + kDB * kDS;     // [128]: 1 / L_jj
+  float* Lb = Dv + kDB;          // [32][kLB]: the current 32 x 32 diagonal factor
+  float* cb = Lb + 32 * kLB;     // [2][32]: column broadcast of the 32 x 32 factorization
+  float* PT = cb + 64;           // [32][kPT]: the current panel, transposed
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  {
-    // every load of the block issued before the first store (one round trip to L2 / DRAM)
+  if (nb == kDB) {
+    float4 ld[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = tid + t * kDiagThreads, i = e >> 5, k = (e & 31) * 4;
+      ld[t] = k <= i ? *reinterpret_cast<const float4*>(Hkk + (int64_t)i * ldh + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = tid + t * kDiagThreads, i = e >> 5, k = (e & 31) * 4;
+      float* s = S + i * kDS + k;
+      float* v = V + i * kDS + k;
+      s[0] = ld[t].x;
+      s[1] = k + 1 <= i ? ld[t].y : 0.0f;
+      s[2] = k + 2 <= i ? ld[t].z : 0.0f;
+      s[3] = k + 3 <= i ? ld[t].w : 0.0f;
+      v[0] = v[1] = v[2] = v[3] = 0.0f;
+    }
+  } else {
     constexpr int kPer = kDB * kDB / kDiagThreads;
     float ld[kPer];
 #pragma unroll
@@ -265,14 +456,15 @@ __global__ void __launch_bounds__(kDiagThreads) chol_diag_kernel(const float* __
   for (int jb = 0; jb < 4; ++jb) {
     const int o = jb * 32;
     if (warp == 0) {
-      // 32 x 32 sub-block: lane = row, pivot column broadcast by shuffles.  1/L_jj comes from
-      // rsqrt of the pivot (no divide), L_jj = pivot * (1/L_jj); Dv keeps 1/L_jj for the
-      // inverse.
+      // 32 x 32 sub-block, lane = row.  Step j scales column j by 1/L_jj (rsqrt of the pivot)
+      // and publishes it in shared memory; every lane then subtracts L_lane,j L_k,j from its
+      // entries k > j.  Entries above the diagonal are computed too (no predicates) and never
+      // stored.
       float* Sd = S + o * kDS + o;
       float r[32];
-      float dinv = 1.0f;
 #pragma unroll
-      for (int k = 0; k < 32; ++k) r[k] = k <= lane ? Sd[lane * kDS + k] : 0.0f;
+      for (int k = 0; k < 32; ++k) r[k] = Sd[lane * kDS + k];
+      float dinv = 1.0f;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         float piv = __shfl_sync(0xffffffffu, r[j], j);
@@ -284,40 +476,60 @@ __global__ void __launch_bounds__(kDiagThreads) chol_diag_kernel(const float* __
         if (lane == j) {
           r[j] = piv * rs;
           dinv = rs;
-        } else if (lane > j) {
+        } else {
           r[j] *= rs;
         }
+        if (j < 31) {
+          float* c = cb + (j & 1) * 32;
+          c[lane] = r[j];
+          __syncwarp();
 #pragma unroll
-        for (int k = 1; k < 32; ++k) {   // uniform bounds keep r[] in registers (full unroll)
-          const float lkj = __shfl_sync(0xffffffffu, r[j], k);
-          if (k > j && lane >= k) r[k] = fmaf(-r[j], lkj, r[k]);
+          for (int k4 = (j + 1) & ~3; k4 < 32; k4 += 4) {
+            const float4 l4 = *reinterpret_cast<const float4*>(c + k4);
+            const float lk[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (k4 + u > j) r[k4 + u] = fmaf(-r[j], lk[u], r[k4 + u]);
+          }
         }
       }
 #pragma unroll
       for (int k = 0; k < 32; ++k)
         if (k <= lane) Sd[lane * kDS + k] = r[k];
+#pragma unroll
+      for (int k4 = 0; k4 < 32; k4 += 4)
+        *reinterpret_cast<float4*>(Lb + lane * kLB + k4) =
+            make_float4(k4 <= lane ? r[k4] : 0.0f, k4 + 1 <= lane ? r[k4 + 1] : 0.0f,
+                        k4 + 2 <= lane ? r[k4 + 2] : 0.0f, k4 + 3 <= lane ? r[k4 + 3] : 0.0f);
       Dv[o + lane] = dinv;
       __syncwarp();
-      // inverse of the 32 x 32 factor, lane = column c: v_i = -(sum_{k<i} L_ik v_k) / L_ii
-      float* Vd = V + o * kDS + o;
+      // inverse of the 32 x 32 factor, lane = column c: v_i = -(sum_{k<i} L_ik v_k) / L_ii,
+      // four partial sums per row
       float v[32];
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
-        float a = 0.0f;
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
 #pragma unroll
-        for (int k = 0; k < i; ++k) a = fmaf(Sd[i * kDS + k], v[k], a);
+        for (int k4 = 0; k4 < i; k4 += 4) {
+          const float4 l4 = *reinterpret_cast<const float4*>(Lb + i * kLB + k4);
+          a0 = fmaf(l4.x, v[k4], a0);
+          if (k4 + 1 < i) a1 = fmaf(l4.y, v[k4 + 1], a1);
+          if (k4 + 2 < i) a2 = fmaf(l4.z, v[k4 + 2], a2);
+          if (k4 + 3 < i) a3 = fmaf(l4.w, v[k4 + 3], a3);
+        }
         const float di = Dv[o + i];
-        v[i] = i < lane ? 0.0f : (i == lane ? di : -a * di);
+        v[i] = i < lane ? 0.0f : (i == lane ? di : -((a0 + a1) + (a2 + a3)) * di);
       }
+      float* Vd = V + o * kDS + o;
 #pragma unroll
       for (int i = 0; i < 32; ++i) Vd[i * kDS + lane] = v[i];
     }
     __syncthreads();
     const int rows = kDB - o - 32;   // 96, 64, 32, 0: whole warps
-    // panel P = S_panel V_jj^T into the (still unused) lower part of V; task = one element
+    // panel P = S_panel V_jj^T, transposed into PT; task = one element
     for (int t = tid; t < rows * 32; t += kDiagThreads) {
-      const int rr = o + 32 + (t % rows), cc = t / rows;
-      const float* Sr = S + rr * kDS + o;
+      const int rr = t % rows, cc = t / rows;
+      const float* Sr = S + (o + 32 + rr) * kDS + o;
       const float* Vc = V + (o + cc) * kDS + o;
       float a0 = 0.0f, a1 = 0.0f;
       int k = 0;
@@ -326,39 +538,38 @@ __global__ void __launch_bounds__(kDiagThreads) chol_diag_kernel(const float* __
         a1 = fmaf(Sr[k + 1], Vc[k + 1], a1);
       }
       if (k <= cc) a0 = fmaf(Sr[k], Vc[k], a0);
-      V[rr * kDS + o + cc] = a0 + a1;
+      PT[cc * kPT + rr] = a0 + a1;
     }
     __syncthreads();
     if (rows > 0) {
-      // P back into S (the factor's panel), and S[i][k] -= sum_c P[i][c] P[k][c] for
-      // o+32 <= k <= i < 128 in 4 x 4 register blocks
+      // P into S (the factor's panel), and S[i][k] -= sum_c P[i][c] P[k][c] for
+      // o+32 <= k <= i < 128 in 4 x 4 register blocks, lower blocks only
       for (int e = tid; e < rows * 32; e += kDiagThreads) {
-        const int rr = o + 32 + (e >> 5), cc = o + (e & 31);
-        S[rr * kDS + cc] = V[rr * kDS + cc];
+        const int rr = e % rows, cc = e / rows;
+        S[(o + 32 + rr) * kDS + o + cc] = PT[cc * kPT + rr];
       }
-      const int nbk = rows / 4;
-      for (int b = tid; b < nbk * nbk; b += kDiagThreads) {
-        const int bi = b / nbk, bk = b - bi * nbk;
-        if (bk > bi) continue;
-        const int i0 = o + 32 + bi * 4, k0 = o + 32 + bk * 4;
+      const int nbk = rows >> 2, nblk = nbk * (nbk + 1) / 2;
+      for (int b = tid; b < nblk; b += kDiagThreads) {
+        int bi = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
+        while ((bi + 1) * (bi + 2) / 2 <= b) ++bi;
+        while (bi * (bi + 1) / 2 > b) --bi;
+        const int bk = b - bi * (bi + 1) / 2;
         float a[4][4];
 #pragma unroll
         for (int t = 0; t < 4; ++t)
 #pragma unroll
           for (int u = 0; u < 4; ++u) a[t][u] = 0.0f;
-#pragma unroll 4
+#pragma unroll 8
         for (int cc = 0; cc < 32; ++cc) {
-          float pi[4], pk[4];
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            pi[t] = V[(i0 + t) * kDS + o + cc];
-            pk[t] = V[(k0 + t) * kDS + o + cc];
-          }
+          const float4 p4 = *reinterpret_cast<const float4*>(PT + cc * kPT + bi * 4);
+          const float4 q4 = *reinterpret_cast<const float4*>(PT + cc * kPT + bk * 4);
+          const float pi[4] = {p4.x, p4.y, p4.z, p4.w}, pk[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
           for (int t = 0; t < 4; ++t)
 #pragma unroll
             for (int u = 0; u < 4; ++u) a[t][u] = fmaf(pi[t], pk[u], a[t][u]);
         }
+        const int i0 = o + 32 + bi * 4, k0 = o + 32 + bk * 4;
 #pragma unroll
         for (int t = 0; t < 4; ++t)
 #pragma unroll
@@ -421,14 +632,23 @@ __global__ void __launch_bounds__(kDiagThreads) chol_diag_kernel(const float* __
     }
     __syncthreads();
   }
-  for (int e = tid; e < nb * nb; e += kDiagThreads) {
-    const int i = e / nb, k = e - (e / nb) * nb;
-    W[(int64_t)i * ldw + k] = k <= i ? V[i * kDS + k] : 0.0f;
+  if (nb == kDB) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = tid + t * kDiagThreads, i = e >> 5, k = (e & 31) * 4;
+      const float* v = V + i * kDS + k;
+      *reinterpret_cast<float4*>(W + (int64_t)i * ldw + k) =
+          make_float4(k <= i ? v[0] : 0.0f, k + 1 <= i ? v[1] : 0.0f, k + 2 <= i ? v[2] : 0.0f, k + 3 <= i ? v[3] : 0.0f);
+    }
+  } else {
+    for (int e = tid; e < nb * nb; e += kDiagThreads) {
+      const int i = e / nb, k = e - (e / nb) * nb;
+      W[(int64_t)i * ldw + k] = k <= i ? V[i * kDS + k] : 0.0f;
+    }
   }
   if (bad && lane == 0) atomicCAS(err, 0, POGS_ERR_NUMERIC);
 }
-
-constexpr size_t kDiagSmem = (size_t)(2 * kDB * kDS + kDB) * sizeof(float);
+constexpr size_t kDiagSmem = (size_t)(2 * kDB * kDS + kDB + 32 * kLB + 64 + 32 * kPT) * sizeof(float);
 
 // Recursive 2 x 2 block inverse on the FP32 factor (leaves already in M).
 // Tensor-core scratch of the inverse (nullptr: SIMT GEMMs only).

@@ -323,16 +323,16 @@ __global__ void __launch_bounds__(256) pogs_rowdot_kernel(const float* __restric
 // padding rows/cols are zero).  One block per tile; partial tile products are reduced by
 // the last block of each tile row (z = M v) or tile column (x = M^T v).
 // ------------------------------------------------------------------------------------------
-// Sum of k partials p[0], p[stride], ... in index order, eight loads in flight per round trip.
+// Sum of k partials p[0], p[stride], ... in index order, sixteen loads in flight per round trip.
 __device__ __forceinline__ float sum_slots(const float* __restrict__ p, int k, int64_t stride) {
   float s = 0.0f;
   int i = 0;
-  for (; i + 8 <= k; i += 8) {
-    float v[8];
+  for (; i + 16 <= k; i += 16) {
+    float v[16];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = __ldcg(p + (int64_t)(i + u) * stride);
+    for (int u = 0; u < 16; ++u) v[u] = __ldcg(p + (int64_t)(i + u) * stride);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) s += v[u];
+    for (int u = 0; u < 16; ++u) s += v[u];
   }
   for (; i < k; ++i) s += __ldcg(p + (int64_t)i * stride);
   return s;
@@ -344,6 +344,18 @@ __device__ __forceinline__ void tile_coords(int b, int& I, int& J) {
   while (i * (i + 1) / 2 > b) --i;
   I = i;
   J = b - i * (i + 1) / 2;
+}
+
+// Tile (I, J) of the lower triangle in column order: column J holds the T - J tiles (J..T-1, J)
+// and starts at index J T - J (J - 1) / 2.
+__device__ __forceinline__ void tile_coords_col(int c, int T, int& I, int& J) {
+  const float tf = (float)T + 0.5f;
+  int j = (int)(tf - sqrtf(fmaxf(tf * tf - 2.0f * (float)c, 0.0f)));
+  if (j < 0) j = 0;
+  while (j > 0 && (int64_t)j * T - (int64_t)j * (j - 1) / 2 > c) --j;
+  while ((int64_t)(j + 1) * T - (int64_t)(j + 1) * j / 2 <= c) ++j;
+  J = j;
+  I = j + (int)(c - ((int64_t)j * T - (int64_t)j * (j - 1) / 2));
 }
 
 template <bool TRANS, int EPI>
@@ -408,8 +420,13 @@ __global__ void __launch_bounds__(256) trmv_kernel(const float* __restrict__ Mt,
 // S_IJ v_J (slot J of block I), and for I > J its columns give block J the contribution
 // S_IJ^T v_I (slot I of block J), both from one read of the tile.  Every output block receives
 // T contributions; the last block to deliver one sums the T slots in slot order and applies the
-// epilogue.  One pass over the packed triangle instead of the two of M v and M^T z.
-template <int EPI>
+// epilogue.  One pass over the packed triangle instead of the two of M v and M^T z.  Blocks
+// take the tiles in column order, so that output block J is complete once tile column J has
+// been read and its final sum overlaps the rest of the pass (in row order every block waits for
+// the last tile row).  LD16: all sixteen rows of a warp in flight at once (one round trip; for
+// grids of at most two blocks per SM), else two batches of eight (fewer registers, more
+// resident blocks).
+template <int EPI, bool LD16>
 __global__ void __launch_bounds__(256) symv_kernel(const float* __restrict__ St, int T, int q,
                                                    const float* __restrict__ vin, float* __restrict__ part,
                                                    unsigned* __restrict__ cnt, EpiArgs ep,
@@ -417,28 +434,32 @@ __global__ void __launch_bounds__(256) symv_kernel(const float* __restrict__ St,
   __shared__ float4 shc[8][32];
   if (guard && guard->done) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int b = blockIdx.x;
   int I, J;
-  tile_coords(b, I, J);
-  const float4* tile = reinterpret_cast<const float4*>(St + (int64_t)b * kTile * kTile);
+  tile_coords_col(blockIdx.x, T, I, J);
+  const int64_t b = (int64_t)I * (I + 1) / 2 + J;
+  const float4* tile = reinterpret_cast<const float4*>(St + b * kTile * kTile);
   const float4 vj = __ldg(reinterpret_cast<const float4*>(vin + (int64_t)J * kTile) + lane);
   const bool off = I != J;
+  // v_I entries of this warp's rows, loaded with the tile (not one dependent load per row)
+  float zh[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) zh[u] = __ldg(vin + (int64_t)I * kTile + warp * 16 + u);
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  // each warp's 16 rows in two batches of 8 (eight loads in flight, few registers):
   // rows -> block I, slot J; columns (off-diagonal tiles) -> block J, slot I
+  constexpr int NB = LD16 ? 1 : 2, NU = 16 / NB;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    float4 a[8];
+  for (int h = 0; h < NB; ++h) {
+    float4 a[NU];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) a[u] = ldg_stream(tile + (warp * 16 + h * 8 + u) * 32 + lane);
+    for (int u = 0; u < NU; ++u) a[u] = ldg_stream(tile + (warp * 16 + h * NU + u) * 32 + lane);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int r = warp * 16 + h * 8 + u;
+    for (int u = 0; u < NU; ++u) {
+      const int r = warp * 16 + h * NU + u;
       float s = a[u].x * vj.x + a[u].y * vj.y + a[u].z * vj.z + a[u].w * vj.w;
       s = warp_sum(s);
       if (lane == 0) part[((int64_t)I * T + J) * kTile + r] = s;
       if (off) {
-        const float zr = __ldg(vin + (int64_t)I * kTile + r);
+        const float zr = zh[h * NU + u];
         acc.x = fmaf(a[u].x, zr, acc.x); acc.y = fmaf(a[u].y, zr, acc.y);
         acc.z = fmaf(a[u].z, zr, acc.z); acc.w = fmaf(a[u].w, zr, acc.w);
       }
@@ -757,12 +778,19 @@ void launch_symv(int epi, const float* St, int T, int q, const float* vin, float
                  const EpiArgs& ep, const DevState* guard, cudaStream_t s) {
   const int nt = T * (T + 1) / 2;
   count_launch();
+  const bool ld16 = nt <= 2 * 148;
+#define POGS_S(E)                                                                         \
+  do {                                                                                    \
+    if (ld16) symv_kernel<E, true><<<nt, 256, 0, s>>>(St, T, q, vin, part, cnt, ep, guard);  \
+    else symv_kernel<E, false><<<nt, 256, 0, s>>>(St, T, q, vin, part, cnt, ep, guard);      \
+  } while (0)
   switch (epi) {
-    case EPR_RAW: symv_kernel<EPR_RAW><<<nt, 256, 0, s>>>(St, T, q, vin, part, cnt, ep, guard); break;
-    case EPR_TALL_X: symv_kernel<EPR_TALL_X><<<nt, 256, 0, s>>>(St, T, q, vin, part, cnt, ep, guard); break;
-    case EPR_FAT_Y: symv_kernel<EPR_FAT_Y><<<nt, 256, 0, s>>>(St, T, q, vin, part, cnt, ep, guard); break;
-    case EPR_ADD: symv_kernel<EPR_ADD><<<nt, 256, 0, s>>>(St, T, q, vin, part, cnt, ep, guard); break;
+    case EPR_RAW: POGS_S(EPR_RAW); break;
+    case EPR_TALL_X: POGS_S(EPR_TALL_X); break;
+    case EPR_FAT_Y: POGS_S(EPR_FAT_Y); break;
+    case EPR_ADD: POGS_S(EPR_ADD); break;
   }
+#undef POGS_S
 }
 
 void launch_trmv(bool trans, int epi, const float* Mt, int T, int q, const float* vin, float* part, unsigned* cnt,
