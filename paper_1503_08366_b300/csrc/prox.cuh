@@ -11,18 +11,26 @@ POGS_DEV float sigmoidf(float z) { return 1.0f / (1.0f + expf(-z)); }
 // strictly increasing, negative at v - 1/r and positive at v.  Safeguarded Newton: a step is
 // replaced by bisection of the current bracket whenever it would leave the bracket or fails to
 // halve the step before it (plain Newton can bounce between the two flat tails of the sigmoid
-// without converging), so the bracket at least halves every other iteration.
+// without converging), so the bracket at least halves every other iteration.  The first guess
+// is the root with sigma replaced by the piecewise-linear clamp(1/2 + z/4, 0, 1) (its middle
+// piece, else the root of the tail's piece).  The iteration stops once |phi| is within the
+// rounding error of its two terms (|phi| <= eps_32 (sigma + r |z - v|)): past that point a
+// Newton step is noise, and at small r with large v (z far inside a wide bracket) the bisection
+// fallback would otherwise halve the bracket down to the 1e-7 tolerance one step at a time.
 POGS_DEV float prox_logistic(float v, float r) {
   float lo = v - 1.0f / r, hi = v;
-  float z = v - sigmoidf(v) / (1.0f + r);   // one implicit-Euler guess
+  float z = (r * v - 0.5f) / (0.25f + r);
+  if (z > 2.0f) z = fmaxf(lo, 2.0f);
+  else if (z < -2.0f) z = fminf(v, -2.0f);
   z = fminf(fmaxf(z, lo), hi);
   float dx_old = hi - lo, dx = dx_old;
 #pragma unroll 1
   for (int it = 0; it < 64; ++it) {
     const float s = sigmoidf(z);
-    const float phi = s + r * (z - v);
+    const float t = r * (z - v);
+    const float phi = s + t;
     const float dphi = s * (1.0f - s) + r;
-    if (phi == 0.0f) break;
+    if (fabsf(phi) <= 1.1920929e-7f * (s + fabsf(t))) break;
     if (phi > 0.0f) hi = z; else lo = z;
     const bool newton_out = ((z - hi) * dphi - phi) * ((z - lo) * dphi - phi) > 0.0f;
     const bool too_slow = fabsf(2.0f * phi) > fabsf(dx_old * dphi);
