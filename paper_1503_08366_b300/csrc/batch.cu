@@ -333,55 +333,117 @@ __device__ __forceinline__ void zero_state(const BInst& I) {
   for (int i = threadIdx.x; i < I.m; i += NT) { I.y[i] = 0.0f; I.yt[i] = 0.0f; }
 }
 
-// Row dots u = A [x1, x2] for the rows of the instance (warp per row); four column steps' loads
-// are issued before they are accumulated (in column order).
-__device__ __forceinline__ void rowdots(const float* A, int lda, int m, int n, const float* x1, const float* x2,
-                                        int i, float& u1, float& u2) {
+// Row dots u = A [x1, x2] for two rows ia and ib of the instance together (one warp; ib ignored
+// when !hasb): lane l takes columns l, l + 32, ... in steps of four loads while a whole step
+// fits, then the remaining ones; the x loads are shared by the two rows.
+__device__ __forceinline__ void rowdots2(const float* A, int lda, int n, const float* x1, const float* x2, int ia,
+                                         int ib, bool hasb, float (&u)[4]) {
   const int lane = threadIdx.x & 31;
-  const float* a = A + (int64_t)i * lda;
-  float s1 = 0.f, s2 = 0.f;
+  const float* a = A + (int64_t)ia * lda;
+  const float* b = A + (int64_t)(hasb ? ib : ia) * lda;
+  float s1a = 0.f, s2a = 0.f, s1b = 0.f, s2b = 0.f;
   int j = lane;
   for (; j + 96 < n; j += 128) {
-    float av[4], v1[4], v2[4];
+    float av[4], bv[4], v1[4], v2[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      av[u] = a[j + 32 * u];
-      v1[u] = x1[j + 32 * u];
-      v2[u] = x2[j + 32 * u];
+    for (int w = 0; w < 4; ++w) {
+      av[w] = a[j + 32 * w];
+      bv[w] = b[j + 32 * w];
+      v1[w] = x1[j + 32 * w];
+      v2[w] = x2[j + 32 * w];
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      s1 = fmaf(av[u], v1[u], s1);
-      s2 = fmaf(av[u], v2[u], s2);
+    for (int w = 0; w < 4; ++w) {
+      s1a = fmaf(av[w], v1[w], s1a);
+      s2a = fmaf(av[w], v2[w], s2a);
+      s1b = fmaf(bv[w], v1[w], s1b);
+      s2b = fmaf(bv[w], v2[w], s2b);
     }
   }
   for (; j < n; j += 32) {
-    const float av = a[j];
-    s1 = fmaf(av, x1[j], s1);
-    s2 = fmaf(av, x2[j], s2);
+    const float av = a[j], bv = b[j], v1 = x1[j], v2 = x2[j];
+    s1a = fmaf(av, v1, s1a);
+    s2a = fmaf(av, v2, s2a);
+    s1b = fmaf(bv, v1, s1b);
+    s2b = fmaf(bv, v2, s2b);
   }
-  u1 = warp_sum(s1);
-  u2 = warp_sum(s2);
+  u[0] = warp_sum(s1a);
+  u[1] = warp_sum(s2a);
+  u[2] = warp_sum(s1b);
+  u[3] = warp_sum(s2b);
 }
 
-// z_i = sum_{k <= i} M_ik r_k for the rows of M (warp per row), loads hoisted as in rowdots.
-__device__ __forceinline__ float lower_rowdot(const float* mi, const float* r, int i) {
+// z_i = sum_{k <= i} M_ik r_k for R rows i0 + t * stride (t < R; rows past q give nothing),
+// one warp.  Each row sums its terms in the order of a single-row walk (lane k, steps of 128
+// with four terms each while k + 96 <= i, then the tail k <= i in steps of 32); the R rows'
+// loads are issued together, so one round trip to L2 serves R rows.
+template <int R>
+__device__ __forceinline__ void lower_rowdots(const float* M, int q, const float* r, int i0, int stride,
+                                              float (&s)[R]) {
   const int lane = threadIdx.x & 31;
-  float s = 0.f;
-  int k = lane;
-  for (; k + 96 <= i; k += 128) {
-    float mv[4], rv[4];
+  int it[R];
+  const float* mi[R];
+  int imax = -1;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      mv[u] = mi[k + 32 * u];
-      rv[u] = r[k + 32 * u];
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) s = fmaf(mv[u], rv[u], s);
+  for (int t = 0; t < R; ++t) {
+    const int i = i0 + t * stride;
+    it[t] = i < q ? i : -1;
+    mi[t] = M + (int64_t)(i < q ? i : 0) * q;
+    imax = it[t] > imax ? it[t] : imax;
+    s[t] = 0.f;
   }
-  for (; k <= i; k += 32) s = fmaf(mi[k], r[k], s);
-  return warp_sum(s);
+  for (int k0 = 0; k0 <= imax; k0 += 128) {
+    const int k = k0 + lane;
+    float rv[4], mv[R][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) rv[u] = k + 32 * u <= imax ? r[k + 32 * u] : 0.f;
+#pragma unroll
+    for (int t = 0; t < R; ++t)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) mv[t][u] = k + 32 * u <= it[t] ? mi[t][k + 32 * u] : 0.f;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      if (k + 96 <= it[t]) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[t] = fmaf(mv[t][u], rv[u], s[t]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (k + 32 * u <= it[t]) s[t] = fmaf(mv[t][u], rv[u], s[t]);
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < R; ++t) s[t] = warp_sum(s[t]);
 }
+
+// z = M r over the q rows of the lower-triangular M: warp w takes rows w, w + NW, ... eight
+// at a time.
+__device__ __forceinline__ void lower_matvec(const float* M, int q, const float* r, float* z) {
+  constexpr int R = 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < q; i += R * NW) {
+    float sv[R];
+    lower_rowdots<R>(M, q, r, i, NW, sv);
+    if (lane == 0) {
+#pragma unroll
+      for (int t = 0; t < R; ++t)
+        if (i + t * NW < q) z[i + t * NW] = sv[t];
+    }
+  }
+}
+
+// Per-row scalars of a warp's rows, 32 rows at a time: lane l loads the values of row
+// i0 + l * NW (the warp's l-th row of the group) before the group's row dots, and finishes that
+// row afterwards, so the rows' epilogues run side by side instead of one after another.
+template <int NS>
+struct RowScalars {
+  float v[NS];
+  __device__ __forceinline__ void load(const float* const (&src)[NS], int i, bool ok) {
+#pragma unroll
+    for (int c = 0; c < NS; ++c) v[c] = ok ? src[c][i] : 1.0f;
+  }
+};
 
 // Copies len floats from src to the shared-memory area dst with every thread (loads in flight
 // together) when `use`; returns the pointer the phase reads.  The caller synchronises.
@@ -394,21 +456,23 @@ __device__ __forceinline__ const float* stage_vec(float* dst, const float* src, 
 // Column sums t_r[j] = sum_i X[i][j] v_r[i] (r < NR) over `rows` rows of a row-major matrix, by
 // the whole CTA: warp w takes rows w, w + NW, ...; lane l the columns c0 + l + 32 t (t < 4) of
 // each 128-column chunk, so every warp reads whole rows; the warps' partial sums meet in `red`
-// (NW x NR x 128 floats) and are added in warp order.  fn(j, t) finishes column j (one thread).
-template <int NR, class Fn>
+// (NW x NR x 128 floats) and are added in warp order.  pre(j) loads what the epilogue of column
+// j needs (before the cross-warp sum, so its latency overlaps it); fn(j, t, p) finishes column j
+// (one thread).  RB rows' loads are in flight per warp step; each column still sums its rows
+// in increasing order.
+template <int NR, int RB, class Pre, class Fn>
 __device__ __forceinline__ void cta_colsum(const float* X, int ldx, int rows, int cols, const float* v1,
-                                           const float* v2, const float* v3, float* red, Fn fn) {
+                                           const float* v2, const float* v3, float* red, Pre pre, Fn fn) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* v[3] = {v1, v2, v3};
   for (int c0 = 0; c0 < cols; c0 += 128) {
     float acc[NR][4];
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.0f;
-    // four rows' loads in flight per step; each column still sums its rows in increasing order
-    for (int i0 = warp; i0 < rows; i0 += 4 * NW) {
-      float a[4][4], w[4][NR];
+    for (int i0 = warp; i0 < rows; i0 += RB * NW) {
+      float a[RB][4], w[RB][NR];
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
+      for (int h = 0; h < RB; ++h) {
         const int i = i0 + h * NW;
         const bool ok = i < rows;
         const float* row = X + (int64_t)(ok ? i : 0) * ldx + c0;
@@ -421,18 +485,20 @@ __device__ __forceinline__ void cta_colsum(const float* X, int ldx, int rows, in
         }
       }
 #pragma unroll
-      for (int h = 0; h < 4; ++h)
+      for (int h = 0; h < RB; ++h)
 #pragma unroll
         for (int t = 0; t < 4; ++t)
 #pragma unroll
           for (int r = 0; r < NR; ++r) acc[r][t] = fmaf(a[h][t], w[h][r], acc[r][t]);
     }
+    const bool mine = tid < 128 && c0 + tid < cols;
+    const auto p = pre(mine ? c0 + tid : 0);
 #pragma unroll
     for (int r = 0; r < NR; ++r)
 #pragma unroll
       for (int t = 0; t < 4; ++t) red[(warp * NR + r) * 128 + lane + 32 * t] = acc[r][t];
     __syncthreads();
-    if (tid < 128 && c0 + tid < cols) {
+    if (mine) {
       float t[NR];
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
@@ -441,11 +507,18 @@ __device__ __forceinline__ void cta_colsum(const float* X, int ldx, int rows, in
         for (int w = 0; w < NW; ++w) sum += red[(w * NR + r) * 128 + tid];
         t[r] = sum;
       }
-      fn(c0 + tid, t);
+      fn(c0 + tid, t, p);
     }
     __syncthreads();
   }
 }
+
+struct F2 {
+  float a, b;
+};
+struct F3 {
+  float a, b, c;
+};
 
 __device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, float* sv, double* red, float* red3,
                              Loop* L, int max_steps) {
@@ -522,38 +595,50 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, floa
       const float* v2 = stage_vec(sv + m, I.nu, m, vs);
       const float* v3 = stage_vec(sv + 2 * m, I.yt, m, vs);
       __syncthreads();
-      cta_colsum<3>(A, lda, m, n, v1, v2, v3, red3, [&](int j, const float* t) {
-        I.r[j] = I.cx[j] + t[0];
-        I.xt[j] = -t[2];
-        const float dr = t[1] + I.mu[j];
-        df_add_prod(rs[2], dr, dr);
-        const float du = dr / I.E[j];
-        df_add_prod(rs[3], du, du);
-      });
+      cta_colsum<3, 4>(
+          A, lda, m, n, v1, v2, v3, red3, [&](int j) { return F3{I.cx[j], I.mu[j], I.E[j]}; },
+          [&](int j, const float* t, const F3& p) {
+            I.r[j] = p.a + t[0];
+            I.xt[j] = -t[2];
+            const float dr = t[1] + p.b;
+            df_add_prod(rs[2], dr, dr);
+            const float du = dr / p.c;
+            df_add_prod(rs[3], du, du);
+          });
       const float* rr = stage_vec(sv, I.r, q, vs);
       __syncthreads();
       float* zz = vs ? sv + q : I.z;
-      for (int i = warp; i < q; i += NW) {   // z = M r
-        const float s = lower_rowdot(I.M + (int64_t)i * q, rr, i);
-        if (lane == 0) zz[i] = s;
-      }
+      lower_matvec(I.M, q, rr, zz);   // z = M r
       __syncthreads();
-      cta_colsum<1>(I.M, q, q, q, zz, nullptr, nullptr, red3, [&](int j, const float* t) {   // x = M^T z
-        I.x[j] = t[0];
-        I.xt[j] += I.cx[j] - t[0];                                                         // x~ += c - x
-      });
+      cta_colsum<1, 8>(
+          I.M, q, q, q, zz, nullptr, nullptr, red3, [&](int j) { return F2{I.xt[j], I.cx[j]}; },
+          [&](int j, const float* t, const F2& p) {   // x = M^T z ; x~ += c - x
+            I.x[j] = t[0];
+            I.xt[j] = p.a + (p.b - t[0]);
+          });
       const float* xx = stage_vec(sv, I.x, n, vs);
       const float* xs = stage_vec(sv + n, I.xh, n, vs);
       __syncthreads();
-      for (int i = warp; i < m; i += NW) {    // y = A x, w = A x^ ; y~ += d - y ; primal residual
-        float u1, u2;
-        rowdots(A, lda, m, n, xx, xs, i, u1, u2);
-        if (lane == 0) {
-          I.y[i] = u1;
-          I.yt[i] += I.dy[i] - u1;
-          const float pr = u2 - I.yh[i];
+      for (int g = warp; g < m; g += 32 * NW) {   // y = A x, w = A x^ ; y~ += d - y ; primal residual
+        RowScalars<4> sc;
+        const float* const src[4] = {I.yt, I.dy, I.yh, I.D};
+        const int im = g + lane * NW;
+        sc.load(src, im, im < m);
+        float mu1 = 0.f, mu2 = 0.f;   // this lane's row of the group
+        for (int t = 0; t < 32; t += 2) {   // two rows per step
+          const int i = g + t * NW;
+          if (i >= m) break;
+          float u[4];
+          rowdots2(A, lda, n, xx, xs, i, i + NW, i + NW < m, u);
+          if (lane == t) { mu1 = u[0]; mu2 = u[1]; }
+          if (lane == t + 1) { mu1 = u[2]; mu2 = u[3]; }
+        }
+        if (im < m) {
+          I.y[im] = mu1;
+          I.yt[im] = sc.v[0] + (sc.v[1] - mu1);
+          const float pr = mu2 - sc.v[2];
           df_add_prod(rs[0], pr, pr);
-          const float pu = pr / I.D[i];
+          const float pu = pr / sc.v[3];
           df_add_prod(rs[1], pu, pu);
         }
       }
@@ -562,43 +647,55 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, floa
       const float* xs = stage_vec(sv + n, I.xh, n, vs);
       __syncthreads();
       float* rw = vs ? sv + 2 * n : I.r;      // r, read by the next phase only
-      for (int i = warp; i < m; i += NW) {    // r = A c - d ; primal residual
-        float u1, u2;
-        rowdots(A, lda, m, n, cc, xs, i, u1, u2);
-        if (lane == 0) {
-          rw[i] = u1 - I.dy[i];
-          const float pr = u2 - I.yh[i];
+      for (int g = warp; g < m; g += 32 * NW) {   // r = A c - d ; primal residual
+        RowScalars<3> sc;
+        const float* const src[3] = {I.dy, I.yh, I.D};
+        const int im = g + lane * NW;
+        sc.load(src, im, im < m);
+        float mu1 = 0.f, mu2 = 0.f;   // this lane's row of the group
+        for (int t = 0; t < 32; t += 2) {   // two rows per step
+          const int i = g + t * NW;
+          if (i >= m) break;
+          float u[4];
+          rowdots2(A, lda, n, cc, xs, i, i + NW, i + NW < m, u);
+          if (lane == t) { mu1 = u[0]; mu2 = u[1]; }
+          if (lane == t + 1) { mu1 = u[2]; mu2 = u[3]; }
+        }
+        if (im < m) {
+          rw[im] = mu1 - sc.v[0];
+          const float pr = mu2 - sc.v[1];
           df_add_prod(rs[0], pr, pr);
-          const float pu = pr / I.D[i];
+          const float pu = pr / sc.v[2];
           df_add_prod(rs[1], pu, pu);
         }
       }
       __syncthreads();
       float* zz = vs ? sv : I.z;               // (r sits after the 2n staged floats: no overlap)
-      for (int i = warp; i < q; i += NW) {    // z = M r
-        const float s = lower_rowdot(I.M + (int64_t)i * q, rw, i);
-        if (lane == 0) zz[i] = s;
-      }
+      lower_matvec(I.M, q, rw, zz);   // z = M r
       __syncthreads();
-      cta_colsum<1>(I.M, q, q, q, zz, nullptr, nullptr, red3, [&](int i, const float* t) {
-        const float d = I.dy[i], yp = d + t[0];   // v = M^T z ; y = d + v ; y~ += d - y ; w = d - y
-        I.y[i] = yp;
-        I.yt[i] += d - yp;
-        I.w[i] = d - yp;
-      });
+      cta_colsum<1, 8>(
+          I.M, q, q, q, zz, nullptr, nullptr, red3, [&](int i) { return F2{I.dy[i], I.yt[i]}; },
+          [&](int i, const float* t, const F2& p) {
+            const float d = p.a, yp = d + t[0];   // v = M^T z ; y = d + v ; y~ += d - y ; w = d - y
+            I.y[i] = yp;
+            I.yt[i] = p.b + (d - yp);
+            I.w[i] = d - yp;
+          });
       const float* v1 = stage_vec(sv, I.w, m, vs);
       const float* v2 = stage_vec(sv + m, I.nu, m, vs);
       const float* v3 = stage_vec(sv + 2 * m, I.yt, m, vs);
       __syncthreads();
-      cta_colsum<3>(A, lda, m, n, v1, v2, v3, red3, [&](int j, const float* t) {
-        const float c = I.cx[j], xp = c + t[0];   // x = c + A^T w ; x~ = -A^T y~ ; dual residual
-        I.x[j] = xp;
-        I.xt[j] = -t[2];
-        const float dr = t[1] + I.mu[j];
-        df_add_prod(rs[2], dr, dr);
-        const float du = dr / I.E[j];
-        df_add_prod(rs[3], du, du);
-      });
+      cta_colsum<3, 4>(
+          A, lda, m, n, v1, v2, v3, red3, [&](int j) { return F3{I.cx[j], I.mu[j], I.E[j]}; },
+          [&](int j, const float* t, const F3& p) {
+            const float xp = p.a + t[0];   // x = c + A^T w ; x~ = -A^T y~ ; dual residual
+            I.x[j] = xp;
+            I.xt[j] = -t[2];
+            const float dr = t[1] + p.b;
+            df_add_prod(rs[2], dr, dr);
+            const float du = dr / p.c;
+            df_add_prod(rs[3], du, du);
+          });
     }
     double rss[4];
     block_sum_df<4>(rs, rss, red);
