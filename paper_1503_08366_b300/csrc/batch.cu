@@ -333,35 +333,55 @@ __device__ __forceinline__ void zero_state(const BInst& I) {
   for (int i = threadIdx.x; i < I.m; i += NT) { I.y[i] = 0.0f; I.yt[i] = 0.0f; }
 }
 
+__device__ __forceinline__ float dot4(const float4 a, const float4 v, float s) {
+  return fmaf(a.w, v.w, fmaf(a.z, v.z, fmaf(a.y, v.y, fmaf(a.x, v.x, s))));
+}
+
 // Row dots u = A [x1, x2] for two rows ia and ib of the instance together (one warp; ib ignored
-// when !hasb): lane l takes columns l, l + 32, ... in steps of four loads while a whole step
-// fits, then the remaining ones; the x loads are shared by the two rows.
+// when !hasb).  Rows and x1, x2 start on 16-byte boundaries (row pitch a multiple of 4
+// floats): lane l takes the float4 column groups l, l + 32, ..., four groups per step while a
+// whole step fits, then one at a time, and the last n mod 4 columns one per lane; every load of
+// a step (eight float4 of A, eight of x) is issued before its arithmetic, and the x loads are
+// shared by the two rows.
 __device__ __forceinline__ void rowdots2(const float* A, int lda, int n, const float* x1, const float* x2, int ia,
                                          int ib, bool hasb, float (&u)[4]) {
   const int lane = threadIdx.x & 31;
-  const float* a = A + (int64_t)ia * lda;
-  const float* b = A + (int64_t)(hasb ? ib : ia) * lda;
+  const float* ar = A + (int64_t)ia * lda;
+  const float* br = A + (int64_t)(hasb ? ib : ia) * lda;
+  const float4* a = reinterpret_cast<const float4*>(ar);
+  const float4* b = reinterpret_cast<const float4*>(br);
+  const float4* p1 = reinterpret_cast<const float4*>(x1);
+  const float4* p2 = reinterpret_cast<const float4*>(x2);
+  const int nf = n >> 2;
   float s1a = 0.f, s2a = 0.f, s1b = 0.f, s2b = 0.f;
-  int j = lane;
-  for (; j + 96 < n; j += 128) {
-    float av[4], bv[4], v1[4], v2[4];
+  int g = lane;
+  for (; g + 96 < nf; g += 128) {
+    float4 av[4], bv[4], v1[4], v2[4];
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-      av[w] = a[j + 32 * w];
-      bv[w] = b[j + 32 * w];
-      v1[w] = x1[j + 32 * w];
-      v2[w] = x2[j + 32 * w];
+      av[w] = a[g + 32 * w];
+      bv[w] = b[g + 32 * w];
+      v1[w] = p1[g + 32 * w];
+      v2[w] = p2[g + 32 * w];
     }
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-      s1a = fmaf(av[w], v1[w], s1a);
-      s2a = fmaf(av[w], v2[w], s2a);
-      s1b = fmaf(bv[w], v1[w], s1b);
-      s2b = fmaf(bv[w], v2[w], s2b);
+      s1a = dot4(av[w], v1[w], s1a);
+      s2a = dot4(av[w], v2[w], s2a);
+      s1b = dot4(bv[w], v1[w], s1b);
+      s2b = dot4(bv[w], v2[w], s2b);
     }
   }
-  for (; j < n; j += 32) {
-    const float av = a[j], bv = b[j], v1 = x1[j], v2 = x2[j];
+  for (; g < nf; g += 32) {
+    const float4 av = a[g], bv = b[g], v1 = p1[g], v2 = p2[g];
+    s1a = dot4(av, v1, s1a);
+    s2a = dot4(av, v2, s2a);
+    s1b = dot4(bv, v1, s1b);
+    s2b = dot4(bv, v2, s2b);
+  }
+  const int c = 4 * nf + lane;
+  if (c < n) {
+    const float v1 = x1[c], v2 = x2[c], av = ar[c], bv = br[c];
     s1a = fmaf(av, v1, s1a);
     s2a = fmaf(av, v2, s2a);
     s1b = fmaf(bv, v1, s1b);
@@ -459,8 +479,9 @@ __device__ __forceinline__ const float* stage_vec(float* dst, const float* src, 
 // (NW x NR x 128 floats) and are added in warp order.  pre(j) loads what the epilogue of column
 // j needs (before the cross-warp sum, so its latency overlaps it); fn(j, t, p) finishes column j
 // (one thread).  RB rows' loads are in flight per warp step; each column still sums its rows
-// in increasing order.
-template <int NR, int RB, class Pre, class Fn>
+// in increasing order.  VEC: lane l takes the four consecutive columns c0 + 4 l .. + 3 with one
+// float4 load per row (X 16-byte aligned, ldx a multiple of 4), else the columns c0 + l + 32 t.
+template <int NR, int RB, bool VEC, class Pre, class Fn>
 __device__ __forceinline__ void cta_colsum(const float* X, int ldx, int rows, int cols, const float* v1,
                                            const float* v2, const float* v3, float* red, Pre pre, Fn fn) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -478,10 +499,20 @@ __device__ __forceinline__ void cta_colsum(const float* X, int ldx, int rows, in
         const float* row = X + (int64_t)(ok ? i : 0) * ldx + c0;
 #pragma unroll
         for (int r = 0; r < NR; ++r) w[h][r] = ok ? v[r][i] : 0.0f;
+        if (VEC) {   // columns c0 + 4 lane .. + 3: one float4 (16-byte rows; columns >= cols read as 0)
+          const int j = 4 * lane;
+          float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (ok && c0 + j < cols) q = *reinterpret_cast<const float4*>(row + j);
+          a[h][0] = q.x;
+          a[h][1] = c0 + j + 1 < cols ? q.y : 0.0f;
+          a[h][2] = c0 + j + 2 < cols ? q.z : 0.0f;
+          a[h][3] = c0 + j + 3 < cols ? q.w : 0.0f;
+        } else {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int j = lane + 32 * t;
-          a[h][t] = (ok && c0 + j < cols) ? row[j] : 0.0f;
+          for (int t = 0; t < 4; ++t) {
+            const int j = lane + 32 * t;
+            a[h][t] = (ok && c0 + j < cols) ? row[j] : 0.0f;
+          }
         }
       }
 #pragma unroll
@@ -496,7 +527,7 @@ __device__ __forceinline__ void cta_colsum(const float* X, int ldx, int rows, in
 #pragma unroll
     for (int r = 0; r < NR; ++r)
 #pragma unroll
-      for (int t = 0; t < 4; ++t) red[(warp * NR + r) * 128 + lane + 32 * t] = acc[r][t];
+      for (int t = 0; t < 4; ++t) red[(warp * NR + r) * 128 + (VEC ? 4 * lane + t : lane + 32 * t)] = acc[r][t];
     __syncthreads();
     if (mine) {
       float t[NR];
@@ -525,14 +556,14 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, floa
   BOut* out = I.out;
   const int m = I.m, n = I.n, q = I.q, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // the vectors each phase reads are staged in shared memory when three of the longest fit
-  const bool vs = 3 * (m > n ? m : n) <= kBatchVecFloats;
+  const int n4 = I.lda;   // n rounded up to a multiple of 4: row pitch and staged-vector offsets
+  const bool vs = 3 * (m > n4 ? m : n4) <= kBatchVecFloats;
   const float* A = I.A;
-  int lda = I.lda;
+  const int lda = I.lda;
   if (I.stage_smem) {   // same values, same loop order: only where they are read from changes
     for (int i = 0; i < m; ++i)
-      for (int j = tid; j < n; j += NT) smemA[i * n + j] = I.A[(int64_t)i * I.lda + j];
+      for (int j = tid; j < n4; j += NT) smemA[i * n4 + j] = j < n ? I.A[(int64_t)i * I.lda + j] : 0.0f;
     A = smemA;
-    lda = n;
   }
   const bool resume = I.loop && I.loop->started;
   if (!resume) zero_state(I);
@@ -595,7 +626,7 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, floa
       const float* v2 = stage_vec(sv + m, I.nu, m, vs);
       const float* v3 = stage_vec(sv + 2 * m, I.yt, m, vs);
       __syncthreads();
-      cta_colsum<3, 4>(
+      cta_colsum<3, 8, true>(
           A, lda, m, n, v1, v2, v3, red3, [&](int j) { return F3{I.cx[j], I.mu[j], I.E[j]}; },
           [&](int j, const float* t, const F3& p) {
             I.r[j] = p.a + t[0];
@@ -610,14 +641,14 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, floa
       float* zz = vs ? sv + q : I.z;
       lower_matvec(I.M, q, rr, zz);   // z = M r
       __syncthreads();
-      cta_colsum<1, 8>(
+      cta_colsum<1, 8, false>(
           I.M, q, q, q, zz, nullptr, nullptr, red3, [&](int j) { return F2{I.xt[j], I.cx[j]}; },
           [&](int j, const float* t, const F2& p) {   // x = M^T z ; x~ += c - x
             I.x[j] = t[0];
             I.xt[j] = p.a + (p.b - t[0]);
           });
       const float* xx = stage_vec(sv, I.x, n, vs);
-      const float* xs = stage_vec(sv + n, I.xh, n, vs);
+      const float* xs = stage_vec(sv + n4, I.xh, n, vs);
       __syncthreads();
       for (int g = warp; g < m; g += 32 * NW) {   // y = A x, w = A x^ ; y~ += d - y ; primal residual
         RowScalars<4> sc;
@@ -644,9 +675,9 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, floa
       }
     } else {
       const float* cc = stage_vec(sv, I.cx, n, vs);
-      const float* xs = stage_vec(sv + n, I.xh, n, vs);
+      const float* xs = stage_vec(sv + n4, I.xh, n, vs);
       __syncthreads();
-      float* rw = vs ? sv + 2 * n : I.r;      // r, read by the next phase only
+      float* rw = vs ? sv + 2 * n4 : I.r;     // r, read by the next phase only
       for (int g = warp; g < m; g += 32 * NW) {   // r = A c - d ; primal residual
         RowScalars<3> sc;
         const float* const src[3] = {I.dy, I.yh, I.D};
@@ -670,10 +701,10 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, floa
         }
       }
       __syncthreads();
-      float* zz = vs ? sv : I.z;               // (r sits after the 2n staged floats: no overlap)
+      float* zz = vs ? sv : I.z;               // (r sits after the 2 n4 staged floats: no overlap)
       lower_matvec(I.M, q, rw, zz);   // z = M r
       __syncthreads();
-      cta_colsum<1, 8>(
+      cta_colsum<1, 8, false>(
           I.M, q, q, q, zz, nullptr, nullptr, red3, [&](int i) { return F2{I.dy[i], I.yt[i]}; },
           [&](int i, const float* t, const F2& p) {
             const float d = p.a, yp = d + t[0];   // v = M^T z ; y = d + v ; y~ += d - y ; w = d - y
@@ -685,7 +716,7 @@ __device__ void run_instance(const BInst& I, const BCfg& cfg, float* smemA, floa
       const float* v2 = stage_vec(sv + m, I.nu, m, vs);
       const float* v3 = stage_vec(sv + 2 * m, I.yt, m, vs);
       __syncthreads();
-      cta_colsum<3, 4>(
+      cta_colsum<3, 8, true>(
           A, lda, m, n, v1, v2, v3, red3, [&](int j) { return F3{I.cx[j], I.mu[j], I.E[j]}; },
           [&](int j, const float* t, const F3& p) {
             const float xp = p.a + t[0];   // x = c + A^T w ; x~ = -A^T y~ ; dual residual

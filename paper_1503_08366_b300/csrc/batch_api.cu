@@ -277,7 +277,7 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
       BCK(cudaEventCreate(&e1));
       float best = 1e30f;
       for (const LaunchCfg& c : kCandidates) {
-        for (auto& I : inst) I.stage_smem = c.smem > 0 && (int64_t)I.m * I.n * 4 <= c.smem;
+        for (auto& I : inst) I.stage_smem = c.smem > 0 && (int64_t)I.m * I.lda * 4 <= c.smem;
         BCK(cudaMemcpyAsync(d_inst, inst.data(), sizeof(BInst) * ns, cudaMemcpyHostToDevice, s));
         BCK(cudaMemcpyAsync(d_order, (c.largest_first ? order_big : order_in).data(), sizeof(int) * ns,
                             cudaMemcpyHostToDevice, s));
@@ -303,7 +303,7 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
       g_tuned[key] = lc;
     }
   }
-  for (auto& I : inst) I.stage_smem = lc.smem > 0 && (int64_t)I.m * I.n * 4 <= lc.smem;
+  for (auto& I : inst) I.stage_smem = lc.smem > 0 && (int64_t)I.m * I.lda * 4 <= lc.smem;
   BCK(cudaMemcpyAsync(d_inst, inst.data(), sizeof(BInst) * ns, cudaMemcpyHostToDevice, s));
   BCK(cudaMemcpyAsync(d_order, (lc.largest_first ? order_big : order_in).data(), sizeof(int) * ns,
                       cudaMemcpyHostToDevice, s));
