@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <set>
 #include <numeric>
 
 #include "../../include/pogs.h"
@@ -69,31 +70,40 @@ class Dissection {
   std::vector<int> tag_, lvl_, out_;
   int cur_ = 0;
 
-  // BFS over the nodes tagged t from s; fills levels (node lists per level).  Returns the node
-  // count reached.
-  int bfs(int s, int t, std::vector<std::vector<int>>& levels) {
-    levels.clear();
-    std::vector<int> front{s};
+  // Level structure of a BFS: the nodes in visiting order, and the start of each level in it
+  // (lo.back() == q.size()).
+  struct Levels {
+    std::vector<int> q, lo;
+    int count() const { return (int)lo.size() - 1; }
+    const int* begin(int l) const { return q.data() + lo[l]; }
+    const int* end(int l) const { return q.data() + lo[l + 1]; }
+  };
+
+  // BFS over the nodes tagged t from s (neighbours in adjacency order, level by level).
+  void bfs(int s, int t, Levels& L) {
+    L.q.clear();
+    L.lo.clear();
+    L.q.push_back(s);
     lvl_[s] = 0;
-    std::vector<int> seen{s};
-    int count = 0;
-    while (!front.empty()) {
-      levels.push_back(front);
-      count += (int)front.size();
-      std::vector<int> next;
-      for (int v : front)
+    size_t b = 0;
+    while (b < L.q.size()) {
+      const size_t e = L.q.size();
+      L.lo.push_back((int)b);
+      const int next = (int)L.lo.size();
+      for (size_t k = b; k < e; ++k) {
+        const int v = L.q[k];
         for (int p = g_.off[v]; p < g_.off[v + 1]; ++p) {
           const int u = g_.adj[p];
           if (tag_[u] == t && lvl_[u] < 0) {
-            lvl_[u] = (int)levels.size();
-            next.push_back(u);
-            seen.push_back(u);
+            lvl_[u] = next;
+            L.q.push_back(u);
           }
         }
-      front.swap(next);
+      }
+      b = e;
     }
-    for (int v : seen) lvl_[v] = -1;
-    return count;
+    L.lo.push_back((int)L.q.size());
+    for (int v : L.q) lvl_[v] = -1;
   }
 
   void dissect(const std::vector<int>& nodes) {
@@ -105,13 +115,12 @@ class Dissection {
     for (int v : nodes) tag_[v] = t;
     // connected parts, each moved to a tag of its own as it is found
     std::vector<std::vector<int>> parts;
-    std::vector<std::vector<int>> levels;
+    Levels levels;
     int tpart = t;
     for (int v : nodes) {
       if (tag_[v] != t) continue;
       bfs(v, t, levels);
-      std::vector<int> part;
-      for (const auto& l : levels) part.insert(part.end(), l.begin(), l.end());
+      std::vector<int> part(levels.q);
       tpart = ++cur_;
       for (int u : part) tag_[u] = tpart;
       parts.push_back(std::move(part));
@@ -125,17 +134,17 @@ class Dissection {
     }
     // one connected part (tag tpart): pseudo-peripheral start, the last node of a BFS, repeated
     // while the depth grows
-    int start = levels.back()[0];
-    int depth = (int)levels.size();
+    int start = *levels.begin(levels.count() - 1);
+    int depth = levels.count();
+    Levels l2;
     for (int it = 0; it < 4; ++it) {
-      std::vector<std::vector<int>> l2;
       bfs(start, tpart, l2);
-      if ((int)l2.size() <= depth) break;
-      depth = (int)l2.size();
-      levels.swap(l2);
-      start = levels.back()[0];
+      if (l2.count() <= depth) break;
+      depth = l2.count();
+      std::swap(levels, l2);
+      start = *levels.begin(levels.count() - 1);
     }
-    if (levels.size() < 3) {          // nearly a clique: no useful separator
+    if (levels.count() < 3) {         // nearly a clique: no useful separator
       std::vector<int> v(nodes);
       std::sort(v.begin(), v.end());
       for (int u : v) out_.push_back(u);
@@ -143,17 +152,16 @@ class Dissection {
     }
     const int half = (int)nodes.size() / 2;
     int acc = 0, L = 1;
-    for (int l = 0; l < (int)levels.size(); ++l) {
-      acc += (int)levels[l].size();
+    for (int l = 0; l < levels.count(); ++l) {
+      acc += levels.lo[l + 1] - levels.lo[l];
       if (acc > half) {
         L = l;
         break;
       }
     }
-    L = std::max(1, std::min(L, (int)levels.size() - 2));
-    std::vector<int> p1, p2, sep(levels[L]);
-    for (int l = 0; l < L; ++l) p1.insert(p1.end(), levels[l].begin(), levels[l].end());
-    for (int l = L + 1; l < (int)levels.size(); ++l) p2.insert(p2.end(), levels[l].begin(), levels[l].end());
+    L = std::max(1, std::min(L, levels.count() - 2));
+    std::vector<int> p1(levels.begin(0), levels.begin(L)), p2(levels.begin(L + 1), levels.end(levels.count() - 1)),
+        sep(levels.begin(L), levels.end(L));
     std::sort(p1.begin(), p1.end());
     std::sort(p2.begin(), p2.end());
     std::sort(sep.begin(), sep.end());
@@ -393,38 +401,49 @@ int ldl_analyze(int m, int n, const int* rp, const int* ci, LdlSymbolic& S) {
     S.level_split[l] = split;
     S.front_max = std::max(S.front_max, acc);
   }
-  // update matrices: an arena with first-fit reuse.  The update of s is written at level(s) and
-  // read at level(parent(s)); its space is free again from the level after that.
+  // update matrices: an arena with best-fit reuse (the smallest free block that holds the
+  // update, lowest offset among equals; free neighbours merge).  The update of s is written at
+  // level(s) and read at level(parent(s)); its space is free again from the level after that.
   {
-    std::map<int64_t, int64_t> free_by_off;   // offset -> size
+    std::map<int64_t, int64_t> free_by_off;            // offset -> size
+    std::set<std::pair<int64_t, int64_t>> free_by_size;  // (size, offset)
     int64_t end = 0;
     std::vector<std::vector<int>> release_after(S.levels + 1);
+    auto insert = [&](int64_t off, int64_t size) {
+      free_by_off[off] = size;
+      free_by_size.insert({size, off});
+    };
+    auto erase = [&](std::map<int64_t, int64_t>::iterator it) {
+      free_by_size.erase({it->second, it->first});
+      return free_by_off.erase(it);
+    };
     auto take = [&](int64_t size) -> int64_t {
-      for (auto it = free_by_off.begin(); it != free_by_off.end(); ++it)
-        if (it->second >= size) {
-          const int64_t off = it->first, rest = it->second - size;
-          free_by_off.erase(it);
-          if (rest > 0) free_by_off[off + size] = rest;
-          return off;
-        }
-      const int64_t off = end;
-      end += size;
+      auto fit = free_by_size.lower_bound({size, INT64_MIN});
+      if (fit == free_by_size.end()) {
+        const int64_t off = end;
+        end += size;
+        return off;
+      }
+      const int64_t off = fit->second, rest = fit->first - size;
+      erase(free_by_off.find(off));
+      if (rest > 0) insert(off + size, rest);
       return off;
     };
     auto give = [&](int64_t off, int64_t size) {
-      auto it = free_by_off.emplace(off, size).first;
-      auto nx = std::next(it);
-      if (nx != free_by_off.end() && it->first + it->second == nx->first) {
-        it->second += nx->second;
-        free_by_off.erase(nx);
+      auto nx = free_by_off.lower_bound(off);
+      if (nx != free_by_off.end() && off + size == nx->first) {
+        size += nx->second;
+        nx = erase(nx);
       }
-      if (it != free_by_off.begin()) {
-        auto pv = std::prev(it);
-        if (pv->first + pv->second == it->first) {
-          pv->second += it->second;
-          free_by_off.erase(it);
+      if (nx != free_by_off.begin()) {
+        auto pv = std::prev(nx);
+        if (pv->first + pv->second == off) {
+          off = pv->first;
+          size += pv->second;
+          erase(pv);
         }
       }
+      insert(off, size);
     };
     for (int l = 0; l < S.levels; ++l) {
       if (l > 0)   // read at level l - 1, which has completed before level l starts
