@@ -96,10 +96,12 @@ void launch_prox_step(int n, int m, const float* x, float* xt, float* xh, float*
 // ------------------------------------------------------------------------------------------
 // Column sums t = A^T [v1, v2] (A row-major m x lda, zero-padded columns).  Block (bx, by)
 // streams rows [by*R, by*R+R) of the 1024-column slab bx (256 threads x float4); partial
-// sums go to part[by][rhs][col]; the last block of each slab reduces the splits in a fixed
-// order and applies the epilogue.
+// sums go to part[by][rhs][col]; with FIN, the last block of each slab reduces the splits in a
+// fixed order and applies the epilogue; without, the launch only streams and
+// pogs_colsum_finish_kernel (the next launch) does the same reduction with every slab's
+// partials in flight at once.
 // ------------------------------------------------------------------------------------------
-template <int NRHS, bool SQ, int EPI>
+template <int NRHS, bool SQ, int EPI, bool FIN = true>
 __global__ void __launch_bounds__(256, 5) pogs_colsum_kernel(const float* __restrict__ A, int64_t lda, int m, int n,
                                                      const float* __restrict__ v1,
                                                      const float* __restrict__ v2,
@@ -165,6 +167,7 @@ __global__ void __launch_bounds__(256, 5) pogs_colsum_kernel(const float* __rest
       *reinterpret_cast<float4*>(part + ((int64_t)blockIdx.y * NRHS + r) * lda + c0) =
           make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
   }
+  if (!FIN) return;
   if (!arrive_last(cnt + blockIdx.x, gridDim.y)) return;
   Df res[2] = {};
   if (active) {
@@ -202,6 +205,66 @@ __global__ void __launch_bounds__(256, 5) pogs_colsum_kernel(const float* __rest
     for (int u = 0; u < 4; ++u) {
       const int64_t j = c0 + u;
       if (j < n) epi_t<EPI>(ep, (int)j, s[0][u], NRHS >= 2 ? s[1][u] : 0.0f, NRHS == 3 ? s[NRHS - 1][u] : 0.0f, res);
+    }
+  }
+  double tot[2];
+  block_sum_df<2>(res, tot, sh);
+  if (threadIdx.x == 0 && ep.res_part) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const float hi = (float)tot[t];
+      ep.res_part[2 * blockIdx.x + t] = Df{hi, (float)(tot[t] - (double)hi)};
+    }
+  }
+}
+
+// Final reduction and epilogue of the column sums after a streaming launch
+// (pogs_colsum_kernel<..., false>): one block per 1024-column slab, NRHS x 256 threads.  Thread
+// (r, c) adds the nsp row splits' partials of right-hand side r for the four columns
+// c0 = 1024 bx + 4 c .. + 3 in split order, eight loads in flight; the first 256 threads then
+// apply the epilogue to their columns, and the block's residual partials go to res_part[bx] as in
+// the streaming kernel's own final reduction.
+template <int NRHS, int EPI>
+__global__ void __launch_bounds__(768) pogs_colsum_finish_kernel(const float* __restrict__ part, int64_t lda, int n,
+                                                                 int nsp, EpiArgs ep,
+                                                                 const DevState* __restrict__ guard) {
+  __shared__ float4 sums[NRHS][256];
+  __shared__ double sh[2 * 24];
+  if (guard && guard->done) return;
+  if (ep.cg_done && *ep.cg_done) return;
+  const int tid = threadIdx.x, r = tid >> 8, c = tid & 255;
+  const int64_t c0 = (int64_t)blockIdx.x * 1024 + 4 * c;
+  const bool active = c0 < lda;
+  if (active) {
+    const int64_t rs = lda >> 2, ss = NRHS * rs;
+    const float4* pp = reinterpret_cast<const float4*>(part + c0) + r * rs;
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    int sp = 0;
+    for (; sp + 8 <= nsp; sp += 8) {
+      float4 q[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) q[u] = __ldcg(pp + (sp + u) * ss);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        t.x += q[u].x; t.y += q[u].y; t.z += q[u].z; t.w += q[u].w;
+      }
+    }
+    for (; sp < nsp; ++sp) {
+      const float4 q = __ldcg(pp + sp * ss);
+      t.x += q.x; t.y += q.y; t.z += q.z; t.w += q.w;
+    }
+    sums[r][c] = t;
+  }
+  __syncthreads();
+  Df res[2] = {};
+  if (r == 0 && active) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 a = sums[0][c], b = NRHS >= 2 ? sums[1][c] : z, d = NRHS == 3 ? sums[NRHS - 1][c] : z;
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w}, dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t j = c0 + u;
+      if (j < n) epi_t<EPI>(ep, (int)j, av[u], NRHS >= 2 ? bv[u] : 0.0f, NRHS == 3 ? dv[u] : 0.0f, res);
     }
   }
   double tot[2];
@@ -702,20 +765,37 @@ static void gemv_t_dispatch(int epi, const float* A, int64_t lda, int m, int n, 
                             const float* v3, const GemvGeom& g, float* part, unsigned* cnt, const EpiArgs& ep,
                             const DevState* guard, cudaStream_t s) {
   dim3 grid(g.t_ncolblk, g.t_nsplit);
-  count_launch();
+  const bool split = colsum_split(g, epi);
+  count_launch(split ? 2 : 1);
 #define POGS_T(E) pogs_colsum_kernel<NRHS, SQ, E><<<grid, 256, 0, s>>>(A, lda, m, n, v1, v2, v3, g.t_rows, part, cnt, ep, guard)
+#define POGS_TS(E)                                                                                              \
+  do {                                                                                                          \
+    if (split) {                                                                                                \
+      pogs_colsum_kernel<NRHS, SQ, E, false><<<grid, 256, 0, s>>>(A, lda, m, n, v1, v2, v3, g.t_rows, part, cnt,  \
+                                                                  ep, guard);                                   \
+      pogs_colsum_finish_kernel<NRHS, E><<<g.t_ncolblk, 256 * NRHS, 0, s>>>(part, lda, n, g.t_nsplit, ep, guard); \
+    } else {                                                                                                    \
+      POGS_T(E);                                                                                                \
+    }                                                                                                           \
+  } while (0)
   switch (epi) {
-    case EPT_RAW: POGS_T(EPT_RAW); break;
-    case EPT_TALL_R: POGS_T(EPT_TALL_R); break;
-    case EPT_FAT_X: POGS_T(EPT_FAT_X); break;
-    case EPT_SK_COL: POGS_T(EPT_SK_COL); break;
-    case EPT_REFINE: POGS_T(EPT_REFINE); break;
+    case EPT_RAW: POGS_TS(EPT_RAW); break;
+    case EPT_TALL_R: POGS_TS(EPT_TALL_R); break;
+    case EPT_FAT_X: POGS_TS(EPT_FAT_X); break;
+    case EPT_SK_COL: POGS_TS(EPT_SK_COL); break;
+    case EPT_REFINE: POGS_TS(EPT_REFINE); break;
     case EPT_CG_R: POGS_T(EPT_CG_R); break;
     case EPT_CG_S0: POGS_T(EPT_CG_S0); break;
     case EPT_CG_Q: POGS_T(EPT_CG_Q); break;
     case EPT_CG_S: POGS_T(EPT_CG_S); break;
   }
 #undef POGS_T
+#undef POGS_TS
+}
+
+bool colsum_split(const GemvGeom& g, int epi) {
+  return !g.sparse && g.t_nsplit >= 4 &&
+         (epi == EPT_RAW || epi == EPT_TALL_R || epi == EPT_FAT_X || epi == EPT_SK_COL || epi == EPT_REFINE);
 }
 
 void launch_gemv_t(int nrhs, bool sq, int epi, const float* A, int64_t lda, int m, int n, const float* v1,

@@ -103,6 +103,9 @@ void launch_prox_step(int n, int m, const float* x, float* xt, float* xh, float*
                       const float* y, float* yt, float* yh, float* dy, float* nu,
                       FnDev g, FnDev f, const DevState* st, const DevCfg* cfg, Df* part,
                       int nblocks, cudaStream_t s);
+// Whether a dense column-sum pass with epilogue epi runs as two launches (streaming, then the
+// final reduction with the epilogue) instead of one with an in-kernel last-block reduction.
+bool colsum_split(const GemvGeom& g, int epi);
 void launch_gemv_t(int nrhs, bool sq, int epi, const float* A, int64_t lda, int m, int n,
                    const float* v1, const float* v2, const float* v3, const GemvGeom& g, float* part,
                    unsigned* cnt,

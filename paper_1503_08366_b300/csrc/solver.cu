@@ -412,7 +412,9 @@ int kernels_per_iteration(const pogs_handle* h, int refine, int cg_steps) {
   // prox, 2 A passes, check, the inverse (one symmetric or two triangular products) (+ refinement:
   // 2 passes and the inverse again)
   const int inv = h->ldl ? ldl_launches(*h->ldl) : h->St ? 1 : 2;
-  return 4 + inv + (refine ? 2 + inv : 0) + pk;
+  // a split column-sum pass is two launches (the main pass, and the refinement's)
+  const int cs = colsum_split(h->geom, h->tall ? EPT_TALL_R : EPT_FAT_X) ? 1 : 0;
+  return 4 + inv + (refine ? 2 + inv : 0) + pk + cs * (refine ? 2 : 1);
 }
 
 int build_graph(pogs_handle* h, int refine, int mode, int cg_steps) {
