@@ -289,37 +289,90 @@ __global__ void __launch_bounds__(NT) bsetup_chol_kernel(BInst* insts, int mixed
 }
 
 // ---------------------------------------------------------------------------------------------
-// Setup 4: M = L^{-1} (FP32, dense lower, ld q), one column per thread by forward substitution
-// with FP64 accumulation.  The loads of each dot product are issued eight at a time before they
-// are accumulated (in the same order), so a column waits for one L2 round trip per eight terms.
+// Setup 4: M = L^{-1} (FP32, dense lower with zeros above the diagonal, ld q) by block forward
+// substitution on 32 x 32 blocks, one block row at a time: W_ii = L_ii^{-1} by FP64 substitution
+// (warp 0, lane = column, rounded to FP32), then for every j < i at once
+// M_ij = -W_ii sum_{k=j}^{i-1} L_ik M_kj, the sum in FP32 over the FP32-rounded L (the warps take
+// the blocks j in turn, lane = column of the block, 32 row accumulators per lane).  FP64 work
+// is q/32 diagonal blocks instead of the whole triangle (B300's FP64 rate is a small fraction of
+// its FP32 rate); the products carry FP32 accuracy, as those of the single-problem inverse.
 // ---------------------------------------------------------------------------------------------
+constexpr int kInvRowMax = 480;   // columns of L left of the last block row (q <= 512)
+constexpr int kInvSmem = kInvRowMax * 32 * (int)sizeof(float);
+
 __global__ void __launch_bounds__(NT) bsetup_inverse_kernel(BInst* insts) {
+  extern __shared__ __align__(16) float Lt[];   // block row i of L left of the diagonal, FP32, Lt[k * 32 + r]
+  __shared__ double Ld[32][33];
+  __shared__ float Wd[32][33];
   BInst I = insts[blockIdx.x];
   if (I.out->status != 0) return;
-  const int q = I.q;
+  const int q = I.q, T = (q + 31) / 32;
   const double* L = I.H;
   float* M = I.M;
-  for (int c = threadIdx.x; c < q; c += NT) {
-    for (int i = 0; i < c; ++i) M[(int64_t)i * q + c] = 0.0f;
-    M[(int64_t)c * q + c] = (float)(1.0 / L[(int64_t)c * q + c]);
-    for (int i = c + 1; i < q; ++i) {
-      const double* li = L + (int64_t)i * q;
-      double acc = 0.0;
-      int k = c;
-      for (; k + 8 <= i; k += 8) {
-        double lv[8];
-        float mv[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          lv[u] = li[k + u];
-          mv[u] = M[(int64_t)(k + u) * q + c];
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc -= lv[u] * (double)mv[u];
-      }
-      for (; k < i; ++k) acc -= li[k] * (double)M[(int64_t)k * q + c];
-      M[(int64_t)i * q + c] = (float)(acc / li[i]);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int ib = 0; ib < T; ++ib) {
+    const int r0 = ib * 32, nb = min(32, q - r0);
+    for (int e = tid; e < 32 * 32; e += NT) {
+      const int r = e >> 5, c = e & 31;
+      Ld[r][c] = (r < nb && c < nb) ? L[(int64_t)(r0 + r) * q + r0 + c] : (r == c ? 1.0 : 0.0);
     }
+    for (int e = tid; e < r0 * 32; e += NT) {
+      const int r = e / r0, k = e - r * r0;   // consecutive threads along a row of L
+      Lt[k * 32 + r] = r < nb ? (float)L[(int64_t)(r0 + r) * q + k] : 0.0f;
+    }
+    // zeros right of the diagonal block
+    for (int r = 0; r < nb; ++r)
+      for (int c = r0 + 32 + tid; c < q; c += NT) M[(int64_t)(r0 + r) * q + c] = 0.0f;
+    __syncthreads();
+    if (warp == 0) {
+      // W = L_ii^{-1}, column c = lane: v_r = (delta_rc - sum_{c<=k<r} L_rk v_k) / L_rr
+      double v[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        double acc = r == lane ? 1.0 : 0.0;
+#pragma unroll
+        for (int k = 0; k < r; ++k) acc -= Ld[r][k] * v[k];
+        v[r] = r < lane ? 0.0 : acc / Ld[r][r];
+      }
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        Wd[r][lane] = (float)v[r];
+        if (r < nb && lane < nb) M[(int64_t)(r0 + r) * q + r0 + lane] = (float)v[r];
+      }
+    }
+    __syncthreads();
+    for (int jb = warp; jb < ib; jb += NW) {
+      const int c = jb * 32 + lane;
+      float t[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) t[r] = 0.0f;
+      for (int k = jb * 32; k < r0; k += 4) {
+        float mk[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) mk[u] = M[(int64_t)(k + u) * q + c];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4* lr = reinterpret_cast<const float4*>(Lt + (k + u) * 32);
+#pragma unroll
+          for (int r4 = 0; r4 < 8; ++r4) {
+            const float4 l = lr[r4];
+            t[4 * r4 + 0] = fmaf(l.x, mk[u], t[4 * r4 + 0]);
+            t[4 * r4 + 1] = fmaf(l.y, mk[u], t[4 * r4 + 1]);
+            t[4 * r4 + 2] = fmaf(l.z, mk[u], t[4 * r4 + 2]);
+            t[4 * r4 + 3] = fmaf(l.w, mk[u], t[4 * r4 + 3]);
+          }
+        }
+      }
+      // M_ij = -W_ii T (W lower triangular)
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        float a = 0.0f;
+#pragma unroll
+        for (int s2 = 0; s2 <= r; ++s2) a = fmaf(Wd[r][s2], t[s2], a);
+        if (r < nb) M[(int64_t)(r0 + r) * q + c] = -a;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -842,14 +895,16 @@ int batch_setup(BInst* d_inst, int count, const BCfg& cfg, cudaStream_t s) {
         if (cudaFuncSetAttribute(bsetup_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, chol_smem) ==
                 cudaSuccess &&
             cudaFuncSetAttribute(batch_admm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 batch_max_smem() + kBatchVecFloats * (int)sizeof(float)) == cudaSuccess)
+                                 batch_max_smem() + kBatchVecFloats * (int)sizeof(float)) == cudaSuccess &&
+            cudaFuncSetAttribute(bsetup_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSmem) ==
+                cudaSuccess)
           return 0;
         cudaGetLastError();
         return -1;
       }) != 0)
     return POGS_ERR_CUDA;
   bsetup_chol_kernel<<<count, NT, chol_smem, s>>>(d_inst, cfg.mixed_chol);
-  bsetup_inverse_kernel<<<count, NT, 0, s>>>(d_inst);
+  bsetup_inverse_kernel<<<count, NT, kInvSmem, s>>>(d_inst);
   return cudaGetLastError() == cudaSuccess ? 0 : POGS_ERR_CUDA;
 }
 
