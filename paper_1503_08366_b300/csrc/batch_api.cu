@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <numeric>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -31,6 +32,66 @@ bool is_dev(const void* p) {
 }
 
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Pinned host memory for staging host inputs and outputs, kept between calls and grown on demand
+// (up to kPinnedMax); one call holds it at a time, and a call that finds it taken, or needs more,
+// stages in pageable memory instead.
+constexpr size_t kPinnedMax = size_t(4) << 30;
+struct PinnedStage {
+  std::mutex mu;
+  char* p = nullptr;
+  size_t cap = 0;
+};
+PinnedStage g_pin;
+
+// The pinned buffer with at least `bytes`, locked by `lk`, or nullptr.
+char* pinned(std::unique_lock<std::mutex>& lk, size_t bytes) {
+  if (bytes > kPinnedMax) return nullptr;
+  lk = std::unique_lock<std::mutex>(g_pin.mu, std::try_to_lock);
+  if (!lk.owns_lock()) return nullptr;
+  if (g_pin.cap < bytes) {
+    if (g_pin.p) cudaFreeHost(g_pin.p);
+    g_pin.p = nullptr;
+    g_pin.cap = 0;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&g_pin.p), bytes, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      g_pin.p = nullptr;
+      lk.unlock();
+      return nullptr;
+    }
+    g_pin.cap = bytes;
+  }
+  return g_pin.p;
+}
+
+// f(k) for k < n on up to eight host threads.
+template <class F>
+void parallel_for(int n, F f) {
+  const int nt = std::max(1, std::min({8, n, (int)std::thread::hardware_concurrency()}));
+  if (nt == 1) {
+    for (int k = 0; k < n; ++k) f(k);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      for (int k = t; k < n; k += nt) f(k);
+    });
+  for (auto& x : th) x.join();
+}
+
+// Returned tuples of all instances into one device buffer (x, y, mu, nu of instance k at
+// out_off[k]), one CTA per instance, for a single copy to the host.
+__global__ void gather_out_kernel(const BInst* __restrict__ insts, const size_t* __restrict__ out_off, float* dst) {
+  const BInst& I = insts[blockIdx.x];
+  float* d = dst + out_off[blockIdx.x];
+  const float* src[4] = {I.ox, I.oy, I.omu, I.onu};
+  const int len[4] = {I.n, I.m, I.n, I.m};
+  for (int t = 0; t < 4; ++t) {
+    for (int i = threadIdx.x; i < len[t]; i += blockDim.x) d[i] = src[t][i];
+    d += len[t];
+  }
+}
 
 // Launch configurations the tuner chooses between; none changes per-instance arithmetic.
 struct LaunchCfg {
@@ -131,6 +192,12 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
   BOut* d_out = nullptr;
   int *d_queue = nullptr, *d_order = nullptr;
   std::vector<char> stage;
+  std::unique_lock<std::mutex> pin_lock;
+  char* hst = nullptr;                 // staging for host inputs and outputs (pinned or `stage`)
+  std::vector<size_t> out_off(ns + 1, 0);
+  size_t* d_outoff = nullptr;
+  float* d_gather = nullptr;
+  bool any_host_out = false;
   std::vector<BOut> hout(ns);
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -151,43 +218,77 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
   }
   BCK(cudaMemsetAsync(d_out, 0, sizeof(BOut) * ns, s));
   // ---- ingest -------------------------------------------------------------------------------
-  for (int k = 0; k < ns && !any_host_in; ++k) any_host_in = !is_dev(probs[small[k]].A);
-  if (any_host_in) stage.assign(in_end, 0);
-  for (int k = 0; k < ns; ++k) {
-    const pogs_problem& pr = probs[small[k]];
-    const int lda4 = (int)round_up(pr.n, 4);
-    if (is_dev(pr.A)) {
-      BCK(cudaMemcpy2DAsync(arena + offA[k], (size_t)lda4 * 4, pr.A, (size_t)pr.lda * 4, (size_t)pr.n * 4, pr.m,
-                            cudaMemcpyDeviceToDevice, s));
-    } else {
-      for (int64_t i = 0; i < pr.m; ++i)
-        memcpy(stage.data() + offA[k] + (size_t)i * lda4 * 4, pr.A + i * pr.lda, (size_t)pr.n * 4);
-    }
-    const void* src[12] = {pr.f.h, pr.f.a, pr.f.b, pr.f.c, pr.f.d, pr.f.e, pr.g.h, pr.g.a, pr.g.b, pr.g.c, pr.g.d, pr.g.e};
-    for (int t = 0; t < 12; ++t) {
-      if (!src[t]) continue;
-      const size_t bytes = (size_t)(t < 6 ? pr.m : pr.n) * ((t % 6) == 0 ? 1 : 4);
-      if (is_dev(src[t])) {
-        BCK(cudaMemcpyAsync(arena + offIn[k * 12 + t], src[t], bytes, cudaMemcpyDeviceToDevice, s));
-      } else {
-        if (stage.empty()) stage.assign(in_end, 0);
-        memcpy(stage.data() + offIn[k * 12 + t], src[t], bytes);
-      }
-    }
-  }
-  if (!stage.empty()) {
-    // inputs that came from the device were copied already; copy the host ones region by region
+  // Device inputs are copied device to device; host inputs are packed (row pitch padded to four
+  // floats) into one staging buffer by several host threads and copied in one transfer when every
+  // input is on the host, else region by region.
+  {
+    std::vector<char> dev_A(ns);
+    std::vector<char> dev_in((size_t)ns * 12);
+    bool all_host = true;
     for (int k = 0; k < ns; ++k) {
       const pogs_problem& pr = probs[small[k]];
-      const int lda4 = (int)round_up(pr.n, 4);
-      if (!is_dev(pr.A))
-        BCK(cudaMemcpyAsync(arena + offA[k], stage.data() + offA[k], (size_t)pr.m * lda4 * 4, cudaMemcpyHostToDevice,
-                            s));
       const void* src[12] = {pr.f.h, pr.f.a, pr.f.b, pr.f.c, pr.f.d, pr.f.e, pr.g.h, pr.g.a, pr.g.b, pr.g.c, pr.g.d, pr.g.e};
-      for (int t = 0; t < 12; ++t)
-        if (src[t] && !is_dev(src[t]))
-          BCK(cudaMemcpyAsync(arena + offIn[k * 12 + t], stage.data() + offIn[k * 12 + t],
-                              (size_t)(t < 6 ? pr.m : pr.n) * ((t % 6) == 0 ? 1 : 4), cudaMemcpyHostToDevice, s));
+      dev_A[k] = is_dev(pr.A);
+      any_host_in |= !dev_A[k];
+      all_host &= !dev_A[k];
+      for (int t = 0; t < 12; ++t) {
+        dev_in[(size_t)k * 12 + t] = src[t] ? is_dev(src[t]) : 0;
+        any_host_in |= src[t] && !dev_in[(size_t)k * 12 + t];
+        all_host &= !src[t] || !dev_in[(size_t)k * 12 + t];
+      }
+    }
+    for (int k = 0; k < ns; ++k) {
+      const pogs_problem& pr = probs[small[k]];
+      out_off[k + 1] = out_off[k] + 2 * (size_t)(pr.n + pr.m);
+      const pogs_result& r = out[small[k]];
+      any_host_out |= (r.x && !is_dev(r.x)) || (r.y && !is_dev(r.y)) || (r.mu && !is_dev(r.mu)) ||
+                      (r.nu && !is_dev(r.nu));
+    }
+    const size_t need = std::max(any_host_in ? in_end : 0, any_host_out ? out_off[ns] * 4 : 0);
+    if (need > 0) {
+      hst = pinned(pin_lock, need);
+      if (!hst) {
+        stage.resize(need);
+        hst = stage.data();
+      }
+    }
+    if (any_host_in) {
+      parallel_for(ns, [&](int k) {
+        const pogs_problem& pr = probs[small[k]];
+        const int lda4 = (int)round_up(pr.n, 4);
+        if (!dev_A[k])
+          for (int64_t i = 0; i < pr.m; ++i) {
+            char* row = hst + offA[k] + (size_t)i * lda4 * 4;
+            memcpy(row, pr.A + i * pr.lda, (size_t)pr.n * 4);
+            if (lda4 > pr.n) memset(row + (size_t)pr.n * 4, 0, (size_t)(lda4 - pr.n) * 4);
+          }
+        const void* src[12] = {pr.f.h, pr.f.a, pr.f.b, pr.f.c, pr.f.d, pr.f.e, pr.g.h, pr.g.a, pr.g.b, pr.g.c, pr.g.d, pr.g.e};
+        for (int t = 0; t < 12; ++t)
+          if (src[t] && !dev_in[(size_t)k * 12 + t])
+            memcpy(hst + offIn[k * 12 + t], src[t], (size_t)(t < 6 ? pr.m : pr.n) * ((t % 6) == 0 ? 1 : 4));
+      });
+    }
+    if (any_host_in && all_host) {
+      BCK(cudaMemcpyAsync(arena, hst, in_end, cudaMemcpyHostToDevice, s));
+    } else {
+      for (int k = 0; k < ns; ++k) {
+        const pogs_problem& pr = probs[small[k]];
+        const int lda4 = (int)round_up(pr.n, 4);
+        if (dev_A[k])
+          BCK(cudaMemcpy2DAsync(arena + offA[k], (size_t)lda4 * 4, pr.A, (size_t)pr.lda * 4, (size_t)pr.n * 4, pr.m,
+                                cudaMemcpyDeviceToDevice, s));
+        else
+          BCK(cudaMemcpyAsync(arena + offA[k], hst + offA[k], (size_t)pr.m * lda4 * 4, cudaMemcpyHostToDevice, s));
+        const void* src[12] = {pr.f.h, pr.f.a, pr.f.b, pr.f.c, pr.f.d, pr.f.e, pr.g.h, pr.g.a, pr.g.b, pr.g.c, pr.g.d, pr.g.e};
+        for (int t = 0; t < 12; ++t) {
+          if (!src[t]) continue;
+          const size_t bytes = (size_t)(t < 6 ? pr.m : pr.n) * ((t % 6) == 0 ? 1 : 4);
+          if (dev_in[(size_t)k * 12 + t])
+            BCK(cudaMemcpyAsync(arena + offIn[k * 12 + t], src[t], bytes, cudaMemcpyDeviceToDevice, s));
+          else
+            BCK(cudaMemcpyAsync(arena + offIn[k * 12 + t], hst + offIn[k * 12 + t], bytes, cudaMemcpyHostToDevice, s));
+        }
+      }
     }
   }
   for (int k = 0; k < ns; ++k) {
@@ -321,6 +422,8 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
   count_launch(1);
   // ---- results ------------------------------------------------------------------------------
   BCK(cudaMemcpyAsync(hout.data(), d_out, sizeof(BOut) * ns, cudaMemcpyDeviceToHost, s));
+  // device destinations directly; host ones gathered on the device, copied in one transfer and
+  // scattered by several host threads
   for (int k = 0; k < ns; ++k) {
     pogs_result& r = out[small[k]];
     const BInst& I = inst[k];
@@ -328,11 +431,34 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
     float* dsts[4] = {r.x, r.y, r.mu, r.nu};
     const int lens[4] = {I.n, I.m, I.n, I.m};
     for (int t = 0; t < 4; ++t)
-      if (dsts[t])
-        BCK(cudaMemcpyAsync(dsts[t], srcs[t], (size_t)lens[t] * 4,
-                            is_dev(dsts[t]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+      if (dsts[t] && is_dev(dsts[t]))
+        BCK(cudaMemcpyAsync(dsts[t], srcs[t], (size_t)lens[t] * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  if (any_host_out) {
+    if (pool_alloc(reinterpret_cast<void**>(&d_outoff), sizeof(size_t) * ns, s) != 0 ||
+        pool_alloc(reinterpret_cast<void**>(&d_gather), out_off[ns] * 4, s) != 0) {
+      rc = POGS_ERR_OOM;
+      goto done;
+    }
+    BCK(cudaMemcpyAsync(d_outoff, out_off.data(), sizeof(size_t) * ns, cudaMemcpyHostToDevice, s));
+    count_launch();
+    gather_out_kernel<<<ns, 256, 0, s>>>(d_inst, d_outoff, d_gather);
+    BCK(cudaGetLastError());
+    BCK(cudaMemcpyAsync(hst, d_gather, out_off[ns] * 4, cudaMemcpyDeviceToHost, s));
   }
   BCK(cudaStreamSynchronize(s));
+  if (any_host_out)
+    parallel_for(ns, [&](int k) {
+      pogs_result& r = out[small[k]];
+      const pogs_problem& pr = probs[small[k]];
+      const float* src = reinterpret_cast<const float*>(hst) + out_off[k];
+      float* dsts[4] = {r.x, r.y, r.mu, r.nu};
+      const int64_t lens[4] = {pr.n, pr.m, pr.n, pr.m};
+      for (int t = 0; t < 4; ++t) {
+        if (dsts[t] && !is_dev(dsts[t])) memcpy(dsts[t], src, (size_t)lens[t] * 4);
+        src += lens[t];
+      }
+    });
   for (int k = 0; k < ns; ++k) {
     pogs_info& info = out[small[k]].info;
     const BOut& o = hout[k];
@@ -359,6 +485,8 @@ done:
   if (d_out) cudaFreeAsync(d_out, s);
   if (d_queue) cudaFreeAsync(d_queue, s);
   if (d_order) cudaFreeAsync(d_order, s);
+  if (d_outoff) cudaFreeAsync(d_outoff, s);
+  if (d_gather) cudaFreeAsync(d_gather, s);
   cudaStreamSynchronize(s);
   return rc;
 }

@@ -73,6 +73,21 @@ def test_batch_of_device_inputs_equals_host_inputs(P):
         assert a[0].iters == b[0].iters and np.array_equal(a[1], b[1])
 
 
+def test_batch_of_mixed_host_and_device_inputs_equals_host_inputs(P):
+    """Some instances' matrices on the device and their parameters on the host, others all on the
+    host: the inputs reach the arena region by region instead of in one transfer."""
+    import torch
+    probs = W.batch_mix(count=7, base_seed=72_500)
+    host = P.pogs_solve_batch(probs, P.pogs_default_params())
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    mixed = [W.Problem(p.name, dev(p.A), p.f, p.g, p.meta) if k % 2 == 0 else p for k, p in enumerate(probs)]
+    mres = P.pogs_solve_batch(mixed, P.pogs_default_params())
+    for a, b in zip(host, mres):
+        assert a[0].iters == b[0].iters
+        for u, v in zip(a[1:], b[1:]):
+            assert np.array_equal(u, v)
+
+
 def test_batch_logistic_instances_converge_and_match_oracle(P):
     """Logistic regression instances (the class whose prox is an inner root-find) in the batched
     engine: every one converges under adaptive rho and matches the oracle."""
