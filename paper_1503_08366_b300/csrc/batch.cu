@@ -405,7 +405,11 @@ __device__ __forceinline__ void rowdots2(const float* A, int lda, int n, const f
   const float4* b = reinterpret_cast<const float4*>(br);
   const float4* p1 = reinterpret_cast<const float4*>(x1);
   const float4* p2 = reinterpret_cast<const float4*>(x2);
-  const int nf = n >> 2;
+  // float4 groups only where every row and vector is 16-byte aligned (the arenas lay them out so);
+  // otherwise every column one at a time below
+  const bool vec4 = ((reinterpret_cast<uintptr_t>(ar) | reinterpret_cast<uintptr_t>(br) |
+                      reinterpret_cast<uintptr_t>(x1) | reinterpret_cast<uintptr_t>(x2)) & 15) == 0;
+  const int nf = vec4 ? n >> 2 : 0;
   float s1a = 0.f, s2a = 0.f, s1b = 0.f, s2b = 0.f;
   int g = lane;
   for (; g + 96 < nf; g += 128) {
@@ -432,8 +436,7 @@ __device__ __forceinline__ void rowdots2(const float* A, int lda, int n, const f
     s1b = dot4(bv, v1, s1b);
     s2b = dot4(bv, v2, s2b);
   }
-  const int c = 4 * nf + lane;
-  if (c < n) {
+  for (int c = 4 * nf + lane; c < n; c += 32) {
     const float v1 = x1[c], v2 = x2[c], av = ar[c], bv = br[c];
     s1a = fmaf(av, v1, s1a);
     s2a = fmaf(av, v2, s2a);
@@ -539,6 +542,8 @@ __device__ __forceinline__ void cta_colsum(const float* X, int ldx, int rows, in
                                            const float* v2, const float* v3, float* red, Pre pre, Fn fn) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* v[3] = {v1, v2, v3};
+  // float4 rows only where X and its pitch keep every row 16-byte aligned
+  const bool v4 = VEC && ((reinterpret_cast<uintptr_t>(X) | ((uintptr_t)ldx * sizeof(float))) & 15) == 0;
   for (int c0 = 0; c0 < cols; c0 += 128) {
     float acc[NR][4];
 #pragma unroll
@@ -552,7 +557,7 @@ __device__ __forceinline__ void cta_colsum(const float* X, int ldx, int rows, in
         const float* row = X + (int64_t)(ok ? i : 0) * ldx + c0;
 #pragma unroll
         for (int r = 0; r < NR; ++r) w[h][r] = ok ? v[r][i] : 0.0f;
-        if (VEC) {   // columns c0 + 4 lane .. + 3: one float4 (16-byte rows; columns >= cols read as 0)
+        if (v4) {   // columns c0 + 4 lane .. + 3: one float4 (16-byte rows; columns >= cols read as 0)
           const int j = 4 * lane;
           float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
           if (ok && c0 + j < cols) q = *reinterpret_cast<const float4*>(row + j);
@@ -580,7 +585,7 @@ __device__ __forceinline__ void cta_colsum(const float* X, int ldx, int rows, in
 #pragma unroll
     for (int r = 0; r < NR; ++r)
 #pragma unroll
-      for (int t = 0; t < 4; ++t) red[(warp * NR + r) * 128 + (VEC ? 4 * lane + t : lane + 32 * t)] = acc[r][t];
+      for (int t = 0; t < 4; ++t) red[(warp * NR + r) * 128 + (v4 ? 4 * lane + t : lane + 32 * t)] = acc[r][t];
     __syncthreads();
     if (mine) {
       float t[NR];

@@ -167,7 +167,7 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
   const size_t in_end = cur;
   for (int k = 0; k < ns; ++k) {
     const pogs_problem& pr = probs[small[k]];
-    const int64_t q = std::min(pr.m, pr.n), vlen = std::max(pr.m, pr.n);
+    const int64_t q = std::min(pr.m, pr.n), vlen = round_up(std::max(pr.m, pr.n), 4);   // 16-byte vectors
     offM[k] = cur;
     cur = al(cur + (size_t)q * q * 4);
     offH[k] = cur;
@@ -316,7 +316,7 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
     I.fe = (float*)fo(5);
     I.gh = (uint8_t*)fo(6); I.ga = (float*)fo(7); I.gb = (float*)fo(8); I.gc = (float*)fo(9); I.gd = (float*)fo(10);
     I.ge = (float*)fo(11);
-    const int64_t vlen = std::max(pr.m, pr.n);
+    const int64_t vlen = round_up(std::max(pr.m, pr.n), 4);   // the iteration reads some vectors as float4
     float* v = reinterpret_cast<float*>(arena + offV[k]);
     float** vecs[] = {&I.x, &I.y, &I.xt, &I.yt, &I.xh, &I.yh, &I.cx, &I.dy, &I.mu, &I.nu, &I.r, &I.z, &I.w,
                       &I.ox, &I.oy, &I.omu, &I.onu};

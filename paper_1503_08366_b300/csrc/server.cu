@@ -71,7 +71,8 @@ struct SReq {
 
 // Device bytes a request holds while resident.
 size_t small_bytes(int64_t m, int64_t n) {
-  const int64_t q = std::min(m, n), v = std::max(m, n), lda4 = (n + 3) / 4 * 4;
+  // vectors at a pitch of a multiple of 4 floats (the iteration reads some of them as float4)
+  const int64_t q = std::min(m, n), v = (std::max(m, n) + 3) / 4 * 4, lda4 = (n + 3) / 4 * 4;
   size_t b = al((size_t)m * lda4 * 4) + al((size_t)q * q * 4) + al((size_t)q * q * 8) + al((size_t)m * 4) +
              al((size_t)n * 4) + al((size_t)17 * v * 4);
   for (int t = 0; t < 24; ++t) b += al((size_t)((t % 12) < 6 ? m : n) * (((t % 6) == 0) ? 1 : 4));
@@ -228,7 +229,7 @@ void layout_small(SReq* r, BOut* out, BLoop* loop) {
   I.fe = (float*)fo[5];
   I.gh = (uint8_t*)fo[6]; I.ga = (float*)fo[7]; I.gb = (float*)fo[8]; I.gc = (float*)fo[9]; I.gd = (float*)fo[10];
   I.ge = (float*)fo[11];
-  const int64_t v = std::max(pr.m, pr.n);
+  const int64_t v = (std::max(pr.m, pr.n) + 3) / 4 * 4;   // 16-byte aligned vectors (float4 reads)
   float* vec = (float*)take((size_t)17 * v * 4);
   float** vecs[] = {&I.x, &I.y, &I.xt, &I.yt, &I.xh, &I.yh, &I.cx, &I.dy, &I.mu, &I.nu, &I.r, &I.z, &I.w,
                     &I.ox, &I.oy, &I.omu, &I.onu};

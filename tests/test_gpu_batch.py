@@ -113,3 +113,23 @@ def test_the_mix_iteration_tail_is_the_methods(P):
     assert abs(res[0][0].obj - ref.obj) <= 1e-3 * max(1.0, abs(ref.obj)), (res[0][0].obj, ref.obj)
     ref2 = OA.solve(stuck.A, stuck.f, stuck.g, OA.Params(max_iter=10000))
     assert ref2.status == 1 and res[1][0].status == 1 and res[1][0].iters == 10000
+
+
+def test_batch_instances_whose_vectors_live_in_global_memory(P):
+    """Instances whose longest side exceeds the shared-memory vector staging (3 max(m, n) floats
+    > 6144) read their phase vectors from the arena; sides that are not multiples of four check
+    that those vectors keep the 16-byte alignment the float4 row dots need.  Tall and fat, alone
+    and in a mix, against the oracle."""
+    probs = [W.lasso(2501, 301, seed=74_001), W.huber(3003, 97, seed=74_002), W.nnls(150, 2403, seed=74_003),
+             W.logistic(2403, 207, seed=74_004), W.svm(2103, 150, seed=74_006), W.svm(400, 90, seed=74_005)]
+    prm = P.pogs_default_params(max_iter=5000)
+    mix = P.pogs_solve_batch(probs, prm)
+    for k, prob in enumerate(probs):
+        info = mix[k][0]
+        assert info.status == 0, (k, prob.name, prob.A.shape, info.as_dict())
+        ref = _tight(prob)
+        assert abs(info.obj - ref.obj) <= 1e-3 * max(1.0, abs(ref.obj)), (k, prob.name, info.obj, ref.obj)
+        alone = P.pogs_solve_batch([prob], prm)[0]
+        assert alone[0].iters == info.iters and alone[0].obj == info.obj
+        for u, v in zip(alone[1:], mix[k][1:]):
+            assert np.array_equal(u, v), k
