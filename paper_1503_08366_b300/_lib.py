@@ -145,13 +145,28 @@ def _check(code: int, where: str) -> int:
 
 
 # ---- marshalling helpers ------------------------------------------------------------------
+_TORCH_DTYPES: dict = {}
+_NP_DTYPES = {np.float32: np.dtype(np.float32), np.uint8: np.dtype(np.uint8)}
+
+
+def _torch_dtype(dtype):
+    if not _TORCH_DTYPES:
+        import torch
+        _TORCH_DTYPES.update({np.float32: torch.float32, np.uint8: torch.uint8})
+    return _TORCH_DTYPES[dtype]
+
+
 def _ptr(a, dtype, keep: list):
     """Raw pointer of a contiguous numpy array or torch tensor (host or device); None -> NULL."""
     if a is None:
         return None
+    if isinstance(a, np.ndarray):
+        if a.dtype is not _NP_DTYPES[dtype] or not a.flags.c_contiguous:
+            a = np.ascontiguousarray(a, dtype=dtype)
+        keep.append(a)
+        return a.ctypes.data
     if hasattr(a, "data_ptr"):   # torch tensor
-        import torch
-        want = {np.float32: torch.float32, np.uint8: torch.uint8}[dtype]
+        want = _torch_dtype(dtype)
         if a.dtype != want or not a.is_contiguous():
             a = a.to(want).contiguous()
         keep.append(a)
@@ -396,16 +411,24 @@ def pogs_solve_batch(problems, params: pogs_params | None = None, stream=None):
     n_p = len(problems)
     probs = (pogs_problem * max(1, n_p))()
     res = (pogs_result * max(1, n_p))()
+    shapes = [pb.A.shape for pb in problems]
+    # all outputs in one host block: instance i's x, y, mu, nu are consecutive views
+    block = np.empty(sum(2 * (m + n) for m, n in shapes), np.float32)
+    base = block.ctypes.data
     outs = []
+    off = 0
     for i, pb in enumerate(problems):
-        m, n = pb.A.shape
-        probs[i].A = _ptr(pb.A, np.float32, keep)
-        probs[i].m, probs[i].n, probs[i].lda = m, n, n
-        probs[i].f = make_fn(pb.f, keep)
-        probs[i].g = make_fn(pb.g, keep)
-        o = [np.empty(n, np.float32), np.empty(m, np.float32), np.empty(n, np.float32), np.empty(m, np.float32)]
-        outs.append(o)
-        res[i].x, res[i].y, res[i].mu, res[i].nu = (a.ctypes.data for a in o)
+        m, n = shapes[i]
+        pr = probs[i]
+        pr.A = _ptr(pb.A, np.float32, keep)
+        pr.m, pr.n, pr.lda = m, n, n
+        pr.f = make_fn(pb.f, keep)
+        pr.g = make_fn(pb.g, keep)
+        r = res[i]
+        r.x, r.y, r.mu, r.nu = base + 4 * off, base + 4 * (off + n), base + 4 * (off + n + m), base + 4 * (off + 2 * n + m)
+        outs.append((block[off:off + n], block[off + n:off + n + m], block[off + n + m:off + 2 * n + m],
+                     block[off + 2 * n + m:off + 2 * (n + m)]))
+        off += 2 * (m + n)
     rc = lib.pogs_solve_batch(n_p, probs, C.byref(params) if params is not None else None, res,
                               _stream_ptr(stream))
     _check(rc, "pogs_solve_batch")

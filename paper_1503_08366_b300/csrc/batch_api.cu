@@ -80,6 +80,59 @@ void parallel_for(int n, F f) {
   for (auto& x : th) x.join();
 }
 
+// One region copied between a caller's device array and an arena: `rows` rows of `row_bytes`
+// bytes, `src_pitch` / `dst_pitch` bytes apart; each destination row is zero-filled from
+// row_bytes to fill_bytes (an arena row's padding).
+struct DevPiece {
+  const char* src;
+  char* dst;
+  int64_t rows, row_bytes, src_pitch, dst_pitch, fill_bytes;
+};
+
+// All regions of one call in one launch: block b takes pieces b, b + grid, ...; 16-byte words
+// where both rows and pitches allow, else 4-byte words, else bytes.
+__global__ void __launch_bounds__(256) copy_pieces_kernel(const DevPiece* __restrict__ pcs, int count) {
+  for (int p = blockIdx.x; p < count; p += gridDim.x) {
+    const DevPiece pc = pcs[p];
+    const uintptr_t al_bits = (uintptr_t)pc.src | (uintptr_t)pc.dst | (uintptr_t)pc.row_bytes |
+                              (uintptr_t)pc.src_pitch | (uintptr_t)pc.dst_pitch | (uintptr_t)pc.fill_bytes;
+    for (int64_t r = 0; r < pc.rows; ++r) {
+      const char* sr = pc.src + r * pc.src_pitch;
+      char* dr = pc.dst + r * pc.dst_pitch;
+      if ((al_bits & 15) == 0) {
+        for (int64_t k = threadIdx.x; k < pc.fill_bytes / 16; k += blockDim.x)
+          reinterpret_cast<float4*>(dr)[k] = 16 * k < pc.row_bytes ? reinterpret_cast<const float4*>(sr)[k]
+                                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+      } else if ((al_bits & 3) == 0) {
+        for (int64_t k = threadIdx.x; k < pc.fill_bytes / 4; k += blockDim.x)
+          reinterpret_cast<float*>(dr)[k] = 4 * k < pc.row_bytes ? reinterpret_cast<const float*>(sr)[k] : 0.0f;
+      } else {
+        for (int64_t k = threadIdx.x; k < pc.fill_bytes; k += blockDim.x) dr[k] = k < pc.row_bytes ? sr[k] : 0;
+      }
+    }
+  }
+}
+
+// Launches copy_pieces_kernel over `pcs` (host vector) through a pool-allocated device table,
+// freed in stream order.
+int copy_pieces(const std::vector<DevPiece>& pcs, cudaStream_t s) {
+  if (pcs.empty()) return 0;
+  DevPiece* d = nullptr;
+  if (pool_alloc(reinterpret_cast<void**>(&d), sizeof(DevPiece) * pcs.size(), s) != 0) return POGS_ERR_OOM;
+  int rc = 0;
+  if (cudaMemcpyAsync(d, pcs.data(), sizeof(DevPiece) * pcs.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    rc = POGS_ERR_CUDA;
+  } else {
+    count_launch();
+    const int grid = (int)std::min<size_t>(pcs.size(), 148 * 16);
+    copy_pieces_kernel<<<grid, 256, 0, s>>>(d, (int)pcs.size());
+    if (cudaGetLastError() != cudaSuccess) rc = POGS_ERR_CUDA;
+  }
+  cudaGetLastError();
+  cudaFreeAsync(d, s);
+  return rc;
+}
+
 // Returned tuples of all instances into one device buffer (x, y, mu, nu of instance k at
 // out_off[k]), one CTA per instance, for a single copy to the host.
 __global__ void gather_out_kernel(const BInst* __restrict__ insts, const size_t* __restrict__ out_off, float* dst) {
@@ -207,6 +260,7 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
   int num_sms = 148, dev = 0;
   std::vector<int> order_big(ns), order_in(ns);
   bool any_host_in = false;
+  std::vector<char> dev_out((size_t)ns * 4);   // per output array: on the device (1) or the host (0)
   // stream-ordered allocations from the library's pool (no device-wide synchronisation)
   if (pool_alloc(reinterpret_cast<void**>(&arena), total, s) != 0 ||
       pool_alloc(reinterpret_cast<void**>(&d_inst), sizeof(BInst) * ns, s) != 0 ||
@@ -241,8 +295,11 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
       const pogs_problem& pr = probs[small[k]];
       out_off[k + 1] = out_off[k] + 2 * (size_t)(pr.n + pr.m);
       const pogs_result& r = out[small[k]];
-      any_host_out |= (r.x && !is_dev(r.x)) || (r.y && !is_dev(r.y)) || (r.mu && !is_dev(r.mu)) ||
-                      (r.nu && !is_dev(r.nu));
+      const float* dsts[4] = {r.x, r.y, r.mu, r.nu};
+      for (int t = 0; t < 4; ++t) {
+        dev_out[(size_t)k * 4 + t] = dsts[t] ? is_dev(dsts[t]) : 0;
+        any_host_out |= dsts[t] && !dev_out[(size_t)k * 4 + t];
+      }
     }
     const size_t need = std::max(any_host_in ? in_end : 0, any_host_out ? out_off[ns] * 4 : 0);
     if (need > 0) {
@@ -268,27 +325,27 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
             memcpy(hst + offIn[k * 12 + t], src[t], (size_t)(t < 6 ? pr.m : pr.n) * ((t % 6) == 0 ? 1 : 4));
       });
     }
-    if (any_host_in && all_host) {
-      BCK(cudaMemcpyAsync(arena, hst, in_end, cudaMemcpyHostToDevice, s));
-    } else {
+    // host regions: the whole packed input region in one transfer (the parts that belong to device
+    // inputs carry nothing and are overwritten next, in stream order); device regions: one launch
+    if (any_host_in) BCK(cudaMemcpyAsync(arena, hst, in_end, cudaMemcpyHostToDevice, s));
+    if (!all_host) {
+      std::vector<DevPiece> pcs;
+      pcs.reserve((size_t)ns * 13);
       for (int k = 0; k < ns; ++k) {
         const pogs_problem& pr = probs[small[k]];
         const int lda4 = (int)round_up(pr.n, 4);
         if (dev_A[k])
-          BCK(cudaMemcpy2DAsync(arena + offA[k], (size_t)lda4 * 4, pr.A, (size_t)pr.lda * 4, (size_t)pr.n * 4, pr.m,
-                                cudaMemcpyDeviceToDevice, s));
-        else
-          BCK(cudaMemcpyAsync(arena + offA[k], hst + offA[k], (size_t)pr.m * lda4 * 4, cudaMemcpyHostToDevice, s));
+          pcs.push_back(DevPiece{reinterpret_cast<const char*>(pr.A), arena + offA[k], pr.m, pr.n * 4, pr.lda * 4,
+                                 (int64_t)lda4 * 4, (int64_t)lda4 * 4});
         const void* src[12] = {pr.f.h, pr.f.a, pr.f.b, pr.f.c, pr.f.d, pr.f.e, pr.g.h, pr.g.a, pr.g.b, pr.g.c, pr.g.d, pr.g.e};
         for (int t = 0; t < 12; ++t) {
-          if (!src[t]) continue;
-          const size_t bytes = (size_t)(t < 6 ? pr.m : pr.n) * ((t % 6) == 0 ? 1 : 4);
-          if (dev_in[(size_t)k * 12 + t])
-            BCK(cudaMemcpyAsync(arena + offIn[k * 12 + t], src[t], bytes, cudaMemcpyDeviceToDevice, s));
-          else
-            BCK(cudaMemcpyAsync(arena + offIn[k * 12 + t], hst + offIn[k * 12 + t], bytes, cudaMemcpyHostToDevice, s));
+          if (!src[t] || !dev_in[(size_t)k * 12 + t]) continue;
+          const int64_t bytes = (t < 6 ? pr.m : pr.n) * ((t % 6) == 0 ? 1 : 4);
+          pcs.push_back(DevPiece{static_cast<const char*>(src[t]), arena + offIn[k * 12 + t], 1, bytes, bytes, bytes, bytes});
         }
       }
+      rc = copy_pieces(pcs, s);
+      if (rc != 0) goto done;
     }
   }
   for (int k = 0; k < ns; ++k) {
@@ -424,15 +481,21 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
   BCK(cudaMemcpyAsync(hout.data(), d_out, sizeof(BOut) * ns, cudaMemcpyDeviceToHost, s));
   // device destinations directly; host ones gathered on the device, copied in one transfer and
   // scattered by several host threads
-  for (int k = 0; k < ns; ++k) {
-    pogs_result& r = out[small[k]];
-    const BInst& I = inst[k];
-    const float* srcs[4] = {I.ox, I.oy, I.omu, I.onu};
-    float* dsts[4] = {r.x, r.y, r.mu, r.nu};
-    const int lens[4] = {I.n, I.m, I.n, I.m};
-    for (int t = 0; t < 4; ++t)
-      if (dsts[t] && is_dev(dsts[t]))
-        BCK(cudaMemcpyAsync(dsts[t], srcs[t], (size_t)lens[t] * 4, cudaMemcpyDeviceToDevice, s));
+  {
+    std::vector<DevPiece> pcs;
+    for (int k = 0; k < ns; ++k) {
+      pogs_result& r = out[small[k]];
+      const BInst& I = inst[k];
+      const float* srcs[4] = {I.ox, I.oy, I.omu, I.onu};
+      float* dsts[4] = {r.x, r.y, r.mu, r.nu};
+      const int64_t bytes[4] = {(int64_t)I.n * 4, (int64_t)I.m * 4, (int64_t)I.n * 4, (int64_t)I.m * 4};
+      for (int t = 0; t < 4; ++t)
+        if (dsts[t] && dev_out[(size_t)k * 4 + t])
+          pcs.push_back(DevPiece{reinterpret_cast<const char*>(srcs[t]), reinterpret_cast<char*>(dsts[t]), 1,
+                                 bytes[t], bytes[t], bytes[t], bytes[t]});
+    }
+    rc = copy_pieces(pcs, s);
+    if (rc != 0) goto done;
   }
   if (any_host_out) {
     if (pool_alloc(reinterpret_cast<void**>(&d_outoff), sizeof(size_t) * ns, s) != 0 ||
@@ -455,7 +518,7 @@ extern "C" int pogs_solve_batch(int count, const pogs_problem* probs, const pogs
       float* dsts[4] = {r.x, r.y, r.mu, r.nu};
       const int64_t lens[4] = {pr.n, pr.m, pr.n, pr.m};
       for (int t = 0; t < 4; ++t) {
-        if (dsts[t] && !is_dev(dsts[t])) memcpy(dsts[t], src, (size_t)lens[t] * 4);
+        if (dsts[t] && !dev_out[(size_t)k * 4 + t]) memcpy(dsts[t], src, (size_t)lens[t] * 4);
         src += lens[t];
       }
     });

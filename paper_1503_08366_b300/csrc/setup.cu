@@ -13,18 +13,48 @@ namespace pogs {
 // ---- ingest --------------------------------------------------------------------------------
 // Row-major (or column-major) source -> padded row-major A (pitch lda, zero padding),
 // flagging non-finite entries.
-__global__ void copy_rowmajor_kernel(const float* __restrict__ src, int64_t m, int64_t n, int64_t lds,
-                                     float* __restrict__ A, int64_t lda, int* err) {
-  const int64_t total = m * lda;
+// Block b takes rows b, b + grid, ...; a row moves as float4 words (four per thread in flight)
+// when the source rows are 16-byte aligned, else one float at a time.  The destination pitch lda
+// is a multiple of 4 floats and A is 16-byte aligned (the handle lays it out so); the same
+// kernel also runs in place (src == A) to zero the padding and check a row-by-row host copy.
+__global__ void __launch_bounds__(256) copy_rowmajor_kernel(const float* __restrict__ src, int64_t m, int64_t n,
+                                                            int64_t lds, float* __restrict__ A, int64_t lda,
+                                                            int* err) {
+  const bool v4 = ((reinterpret_cast<uintptr_t>(src) | (uintptr_t)(lds * sizeof(float))) & 15) == 0;
+  const int64_t nv = lda >> 2, nfull = n >> 2;   // float4 words per destination row; words wholly inside n
   int bad = 0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / lda, j = e - i * lda;
-    float v = 0.0f;
-    if (j < n) {
-      v = src[i * lds + j];
-      if (!isfinite(v)) bad = 1;
+  for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+    const float* sr = src + i * lds;
+    float4* dr = reinterpret_cast<float4*>(A + i * lda);
+    int64_t c = threadIdx.x;
+    if (v4) {
+      const float4* s4 = reinterpret_cast<const float4*>(sr);
+      for (; c + 768 < nfull; c += 1024) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = s4[c + 256 * u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          bad |= !isfinite(v[u].x) | !isfinite(v[u].y) | !isfinite(v[u].z) | !isfinite(v[u].w);
+          dr[c + 256 * u] = v[u];
+        }
+      }
+      for (; c < nfull; c += 256) {
+        const float4 v = s4[c];
+        bad |= !isfinite(v.x) | !isfinite(v.y) | !isfinite(v.z) | !isfinite(v.w);
+        dr[c] = v;
+      }
     }
-    A[e] = v;
+    for (; c < nv; c += 256) {   // the rest of the row one float at a time, zeros past n
+      float w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t j = 4 * c + u;
+        w[u] = j < n ? sr[j] : 0.0f;
+        if (j < n && !isfinite(w[u])) bad = 1;
+      }
+      dr[c] = make_float4(w[0], w[1], w[2], w[3]);
+    }
   }
   if (bad) atomicCAS(err, 0, POGS_ERR_NONFINITE);   // first error wins
 }
@@ -54,7 +84,7 @@ __global__ void copy_colmajor_kernel(const float* __restrict__ src, int64_t m, i
 void launch_copy_in(const float* src, int64_t m, int64_t n, int64_t lds, bool colmajor, float* A, int64_t lda,
                     int* err, cudaStream_t s) {
   if (!colmajor) {
-    int64_t g = std::min<int64_t>((m * lda + 255) / 256, 148 * 16);
+    const int64_t g = std::min<int64_t>(m, 148 * 8);
     count_launch();
     copy_rowmajor_kernel<<<(int)g, 256, 0, s>>>(src, m, n, lds, A, lda, err);
   } else {
@@ -64,17 +94,50 @@ void launch_copy_in(const float* src, int64_t m, int64_t n, int64_t lds, bool co
   }
 }
 
-// A^ = D A E in place (Section 4.1).
-__global__ void scale_kernel(float* A, int64_t lda, int64_t m, int64_t n, const float* D, const float* E) {
-  const int64_t total = m * lda;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / lda, j = e - i * lda;
-    if (j < n) A[e] *= D[i] * E[j];
+// A^ = D A E in place (Section 4.1).  Block b takes rows b, b + grid, ...; float4 words of the
+// row (pitch lda a multiple of 4 floats, A 16-byte aligned), each element times D_i E_j; the
+// zero padding past n stays zero.
+__global__ void __launch_bounds__(256) scale_kernel(float* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                                                    const float* __restrict__ D, const float* __restrict__ E) {
+  const int64_t nw = (n + 3) >> 2;   // words holding columns < n
+  for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+    float4* r = reinterpret_cast<float4*>(A + i * lda);
+    const float di = D[i];
+    int64_t c = threadIdx.x;
+    for (; c + 256 < nw; c += 512) {
+      float4 v[2];
+      float e[2][4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        v[u] = r[c + 256 * u];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int64_t j = 4 * (c + 256 * u) + t;
+          e[u][t] = j < n ? E[j] : 0.0f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        v[u].x *= di * e[u][0]; v[u].y *= di * e[u][1]; v[u].z *= di * e[u][2]; v[u].w *= di * e[u][3];
+        r[c + 256 * u] = v[u];
+      }
+    }
+    for (; c < nw; c += 256) {
+      float4 v = r[c];
+      float e[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int64_t j = 4 * c + t;
+        e[t] = j < n ? E[j] : 0.0f;
+      }
+      v.x *= di * e[0]; v.y *= di * e[1]; v.z *= di * e[2]; v.w *= di * e[3];
+      r[c] = v;
+    }
   }
 }
 
 void launch_scale(float* A, int64_t lda, int64_t m, int64_t n, const float* D, const float* E, cudaStream_t s) {
-  int64_t g = std::min<int64_t>((m * lda + 255) / 256, 148 * 16);
+  const int64_t g = std::min<int64_t>(m, 148 * 8);
   count_launch();
   scale_kernel<<<(int)g, 256, 0, s>>>(A, lda, m, n, D, E);
 }
