@@ -150,6 +150,24 @@ POGS_DEV void block_sum(double (&v)[NV], double* sh) {
   __syncthreads();
 }
 
+// L2 policy marking lines as the first to evict: for matrices streamed once per pass (far
+// larger than L2), so that what a pass writes for its next launch (split partial sums) and the
+// vectors it reads stay in L2 instead of being pushed out by the stream.
+POGS_DEV uint64_t l2_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+// Streamed load (no L1 allocation) under an L2 policy from l2_evict_first().
+POGS_DEV float4 ldg_stream(const float4* p, uint64_t pol) {
+  float4 r;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "l"(p), "l"(pol));
+  return r;
+}
+
 POGS_DEV float4 ldg_stream(const float4* p) {
   float4 r;
   asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"

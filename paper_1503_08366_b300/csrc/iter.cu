@@ -121,11 +121,13 @@ __global__ void __launch_bounds__(256, 5) pogs_colsum_kernel(const float* __rest
   for (int r = 0; r < NRHS; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.0f;
   if (active) {
     const float* Ap = A + c0;
+    const uint64_t pol = l2_evict_first();
     int i = r0;
     for (; i + 8 <= r1; i += 8) {
       float4 a[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) a[u] = ldg_stream(reinterpret_cast<const float4*>(Ap + (int64_t)(i + u) * lda));
+      for (int u = 0; u < 8; ++u)
+        a[u] = ldg_stream(reinterpret_cast<const float4*>(Ap + (int64_t)(i + u) * lda), pol);
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         float4 av = a[u];
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(256, 5) pogs_colsum_kernel(const float* __rest
       }
     }
     for (; i < r1; ++i) {
-      float4 av = ldg_stream(reinterpret_cast<const float4*>(Ap + (int64_t)i * lda));
+      float4 av = ldg_stream(reinterpret_cast<const float4*>(Ap + (int64_t)i * lda), pol);
       if (SQ) { av.x *= av.x; av.y *= av.y; av.z *= av.z; av.w *= av.w; }
       const float w1 = __ldg(v1 + i);
       acc[0][0] = fmaf(av.x, w1, acc[0][0]); acc[0][1] = fmaf(av.y, w1, acc[0][1]);
@@ -221,21 +223,22 @@ __global__ void __launch_bounds__(256, 5) pogs_colsum_kernel(const float* __rest
 // Final reduction and epilogue of the column sums after a streaming launch
 // (pogs_colsum_kernel<..., false>): one block per 1024-column slab, NRHS x 256 threads.  Thread
 // (r, c) adds the nsp row splits' partials of right-hand side r for the four columns
-// c0 = 1024 bx + 4 c .. + 3 in split order, eight loads in flight; the first 256 threads then
-// apply the epilogue to their columns, and the block's residual partials go to res_part[bx] as in
-// the streaming kernel's own final reduction.
+// c0 = 1024 bx + 4 c .. + 3 in split order, eight loads in flight, into shared memory; then
+// every thread applies the epilogue to the slab's columns bx * 1024 + tid, + blockDim, ...
+// (consecutive threads on consecutive columns), and the block's residual partials go to
+// res_part[bx] as in the streaming kernel's own final reduction.
 template <int NRHS, int EPI>
-__global__ void __launch_bounds__(768) pogs_colsum_finish_kernel(const float* __restrict__ part, int64_t lda, int n,
-                                                                 int nsp, EpiArgs ep,
-                                                                 const DevState* __restrict__ guard) {
+__global__ void __launch_bounds__(768, 1) pogs_colsum_finish_kernel(const float* __restrict__ part, int64_t lda,
+                                                                    int n, int nsp, EpiArgs ep,
+                                                                    const DevState* __restrict__ guard) {
   __shared__ float4 sums[NRHS][256];
   __shared__ double sh[2 * 24];
   if (guard && guard->done) return;
   if (ep.cg_done && *ep.cg_done) return;
   const int tid = threadIdx.x, r = tid >> 8, c = tid & 255;
-  const int64_t c0 = (int64_t)blockIdx.x * 1024 + 4 * c;
-  const bool active = c0 < lda;
-  if (active) {
+  const int64_t cb = (int64_t)blockIdx.x * 1024;
+  const int64_t c0 = cb + 4 * c;
+  if (c0 < lda) {
     const int64_t rs = lda >> 2, ss = NRHS * rs;
     const float4* pp = reinterpret_cast<const float4*>(part + c0) + r * rs;
     float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -257,15 +260,12 @@ __global__ void __launch_bounds__(768) pogs_colsum_finish_kernel(const float* __
   }
   __syncthreads();
   Df res[2] = {};
-  if (r == 0 && active) {
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 a = sums[0][c], b = NRHS >= 2 ? sums[1][c] : z, d = NRHS == 3 ? sums[NRHS - 1][c] : z;
-    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w}, dv[4] = {d.x, d.y, d.z, d.w};
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t j = c0 + u;
-      if (j < n) epi_t<EPI>(ep, (int)j, av[u], NRHS >= 2 ? bv[u] : 0.0f, NRHS == 3 ? dv[u] : 0.0f, res);
-    }
+  const float* s0 = reinterpret_cast<const float*>(sums[0]);
+  const float* s1 = reinterpret_cast<const float*>(sums[NRHS >= 2 ? 1 : 0]);
+  const float* s2 = reinterpret_cast<const float*>(sums[NRHS - 1]);
+  for (int l = tid; l < 1024; l += blockDim.x) {
+    const int64_t j = cb + l;
+    if (j < n) epi_t<EPI>(ep, (int)j, s0[l], NRHS >= 2 ? s1[l] : 0.0f, NRHS == 3 ? s2[l] : 0.0f, res);
   }
   double tot[2];
   block_sum_df<2>(res, tot, sh);
@@ -308,6 +308,7 @@ __global__ void __launch_bounds__(256) pogs_rowdot_kernel(const float* __restric
   __syncthreads();
   const int r0 = blockIdx.x * rows;
   const int r1 = min(m, r0 + rows);
+  const uint64_t pol = l2_evict_first();
   for (int row = r0 + warp; row < r1; row += 8) {
     const float4* Ar = reinterpret_cast<const float4*>(A + (int64_t)row * lda + cbeg);
     float s1 = 0.0f, s2 = 0.0f;
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(256) pogs_rowdot_kernel(const float* __restric
     for (; qq + 32 * (U - 1) < nq; qq += 32 * U) {
       float4 a[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) a[u] = ldg_stream(Ar + qq + 32 * u);
+      for (int u = 0; u < U; ++u) a[u] = ldg_stream(Ar + qq + 32 * u, pol);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         float4 av = a[u];
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(256) pogs_rowdot_kernel(const float* __restric
       }
     }
     for (; qq < nq; qq += 32) {
-      float4 av = ldg_stream(Ar + qq);
+      float4 av = ldg_stream(Ar + qq, pol);
       if (SQ) { av.x *= av.x; av.y *= av.y; av.z *= av.z; av.w *= av.w; }
       const float4 xv = sx[qq];
       s1 = fmaf(av.x, xv.x, fmaf(av.y, xv.y, fmaf(av.z, xv.z, fmaf(av.w, xv.w, s1))));
