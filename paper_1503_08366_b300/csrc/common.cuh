@@ -159,7 +159,15 @@ POGS_DEV uint64_t l2_evict_first() {
   return pol;
 }
 
-// Streamed load (no L1 allocation) under an L2 policy from l2_evict_first().
+// L2 policy marking lines as the last to evict: for the leading rows of a matrix that every
+// pass reads, so that they stay in L2 from one pass to the next while the rest streams.
+POGS_DEV uint64_t l2_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+// Streamed load (no L1 allocation) under an L2 policy from l2_evict_first() or l2_evict_last().
 POGS_DEV float4 ldg_stream(const float4* p, uint64_t pol) {
   float4 r;
   asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"

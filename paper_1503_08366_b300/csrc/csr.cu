@@ -351,6 +351,7 @@ void csr_geometry(GemvGeom& g, int64_t m, int64_t n, int64_t nnz, int num_sms) {
   g.sp_lanes_t = csr_lanes(n, nnz);
   g.n_nrowblk = grid_rows(m, 256 / g.sp_lanes_n, num_sms, kSpmvBlocksPerSm);
   g.t_ncolblk = grid_rows(n, 256 / g.sp_lanes_t, num_sms, kSpmvBlocksPerSm);
+  g.keep_rows = 0;
   // the dense kernels' partial buffers are not used
   g.t_cols_per_blk = 1024;
   g.t_nsplit = 1;

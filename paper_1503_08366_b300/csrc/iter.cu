@@ -105,7 +105,7 @@ template <int NRHS, bool SQ, int EPI, bool FIN = true>
 __global__ void __launch_bounds__(256, 5) pogs_colsum_kernel(const float* __restrict__ A, int64_t lda, int m, int n,
                                                      const float* __restrict__ v1,
                                                      const float* __restrict__ v2,
-                                                     const float* __restrict__ v3, int rows,
+                                                     const float* __restrict__ v3, int rows, int keep_rows,
                                                      float* __restrict__ part, unsigned* __restrict__ cnt,
                                                      EpiArgs ep, const DevState* __restrict__ guard) {
   __shared__ double sh[2 * 8];
@@ -121,10 +121,11 @@ __global__ void __launch_bounds__(256, 5) pogs_colsum_kernel(const float* __rest
   for (int r = 0; r < NRHS; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.0f;
   if (active) {
     const float* Ap = A + c0;
-    const uint64_t pol = l2_evict_first();
+    const uint64_t ps = l2_evict_first(), pk = l2_evict_last();
     int i = r0;
     for (; i + 8 <= r1; i += 8) {
       float4 a[8];
+      const uint64_t pol = i < keep_rows ? pk : ps;   // by the batch's first row
 #pragma unroll
       for (int u = 0; u < 8; ++u)
         a[u] = ldg_stream(reinterpret_cast<const float4*>(Ap + (int64_t)(i + u) * lda), pol);
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(256, 5) pogs_colsum_kernel(const float* __rest
       }
     }
     for (; i < r1; ++i) {
-      float4 av = ldg_stream(reinterpret_cast<const float4*>(Ap + (int64_t)i * lda), pol);
+      float4 av = ldg_stream(reinterpret_cast<const float4*>(Ap + (int64_t)i * lda), i < keep_rows ? pk : ps);
       if (SQ) { av.x *= av.x; av.y *= av.y; av.z *= av.z; av.w *= av.w; }
       const float w1 = __ldg(v1 + i);
       acc[0][0] = fmaf(av.x, w1, acc[0][0]); acc[0][1] = fmaf(av.y, w1, acc[0][1]);
@@ -290,7 +291,8 @@ template <int NRHS, bool SQ, int EPI, int U>
 __global__ void __launch_bounds__(256) pogs_rowdot_kernel(const float* __restrict__ A, int64_t lda, int m, int n,
                                                      const float* __restrict__ x1,
                                                      const float* __restrict__ x2, int rows, int cols,
-                                                     float* __restrict__ part, unsigned* __restrict__ cnt,
+                                                     int keep_rows, float* __restrict__ part,
+                                                     unsigned* __restrict__ cnt,
                                                      EpiArgs ep, const DevState* __restrict__ guard) {
   extern __shared__ float4 sx[];
   __shared__ double sh[2 * 8];
@@ -308,9 +310,10 @@ __global__ void __launch_bounds__(256) pogs_rowdot_kernel(const float* __restric
   __syncthreads();
   const int r0 = blockIdx.x * rows;
   const int r1 = min(m, r0 + rows);
-  const uint64_t pol = l2_evict_first();
+  const uint64_t ps = l2_evict_first(), pk = l2_evict_last();
   for (int row = r0 + warp; row < r1; row += 8) {
     const float4* Ar = reinterpret_cast<const float4*>(A + (int64_t)row * lda + cbeg);
+    const uint64_t pol = row < keep_rows ? pk : ps;
     float s1 = 0.0f, s2 = 0.0f;
     int qq = lane;
     for (; qq + 32 * (U - 1) < nq; qq += 32 * U) {
@@ -731,8 +734,33 @@ void launch_axpby(int64_t k, float a, const float* x, float b, const float* y, f
 // ------------------------------------------------------------------------------------------
 // Dispatch.
 // ------------------------------------------------------------------------------------------
+// A^ between 128 MB and 512 MB (one to four times L2) keeps its leading 48 MB in L2 across the
+// passes; a larger one gains too little from it, a smaller one stays in L2 largely anyway.
+constexpr size_t kL2KeepBytes = size_t(48) << 20;
+constexpr size_t kL2KeepMin = size_t(128) << 20, kL2KeepMax = size_t(512) << 20;
+
+// Returns the lines of `bytes` at p to normal L2 eviction priority (one 128-byte line per
+// thread step): the end of the passes over a matrix whose leading rows were read evict-last.
+__global__ void l2_release_kernel(const char* __restrict__ p, int64_t lines) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < lines; i += (int64_t)gridDim.x * blockDim.x)
+    asm volatile("applypriority.global.L2::evict_normal [%0], 128;" ::"l"(p + 128 * i) : "memory");
+}
+
+void launch_l2_release(const float* A, size_t bytes, cudaStream_t s) {
+  const int64_t lines = (int64_t)(bytes / 128);
+  if (lines <= 0) return;
+  count_launch();
+  l2_release_kernel<<<(int)std::min<int64_t>(cdiv(lines, 256), 148 * 8), 256, 0, s>>>(
+      reinterpret_cast<const char*>(A), lines);
+}
 GemvGeom choose_geometry(int64_t m, int64_t n, int64_t lda, int num_sms) {
   GemvGeom g{};
+  // the leading rows of A^ up to kL2KeepBytes stay in L2 across passes (the rest streams through
+  // under evict-first), so each pass reads that much less from HBM
+  const size_t abytes = (size_t)m * lda * sizeof(float);
+  g.keep_rows = abytes > kL2KeepMin && abytes <= kL2KeepMax
+                    ? (int)std::min<int64_t>(m, (int64_t)(kL2KeepBytes / ((size_t)lda * sizeof(float))))
+                    : 0;
   // column sums: 1024-column slabs, rows split so that the grid covers ~4 blocks per SM
   g.t_cols_per_blk = 1024;
   g.t_ncolblk = (int)cdiv(lda, 1024);
@@ -768,12 +796,12 @@ static void gemv_t_dispatch(int epi, const float* A, int64_t lda, int m, int n, 
   dim3 grid(g.t_ncolblk, g.t_nsplit);
   const bool split = colsum_split(g, epi);
   count_launch(split ? 2 : 1);
-#define POGS_T(E) pogs_colsum_kernel<NRHS, SQ, E><<<grid, 256, 0, s>>>(A, lda, m, n, v1, v2, v3, g.t_rows, part, cnt, ep, guard)
+#define POGS_T(E) pogs_colsum_kernel<NRHS, SQ, E><<<grid, 256, 0, s>>>(A, lda, m, n, v1, v2, v3, g.t_rows, g.keep_rows, part, cnt, ep, guard)
 #define POGS_TS(E)                                                                                              \
   do {                                                                                                          \
     if (split) {                                                                                                \
-      pogs_colsum_kernel<NRHS, SQ, E, false><<<grid, 256, 0, s>>>(A, lda, m, n, v1, v2, v3, g.t_rows, part, cnt,  \
-                                                                  ep, guard);                                   \
+      pogs_colsum_kernel<NRHS, SQ, E, false><<<grid, 256, 0, s>>>(A, lda, m, n, v1, v2, v3, g.t_rows, g.keep_rows, \
+                                                                  part, cnt, ep, guard);                        \
       pogs_colsum_finish_kernel<NRHS, E><<<g.t_ncolblk, 256 * NRHS, 0, s>>>(part, lda, n, g.t_nsplit, ep, guard); \
     } else {                                                                                                    \
       POGS_T(E);                                                                                                \
@@ -823,11 +851,11 @@ static void gemv_n_dispatch(int epi, const float* A, int64_t lda, int m, int n, 
 #define POGS_N(E)                                                                                         \
   do {                                                                                                    \
     if (g.n_rows >= 32)                                                                                   \
-      pogs_rowdot_kernel<NRHS, SQ, E, 8><<<grid, 256, smem, s>>>(A, lda, m, n, x1, x2, g.n_rows, g.n_cols, part, \
-                                                            cnt, ep, guard);                               \
+      pogs_rowdot_kernel<NRHS, SQ, E, 8><<<grid, 256, smem, s>>>(A, lda, m, n, x1, x2, g.n_rows, g.n_cols,        \
+                                                            g.keep_rows, part, cnt, ep, guard);            \
     else                                                                                                  \
-      pogs_rowdot_kernel<NRHS, SQ, E, 4><<<grid, 256, smem, s>>>(A, lda, m, n, x1, x2, g.n_rows, g.n_cols, part, \
-                                                            cnt, ep, guard);                               \
+      pogs_rowdot_kernel<NRHS, SQ, E, 4><<<grid, 256, smem, s>>>(A, lda, m, n, x1, x2, g.n_rows, g.n_cols,        \
+                                                            g.keep_rows, part, cnt, ep, guard);            \
   } while (0)
   switch (epi) {
     case EPN_RAW: POGS_N(EPN_RAW); break;

@@ -63,6 +63,7 @@ struct DevCfg {
 struct GemvGeom {
   int t_cols_per_blk;   // 1024 (fixed: 256 threads x float4)
   int t_ncolblk, t_nsplit, t_rows;
+  int keep_rows;   // leading rows of A^ every dense pass reads under the L2 evict-last policy
   int n_rows, n_cols, n_nrowblk, n_ncolsplit;
   // Sparse A (csr.cu): the two passes run the CSR kernels over A^ (m rows) and A^T (n rows)
   // instead; n_nrowblk and t_ncolblk are then their grid sizes (the number of residual
@@ -73,6 +74,8 @@ struct GemvGeom {
   float* pack;   // max(m, n) x 4 floats: interleaved right-hand sides of the long gathers
 };
 GemvGeom choose_geometry(int64_t m, int64_t n, int64_t lda, int num_sms);
+// Back to normal L2 eviction priority for the first `bytes` of A (see GemvGeom::keep_rows).
+void launch_l2_release(const float* A, size_t bytes, cudaStream_t s);
 
 // ---- sparse A (csr.cu) ---------------------------------------------------------------------
 void csr_geometry(GemvGeom& g, int64_t m, int64_t n, int64_t nnz, int num_sms);

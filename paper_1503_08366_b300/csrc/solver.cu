@@ -395,6 +395,13 @@ void enqueue_projection(pogs_handle* h, int refine, int cg_steps, cudaStream_t s
   }
 }
 
+// The passes read the leading GemvGeom::keep_rows rows of A^ evict-last; an entry point that ran
+// passes hands those lines back to normal L2 priority before it returns.
+void release_kept_rows(pogs_handle* h, cudaStream_t s) {
+  if (!h->sparse && h->A && h->geom.keep_rows > 0)
+    launch_l2_release(h->A, (size_t)h->geom.keep_rows * h->lda * sizeof(float), s);
+}
+
 void enqueue_iteration(pogs_handle* h, int refine, int cg_steps, cudaStream_t s, unsigned long long cond,
                        int use_cond) {
   launch_prox_step((int)h->n, (int)h->m, h->x, h->xt, h->xh, h->cx, h->mu, h->y, h->yt, h->yh, h->dy, h->nu,
@@ -613,6 +620,7 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order, const Cs
     phase("gram");
     phase("cholesky");
     phase("inverse");
+    release_kept_rows(h, s);
     CK(cudaStreamSynchronize(s));
     return 0;
   }
@@ -732,6 +740,7 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order, const Cs
   }
   CK(cudaGetLastError());
   phase("inverse");
+  release_kept_rows(h, s);
   CK(cudaStreamSynchronize(s));
   return 0;
 }
@@ -1061,6 +1070,7 @@ int pogs_solve_warm(pogs_handle* h, const pogs_fn* f, const pogs_fn* g, const po
       if (h->st_host->done) break;
     }
   }
+  release_kept_rows(h, s);
   launch_unscale((int)h->n, (int)h->m, h->xh, h->mu, h->yh, h->nu, h->D, h->E, x ? h->ox : nullptr,
                  mu ? h->omu : nullptr, y ? h->oy : nullptr, nu ? h->onu : nullptr, s);
   CK(cudaGetLastError());
@@ -1172,6 +1182,7 @@ int pogs_project(pogs_handle* h, const float* c, const float* d, float* x, float
   CK(cudaMemsetAsync(h->yh, 0, h->mv * sizeof(float), s));
   CK(cudaMemsetAsync(h->nu, 0, h->mv * sizeof(float), s));
   enqueue_projection(h, p->refine_steps, cg_steps_for(h, p), s);
+  release_kept_rows(h, s);
   CK(cudaGetLastError());
   TRY(copy_out(h->x, x, h->n, s));
   TRY(copy_out(h->y, y, h->m, s));
@@ -1345,6 +1356,7 @@ int pogs_time_kernels(pogs_handle* h, int reps, double* ms, double* bytes) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  release_kept_rows(h, s);
   CK(cudaGetLastError());
   h->solved = false;   // iterate state is no longer a solve result
   for (int k = 0; k < 7; ++k) {
