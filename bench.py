@@ -1029,6 +1029,25 @@ def run_next(args):
                           "indirect vs direct projection; sparse A", **out)))
 
 
+def run_kernels(args):
+    """One full-size problem of the default step (--shape tall: the 40000x10000 Lasso, fat: the
+    2000x40000 logistic): setup, one solve, then each kernel of one ADMM iteration timed with CUDA
+    events through pogs_time_kernels (launched back to back from the host; small kernels read the
+    host's launch rate).  The launch sequence is fixed, so a profiler can select launches by
+    index: the setup's Sinkhorn-Knopp passes come first, then the timed launches."""
+    import torch
+    import workloads as W
+    import paper_1503_08366_b300 as P
+    torch.cuda.set_device(0)
+    prob = (W.lasso_tall_large if args.shape == "tall" else W.logistic_fat_large)()
+    A = torch.from_numpy(prob.A).cuda()
+    with P.Solver(A, P.pogs_default_params()) as s:
+        info, *_ = s.solve(prob.f, prob.g)
+        kt = P.pogs_time_kernels(s.handle, reps=args.reps)
+    print(json.dumps(dict(workload="kernels", shape=list(prob.A.shape), iters=info.iters, obj=info.obj,
+                          reps=args.reps, kernels={k: dict(ms=v[0], bytes=v[1]) for k, v in kt.items()})))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1036,7 +1055,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve", "precision", "next"])
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "batch", "serve", "precision", "next", "kernels"])
+    ap.add_argument("--shape", default="fat", choices=["fat", "tall"], help="kernels workload: which problem")
+    ap.add_argument("--reps", type=int, default=10, help="kernels workload: timed launches per kernel")
     ap.add_argument("--count", type=int, default=2048, help="batch workload: instances")
     ap.add_argument("--plain-sample", type=int, default=128, help="batch workload: plain-path sample")
     ap.add_argument("--requests", type=int, default=20000, help="serve workload: requests in the trace")
@@ -1062,6 +1084,8 @@ def main():
         run_precision(args)
     elif args.workload == "next":
         run_next(args)
+    elif args.workload == "kernels":
+        run_kernels(args)
     else:
         run_ours(args)
 
