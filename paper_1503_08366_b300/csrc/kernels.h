@@ -168,6 +168,15 @@ void launch_copy_in(const float* src, int64_t m, int64_t n, int64_t lds, bool co
                     int64_t lda, int* err, cudaStream_t s);
 void launch_scale(float* A, int64_t lda, int64_t m, int64_t n, const float* D, const float* E,
                   cudaStream_t s);
+// One Sinkhorn-Knopp sweep (d from e, then e from d) in one pass over A: for lda <= 12288 and
+// m >= 2368 (sk_sweep_fits).  part: sk_sweep_blocks() x lda floats; frob_part:
+// 2 sk_sweep_finish_blocks(lda) pairs (the Frobenius partials of the sweep's e, as the
+// column-sum pass leaves them for launch_sk_finish).
+bool sk_sweep_fits(int64_t m, int64_t lda);
+int sk_sweep_blocks();
+int sk_sweep_finish_blocks(int64_t lda);
+int launch_sk_sweep(const float* A, int64_t lda, int64_t m, int64_t n, float* dvec, float* evec, double gamma,
+                    float* part, Df* frob_part, cudaStream_t s);
 void launch_sk_finish(const float* dvec, const float* evec, int64_t m, int64_t n, const Df* frob_part,
                       int nfrob, int64_t q, float* D, float* E, cudaStream_t s);
 // C[M x N] = alpha op(A) op(B) + beta C (row-major, SIMT); lower_only skips tiles above

@@ -165,6 +165,161 @@ void launch_sk_finish(const float* dvec, const float* evec, int64_t m, int64_t n
   sk_finish_kernel<<<1, 1024, 0, s>>>(dvec, evec, m, n, frob_part, nfrob, q, D, E);
 }
 
+// ---- one Sinkhorn-Knopp sweep in one pass over A^ (Algorithm 2, p = 2) ----------------------
+// For a row-major A (pitch lda, zero padding, lda <= 1024 kSkGroups floats): block b takes the
+// rows [b R, b R + R) four at a time.  Two warps per row form the row sum of A_ij^2 e_j over
+// their halves of the row (e staged in shared memory) and d_i = num_r / (sum + reg_r), which
+// is written out; then every thread adds A_ij^2 d_i of the four rows into its columns'
+// accumulators (lane-contiguous float4 groups, rows re-read from L2, where the first read left
+// them).  That is Algorithm 2's d update followed by the column sums of its e update, with A
+// streamed from HBM once per sweep instead of twice.  The block's column sums go to
+// part[b][0, lda); sk_sweep_finish_kernel adds the blocks in order and forms e.
+constexpr int kSkGroups = 12;   // float4 column groups per thread: lda <= 12288
+constexpr int kSkBlocks = 296;  // two 256-thread blocks per SM
+
+__global__ void __launch_bounds__(256, 2) sk_sweep_kernel(const float* __restrict__ A, int64_t lda, int m,
+                                                          int rows_per_blk, const float* __restrict__ e_in,
+                                                          float* __restrict__ d_out, float num_r, float reg_r,
+                                                          float* __restrict__ part) {
+  extern __shared__ float4 se4[];   // e over the padded row, lda / 4 groups
+  __shared__ float psum[8];
+  __shared__ float dsh[4];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ng = (int)(lda >> 2), half = (ng + 1) >> 1;
+  for (int g = tid; g < ng; g += 256) se4[g] = reinterpret_cast<const float4*>(e_in)[g];
+  __syncthreads();
+  float4 acc[kSkGroups];
+#pragma unroll
+  for (int u = 0; u < kSkGroups; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int r0 = blockIdx.x * rows_per_blk, r1 = min(m, r0 + rows_per_blk);
+  const uint64_t ps = l2_evict_first();
+  for (int c = r0; c < r1; c += 4) {
+    // row sums: warp w takes row c + w / 2, column groups [h half, h half + half), h = w % 2
+    const int row = c + (warp >> 1);
+    float sum = 0.0f;
+    if (row < r1) {
+      const float4* ar = reinterpret_cast<const float4*>(A + (int64_t)row * lda);
+      const int g0 = (warp & 1) * half, g1 = min(ng, g0 + half);
+      int g = g0 + lane;
+      for (; g + 224 < g1; g += 256) {
+        float4 a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = ar[g + 32 * u];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float4 e = se4[g + 32 * u];
+          sum = fmaf(a[u].x * a[u].x, e.x, sum); sum = fmaf(a[u].y * a[u].y, e.y, sum);
+          sum = fmaf(a[u].z * a[u].z, e.z, sum); sum = fmaf(a[u].w * a[u].w, e.w, sum);
+        }
+      }
+      for (; g < g1; g += 32) {
+        const float4 a = ar[g], e = se4[g];
+        sum = fmaf(a.x * a.x, e.x, sum); sum = fmaf(a.y * a.y, e.y, sum);
+        sum = fmaf(a.z * a.z, e.z, sum); sum = fmaf(a.w * a.w, e.w, sum);
+      }
+    }
+    sum = warp_sum(sum);
+    if (lane == 0) psum[warp] = sum;
+    __syncthreads();
+    if (tid < 4 && c + tid < r1) {
+      const float d = num_r / ((psum[2 * tid] + psum[2 * tid + 1]) + reg_r);
+      dsh[tid] = d;
+      d_out[c + tid] = d;
+    }
+    __syncthreads();
+    // column sums of A_ij^2 d_i over the four rows, in row order
+    const int nr = min(4, r1 - c);
+    for (int k = 0; k < nr; ++k) {
+      const float d = dsh[k];
+      const float4* ar = reinterpret_cast<const float4*>(A + (int64_t)(c + k) * lda);
+#pragma unroll
+      for (int u = 0; u < kSkGroups; ++u) {
+        const int g = tid + 256 * u;
+        if (g < ng) {
+          const float4 a = ldg_stream(ar + g, ps);
+          acc[u].x = fmaf(a.x * a.x, d, acc[u].x); acc[u].y = fmaf(a.y * a.y, d, acc[u].y);
+          acc[u].z = fmaf(a.z * a.z, d, acc[u].z); acc[u].w = fmaf(a.w * a.w, d, acc[u].w);
+        }
+      }
+    }
+  }
+  float4* pb = reinterpret_cast<float4*>(part + (int64_t)blockIdx.x * lda);
+#pragma unroll
+  for (int u = 0; u < kSkGroups; ++u) {
+    const int g = tid + 256 * u;
+    if (g < ng) pb[g] = acc[u];
+  }
+}
+
+// e_j = num_c / (sum_b part[b][j] + reg_c) for j < n (blocks added in order: warp w adds the
+// blocks b = w, w + 8, ... for the block's 32 columns, then the eight warp sums in warp order)
+// and the Frobenius partial sum_j e_j t_j = ||D A E||_F^2 of the block's columns into
+// frob_part[2 blockIdx.x] (the second entry of the pair is 0).
+__global__ void __launch_bounds__(256) sk_sweep_finish_kernel(const float* __restrict__ part, int nblk, int64_t lda,
+                                                              int64_t n, float num_c, float reg_c,
+                                                              float* __restrict__ e_out, Df* __restrict__ frob_part) {
+  __shared__ float ws[8][32];
+  __shared__ double sh[2 * 8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t j = (int64_t)blockIdx.x * 32 + lane;
+  float t = 0.0f;
+  if (j < lda) {
+    int b = warp;
+    for (; b + 56 < nblk; b += 64) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldcg(part + (int64_t)(b + 8 * u) * lda + j);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t += v[u];
+    }
+    for (; b < nblk; b += 8) t += __ldcg(part + (int64_t)b * lda + j);
+  }
+  ws[warp][lane] = t;
+  __syncthreads();
+  Df res[2] = {};
+  if (warp == 0 && j < n) {
+    float tj = 0.0f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) tj += ws[w][lane];
+    const float ej = num_c / (tj + reg_c);
+    e_out[j] = ej;
+    df_add_prod(res[0], ej, tj);
+  }
+  double tot[2];
+  block_sum_df<2>(res, tot, sh);
+  if (tid == 0) {
+    const float hi = (float)tot[0];
+    frob_part[2 * blockIdx.x] = Df{hi, (float)(tot[0] - (double)hi)};
+    frob_part[2 * blockIdx.x + 1] = Df{0.0f, 0.0f};
+  }
+}
+
+bool sk_sweep_fits(int64_t m, int64_t lda) { return lda <= 1024 * kSkGroups && m >= 8 * kSkBlocks; }
+int sk_sweep_blocks() { return kSkBlocks; }
+int sk_sweep_finish_blocks(int64_t lda) { return (int)cdiv(lda, 32); }
+
+int launch_sk_sweep(const float* A, int64_t lda, int64_t m, int64_t n, float* dvec, float* evec, double gamma,
+                    float* part, Df* frob_part, cudaStream_t s) {
+  const int rows = (int)round_up(cdiv(m, kSkBlocks), 4);
+  const int smem = (int)(lda * sizeof(float));
+  static PerDeviceOnce attr;
+  if (attr.run([&] {
+        return cudaFuncSetAttribute(sk_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    1024 * kSkGroups * (int)sizeof(float)) == cudaSuccess
+                   ? 0
+                   : -1;
+      }) != 0) {
+    cudaGetLastError();
+    return POGS_ERR_CUDA;
+  }
+  count_launch(2);
+  sk_sweep_kernel<<<kSkBlocks, 256, smem, s>>>(A, lda, (int)m, rows, evec, dvec, (float)n, (float)(gamma / (double)m),
+                                              part);
+  sk_sweep_finish_kernel<<<sk_sweep_finish_blocks(lda), 256, 0, s>>>(part, kSkBlocks, lda, n, (float)m,
+                                                                     (float)(gamma / (double)n), evec, frob_part);
+  return cudaGetLastError() == cudaSuccess ? 0 : POGS_ERR_CUDA;
+}
+
 // ---- dense SIMT GEMM -----------------------------------------------------------------------
 // C = alpha op(A) op(B) + beta C, row-major, storage type TI, products and accumulation in
 // TC (TI = double with TC = float gives FP32 products of FP32-rounded inputs added to an FP64

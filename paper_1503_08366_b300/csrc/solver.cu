@@ -570,7 +570,17 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order, const Cs
   launch_fill(dvec, m, 1.0f, s);
   const double gamma = h->sp.gamma > 0 ? h->sp.gamma : (double)(m + n) * sqrt(1.1920928955078125e-07);
   const int sweeps = h->sp.equil ? h->sp.sk_sweeps : 0;
-  for (int it = 0; it < sweeps; ++it) {
+  // dense A with rows of at most 12288 floats and enough of them: each sweep in one pass
+  const bool fused = !csr && sweeps > 0 && sk_sweep_fits(m, h->lda);
+  float* skpart = nullptr;
+  Df* skfrob = nullptr;
+  if (fused) {
+    TRY(scr.get(&skpart, (size_t)sk_sweep_blocks() * h->lda, s));
+    TRY(scr.get(&skfrob, (size_t)sk_sweep_finish_blocks(h->lda) * 2, s));
+  }
+  for (int it = 0; fused && it < sweeps; ++it)
+    TRY(launch_sk_sweep(h->A, h->lda, m, n, dvec, evec, gamma, skpart, skfrob, s));
+  for (int it = 0; !fused && it < sweeps; ++it) {
     EpiArgs er = epi0();
     er.sk_vec = dvec; er.sk_num = (float)n; er.sk_reg = (float)(gamma / (double)m);
     launch_gemv_n(1, true, EPN_SK_ROW, h->A, h->lda, (int)m, (int)n, evec, nullptr, h->geom, h->part_n, h->cnt_n,
@@ -589,7 +599,7 @@ int setup_impl(pogs_handle* h, const float* A, int64_t lds, char order, const Cs
                   h->cnt_t,
                   ec, nullptr, s);
   }
-  launch_sk_finish(dvec, evec, m, n, h->dual_part, h->geom.t_ncolblk, q, h->D, h->E, s);
+  launch_sk_finish(dvec, evec, m, n, fused ? skfrob : h->dual_part, fused ? sk_sweep_finish_blocks(h->lda) : h->geom.t_ncolblk, q, h->D, h->E, s);
   if (csr) launch_csr_scale(h->csr_rp, h->csr_ci, h->csr_va, m, h->D, h->E, h->csc_perm, h->nnz, h->csc_va, s);
   else launch_scale(h->A, h->lda, m, n, h->D, h->E, s);
   CK(cudaGetLastError());

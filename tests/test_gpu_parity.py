@@ -104,6 +104,22 @@ def test_equilibration_matches_oracle(P, shape):
     s.close()
 
 
+@pytest.mark.parametrize("shape", [(2369, 1000),     # rows just past the one-pass sweep's threshold: empty blocks
+                                   (5003, 77),       # ragged n (row pitch 96), most threads idle in the column sums
+                                   (12000, 12288),   # the longest row the one-pass sweep takes
+                                   (3000, 12289)])   # one column more: the two-pass sweeps
+def test_equilibration_one_pass_sweeps_match_oracle(P, shape):
+    """Algorithm 2 with each sweep in one pass over A^ (row sums to d, then the column sums of the
+    e update from the same rows) gives the oracle's D and E, at the shapes around its limits."""
+    m, n = shape
+    prob = W.lasso(m, n, seed=8)
+    prm = P.pogs_default_params(gram_prec="FP32")
+    with P.Solver(prob.A, prm) as s:
+        D, E = s.equil()
+    eq = OE.equilibrate(prob.A.astype(np.float64), prm.sk_sweeps, OE.default_gamma(m, n))
+    assert _rel(D, eq.D) < 1e-5 and _rel(E, eq.E) < 1e-5, (_rel(D, eq.D), _rel(E, eq.E))
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("refine", [0, 1])
 def test_projection_matches_oracle(P, shape, refine):
