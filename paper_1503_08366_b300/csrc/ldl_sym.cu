@@ -1,9 +1,11 @@
 // Symbolic analysis for the sparse LDL^T of K = [I A^T; A -I] (host code; see ldl.h).
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <set>
 #include <numeric>
+#include <thread>
 
 #include "../../include/pogs.h"
 #include "ldl.h"
@@ -11,10 +13,11 @@
 namespace pogs {
 namespace {
 
-// Undirected graph of K without the diagonal: x_j -- y_i for every nonzero A_ij.
+// Undirected graph of K without the diagonal: x_j -- y_i for every nonzero A_ij.  eid[p] is the
+// CSR index of the A entry behind adjacency entry p.
 struct Graph {
   int N = 0;
-  std::vector<int> off, adj;
+  std::vector<int> off, adj, eid;
 };
 
 Graph build_graph(int m, int n, const int* rp, const int* ci) {
@@ -29,10 +32,13 @@ Graph build_graph(int m, int n, const int* rp, const int* ci) {
   g.off.assign(g.N + 1, 0);
   for (int v = 0; v < g.N; ++v) g.off[v + 1] = g.off[v] + deg[v];
   g.adj.resize(g.off[g.N]);
+  g.eid.resize(g.off[g.N]);
   std::vector<int> pos(g.off.begin(), g.off.end() - 1);
   for (int i = 0; i < m; ++i)
     for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      g.eid[pos[ci[p]]] = p;
       g.adj[pos[ci[p]]++] = n + i;   // x_j's neighbours: rows in increasing order
+      g.eid[pos[n + i]] = p;
       g.adj[pos[n + i]++] = ci[p];   // y_i's neighbours: columns in increasing order
     }
   return g;
@@ -47,28 +53,37 @@ Graph build_graph(int m, int n, const int* rp, const int* ci) {
 class Dissection {
  public:
   static constexpr int kLeaf = 8;
-  explicit Dissection(const Graph& g) : g_(g), tag_(g.N, 0), lvl_(g.N, -1) {}
+  // Below a separator the two halves touch disjoint nodes (a half's neighbours lie in that half or
+  // in separators already ordered), so halves of at least kParallelMin nodes each are ordered on two
+  // threads, down to par_depth_ levels of the recursion; the result is the same as in one thread.
+  static constexpr int kParallelMin = 16384;
+  explicit Dissection(const Graph& g) : g_(g), tag_(g.N, 0) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    while (par_depth_ < 4 && (2u << par_depth_) <= hw) ++par_depth_;
+  }
 
   std::vector<int> order() {
     const int N = g_.N;
-    out_.clear();
-    out_.reserve(N);
-    if (N == 0) return out_;
+    std::vector<int> out;
+    out.reserve(N);
+    if (N == 0) return out;
     const double avg = (double)g_.adj.size() / N;
     const int dense_deg = std::max(64, (int)(10.0 * avg));
     std::vector<int> rest, dense;
     for (int v = 0; v < N; ++v) (g_.off[v + 1] - g_.off[v] > dense_deg ? dense : rest).push_back(v);
-    ++cur_;
     for (int v : dense) tag_[v] = -1;   // excluded from every part
-    dissect(rest);
-    for (int v : dense) out_.push_back(v);
-    return out_;
+    dissect(rest, out, 0);
+    for (int v : dense) out.push_back(v);
+    return out;
   }
 
  private:
   const Graph& g_;
-  std::vector<int> tag_, lvl_, out_;
-  int cur_ = 0;
+  std::vector<int> tag_;
+  std::atomic<int> cur_{0};
+  int par_depth_ = 0;
+
+  int new_tag() { return cur_.fetch_add(1, std::memory_order_relaxed) + 1; }
 
   // Level structure of a BFS: the nodes in visiting order, and the start of each level in it
   // (lo.back() == q.size()).
@@ -79,23 +94,23 @@ class Dissection {
     const int* end(int l) const { return q.data() + lo[l + 1]; }
   };
 
-  // BFS over the nodes tagged t from s (neighbours in adjacency order, level by level).
-  void bfs(int s, int t, Levels& L) {
+  // BFS over the nodes tagged t from s (neighbours in adjacency order, level by level).  Visited
+  // nodes are tagged `seen`; with restore they get t back at the end.
+  void bfs(int s, int t, int seen, bool restore, Levels& L) {
     L.q.clear();
     L.lo.clear();
     L.q.push_back(s);
-    lvl_[s] = 0;
+    tag_[s] = seen;
     size_t b = 0;
     while (b < L.q.size()) {
       const size_t e = L.q.size();
       L.lo.push_back((int)b);
-      const int next = (int)L.lo.size();
       for (size_t k = b; k < e; ++k) {
         const int v = L.q[k];
         for (int p = g_.off[v]; p < g_.off[v + 1]; ++p) {
           const int u = g_.adj[p];
-          if (tag_[u] == t && lvl_[u] < 0) {
-            lvl_[u] = next;
+          if (tag_[u] == t) {
+            tag_[u] = seen;
             L.q.push_back(u);
           }
         }
@@ -103,51 +118,52 @@ class Dissection {
       b = e;
     }
     L.lo.push_back((int)L.q.size());
-    for (int v : L.q) lvl_[v] = -1;
+    if (restore)
+      for (int v : L.q) tag_[v] = t;
   }
 
-  void dissect(const std::vector<int>& nodes) {
+  // Appends the order of `nodes` (increasing node numbers) to out.
+  void dissect(const std::vector<int>& nodes, std::vector<int>& out, int depth) {
     if ((int)nodes.size() <= kLeaf) {
-      for (int v : nodes) out_.push_back(v);
+      out.insert(out.end(), nodes.begin(), nodes.end());
       return;
     }
-    const int t = ++cur_;
+    const int t = new_tag();
     for (int v : nodes) tag_[v] = t;
     // connected parts, each moved to a tag of its own as it is found
     std::vector<std::vector<int>> parts;
+    std::vector<int> ptag;
     Levels levels;
     int tpart = t;
     for (int v : nodes) {
       if (tag_[v] != t) continue;
-      bfs(v, t, levels);
-      std::vector<int> part(levels.q);
-      tpart = ++cur_;
-      for (int u : part) tag_[u] = tpart;
-      parts.push_back(std::move(part));
+      tpart = new_tag();
+      bfs(v, t, tpart, false, levels);
+      parts.push_back(levels.q);
+      ptag.push_back(tpart);
     }
     if (parts.size() > 1) {
-      for (auto& part : parts) {
-        std::sort(part.begin(), part.end());
-        dissect(part);
-      }
+      // each part in increasing node order: one walk over the (increasing) input; the parts' tags
+      // increase in the order the parts were found
+      for (auto& part : parts) part.clear();
+      for (int v : nodes) parts[std::lower_bound(ptag.begin(), ptag.end(), tag_[v]) - ptag.begin()].push_back(v);
+      for (auto& part : parts) dissect(part, out, depth);
       return;
     }
     // one connected part (tag tpart): pseudo-peripheral start, the last node of a BFS, repeated
     // while the depth grows
     int start = *levels.begin(levels.count() - 1);
-    int depth = levels.count();
+    int bfs_depth = levels.count();
     Levels l2;
     for (int it = 0; it < 4; ++it) {
-      bfs(start, tpart, l2);
-      if (l2.count() <= depth) break;
-      depth = l2.count();
+      bfs(start, tpart, new_tag(), true, l2);
+      if (l2.count() <= bfs_depth) break;
+      bfs_depth = l2.count();
       std::swap(levels, l2);
       start = *levels.begin(levels.count() - 1);
     }
     if (levels.count() < 3) {         // nearly a clique: no useful separator
-      std::vector<int> v(nodes);
-      std::sort(v.begin(), v.end());
-      for (int u : v) out_.push_back(u);
+      out.insert(out.end(), nodes.begin(), nodes.end());
       return;
     }
     const int half = (int)nodes.size() / 2;
@@ -160,22 +176,43 @@ class Dissection {
       }
     }
     L = std::max(1, std::min(L, levels.count() - 2));
-    std::vector<int> p1(levels.begin(0), levels.begin(L)), p2(levels.begin(L + 1), levels.end(levels.count() - 1)),
-        sep(levels.begin(L), levels.end(L));
-    std::sort(p1.begin(), p1.end());
-    std::sort(p2.begin(), p2.end());
-    std::sort(sep.begin(), sep.end());
-    dissect(p1);
-    dissect(p2);
-    for (int v : sep) out_.push_back(v);
+    // levels [0, L) | level L (the separator) | levels (L, end), each in increasing node order
+    const int t1 = new_tag(), ts = new_tag();
+    for (const int* v = levels.begin(0); v != levels.begin(L); ++v) tag_[*v] = t1;
+    for (const int* v = levels.begin(L); v != levels.end(L); ++v) tag_[*v] = ts;
+    std::vector<int> p1, p2, sep;
+    p1.reserve(levels.lo[L]);
+    sep.reserve(levels.lo[L + 1] - levels.lo[L]);
+    p2.reserve(nodes.size() - levels.lo[L + 1]);
+    for (int v : nodes) (tag_[v] == t1 ? p1 : tag_[v] == ts ? sep : p2).push_back(v);
+    levels = Levels();
+    l2 = Levels();
+    std::vector<int> out1;
+    std::thread th;
+    if (depth < par_depth_ && (int)p1.size() >= kParallelMin && (int)p2.size() >= kParallelMin) {
+      try {
+        th = std::thread([&] { dissect(p1, out1, depth + 1); });
+      } catch (...) {   // no thread available: order both halves here
+      }
+    }
+    if (!th.joinable()) {
+      dissect(p1, out, depth + 1);
+      dissect(p2, out, depth + 1);
+    } else {
+      std::vector<int> out2;
+      try {
+        dissect(p2, out2, depth + 1);
+      } catch (...) {
+        th.join();
+        throw;
+      }
+      th.join();
+      out.insert(out.end(), out1.begin(), out1.end());
+      out.insert(out.end(), out2.begin(), out2.end());
+    }
+    out.insert(out.end(), sep.begin(), sep.end());
   }
 };
-
-// Position of value x in the sorted range [b, e), or -1.
-int find_sorted(const int* b, const int* e, int x) {
-  const int* p = std::lower_bound(b, e, x);
-  return (p != e && *p == x) ? (int)(p - b) : -1;
-}
 
 }  // namespace
 
@@ -212,34 +249,72 @@ int ldl_analyze(int m, int n, const int* rp, const int* ci, LdlSymbolic& S) {
       }
     }
   }
-  // ---- column structures: struct(j) = higher neighbours of j  U  struct(children) \ {j} -------
-  std::vector<std::vector<int>> st(N);
+  // ---- column counts ----------------------------------------------------------------------------
+  // cc(j) = |struct(j)| + 1 is the number of row subtrees T_r(i) (the columns k with L_ik != 0, a
+  // subtree of the elimination tree rooted at i) that contain j.  Each T_r(i) is given weight +1 at
+  // every leaf, -1 at the lowest common ancestor of each pair of leaves adjacent in postorder and -1
+  // at parent(i); the weights summed over the subtree of j then count the row subtrees through j
+  // (Gilbert, Ng and Peyton's row/column count method).  Leaves are found in one postorder sweep
+  // (k is a leaf of T_r(i) when no earlier member of T_r(i) lies in the subtree of k), ancestors by
+  // a disjoint-set forest of the finished nodes.
+  S.colcount.resize(N);
   {
-    std::vector<std::vector<int>> kids(N);
-    for (int j = 0; j < N; ++j)
-      if (S.parent[j] >= 0) kids[S.parent[j]].push_back(j);
-    std::vector<int> mark(N, -1);
-    for (int j = 0; j < N; ++j) {
-      std::vector<int>& s = st[j];
-      const int v = S.perm[j];
-      for (int p = g.off[v]; p < g.off[v + 1]; ++p) {
-        const int i = S.iperm[g.adj[p]];
-        if (i > j && mark[i] != j) {
-          mark[i] = j;
-          s.push_back(i);
+    std::vector<int> head(N, -1), nxt(N, -1), post, first(N, -1);
+    post.reserve(N);
+    for (int j = N - 1; j >= 0; --j)
+      if (S.parent[j] >= 0) {
+        nxt[j] = head[S.parent[j]];
+        head[S.parent[j]] = j;
+      }
+    std::vector<int> stack;
+    for (int r = 0; r < N; ++r) {
+      if (S.parent[r] >= 0) continue;
+      stack.push_back(r);
+      while (!stack.empty()) {
+        const int v = stack.back(), c = head[v];
+        if (c >= 0) {
+          head[v] = nxt[c];
+          stack.push_back(c);
+        } else {
+          stack.pop_back();
+          post.push_back(v);
         }
       }
-      for (int c : kids[j])
-        for (int i : st[c])
-          if (i > j && mark[i] != j) {
-            mark[i] = j;
-            s.push_back(i);
-          }
-      std::sort(s.begin(), s.end());
+    }
+    for (int k = 0; k < N; ++k)
+      for (int u = post[k]; u >= 0 && first[u] < 0; u = S.parent[u]) first[u] = k;
+    std::vector<int> delta(N, 0), maxfirst(N, -1), prevleaf(N, -1), uf(N);
+    std::iota(uf.begin(), uf.end(), 0);
+    auto find = [&](int x) {
+      int r = x;
+      while (uf[r] != r) r = uf[r];
+      while (uf[x] != r) {
+        const int nx = uf[x];
+        uf[x] = r;
+        x = nx;
+      }
+      return r;
+    };
+    for (int k = 0; k < N; ++k) {
+      const int j = post[k], v = S.perm[j];
+      if (S.parent[j] >= 0) --delta[S.parent[j]];
+      for (int p = g.off[v]; p < g.off[v + 1]; ++p) {
+        const int i = S.iperm[g.adj[p]];
+        if (i <= j || first[j] <= maxfirst[i]) continue;
+        ++delta[j];              // j is a leaf of T_r(i)
+        maxfirst[i] = first[j];
+        if (prevleaf[i] >= 0) --delta[find(prevleaf[i])];
+        prevleaf[i] = j;
+      }
+      if (maxfirst[j] < first[j]) ++delta[j];   // T_r(j) = {j}
+      if (S.parent[j] >= 0) uf[j] = S.parent[j];
+    }
+    for (int k = 0; k < N; ++k) {
+      const int j = post[k];
+      if (S.parent[j] >= 0) delta[S.parent[j]] += delta[j];
+      S.colcount[j] = delta[j] - 1;
     }
   }
-  S.colcount.resize(N);
-  for (int j = 0; j < N; ++j) S.colcount[j] = (int)st[j].size();
   // ---- supernodes: fundamental, then chains merged while small and with little zero fill ------
   std::vector<int> nkids(N, 0);
   for (int j = 0; j < N; ++j)
@@ -247,7 +322,7 @@ int ldl_analyze(int m, int n, const int* rp, const int* ci, LdlSymbolic& S) {
   std::vector<int> sfirst, swidth;
   for (int j = 0; j < N;) {
     int l = j;
-    while (l + 1 < N && S.parent[l] == l + 1 && nkids[l + 1] == 1 && st[l].size() == st[l + 1].size() + 1) ++l;
+    while (l + 1 < N && S.parent[l] == l + 1 && nkids[l + 1] == 1 && S.colcount[l] == S.colcount[l + 1] + 1) ++l;
     sfirst.push_back(j);
     swidth.push_back(l - j + 1);
     j = l + 1;
@@ -263,8 +338,8 @@ int ldl_analyze(int m, int n, const int* rp, const int* ci, LdlSymbolic& S) {
       while (i + 1 < cnt) {
         const int l = f + w - 1, fp = sfirst[i + 1], wp = swidth[i + 1];
         if (S.parent[l] != fp || nkids[fp] != 1 || w + wp > 32) break;
-        const int64_t hp = (int64_t)st[fp + wp - 1].size();
-        const int64_t h_s = (int64_t)st[l].size();
+        const int64_t hp = S.colcount[fp + wp - 1];
+        const int64_t h_s = S.colcount[l];
         // each of s's w columns grows from (its own) to wp + hp rows below the merged block
         const int64_t zeros = (int64_t)w * (wp + hp - h_s);
         const int64_t panel = (int64_t)(w + wp) * (w + wp + hp);
@@ -285,13 +360,6 @@ int ldl_analyze(int m, int n, const int* rp, const int* ci, LdlSymbolic& S) {
   std::vector<int> col2sn(N);
   for (int s = 0; s < ns; ++s)
     for (int j = sfirst[s]; j < sfirst[s] + swidth[s]; ++j) col2sn[j] = s;
-  S.row_off.assign(ns + 1, 0);
-  for (int s = 0; s < ns; ++s) S.row_off[s + 1] = S.row_off[s] + (int)st[sfirst[s] + swidth[s] - 1].size();
-  S.rows.resize(S.row_off[ns]);
-  for (int s = 0; s < ns; ++s) {
-    const auto& r = st[sfirst[s] + swidth[s] - 1];
-    std::copy(r.begin(), r.end(), S.rows.begin() + S.row_off[s]);
-  }
   S.sparent.assign(ns, -1);
   for (int s = 0; s < ns; ++s) {
     const int p = S.parent[sfirst[s] + swidth[s] - 1];
@@ -320,51 +388,86 @@ int ldl_analyze(int m, int n, const int* rp, const int* ci, LdlSymbolic& S) {
     std::vector<int> pos(S.level_off.begin(), S.level_off.end() - 1);
     for (int s = 0; s < ns; ++s) S.level_nodes[pos[S.level[s]]++] = s;
   }
+  // ---- row structures of the supernodes -------------------------------------------------------
+  // The columns of a supernode form a chain of the elimination tree, so the subtree of its last
+  // column l is its own columns plus the subtrees of its child supernodes' last columns, and
+  // struct(l) = {i > l : i a neighbour of one of its columns, or a row of a child supernode}.
+  S.row_off.assign(ns + 1, 0);
+  for (int s = 0; s < ns; ++s) S.row_off[s + 1] = S.row_off[s] + S.colcount[sfirst[s] + swidth[s] - 1];
+  S.rows.resize(S.row_off[ns]);
+  std::vector<int> fpos(N, -1);   // scatter map: front position of a row in the current supernode
+  {
+    std::vector<int> tmp;
+    for (int s = 0; s < ns; ++s) {
+      const int f = sfirst[s], l = f + swidth[s] - 1;
+      tmp.clear();
+      for (int j = f; j <= l; ++j) {
+        const int v = S.perm[j];
+        for (int p = g.off[v]; p < g.off[v + 1]; ++p) {
+          const int i = S.iperm[g.adj[p]];
+          if (i > l && fpos[i] != s) {
+            fpos[i] = s;
+            tmp.push_back(i);
+          }
+        }
+      }
+      for (int c = S.child_off[s]; c < S.child_off[s + 1]; ++c) {
+        const int ch = S.child[c];
+        for (int a = S.row_off[ch]; a < S.row_off[ch + 1]; ++a) {
+          const int i = S.rows[a];
+          if (i > l && fpos[i] != s) {
+            fpos[i] = s;
+            tmp.push_back(i);
+          }
+        }
+      }
+      if ((int)tmp.size() != S.row_off[s + 1] - S.row_off[s]) return POGS_ERR_ARG;   // counts disagree: cannot happen
+      std::sort(tmp.begin(), tmp.end());
+      std::copy(tmp.begin(), tmp.end(), S.rows.begin() + S.row_off[s]);
+    }
+  }
   // ---- index maps: children's rows in the parent's front; original entries of K -----------------
-  auto local = [&](int s, int i) -> int {   // front position of row i (new index) in supernode s
-    const int f = sfirst[s], w = swidth[s];
-    if (i >= f && i < f + w) return i - f;
-    const int a = find_sorted(S.rows.data() + S.row_off[s], S.rows.data() + S.row_off[s + 1], i);
-    return a < 0 ? -1 : w + a;
-  };
+  // Supernode by supernode, fpos holds the front position of each of its rows (own columns first,
+  // then its row structure) while its children's rows and its original entries are looked up.
   S.rel_off.assign(ns + 1, 0);
   for (int s = 0; s < ns; ++s) S.rel_off[s + 1] = S.rel_off[s] + (S.sparent[s] >= 0 ? S.row_off[s + 1] - S.row_off[s] : 0);
   S.rel.resize(S.rel_off[ns]);
-  for (int s = 0; s < ns; ++s) {
-    const int p = S.sparent[s];
-    if (p < 0) continue;
-    for (int a = S.row_off[s]; a < S.row_off[s + 1]; ++a) {
-      const int loc = local(p, S.rows[a]);
-      if (loc < 0) return POGS_ERR_ARG;   // cannot happen for an elimination tree
-      S.rel[S.rel_off[s] + (a - S.row_off[s])] = loc;
-    }
-  }
   S.asm_off.assign(ns + 1, 0);
   S.asm_pos.clear();
   S.asm_src.clear();
+  S.asm_pos.reserve((size_t)N + g.adj.size() / 2);   // each diagonal entry, each A entry once
+  S.asm_src.reserve((size_t)N + g.adj.size() / 2);
+  std::fill(fpos.begin(), fpos.end(), -1);
   for (int s = 0; s < ns; ++s) {
     const int f = sfirst[s], w = swidth[s];
     const int nf = w + (S.row_off[s + 1] - S.row_off[s]);
+    for (int j = f; j < f + w; ++j) fpos[j] = j - f;
+    for (int a = S.row_off[s]; a < S.row_off[s + 1]; ++a) fpos[S.rows[a]] = w + (a - S.row_off[s]);
+    for (int c = S.child_off[s]; c < S.child_off[s + 1]; ++c) {
+      const int ch = S.child[c];
+      for (int a = S.row_off[ch]; a < S.row_off[ch + 1]; ++a) {
+        const int loc = fpos[S.rows[a]];
+        if (loc < 0) return POGS_ERR_ARG;   // cannot happen for an elimination tree
+        S.rel[S.rel_off[ch] + (a - S.row_off[ch])] = loc;
+      }
+    }
     for (int j = f; j < f + w; ++j) {
       const int v = S.perm[j];
       const int lc = j - f;
       S.asm_pos.push_back(lc * nf + lc);
       S.asm_src.push_back(v < n ? -1 : -2);
       for (int p = g.off[v]; p < g.off[v + 1]; ++p) {
-        const int u = g.adj[p];
-        const int i = S.iperm[u];
+        const int i = S.iperm[g.adj[p]];
         if (i <= j) continue;
-        const int lr = local(s, i);
+        const int lr = fpos[i];
         if (lr < 0) return POGS_ERR_ARG;
-        // the A entry linking x_col and y_row
-        const int row = v < n ? u - n : v - n;
-        const int col = v < n ? v : u;
-        const int k = find_sorted(ci + rp[row], ci + rp[row + 1], col);
         S.asm_pos.push_back(lr * nf + lc);
-        S.asm_src.push_back(rp[row] + k);
+        S.asm_src.push_back(g.eid[p]);   // the A entry linking the two unknowns
       }
     }
     S.asm_off[s + 1] = (int)S.asm_pos.size();
+    for (int j = f; j < f + w; ++j) fpos[j] = -1;
+    for (int a = S.row_off[s]; a < S.row_off[s + 1]; ++a) fpos[S.rows[a]] = -1;
   }
   // ---- storage ----------------------------------------------------------------------------------
   S.panel_off.assign(ns + 1, 0);

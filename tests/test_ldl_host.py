@@ -119,3 +119,55 @@ def test_malformed_pattern_is_rejected(P):
         P.pogs_ldl_analyze(rp, np.array([1, 0, 2], np.int32), (2, 3))     # unsorted row
     with pytest.raises(P.PogsError):
         P.pogs_ldl_analyze(rp, np.array([0, 1, 3], np.int32), (2, 3))     # column out of range
+
+
+def _colcounts_by_column_structures(A, perm):
+    """Column counts of L for P K P^T by the column-structure recurrence: struct(j) = the later
+    neighbours of j, together with struct(c) minus {j} for every child c of j in the elimination
+    tree (the tree computed here with ancestor links)."""
+    m, n = A.shape
+    N = m + n
+    adj = [[] for _ in range(N)]
+    coo = A.tocoo()
+    for i, j in zip(coo.row.tolist(), coo.col.tolist()):
+        adj[j].append(n + i)
+        adj[n + i].append(j)
+    iperm = np.empty(N, np.int64)
+    iperm[np.asarray(perm)] = np.arange(N)
+    nadj = [[int(iperm[u]) for u in adj[perm[k]]] for k in range(N)]
+    parent, anc = [-1] * N, [-1] * N
+    for k in range(N):
+        for i in nadj[k]:
+            while i != -1 and i < k:
+                nxt = anc[i]
+                anc[i] = k
+                if nxt == -1:
+                    parent[i] = k
+                i = nxt
+    kids = [[] for _ in range(N)]
+    for j in range(N):
+        if parent[j] >= 0:
+            kids[parent[j]].append(j)
+    st, counts = [None] * N, np.zeros(N, np.int64)
+    for j in range(N):
+        s = {i for i in nadj[j] if i > j}
+        for c in kids[j]:
+            s |= st[c]
+            st[c] = None            # a child's structure is read by its parent only
+        s.discard(j)
+        st[j], counts[j] = s, len(s)
+    return counts
+
+
+def test_large_pattern_counts_and_deterministic_ordering(P):
+    """A pattern large enough that the ordering's halves are dissected on separate threads: the
+    ordering is the same on every call, and the column counts agree with the column-structure
+    recurrence evaluated independently here."""
+    A = W.banded_lasso(40000, 20000, seed=9, half_band=2).A
+    m, n = A.shape
+    stats, perm, cc = P.pogs_ldl_analyze(A.indptr, A.indices, A.shape)
+    _, perm2, cc2 = P.pogs_ldl_analyze(A.indptr, A.indices, A.shape)
+    assert np.array_equal(perm, perm2) and np.array_equal(cc, cc2)
+    assert np.array_equal(np.sort(perm), np.arange(m + n))
+    assert np.array_equal(cc, _colcounts_by_column_structures(A, perm.tolist()))
+    assert stats["nnz_l"] >= int(cc.sum())
