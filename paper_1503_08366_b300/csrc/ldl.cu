@@ -6,14 +6,17 @@
 // rows R_s below them) from the entries of K in its columns and the update matrices of its
 // children (in child order, so the sums are the same on every run), eliminates the w own columns
 // in FP64 (right-looking LDL^T without pivoting: K is quasi-definite, every pivot is nonzero), and
-// writes its panel [L11; L21] with D on the diagonal and its update matrix F22 - L21 D L21^T.
-// Fronts of up to 96 rows live in shared memory, larger ones in global scratch.
+// writes its panel [X11; L21] with D on the diagonal, X11 = L11^{-1} (unit lower, strictly lower
+// part stored) formed once here, and its update matrix F22 - L21 D L21^T.  Fronts of up to 96 rows
+// live in shared memory, larger ones in global scratch.
 //
 // Solve (per projection): permute the right-hand side into the new order, forward substitution
-// level by level from the leaves (each supernode adds its children's update vectors, solves with
-// its unit lower L11 and passes -L21 y_s on to its parent as its own update vector), division by
-// D, backward substitution from the root (each supernode gathers the finished unknowns of R_s),
-// then the epilogue of the projection on the unknowns it returns.
+// level by level from the leaves (each supernode adds its children's update vectors, forms
+// y_s = X11 t_s and passes -L21 y_s on to its parent as its own update vector), division by D,
+// backward substitution from the root (each supernode gathers the finished unknowns of R_s, then
+// applies X11^T), then the epilogue of the projection on the unknowns it returns.  With the
+// inverse diagonal blocks cached, a supernode's part of each solve is a few dense matrix-vector
+// products with all their loads independent, not a chain of w dependent column steps.
 #include <algorithm>
 #include <cstring>
 
@@ -73,10 +76,21 @@ __device__ void ldl_front(const FrontArgs& a, int s, double* F) {
     __syncthreads();
   }
   if (tid == 0 && s_bad) atomicExch(a.err, POGS_ERR_NUMERIC);
+  // X11 = L11^{-1}: from L11 X11 = I, X_ij = -sum_{k=j}^{i-1} L_ik X_kj (i > j, X_jj = 1); thread j
+  // forms column j top down and keeps it in row j of F's upper triangle (F[j][i] = X_ij), which
+  // the elimination leaves unused and no other thread reads
+  for (int j = tid; j < w; j += blockDim.x)
+    for (int i = j + 1; i < w; ++i) {
+      double acc = F[i * nf + j];
+      for (int k = j + 1; k < i; ++k) acc = fma(F[i * nf + k], F[j * nf + k], acc);
+      F[j * nf + i] = -acc;
+    }
+  __syncthreads();
+  // panel: rows i < w hold X11 below the diagonal and D on it, rows i >= w hold L21
   double* P = a.panel + a.panel_off[s];
   for (int idx = tid; idx < nf * w; idx += blockDim.x) {
     const int i = idx / w, j = idx - i * w;
-    P[idx] = (i >= j) ? F[i * nf + j] : 0.0;
+    P[idx] = i >= w ? F[i * nf + j] : i > j ? F[j * nf + i] : i == j ? F[i * nf + i] : 0.0;
   }
   if (h > 0 && a.upd_off) {
     double* U = a.upd + a.upd_off[s];
@@ -105,8 +119,8 @@ struct SolveArgs {
 };
 
 // Forward substitution for the supernodes of one level: t = [y_s; 0] + children's update
-// vectors, t <- L^{-1} t over the w own columns (the rows of R_s receive -L21 y_s), y_s = t[:w],
-// the supernode's update vector = t[w:].
+// vectors, t[:w] <- X11 t[:w], t[w:] -= L21 t[:w]; y_s = t[:w], the supernode's update vector =
+// t[w:].
 __global__ void __launch_bounds__(128) ldl_forward_kernel(SolveArgs a, int base) {
   extern __shared__ double t[];
   const int s = a.nodes[base + blockIdx.x];
@@ -123,11 +137,29 @@ __global__ void __launch_bounds__(128) ldl_forward_kernel(SolveArgs a, int base)
     __syncthreads();
   }
   const double* P = a.panel + a.panel_off[s];
-  for (int k = 0; k < w; ++k) {
-    const double tk = t[k];
-    for (int i = k + 1 + tid; i < nf; i += blockDim.x) t[i] -= P[i * w + k] * tk;
+  // t[0:w] <- X11 t[0:w], z_i = t_i + sum_{k<i} X_ik t_k: rows in chunks of blockDim, the last chunk
+  // first (a chunk reads t only at its own and earlier rows, which are still unchanged)
+  const int bd = blockDim.x;
+  for (int c0 = ((w - 1) / bd) * bd; c0 >= 0; c0 -= bd) {
+    const int i = c0 + tid;
+    double z = 0.0;
+    if (i < w) {
+      const double* Xi = P + (int64_t)i * w;
+      z = t[i];
+      for (int k = 0; k < i; ++k) z = fma(Xi[k], t[k], z);
+    }
+    __syncthreads();
+    if (i < w) t[i] = z;
     __syncthreads();
   }
+  // t[w:] -= L21 t[0:w]
+  for (int r = w + tid; r < nf; r += blockDim.x) {
+    const double* Lr = P + (int64_t)r * w;
+    double acc = 0.0;
+    for (int k = 0; k < w; ++k) acc = fma(Lr[k], t[k], acc);
+    t[r] -= acc;
+  }
+  __syncthreads();
   for (int i = tid; i < nf; i += blockDim.x) {
     if (i < w) a.y[f + i] = t[i];
     else a.uvec[a.vec_off[s] + i - w] = t[i];
@@ -135,7 +167,7 @@ __global__ void __launch_bounds__(128) ldl_forward_kernel(SolveArgs a, int base)
 }
 
 // Backward substitution for the supernodes of one level (from the root): t = D^{-1} y_s -
-// L21^T y[R_s] (rows of R_s are finished), then t <- L11^{-T} t.
+// L21^T y[R_s] (rows of R_s are finished), then t <- L11^{-T} t = X11^T t.
 __global__ void __launch_bounds__(128) ldl_backward_kernel(SolveArgs a, int base) {
   extern __shared__ double t[];
   const int s = a.nodes[base + blockIdx.x];
@@ -151,9 +183,18 @@ __global__ void __launch_bounds__(128) ldl_backward_kernel(SolveArgs a, int base
     t[k] -= acc;
   }
   __syncthreads();
-  for (int k = w - 1; k > 0; --k) {
-    const double tk = t[k];
-    for (int j = tid; j < k; j += blockDim.x) t[j] -= P[k * w + j] * tk;
+  // t[0:w] <- X11^T t[0:w], x_k = t_k + sum_{i>k} X_ik t_i: rows in chunks of blockDim, the first
+  // chunk first (a chunk reads t only at its own and later rows, which are still unchanged)
+  const int bd = blockDim.x;
+  for (int c0 = 0; c0 < w; c0 += bd) {
+    const int k = c0 + tid;
+    double x = 0.0;
+    if (k < w) {
+      x = t[k];
+      for (int i = k + 1; i < w; ++i) x = fma(P[(int64_t)i * w + k], t[i], x);
+    }
+    __syncthreads();
+    if (k < w) t[k] = x;
     __syncthreads();
   }
   for (int i = tid; i < w; i += blockDim.x) a.y[f + i] = t[i];
@@ -219,6 +260,18 @@ int ldl_factor(const LdlSymbolic& S, const float* va, LdlFactor& F, int* err, cu
   F.max_front = S.max_front;
   F.panel_entries = S.panel_total;
   F.level_off = S.level_off;
+  // the solve kernels loop over any block size: each level gets the smallest of 32, 64 or 128
+  // threads that covers its largest front (the many small fronts near the leaves then fit more
+  // CTAs per SM)
+  F.level_threads.assign(S.levels, 32);
+  for (int l = 0; l < S.levels; ++l) {
+    int nfmax = 0;
+    for (int k = S.level_off[l]; k < S.level_off[l + 1]; ++k) {
+      const int s2 = S.level_nodes[k];
+      nfmax = std::max(nfmax, S.width[s2] + (S.row_off[s2 + 1] - S.row_off[s2]));
+    }
+    F.level_threads[l] = nfmax <= 32 ? 32 : nfmax <= 64 ? 64 : 128;
+  }
   // the solve keeps one front column vector per CTA in shared memory
   if ((size_t)S.max_front * sizeof(double) > 160 * 1024) return POGS_ERR_CAPACITY;
   int rc = 0;
@@ -305,11 +358,11 @@ void ldl_apply(const LdlFactor& F, bool tall, const float* v, int epi, const Epi
   const size_t smem = (size_t)F.max_front * sizeof(double);
   for (int l = 0; l < F.levels; ++l) {
     const int b = F.level_off[l], cnt = F.level_off[l + 1] - b;
-    ldl_forward_kernel<<<cnt, 128, smem, s>>>(a, b);
+    ldl_forward_kernel<<<cnt, F.level_threads[l], smem, s>>>(a, b);
   }
   for (int l = F.levels - 1; l >= 0; --l) {
     const int b = F.level_off[l], cnt = F.level_off[l + 1] - b;
-    ldl_backward_kernel<<<cnt, 128, smem, s>>>(a, b);
+    ldl_backward_kernel<<<cnt, F.level_threads[l], smem, s>>>(a, b);
   }
   switch (epi) {
     case EPR_RAW: ldl_permute_out_kernel<EPR_RAW><<<grid, 256, 0, s>>>(F.perm, F.N, base, len, F.y, ep); break;

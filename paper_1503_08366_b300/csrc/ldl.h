@@ -59,11 +59,13 @@ struct LdlFactor {
   int N = 0, n = 0, m = 0, ns = 0, levels = 0, max_front = 0;
   int64_t panel_entries = 0;
   std::vector<int> level_off;             // host copy: supernodes per level (launch sizes)
+  std::vector<int> level_threads;         // host copy: solve threads per CTA of each level (32, 64 or 128)
   int *perm = nullptr, *first = nullptr, *width = nullptr, *row_off = nullptr, *rows = nullptr;
   int *child_off = nullptr, *child = nullptr, *level_nodes = nullptr, *rel_off = nullptr, *rel = nullptr;
   int* vec_off = nullptr;
   int64_t* panel_off = nullptr;
-  double* panel = nullptr;                // per supernode nf x w: L (unit diagonal implied), D on the diagonal
+  double* panel = nullptr;                // per supernode nf x w: rows < w X11 = L11^{-1} below the diagonal
+                                          // (unit diagonal implied) and D on it, rows >= w L21
   double* y = nullptr;                    // N: the solve's work vector (new order)
   double* uvec = nullptr;                 // update vectors of the forward solve
   int64_t device_bytes = 0;
