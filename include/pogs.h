@@ -376,7 +376,8 @@ int pogs_check_bounded_wait(void* stream);
  * K = [I A^T; A -I] (Section 3.5: for sparse A, factor K once and cache the factor), for the
  * m x n pattern of A given in CSR (rowptr: m + 1 entries, rowptr[0] = 0; colind: sorted and
  * unique within each row, in [0, n); host arrays the caller keeps).  Host work only, no device
- * call.  The unknowns of K are numbered x_0..x_{n-1}, then y_0..y_{m-1} (index n + i).
+ * call; the ordering runs on up to 16 host threads (same result on any number), and calls from
+ * several threads at once are independent.  The unknowns of K are numbered x_0..x_{n-1}, then y_0..y_{m-1} (index n + i).
  * Outputs (each may be NULL): stats[0..7] = N = n + m, structural nonzeros of L below the
  * diagonal, supernodes, levels of the supernodal tree, largest frontal matrix, factor entries
  * stored, update-matrix entries, frontal scratch entries; perm[N]: the fill-reducing ordering
