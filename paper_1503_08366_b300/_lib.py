@@ -404,31 +404,93 @@ def pogs_gram_noalloc(A, G, gram_prec="BF16X3", stream=None):
                   "pogs_gram_noalloc")
 
 
+def _ptrs(arrs, dtype, keep: list, block: bool) -> np.ndarray:
+    """Raw pointers (0 for None) of a sequence of arrays or tensors, by the rules of _ptr, as
+    uint64.  Torch tensors keep their own storage (a converted copy when the dtype or layout
+    differs).  With block, host arrays are copied end to end into one array of `dtype` (one
+    allocation and one pass; a pointer lookup per numpy array costs microseconds, thousands of
+    times per batch); without it each points at its own storage, as in _ptr."""
+    out = np.zeros(len(arrs), np.uint64)
+    if block and arrs and all(type(a) is np.ndarray and a.ndim == 1 for a in arrs):   # the common case
+        blk = np.concatenate(arrs, dtype=dtype, casting="unsafe")
+        keep.append(blk)
+        sizes = np.fromiter((a.size for a in arrs), np.int64, len(arrs))
+        starts = (np.cumsum(sizes) - sizes).astype(np.uint64)
+        out[:] = np.uint64(blk.ctypes.data) + starts * np.uint64(blk.itemsize)
+        return out
+    if arrs and hasattr(arrs[0], "data_ptr"):
+        want_t, tt = _torch_dtype(dtype), type(arrs[0])
+        if all(type(a) is tt and a.dtype is want_t and a.is_contiguous() for a in arrs):   # tensors as given
+            out[:] = np.fromiter((a.data_ptr() for a in arrs), np.uint64, len(arrs))
+            return out
+    host_i, host_a = [], []
+    want_t = None
+    for i, a in enumerate(arrs):
+        if a is None:
+            continue
+        if hasattr(a, "data_ptr"):   # torch tensor
+            if want_t is None:
+                want_t = _torch_dtype(dtype)
+            if a.dtype != want_t or not a.is_contiguous():
+                a = a.to(want_t).contiguous()
+                keep.append(a)
+            out[i] = a.data_ptr()
+        elif block:
+            host_i.append(i)
+            host_a.append(np.ravel(a))
+        else:
+            out[i] = _ptr(a, dtype, keep)
+    if host_a:
+        blk = np.concatenate(host_a, dtype=dtype, casting="unsafe")
+        keep.append(blk)
+        sizes = np.fromiter((x.size for x in host_a), np.int64, len(host_a))
+        starts = (np.cumsum(sizes) - sizes).astype(np.uint64)
+        out[host_i] = np.uint64(blk.ctypes.data) + starts * np.uint64(blk.itemsize)
+    return out
+
+
+# pogs_problem and pogs_result as rows of 8-byte words (filled column by column below)
+_PROBLEM_WORDS = C.sizeof(pogs_problem) // 8
+_RESULT_WORDS = C.sizeof(pogs_result) // 8
+assert C.sizeof(pogs_problem) == 16 * 8 and pogs_problem.f.offset == 32 and pogs_problem.g.offset == 80
+assert pogs_result.info.offset == 32 and C.sizeof(pogs_result) % 8 == 0
+
+
 def pogs_solve_batch(problems, params: pogs_params | None = None, stream=None):
     """problems: objects with A (m x n float32, host array or CUDA tensor), f and g (h, a..e).
     Returns a list of (info, x, y, mu, nu) with host float32 outputs."""
     keep: list = []
     n_p = len(problems)
-    probs = (pogs_problem * max(1, n_p))()
-    res = (pogs_result * max(1, n_p))()
-    shapes = [pb.A.shape for pb in problems]
+    cnt = max(1, n_p)
+    probs = (pogs_problem * cnt)()
+    res = (pogs_result * cnt)()
+    mn = np.array([pb.A.shape for pb in problems], np.int64).reshape(n_p, 2)
+    m, n = mn[:, 0], mn[:, 1]
+    # words of each pogs_problem: A, m, n, lda, f.h .. f.e, g.h .. g.e
+    w = np.frombuffer(probs, np.uint64).reshape(cnt, _PROBLEM_WORDS)[:n_p]
+    w[:, 0] = _ptrs([pb.A for pb in problems], np.float32, keep, block=False)
+    w[:, 1] = m
+    w[:, 2] = n
+    w[:, 3] = n
+    fs = [pb.f for pb in problems]
+    gs = [pb.g for pb in problems]
+    w[:, 4] = _ptrs([f.h for f in fs], np.uint8, keep, block=True)
+    w[:, 10] = _ptrs([g.h for g in gs], np.uint8, keep, block=True)
+    for j, k in enumerate("abcde"):
+        w[:, 5 + j] = _ptrs([getattr(f, k, None) for f in fs], np.float32, keep, block=True)
+        w[:, 11 + j] = _ptrs([getattr(g, k, None) for g in gs], np.float32, keep, block=True)
     # all outputs in one host block: instance i's x, y, mu, nu are consecutive views
-    block = np.empty(sum(2 * (m + n) for m, n in shapes), np.float32)
-    base = block.ctypes.data
-    outs = []
-    off = 0
-    for i, pb in enumerate(problems):
-        m, n = shapes[i]
-        pr = probs[i]
-        pr.A = _ptr(pb.A, np.float32, keep)
-        pr.m, pr.n, pr.lda = m, n, n
-        pr.f = make_fn(pb.f, keep)
-        pr.g = make_fn(pb.g, keep)
-        r = res[i]
-        r.x, r.y, r.mu, r.nu = base + 4 * off, base + 4 * (off + n), base + 4 * (off + n + m), base + 4 * (off + 2 * n + m)
-        outs.append((block[off:off + n], block[off + n:off + n + m], block[off + n + m:off + 2 * n + m],
-                     block[off + 2 * n + m:off + 2 * (n + m)]))
-        off += 2 * (m + n)
+    tot = 2 * (m + n)
+    off = np.cumsum(tot) - tot
+    block = np.empty(int(tot.sum()), np.float32)
+    base = np.uint64(block.ctypes.data)
+    r = np.frombuffer(res, np.uint64).reshape(cnt, _RESULT_WORDS)[:n_p]
+    r[:, 0] = base + 4 * off.astype(np.uint64)
+    r[:, 1] = base + 4 * (off + n).astype(np.uint64)
+    r[:, 2] = base + 4 * (off + n + m).astype(np.uint64)
+    r[:, 3] = base + 4 * (off + 2 * n + m).astype(np.uint64)
+    outs = [(block[o:o + ni], block[o + ni:o + ni + mi], block[o + ni + mi:o + 2 * ni + mi],
+             block[o + 2 * ni + mi:o + 2 * (ni + mi)]) for o, mi, ni in zip(off.tolist(), m.tolist(), n.tolist())]
     rc = lib.pogs_solve_batch(n_p, probs, C.byref(params) if params is not None else None, res,
                               _stream_ptr(stream))
     _check(rc, "pogs_solve_batch")
