@@ -44,6 +44,69 @@ Graph build_graph(int m, int n, const int* rp, const int* ci) {
   return g;
 }
 
+// Runs f(begin, end, worker) over [0, count) in up to 16 contiguous chunks of at least `grain`
+// items, on host threads (chunk 0 on the calling thread, and any chunk whose thread cannot be
+// started); f must be safe on disjoint ranges at once.  Returns the first nonzero code of the
+// chunks, in chunk order.
+template <class F>
+int parallel_chunks(int count, int grain, F f) {
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nw = std::min({16, hw, std::max(1, count / std::max(1, grain))});
+  if (nw <= 1) return f(0, count, 0);
+  std::vector<int> rc(nw, 0);
+  auto chunk = [&](int w) {
+    rc[w] = f((int)((int64_t)count * w / nw), (int)((int64_t)count * (w + 1) / nw), w);
+  };
+  std::vector<std::thread> th;
+  int started = 1;
+  try {
+    for (; started < nw; ++started) th.emplace_back(chunk, started);
+  } catch (...) {   // no more threads: the remaining chunks run here
+  }
+  chunk(0);
+  for (int w = started; w < nw; ++w) chunk(w);
+  for (auto& t : th) t.join();
+  for (int r : rc)
+    if (r) return r;
+  return 0;
+}
+
+// Runs f(bounds[w], bounds[w + 1], w) for every w on its own host thread (w = 0 on the calling
+// thread, and any chunk whose thread cannot be started); returns the first nonzero code.
+template <class F>
+int parallel_ranges(const std::vector<int>& bounds, F f) {
+  const int nw = (int)bounds.size() - 1;
+  if (nw <= 1) return nw == 1 ? f(bounds[0], bounds[1], 0) : 0;
+  std::vector<int> rc(nw, 0);
+  auto chunk = [&](int w) { rc[w] = f(bounds[w], bounds[w + 1], w); };
+  std::vector<std::thread> th;
+  int started = 1;
+  try {
+    for (; started < nw; ++started) th.emplace_back(chunk, started);
+  } catch (...) {   // no more threads: the remaining chunks run here
+  }
+  chunk(0);
+  for (int w = started; w < nw; ++w) chunk(w);
+  for (auto& t : th) t.join();
+  for (int r : rc)
+    if (r) return r;
+  return 0;
+}
+
+// Cut [0, cost.size()) into at most `parts` contiguous ranges of about equal total cost.
+std::vector<int> balanced_bounds(const std::vector<int64_t>& cost, int parts) {
+  int64_t total = 0;
+  for (int64_t c : cost) total += c;
+  std::vector<int> b{0};
+  int64_t acc = 0;
+  for (int i = 0; i < (int)cost.size(); ++i) {
+    acc += cost[i];
+    if ((int)b.size() < parts && acc * parts >= total * (int64_t)b.size() && i + 1 < (int)cost.size()) b.push_back(i + 1);
+  }
+  b.push_back((int)cost.size());
+  return b;
+}
+
 // Nested dissection by breadth-first level structures.  A connected part is split at the level
 // that holds the middle node of a BFS from a pseudo-peripheral node; that level is a vertex
 // separator and is ordered after both halves.  Disconnected parts are ordered one after another,
@@ -227,19 +290,36 @@ int ldl_analyze(int m, int n, const int* rp, const int* ci, LdlSymbolic& S) {
   S.n = n;
   S.m = m;
   const int N = S.N = n + m;
-  const Graph g = build_graph(m, n, rp, ci);
-  // ---- ordering -------------------------------------------------------------------------------
-  S.perm = Dissection(g).order();
-  S.iperm.assign(N, -1);
-  for (int k = 0; k < N; ++k) S.iperm[S.perm[k]] = k;
+  Graph pg;   // the graph in the new numbering (neighbours of each node in their order in g)
+  {
+    const Graph g = build_graph(m, n, rp, ci);
+    // ---- ordering -----------------------------------------------------------------------------
+    S.perm = Dissection(g).order();
+    S.iperm.assign(N, -1);
+    for (int k = 0; k < N; ++k) S.iperm[S.perm[k]] = k;
+    pg.N = N;
+    pg.off.assign(N + 1, 0);
+    for (int k = 0; k < N; ++k) pg.off[k + 1] = pg.off[k] + (g.off[S.perm[k] + 1] - g.off[S.perm[k]]);
+    pg.adj.resize(g.adj.size());
+    pg.eid.resize(g.eid.size());
+    parallel_chunks(N, 8192, [&](int b, int e, int) -> int {
+      for (int k = b; k < e; ++k) {
+        const int v = S.perm[k];
+        for (int p = g.off[v], q = pg.off[k]; p < g.off[v + 1]; ++p, ++q) {
+          pg.adj[q] = S.iperm[g.adj[p]];
+          pg.eid[q] = g.eid[p];
+        }
+      }
+      return 0;
+    });
+  }
   // ---- elimination tree (ancestor links with path compression) ------------------------------
   S.parent.assign(N, -1);
   {
     std::vector<int> anc(N, -1);
     for (int k = 0; k < N; ++k) {
-      const int v = S.perm[k];
-      for (int p = g.off[v]; p < g.off[v + 1]; ++p) {
-        int i = S.iperm[g.adj[p]];
+      for (int p = pg.off[k]; p < pg.off[k + 1]; ++p) {
+        int i = pg.adj[p];
         while (i != -1 && i < k) {
           const int next = anc[i];
           anc[i] = k;
@@ -296,10 +376,10 @@ int ldl_analyze(int m, int n, const int* rp, const int* ci, LdlSymbolic& S) {
       return r;
     };
     for (int k = 0; k < N; ++k) {
-      const int j = post[k], v = S.perm[j];
+      const int j = post[k];
       if (S.parent[j] >= 0) --delta[S.parent[j]];
-      for (int p = g.off[v]; p < g.off[v + 1]; ++p) {
-        const int i = S.iperm[g.adj[p]];
+      for (int p = pg.off[j]; p < pg.off[j + 1]; ++p) {
+        const int i = pg.adj[p];
         if (i <= j || first[j] <= maxfirst[i]) continue;
         ++delta[j];              // j is a leaf of T_r(i)
         maxfirst[i] = first[j];
@@ -395,80 +475,129 @@ int ldl_analyze(int m, int n, const int* rp, const int* ci, LdlSymbolic& S) {
   S.row_off.assign(ns + 1, 0);
   for (int s = 0; s < ns; ++s) S.row_off[s + 1] = S.row_off[s] + S.colcount[sfirst[s] + swidth[s] - 1];
   S.rows.resize(S.row_off[ns]);
-  std::vector<int> fpos(N, -1);   // scatter map: front position of a row in the current supernode
-  {
-    std::vector<int> tmp;
-    for (int s = 0; s < ns; ++s) {
-      const int f = sfirst[s], l = f + swidth[s] - 1;
-      tmp.clear();
-      for (int j = f; j <= l; ++j) {
-        const int v = S.perm[j];
-        for (int p = g.off[v]; p < g.off[v + 1]; ++p) {
-          const int i = S.iperm[g.adj[p]];
-          if (i > l && fpos[i] != s) {
-            fpos[i] = s;
-            tmp.push_back(i);
-          }
+  // Supernodes of one level of the supernodal tree are independent (their children lie in lower
+  // levels): the levels from the leaves up, while they hold many supernodes, are done on several
+  // threads, each with its own marker array; the rest in index order on this thread (children
+  // before parents, and a supernode's children's rows are usually still in cache).
+  std::vector<std::vector<int>> marks(16), tmps(16);
+  // The rows of s in increasing order: its columns' later neighbours (sorted), then each child's
+  // rows not yet present, a sorted run merged in (with many children, one sort at the end).
+  auto rows_of = [&](int s, std::vector<int>& mark, std::vector<int>& tmp) -> int {
+    const int f = sfirst[s], l = f + swidth[s] - 1;
+    const bool merge = S.child_off[s + 1] - S.child_off[s] <= 16;
+    tmp.clear();
+    for (int j = f; j <= l; ++j)
+      for (int p = pg.off[j]; p < pg.off[j + 1]; ++p) {
+        const int i = pg.adj[p];
+        if (i > l && mark[i] != s) {
+          mark[i] = s;
+          tmp.push_back(i);
         }
       }
-      for (int c = S.child_off[s]; c < S.child_off[s + 1]; ++c) {
-        const int ch = S.child[c];
-        for (int a = S.row_off[ch]; a < S.row_off[ch + 1]; ++a) {
-          const int i = S.rows[a];
-          if (i > l && fpos[i] != s) {
-            fpos[i] = s;
-            tmp.push_back(i);
-          }
+    if (merge) std::sort(tmp.begin(), tmp.end());
+    for (int c = S.child_off[s]; c < S.child_off[s + 1]; ++c) {
+      const int ch = S.child[c];
+      const size_t mid = tmp.size();
+      for (int a = S.row_off[ch]; a < S.row_off[ch + 1]; ++a) {
+        const int i = S.rows[a];
+        if (i > l && mark[i] != s) {
+          mark[i] = s;
+          tmp.push_back(i);
         }
       }
-      if ((int)tmp.size() != S.row_off[s + 1] - S.row_off[s]) return POGS_ERR_ARG;   // counts disagree: cannot happen
-      std::sort(tmp.begin(), tmp.end());
-      std::copy(tmp.begin(), tmp.end(), S.rows.begin() + S.row_off[s]);
+      if (merge && mid > 0 && mid < tmp.size()) std::inplace_merge(tmp.begin(), tmp.begin() + mid, tmp.end());
     }
+    if ((int)tmp.size() != S.row_off[s + 1] - S.row_off[s]) return POGS_ERR_ARG;   // counts disagree: cannot happen
+    if (!merge) std::sort(tmp.begin(), tmp.end());
+    std::copy(tmp.begin(), tmp.end(), S.rows.begin() + S.row_off[s]);
+    return 0;
+  };
+  int wide = 0;   // levels [0, wide) done in parallel
+  for (; wide < S.levels && S.level_off[wide + 1] - S.level_off[wide] >= 2048; ++wide) {
+    const int lb = S.level_off[wide];
+    const int rc = parallel_chunks(S.level_off[wide + 1] - lb, 1024, [&](int b, int e, int wk) -> int {
+      if (marks[wk].empty()) marks[wk].assign(N, -1);
+      for (int k = lb + b; k < lb + e; ++k) {
+        const int r = rows_of(S.level_nodes[k], marks[wk], tmps[wk]);
+        if (r) return r;
+      }
+      return 0;
+    });
+    if (rc) return rc;
   }
+  if (marks[0].empty()) marks[0].assign(N, -1);
+  for (int s = 0; s < ns; ++s)
+    if (S.level[s] >= wide) {
+      const int r = rows_of(s, marks[0], tmps[0]);
+      if (r) return r;
+    }
   // ---- index maps: children's rows in the parent's front; original entries of K -----------------
   // Supernode by supernode, fpos holds the front position of each of its rows (own columns first,
   // then its row structure) while its children's rows and its original entries are looked up.
   S.rel_off.assign(ns + 1, 0);
   for (int s = 0; s < ns; ++s) S.rel_off[s + 1] = S.rel_off[s] + (S.sparent[s] >= 0 ? S.row_off[s + 1] - S.row_off[s] : 0);
   S.rel.resize(S.rel_off[ns]);
+  // entries per supernode (each own column's diagonal and its neighbours below it), then every
+  // supernode's entries at its offset, supernodes in contiguous chunks on several threads
   S.asm_off.assign(ns + 1, 0);
-  S.asm_pos.clear();
-  S.asm_src.clear();
-  S.asm_pos.reserve((size_t)N + g.adj.size() / 2);   // each diagonal entry, each A entry once
-  S.asm_src.reserve((size_t)N + g.adj.size() / 2);
-  std::fill(fpos.begin(), fpos.end(), -1);
+  parallel_chunks(ns, 1024, [&](int b, int e, int) -> int {
+    for (int s = b; s < e; ++s) {
+      int c = 0;
+      for (int j = sfirst[s]; j < sfirst[s] + swidth[s]; ++j) {
+        ++c;
+        for (int p = pg.off[j]; p < pg.off[j + 1]; ++p) c += pg.adj[p] > j;
+      }
+      S.asm_off[s + 1] = c;
+    }
+    return 0;
+  });
+  for (int s = 0; s < ns; ++s) S.asm_off[s + 1] += S.asm_off[s];
+  S.asm_pos.assign(S.asm_off[ns], 0);
+  S.asm_src.assign(S.asm_off[ns], 0);
+  std::vector<int64_t> cost(ns);   // a supernode's share: its entries, rows and children's rows
   for (int s = 0; s < ns; ++s) {
-    const int f = sfirst[s], w = swidth[s];
-    const int nf = w + (S.row_off[s + 1] - S.row_off[s]);
-    for (int j = f; j < f + w; ++j) fpos[j] = j - f;
-    for (int a = S.row_off[s]; a < S.row_off[s + 1]; ++a) fpos[S.rows[a]] = w + (a - S.row_off[s]);
-    for (int c = S.child_off[s]; c < S.child_off[s + 1]; ++c) {
-      const int ch = S.child[c];
-      for (int a = S.row_off[ch]; a < S.row_off[ch + 1]; ++a) {
-        const int loc = fpos[S.rows[a]];
-        if (loc < 0) return POGS_ERR_ARG;   // cannot happen for an elimination tree
-        S.rel[S.rel_off[ch] + (a - S.row_off[ch])] = loc;
-      }
-    }
-    for (int j = f; j < f + w; ++j) {
-      const int v = S.perm[j];
-      const int lc = j - f;
-      S.asm_pos.push_back(lc * nf + lc);
-      S.asm_src.push_back(v < n ? -1 : -2);
-      for (int p = g.off[v]; p < g.off[v + 1]; ++p) {
-        const int i = S.iperm[g.adj[p]];
-        if (i <= j) continue;
-        const int lr = fpos[i];
-        if (lr < 0) return POGS_ERR_ARG;
-        S.asm_pos.push_back(lr * nf + lc);
-        S.asm_src.push_back(g.eid[p]);   // the A entry linking the two unknowns
-      }
-    }
-    S.asm_off[s + 1] = (int)S.asm_pos.size();
-    for (int j = f; j < f + w; ++j) fpos[j] = -1;
-    for (int a = S.row_off[s]; a < S.row_off[s + 1]; ++a) fpos[S.rows[a]] = -1;
+    cost[s] = (S.asm_off[s + 1] - S.asm_off[s]) + 2 * (S.row_off[s + 1] - S.row_off[s]) + swidth[s];
+    for (int c = S.child_off[s]; c < S.child_off[s + 1]; ++c) cost[s] += S.row_off[S.child[c] + 1] - S.row_off[S.child[c]];
   }
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int mrc = parallel_ranges(balanced_bounds(cost, std::min({16, hw, std::max(1, ns / 1024)})),
+                                  [&](int b, int e, int wk) -> int {
+    std::vector<int>& fpos = marks[wk];   // front position of each row of the current supernode
+    if (fpos.empty()) fpos.assign(N, -1);
+    std::fill(fpos.begin(), fpos.end(), -1);
+    for (int s = b; s < e; ++s) {
+      const int f = sfirst[s], w = swidth[s];
+      const int nf = w + (S.row_off[s + 1] - S.row_off[s]);
+      for (int j = f; j < f + w; ++j) fpos[j] = j - f;
+      for (int a = S.row_off[s]; a < S.row_off[s + 1]; ++a) fpos[S.rows[a]] = w + (a - S.row_off[s]);
+      for (int c = S.child_off[s]; c < S.child_off[s + 1]; ++c) {
+        const int ch = S.child[c];
+        for (int a = S.row_off[ch]; a < S.row_off[ch + 1]; ++a) {
+          const int loc = fpos[S.rows[a]];
+          if (loc < 0) return POGS_ERR_ARG;   // cannot happen for an elimination tree
+          S.rel[S.rel_off[ch] + (a - S.row_off[ch])] = loc;
+        }
+      }
+      int t = S.asm_off[s];
+      for (int j = f; j < f + w; ++j) {
+        const int lc = j - f;
+        S.asm_pos[t] = lc * nf + lc;
+        S.asm_src[t++] = S.perm[j] < n ? -1 : -2;
+        for (int p = pg.off[j]; p < pg.off[j + 1]; ++p) {
+          const int i = pg.adj[p];
+          if (i <= j) continue;
+          const int lr = fpos[i];
+          if (lr < 0) return POGS_ERR_ARG;
+          S.asm_pos[t] = lr * nf + lc;
+          S.asm_src[t++] = pg.eid[p];   // the A entry linking the two unknowns
+        }
+      }
+      for (int j = f; j < f + w; ++j) fpos[j] = -1;
+      for (int a = S.row_off[s]; a < S.row_off[s + 1]; ++a) fpos[S.rows[a]] = -1;
+    }
+    return 0;
+  });
+  if (mrc) return mrc;
   // ---- storage ----------------------------------------------------------------------------------
   S.panel_off.assign(ns + 1, 0);
   S.upd_off.assign(ns, 0);
