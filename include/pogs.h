@@ -382,7 +382,7 @@ int pogs_check_bounded_wait(void* stream);
  * diagonal, supernodes, levels of the supernodal tree, largest frontal matrix, factor entries
  * stored, update-matrix entries, frontal scratch entries; perm[N]: the fill-reducing ordering
  * (new position -> unknown); colcount[N]: nonzeros of each column of L below the diagonal, in
- * the new order.  Errors: ARG (sizes, NULL, malformed pattern). */
+ * the new order.  Errors: ARG (sizes, NULL, malformed pattern), OOM (host memory). */
 int pogs_ldl_analyze(int64_t m, int64_t n, const int* rowptr, const int* colind, int64_t* stats, int* perm,
                      int* colcount);
 

@@ -85,7 +85,8 @@ void ldl_apply(const LdlFactor& F, bool tall, const float* v, int epi, const Epi
 int ldl_launches(const LdlFactor& F);    // kernel launches of one ldl_apply
 
 // Symbolic analysis of K for the m x n pattern of A given in CSR (rowptr m + 1, colind sorted and
-// unique within each row, host arrays).  Returns 0, or POGS_ERR_ARG on a malformed pattern.
+// unique within each row, host arrays).  Returns 0, POGS_ERR_ARG on a malformed pattern, or
+// POGS_ERR_OOM when host memory runs out.
 int ldl_analyze(int m, int n, const int* rowptr, const int* colind, LdlSymbolic& S);
 
 }  // namespace pogs

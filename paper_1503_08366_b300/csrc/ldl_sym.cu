@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <exception>
 #include <map>
 #include <set>
 #include <numeric>
@@ -44,18 +45,20 @@ Graph build_graph(int m, int n, const int* rp, const int* ci) {
   return g;
 }
 
-// Runs f(begin, end, worker) over [0, count) in up to 16 contiguous chunks of at least `grain`
-// items, on host threads (chunk 0 on the calling thread, and any chunk whose thread cannot be
-// started); f must be safe on disjoint ranges at once.  Returns the first nonzero code of the
-// chunks, in chunk order.
+// Runs f(bounds[w], bounds[w + 1], w) for every w on its own host thread (w = 0 on the calling
+// thread, and any chunk whose thread cannot be started); returns the first nonzero code, in chunk
+// order.  A chunk that throws (an allocation failure) reports POGS_ERR_OOM instead.
 template <class F>
-int parallel_chunks(int count, int grain, F f) {
-  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-  const int nw = std::min({16, hw, std::max(1, count / std::max(1, grain))});
-  if (nw <= 1) return f(0, count, 0);
+int parallel_ranges(const std::vector<int>& bounds, F f) {
+  const int nw = (int)bounds.size() - 1;
+  if (nw < 1) return 0;
   std::vector<int> rc(nw, 0);
   auto chunk = [&](int w) {
-    rc[w] = f((int)((int64_t)count * w / nw), (int)((int64_t)count * (w + 1) / nw), w);
+    try {
+      rc[w] = f(bounds[w], bounds[w + 1], w);
+    } catch (...) {
+      rc[w] = POGS_ERR_OOM;
+    }
   };
   std::vector<std::thread> th;
   int started = 1;
@@ -71,26 +74,15 @@ int parallel_chunks(int count, int grain, F f) {
   return 0;
 }
 
-// Runs f(bounds[w], bounds[w + 1], w) for every w on its own host thread (w = 0 on the calling
-// thread, and any chunk whose thread cannot be started); returns the first nonzero code.
+// parallel_ranges over [0, count) cut into up to 16 equal contiguous chunks of at least `grain`
+// items (one chunk on the calling thread when count is small).
 template <class F>
-int parallel_ranges(const std::vector<int>& bounds, F f) {
-  const int nw = (int)bounds.size() - 1;
-  if (nw <= 1) return nw == 1 ? f(bounds[0], bounds[1], 0) : 0;
-  std::vector<int> rc(nw, 0);
-  auto chunk = [&](int w) { rc[w] = f(bounds[w], bounds[w + 1], w); };
-  std::vector<std::thread> th;
-  int started = 1;
-  try {
-    for (; started < nw; ++started) th.emplace_back(chunk, started);
-  } catch (...) {   // no more threads: the remaining chunks run here
-  }
-  chunk(0);
-  for (int w = started; w < nw; ++w) chunk(w);
-  for (auto& t : th) t.join();
-  for (int r : rc)
-    if (r) return r;
-  return 0;
+int parallel_chunks(int count, int grain, F f) {
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nw = std::min({16, hw, std::max(1, count / std::max(1, grain))});
+  std::vector<int> bounds(nw + 1);
+  for (int w = 0; w <= nw; ++w) bounds[w] = (int)((int64_t)count * w / nw);
+  return parallel_ranges(bounds, f);
 }
 
 // Cut [0, cost.size()) into at most `parts` contiguous ranges of about equal total cost.
@@ -251,10 +243,17 @@ class Dissection {
     levels = Levels();
     l2 = Levels();
     std::vector<int> out1;
+    std::exception_ptr err1;   // an exception of the other thread, rethrown here after the join
     std::thread th;
     if (depth < par_depth_ && (int)p1.size() >= kParallelMin && (int)p2.size() >= kParallelMin) {
       try {
-        th = std::thread([&] { dissect(p1, out1, depth + 1); });
+        th = std::thread([&] {
+          try {
+            dissect(p1, out1, depth + 1);
+          } catch (...) {
+            err1 = std::current_exception();
+          }
+        });
       } catch (...) {   // no thread available: order both halves here
       }
     }
@@ -270,6 +269,7 @@ class Dissection {
         throw;
       }
       th.join();
+      if (err1) std::rethrow_exception(err1);
       out.insert(out.end(), out1.begin(), out1.end());
       out.insert(out.end(), out2.begin(), out2.end());
     }
@@ -279,7 +279,9 @@ class Dissection {
 
 }  // namespace
 
-int ldl_analyze(int m, int n, const int* rp, const int* ci, LdlSymbolic& S) {
+namespace {
+
+int analyze(int m, int n, const int* rp, const int* ci, LdlSymbolic& S) {
   if (m < 1 || n < 1 || !rp || !ci || rp[0] != 0) return POGS_ERR_ARG;
   for (int i = 0; i < m; ++i) {
     if (rp[i + 1] < rp[i]) return POGS_ERR_ARG;
@@ -696,6 +698,17 @@ int ldl_analyze(int m, int n, const int* rp, const int* ci, LdlSymbolic& S) {
   S.panel_total = S.panel_off[ns];
   S.vec_total = S.vec_off[ns];
   return 0;
+}
+
+}  // namespace
+
+int ldl_analyze(int m, int n, const int* rp, const int* ci, LdlSymbolic& S) {
+  try {
+    return analyze(m, n, rp, ci, S);
+  } catch (...) {   // host memory exhausted (the analysis allocates all its work arrays)
+    S = LdlSymbolic();
+    return POGS_ERR_OOM;
+  }
 }
 
 }  // namespace pogs

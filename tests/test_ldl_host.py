@@ -171,3 +171,37 @@ def test_large_pattern_counts_and_deterministic_ordering(P):
     assert np.array_equal(np.sort(perm), np.arange(m + n))
     assert np.array_equal(cc, _colcounts_by_column_structures(A, perm.tolist()))
     assert stats["nnz_l"] >= int(cc.sum())
+
+
+_OOM_CHILD = r"""
+import resource, sys
+import numpy as np
+import paper_1503_08366_b300 as P
+import workloads as W
+A = W.banded_lasso(200000, 100000, seed=1, half_band=8).A
+rp = np.ascontiguousarray(A.indptr, np.int32)
+ci = np.ascontiguousarray(A.indices, np.int32)
+size = next(int(l.split()[1]) * 1024 for l in open('/proc/self/status') if l.startswith('VmSize'))
+resource.setrlimit(resource.RLIMIT_AS, (size + 64 * 2**20, resource.RLIM_INFINITY))
+try:
+    P.pogs_ldl_analyze(rp, ci, A.shape)
+    print('NO ERROR')
+except P.PogsError as e:
+    print('ERROR', e.code)
+"""
+
+
+def test_analysis_out_of_host_memory_returns_an_error():
+    """With the process's address space capped just above its current size, the analysis of a
+    large pattern runs out of host memory: it returns POGS_ERR_OOM (in a worker thread or the
+    calling one) instead of ending the process."""
+    import os
+    import subprocess
+    import sys
+    from paper_1503_08366_b300 import _lib
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _OOM_CHILD], cwd=root, capture_output=True, text=True, timeout=600,
+                       env=dict(os.environ, PYTHONPATH=root))
+    assert r.returncode == 0, r.stderr[-2000:]
+    oom = next(k for k, v in _lib.ERR.items() if v == "OOM")
+    assert r.stdout.split() == ["ERROR", str(oom)], r.stdout
